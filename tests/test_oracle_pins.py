@@ -1,0 +1,406 @@
+"""Pins of the CPU oracle against values fixed by the mathematics.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, library routines (cuRAND's host Philox generator,
+Qhull, SLSQP), closed forms (degree-2 exactness of the 4-point rule, volumes
+of cut tetrahedra, spherical sectors, ball moments) and invariants that hold
+in exact arithmetic (symmetry and zero row sums of the stiffness matrix,
+partition of unity).  A dropped term, a wrong sign, a transposed operand or a
+wrong constant anywhere in the oracle fails at least one of them.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+import pytest
+
+import nl_inputs as I
+import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+QA = (5 + 3 * math.sqrt(5)) / 20
+QB = (5 - math.sqrt(5)) / 20
+
+
+def rand_tet(rng, scale=1.0):
+    while True:
+        v = rng.normal(size=(4, 3)) * scale
+        e = v[1:] - v[0]
+        if abs(np.linalg.det(e)) > 0.05 * scale ** 3:
+            return v
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    """Random123 known-answer vectors for Philox4x32-10 (SC'11 paper's library)."""
+    with open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        vals = [int(x, 16) for x in r]
+        out = O.philox(vals[0:4], vals[4:6])
+        assert [int(x) for x in out] == vals[6:10]
+
+
+def _curand_host():
+    for name in ("libcurand.so", "libcurand.so.10", "/usr/local/cuda/lib64/libcurand.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    return None
+
+
+def test_philox_matches_curand_host_generator():
+    """cuRAND's host Philox4_32_10 generator with seed s emits, as its n-th
+    block of four words, philox(ctr=(n // 65536, 0, n % 65536, 0), key=(s_lo, s_hi))
+    (a library routine, run here as an independent reference)."""
+    cr = _curand_host()
+    if cr is None:
+        pytest.skip("libcurand not loadable")
+    gen = ctypes.c_void_p()
+    CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+    if cr.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) != 0:
+        pytest.skip("cuRAND host generator unavailable")
+    try:
+        nblk = 65536 + 16
+        for seed in (0, 1, 0x123456789ABCDEF0, 2 ** 64 - 1):
+            cr.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed))
+            cr.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(0))
+            buf = (ctypes.c_uint32 * (4 * nblk))()
+            assert cr.curandGenerate(gen, buf, ctypes.c_size_t(4 * nblk)) == 0
+            got = np.frombuffer(buf, dtype=np.uint32).reshape(nblk, 4)
+            key = [seed & 0xFFFFFFFF, seed >> 32]
+            for n in list(range(16)) + list(range(65536, 65536 + 16)):
+                ctr = [n // 65536, 0, n % 65536, 0]
+                assert list(O.philox(ctr, key)) == list(got[n])
+    finally:
+        cr.curandDestroyGenerator(gen)
+
+
+# ---------------------------------------------------------------- quadrature
+def _monomial_integral(alpha, vol):
+    # int_T prod lambda_k^alpha_k = vol * 3! * prod(alpha_k!) / (|alpha|+3)!
+    num = math.prod(math.factorial(a) for a in alpha)
+    return vol * 6.0 * num / math.factorial(sum(alpha) + 3)
+
+
+def test_quad_points_are_the_degree2_rule():
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        v = rand_tet(rng)
+        xq = O.quad_points(v)
+        vol = O.tet_volume(v)
+        assert vol == pytest.approx(abs(np.linalg.det(v[1:] - v[0])) / 6.0, rel=1e-14)
+        # barycentric coordinates of x_q are a on vertex q and b elsewhere
+        M = np.vstack([v.T, np.ones(4)])
+        for q in range(4):
+            lam = np.linalg.solve(M, np.append(xq[q], 1.0))
+            expect = np.full(4, QB)
+            expect[q] = QA
+            assert np.allclose(lam, expect, atol=1e-13)
+        # exact for every monomial of degree <= 2 in the barycentrics
+        lam_q = np.full((4, 4), QB) + np.eye(4) * (QA - QB)
+        for alpha in [(0, 0, 0, 0), (1, 0, 0, 0), (0, 2, 0, 0), (1, 1, 0, 0), (0, 0, 1, 1)]:
+            approx = vol / 4 * sum(np.prod(lam_q[q] ** np.array(alpha)) for q in range(4))
+            assert approx == pytest.approx(_monomial_integral(alpha, vol), rel=1e-13)
+
+
+def test_grundmann_moeller_rule_degree5():
+    bary, w = O.grundmann_moeller(2)
+    assert w.sum() == pytest.approx(1.0, rel=1e-13)
+    for alpha in [(5, 0, 0, 0), (2, 2, 1, 0), (1, 1, 1, 1), (0, 3, 0, 2), (4, 0, 1, 0)]:
+        approx = np.sum(w * np.prod(bary ** np.array(alpha), axis=1))
+        assert approx == pytest.approx(_monomial_integral(alpha, 1.0), rel=1e-12)
+
+
+# ---------------------------------------------------------------- geometry
+def test_dist2_point_tet_matches_constrained_minimisation():
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(2)
+    for _ in range(40):
+        v = rand_tet(rng)
+        p = rng.normal(size=3) * 1.5
+        d2 = O.dist2_point_tet(p, v)
+        f = lambda lam: float(np.sum((lam @ v - p) ** 2))
+        best = np.inf
+        for start in np.eye(4).tolist() + [[0.25] * 4]:
+            res = minimize(f, start, method="SLSQP", bounds=[(0, 1)] * 4,
+                           constraints=[{"type": "eq", "fun": lambda l: l.sum() - 1}],
+                           options={"ftol": 1e-15, "maxiter": 500})
+            best = min(best, res.fun)
+        assert d2 == pytest.approx(best, rel=1e-6, abs=1e-10)
+        # inside points have distance 0
+        lam = rng.dirichlet(np.ones(4))
+        assert O.dist2_point_tet(lam @ v, v) == 0.0
+
+
+def test_hull_volume_matches_qhull():
+    from scipy.spatial import ConvexHull
+    rng = np.random.default_rng(3)
+    for n in (4, 5, 7, 10):
+        for _ in range(10):
+            p = rng.normal(size=(n, 3))
+            assert O.hull_volume(p) == pytest.approx(ConvexHull(p).volume, rel=1e-12)
+    # coplanar facets and interior/edge points: cube corners + face centres + edge midpoints
+    c = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)], dtype=float)
+    extra = np.array([[0.5, 0.5, 0], [0.5, 0, 0.5]])
+    assert O.hull_volume(np.vstack([c, extra])) == pytest.approx(1.0, rel=1e-13)
+    assert O.hull_volume(np.vstack([c[:4], [[0.0, 0.3, 0.3]]])) == 0.0  # flat
+
+
+def _sphere_t(vin, vout, x, delta):
+    # root of |vin + t (vout-vin) - x| = delta in (0,1), by numpy's polynomial roots
+    e = vout - vin
+    w = vin - x
+    r = np.roots([e @ e, 2 * (e @ w), w @ w - delta ** 2])
+    r = r[(r.real > 0) & (r.real < 1) & (abs(r.imag) < 1e-12)].real
+    assert r.size == 1
+    return float(r[0])
+
+
+def test_nocaps_cells_volume_closed_forms():
+    """m=1: |T'| t_ab t_ac t_ad;  m=3: |T'| (1 - (1-t_ad)(1-t_bd)(1-t_cd));
+    m=2: volume of the convex hull of the six points (Qhull); m=4: |T'|."""
+    from scipy.spatial import ConvexHull
+    rng = np.random.default_rng(4)
+    seen = set()
+    for _ in range(4000):
+        v = rand_tet(rng)
+        x = rng.normal(size=3) * 0.8
+        delta = float(rng.uniform(0.3, 1.5))
+        inside = np.sum((v - x) ** 2, axis=1) < delta ** 2
+        m = int(inside.sum())
+        if m in seen and len(seen) == 5 and rng.random() > 0.05:
+            continue
+        seen.add(m)
+        M, _, _ = O.region_moments(v, x, delta, O.NOCAPS)
+        V = O.tet_volume(v)
+        ins = np.nonzero(inside)[0]
+        out = np.nonzero(~inside)[0]
+        if m == 0:
+            assert M[0] == 0.0
+        elif m == 4:
+            assert M[0] == pytest.approx(V, rel=1e-14)
+        elif m == 1:
+            a = ins[0]
+            t = [_sphere_t(v[a], v[o], x, delta) for o in out]
+            assert M[0] == pytest.approx(V * t[0] * t[1] * t[2], rel=1e-9)
+        elif m == 3:
+            d = out[0]
+            t = [_sphere_t(v[i], v[d], x, delta) for i in ins]
+            assert M[0] == pytest.approx(V * (1 - (1 - t[0]) * (1 - t[1]) * (1 - t[2])), rel=1e-9)
+        else:
+            pts = [v[i] for i in ins]
+            for i in ins:
+                for o in out:
+                    t = _sphere_t(v[i], v[o], x, delta)
+                    pts.append(v[i] + t * (v[o] - v[i]))
+            assert M[0] == pytest.approx(ConvexHull(np.array(pts)).volume, rel=1e-9)
+    assert seen == {0, 1, 2, 3, 4}
+
+
+def test_moments_closed_form_and_partition_of_unity():
+    rng = np.random.default_rng(5)
+    v = rand_tet(rng)
+    x = v.mean(axis=0)
+    M, _, _ = O.region_moments(v, x, 100.0, O.NOCAPS)       # m = 4
+    V = O.tet_volume(v)
+    assert M[0] == pytest.approx(V, rel=1e-14)
+    assert np.allclose(M[1:5], V / 4, rtol=1e-13)
+    k = 5
+    for a in range(4):
+        for b in range(a, 4):
+            assert M[k] == pytest.approx(V * (2 if a == b else 1) / 20, rel=1e-13)
+            k += 1
+    # partition of unity for every strategy on cut cases
+    for strat in (O.NOCAPS, O.APPROXCAPS, O.FULLCAPS):
+        for _ in range(50):
+            v = rand_tet(rng)
+            x = v[rng.integers(4)] + rng.normal(size=3) * 0.3
+            M, _, _ = O.region_moments(v, x, 0.8, strat, nmc=64, seed=3, idT=1, idTp=2, q=3)
+            assert M[1:5].sum() == pytest.approx(M[0], rel=1e-12, abs=1e-15)
+            M2 = np.zeros((4, 4))
+            k = 5
+            for a in range(4):
+                for b in range(a, 4):
+                    M2[a, b] = M2[b, a] = M[k]
+                    k += 1
+            assert np.allclose(M2.sum(axis=1), M[1:5], rtol=1e-12, atol=1e-15)
+
+
+def test_vertex_permutation_invariance():
+    rng = np.random.default_rng(6)
+    for strat in (O.NOCAPS, O.APPROXCAPS):
+        for _ in range(100):
+            v = rand_tet(rng)
+            x = v[rng.integers(4)] + rng.normal(size=3) * 0.4
+            M, _, _ = O.region_moments(v, x, 0.9, strat)
+            perm = rng.permutation(4)
+            Mp, _, _ = O.region_moments(v[perm], x, 0.9, strat)
+            assert Mp[0] == pytest.approx(M[0], rel=1e-11, abs=1e-15)
+            assert np.allclose(Mp[1:5], M[1:5][perm], rtol=1e-10, atol=1e-15)
+
+
+def _solid_angle(a, b, c):
+    # Van Oosterom & Strackee (1983)
+    la, lb, lc = np.linalg.norm(a), np.linalg.norm(b), np.linalg.norm(c)
+    num = abs(a @ np.cross(b, c))
+    den = la * lb * lc + (a @ b) * lc + (a @ c) * lb + (b @ c) * la
+    return 2.0 * math.atan2(num, den)
+
+
+def test_fullcaps_unbiased_on_a_spherical_sector():
+    """Apex at the ball centre, far face beyond delta: T' cap B is the sector
+    delta^3 * solid_angle / 3; the fullcaps estimate averages to it."""
+    v = np.array([[0.0, 0, 0], [1.0, 0.1, 0.05], [0.15, 1.1, 0.0], [0.05, 0.2, 1.2]])
+    x = v[0].copy()
+    delta = 0.6
+    Om = _solid_angle(v[1] - x, v[2] - x, v[3] - x)
+    exact = delta ** 3 * Om / 3
+    vals = []
+    for seed in range(400):
+        M, mcv, _ = O.region_moments(v, x, delta, O.FULLCAPS, nmc=128, seed=seed, idT=5, idTp=9, q=1)
+        vals.append(M[0])
+    vals = np.array(vals)
+    nocaps = O.region_moments(v, x, delta, O.NOCAPS)[0][0]
+    assert nocaps < exact
+    se = vals.std(ddof=1) / math.sqrt(len(vals))
+    assert abs(vals.mean() - exact) < 4 * se + 1e-12
+    approx = O.region_moments(v, x, delta, O.APPROXCAPS)[0][0]
+    assert nocaps < approx < exact
+
+
+def _ball_sums(mesh, x, delta, strat, nmc, seed):
+    """Sum over all elements of (M0, first moment, second moment about x)."""
+    m0, m1, m2 = 0.0, np.zeros(3), np.zeros((3, 3))
+    for t in range(mesh.nt):
+        v = mesh.verts[mesh.tets[t]]
+        if O.dist2_point_tet(x, v) > delta * delta:
+            continue
+        M, _, _ = O.region_moments(v, x, delta, strat, nmc=nmc, seed=seed, idT=0, idTp=t, q=0)
+        lam2 = np.zeros((4, 4))
+        k = 5
+        for a in range(4):
+            for b in range(a, 4):
+                lam2[a, b] = lam2[b, a] = M[k]
+                k += 1
+        w = v - x
+        m0 += M[0]
+        m1 += M[1:5] @ w
+        m2 += w.T @ lam2 @ w
+    return m0, m1, m2
+
+
+def test_ball_volume_bounds_and_fullcaps_moments():
+    """Lemma (nocaps) and Thm (inscribed): (4pi/3)(delta^2-h^2/2)^{3/2} <= V_nocaps
+    <= V_approxcaps <= 4 pi delta^3/3; fullcaps recovers the ball's volume,
+    centroid and second moment (4 pi delta^5/15) I in expectation, so that
+    gamma * int_B |y-x|^2 = 6 for gamma = 15/(2 pi delta^5)."""
+    mesh, delta = I.cube_problem(4, 2)      # h = 1/4, delta = 1/2
+    hmax = math.sqrt(3) * mesh.h
+    rng = np.random.default_rng(7)
+    ball = 4 * math.pi * delta ** 3 / 3
+    for _ in range(2):
+        x = 0.5 + rng.uniform(-0.05, 0.05, size=3)
+        vn = _ball_sums(mesh, x, delta, O.NOCAPS, 0, 0)[0]
+        va = _ball_sums(mesh, x, delta, O.APPROXCAPS, 0, 0)[0]
+        lower = 4 * math.pi / 3 * (delta ** 2 - hmax ** 2 / 2) ** 1.5
+        assert lower <= vn < va < ball
+    x = np.array([0.47, 0.52, 0.49])
+    vols, firsts, seconds = [], [], []
+    for seed in range(24):
+        m0, m1, m2 = _ball_sums(mesh, x, delta, O.FULLCAPS, 128, seed)
+        vols.append(m0); firsts.append(m1); seconds.append(np.trace(m2))
+    vols, firsts, seconds = map(np.array, (vols, firsts, seconds))
+    for arr, exact in ((vols, ball), (seconds, 4 * math.pi * delta ** 5 / 5)):
+        se = arr.std(ddof=1) / math.sqrt(arr.size)
+        assert abs(arr.mean() - exact) < 4 * se + 1e-12 * exact
+    se1 = firsts.std(axis=0, ddof=1) / math.sqrt(len(firsts))
+    assert np.all(np.abs(firsts.mean(axis=0)) < 4 * se1 + 1e-12)
+    lap = I.gamma_const(delta) * seconds.mean()
+    assert abs(lap - 6.0) < 4 * I.gamma_const(delta) * seconds.std(ddof=1) / math.sqrt(seconds.size)
+
+
+# ---------------------------------------------------------------- mesh and pairs
+def test_kuhn_mesh_is_a_conforming_triangulation():
+    for jit in (0.0, 0.2):
+        m = I.kuhn_box(-0.25, 1.25, 6, jitter_frac=jit, seed=7)
+        v = m.verts[m.tets]
+        vol = np.einsum("ij,ij->i", v[:, 1] - v[:, 0], np.cross(v[:, 2] - v[:, 0], v[:, 3] - v[:, 0])) / 6
+        assert np.all(vol > 0)
+        assert vol.sum() == pytest.approx(1.5 ** 3, rel=1e-12)
+        assert vol[m.tet_in_omega == 1].sum() == pytest.approx(1.0, rel=1e-12)
+        faces = np.sort(np.concatenate([m.tets[:, [1, 2, 3]], m.tets[:, [0, 2, 3]],
+                                        m.tets[:, [0, 1, 3]], m.tets[:, [0, 1, 2]]]), axis=1)
+        _, cnt = np.unique(faces, axis=0, return_counts=True)
+        assert cnt.max() == 2
+        # boundary faces: 6 sides * 36 squares * 2 triangles
+        assert np.sum(cnt == 1) == 6 * 36 * 2
+        free = m.verts[m.node_free == 1]
+        assert np.all((free > 0) & (free < 1))
+        assert m.node_free.sum() == 27
+
+
+def test_pairs_grid_equals_brute_force():
+    for jit in (0.0, 0.2):
+        m = I.kuhn_box(-0.25, 1.25, 6, jitter_frac=jit, seed=11)
+        a = O.pairs(m, 0.25, use_grid=True)
+        b = O.pairs(m, 0.25, use_grid=False)
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+        # every outer element pairs with itself
+        pT, pTp = O.pair_arrays(*a)
+        assert np.all(np.isin(a[0], pTp[pT == pTp]))
+
+
+# ---------------------------------------------------------------- assembly and solve
+@pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS])
+def test_stiffness_symmetric_zero_row_sums_psd(strat):
+    m, delta = I.config_mesh("cube6_d025")
+    K = O.assemble_K(m, delta, I.gamma_const(delta), strat, nmc=64, seed=1)
+    Kd = K.toarray()
+    scale = np.abs(Kd).sum(axis=1)
+    assert np.all(np.abs(Kd.sum(axis=1)) <= 1e-13 * scale.max())
+    assert np.abs(Kd - Kd.T).max() <= 1e-14 * np.abs(Kd).max()
+    ev = np.linalg.eigvalsh(Kd)
+    assert ev.min() > -1e-12 * ev.max()
+    F = O.load_vector(m, -6.0)
+    g = I.quadratic_g(m.verts)
+    A, b, free = O.system(m, K, F, g)
+    np.linalg.cholesky(A.toarray())          # SPD
+    x, it = O.cg(A, b, rtol=1e-12)
+    xc = O.cholesky_solve(A, b)
+    assert np.abs(x - xc).max() <= 1e-10 * np.abs(xc).max()
+
+
+def test_load_vector_integrates_f():
+    m, _ = I.config_mesh("cube6_d025")
+    F = O.load_vector(m, -6.0)
+    assert F.sum() == pytest.approx(-6.0, rel=1e-13)     # |Omega| = 1
+    assert np.all(F[np.unique(m.tets[m.tet_in_omega == 0])] <= 0)
+
+
+def test_collar_weight_and_kernel_constant_by_convergence():
+    """u = |x|^2, f = -6: with the collar weight 2 and psi = gamma/2 the
+    discrete solution converges to u; a factor wrong anywhere does not."""
+    errs = []
+    for inv_h in (4, 8):
+        m, delta = I.cube_problem(inv_h, 2)
+        K = O.assemble_K(m, delta, I.gamma_const(delta), O.APPROXCAPS)
+        A, b, free = O.system(m, K, O.load_vector(m, -6.0), I.quadratic_g(m.verts))
+        x, _ = O.cg(A, b)
+        u = I.quadratic_g(m.verts)
+        u[free] = x
+        errs.append(O.l2_error(m, u, lambda X: (X * X).sum(axis=1)))
+    assert errs[0] < 0.05
+    assert errs[1] < errs[0] / 3.0          # ~O(h^2)
+
+
+def test_translation_invariance():
+    m, delta = I.config_mesh("cube6_d025")
+    K1 = O.assemble_K(m, delta, I.gamma_const(delta), O.NOCAPS).toarray()
+    m2 = I.kuhn_box(-0.25, 1.25, 6)
+    m2.verts = m2.verts + np.array([0.5, -0.25, 1.0])
+    K2 = O.assemble_K(m2, delta, I.gamma_const(delta), O.NOCAPS).toarray()
+    assert np.abs(K1 - K2).max() <= 1e-12 * np.abs(K1).max()
