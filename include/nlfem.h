@@ -1,0 +1,250 @@
+/*
+ * nlfem — GB300 (sm_103a) assembly and solve of the nonlocal Poisson problem
+ * with a constant truncated kernel on P1 tetrahedra, after Chen, Ma & Zhang,
+ * "High performance implementation of 3D FEM for nonlocal Poisson problem
+ * with different ball approximation strategies".
+ *
+ * Problem (Sec. 2.1, Eq. nonlocalproblem):  -L u = f in Omega,  u = g on the
+ * interaction collar Omega_I, with L u(x) = int_{B_delta(x)} (u(y)-u(x)) gamma dy
+ * and a constant gamma inside the ball.  The library assembles the Galerkin
+ * system of Eqs. (modified_linear), (Ah), (Fh) with the approximate ball
+ * B_{delta,h}(x) of one strategy (Def. nocaps; the simplified 3D approxcaps of
+ * Sec. 3.3; fullcaps of Sec. 4.3.2), using the 4-point degree-2 rule for the
+ * outer and inner integrals (Sec. 4.3.1), and solves it by conjugate
+ * gradients (Alg. 5, last line).
+ *
+ * Conventions for every call:
+ *   - Every call returns an nl_status and never aborts; nl_last_error() gives
+ *     a thread-local message for the last failure.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  Arrays
+ *     flagged NL_DEVICE must be device pointers of the current CUDA device;
+ *     they are read on the handle's stream and may be reused once the call
+ *     returns (every call that reads caller memory synchronises its stream
+ *     before returning).
+ *   - Device memory owned by a handle is obtained from nl_device.alloc (or
+ *     cudaMalloc when alloc is NULL) and released by the matching destroy.
+ *   - All device work runs on nl_device.stream (NULL = legacy default).
+ *   - Handles are not thread-safe; use one handle per thread or serialise.
+ *   - No call uses the CPU to compute any step of the method: every step
+ *     runs in this library's CUDA kernels.  A missing or unusable GPU gives
+ *     NL_ECUDA.
+ */
+#ifndef NLFEM_H
+#define NLFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NL_OK = 0,
+    NL_EINVAL = 1,      /* bad argument, malformed or inverted mesh */
+    NL_ENOMEM = 2,      /* allocator returned NULL */
+    NL_ECUDA = 3,       /* CUDA runtime error (message in nl_last_error) */
+    NL_ENOTCONV = 4,    /* CG stopped at max_iter above the tolerance */
+    NL_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    NL_EBUSY = 6        /* resource limit reached (server queue full) */
+} nl_status;
+
+typedef enum { NL_NOCAPS = 0, NL_APPROXCAPS = 1, NL_FULLCAPS = 2 } nl_strategy;
+typedef enum { NL_FP64 = 0, NL_FP32_COMP = 1 } nl_precision;
+typedef enum { NL_HOST = 0, NL_DEVICE = 1 } nl_where;
+typedef enum { NL_MAT_K = 0, NL_MAT_A = 1 } nl_matrix;
+
+/* Device context: allocator hooks (for example PyTorch's caching allocator)
+ * and the stream all work is ordered on.  alloc must return memory usable on
+ * the current device, aligned to at least 256 bytes, or NULL. */
+typedef struct nl_device {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+    void *stream;                     /* cudaStream_t */
+} nl_device;
+
+typedef struct nl_mesh nl_mesh;
+typedef struct nl_pairs nl_pairs;
+typedef struct nl_system nl_system;
+
+/* ---------------------------------------------------------------------------
+ * nl_mesh_create — upload a triangulation of Omega-hat = Omega u Omega_I
+ * (Sec. 3.1: conforming, elements of Omega and Omega_I do not straddle dOmega)
+ * and precompute per element its volume, centroid, bounding radius and the
+ * four quadrature points of the 4-point rule (Sec. 4.3.1).
+ *   verts         [nv][3] float64 coordinates.
+ *   tets          [nt][4] int32 vertex ids, 0 <= id < nv.
+ *   tet_in_omega  [nt] uint8: 1 = element of Omega, 0 = element of the collar.
+ *   node_free     [nv] uint8: 1 = node in the open domain Omega (an unknown);
+ *                 0 = node in the closed collar, dOmega included (Sec. 3.2),
+ *                 where the volume constraint fixes the value.
+ *   where         NL_HOST or NL_DEVICE for all four arrays.
+ * Errors: NL_EINVAL for nv<4, nt<1, an id out of range or an element with
+ * non-positive signed volume (vertices must be positively oriented);
+ * NL_ENOMEM; NL_ECUDA.  The mesh keeps a pointer to *dev (must outlive it). */
+nl_status nl_mesh_create(const nl_device *dev, const double *verts, int64_t nv,
+                         const int32_t *tets, int64_t nt, const uint8_t *tet_in_omega,
+                         const uint8_t *node_free, int where, nl_mesh **out);
+void nl_mesh_destroy(nl_mesh *mesh);
+
+/* ---------------------------------------------------------------------------
+ * nl_pairs_build — element pairs and the fixed sparsity pattern for a horizon
+ * delta.  A pair (T, T') has T in Omega and T' any element with
+ *     min_q |x_q(T) - T'|^2 <= delta^2
+ * over the four quadrature points x_q of T, i.e. T' meets the closed ball
+ * around some outer point (the cells kept by Alg. 2).  Pairs are ordered by
+ * T (increasing element id), then T'.  The pattern is the union over pairs
+ * of (nodes(T) u nodes(T'))^2, symmetric, in CSR with sorted columns.
+ * Built once per (mesh, delta) and reused by every strategy.
+ * Errors: NL_EINVAL (delta <= 0 or not finite, or more than 65535 columns in
+ * one row), NL_ENOMEM, NL_ECUDA.  The pairs keep a pointer to the mesh. */
+nl_status nl_pairs_build(nl_mesh *mesh, double delta, nl_pairs **out);
+void nl_pairs_destroy(nl_pairs *pairs);
+
+typedef struct {
+    int64_t n_vert, n_tet, n_outer;    /* n_outer = elements of Omega */
+    int64_t n_pairs;
+    int64_t nnz;                       /* pattern of the full matrix K (all nodes) */
+    int64_t n_free, nnz_a;             /* unknowns and nnz of A = K[free,free] */
+    int32_t max_row;                   /* longest row of K */
+    double delta;
+} nl_pairs_info;
+nl_status nl_pairs_get_info(const nl_pairs *pairs, nl_pairs_info *info);
+
+/* Copy the pair list out: outer[n_outer] (element ids of Omega, increasing),
+ * ptr[n_outer+1] (int64 offsets), tp[n_pairs] (partner ids).  Any pointer may
+ * be NULL to skip it.  where = NL_HOST or NL_DEVICE for the destinations. */
+nl_status nl_pairs_export(const nl_pairs *pairs, int32_t *outer, int64_t *ptr, int32_t *tp, int where);
+
+/* ---------------------------------------------------------------------------
+ * nl_assemble — stiffness matrix and right-hand side (Alg. 5 with the
+ * approximate ball of the chosen strategy).  For every pair and outer point
+ * x_q the inner region R = T' n B_{delta,h}(x_q) is:
+ *   - T' when all four vertices lie in the open ball;
+ *   - nocaps: the convex hull of the inside vertices and the edge/sphere
+ *     points (Def. simplex's dividing strategy, Def. nocaps);
+ *   - approxcaps: that hull enlarged by the midpoints of the sphere's arcs on
+ *     the faces of T' (Sec. 3.3);
+ *   - fullcaps: the nocaps cells plus a Monte Carlo estimate over the cap
+ *     T' \ hull with mc_points Philox4x32-10 samples keyed by (seed) with
+ *     counter (T, T', q, k) (Sec. 4.3.2, Alg. 4).
+ * The local contribution is omega*(gamma/2)*|T|/4 * int_R d d^T with
+ * d = (-phi_T(x_q), +phi_T'(y)) and omega = 2 when T' is a collar element
+ * (Eqs. Ah, replaceBasis), so K (all nodes) is symmetric with zero row sums.
+ * With g the nodal volume constraint: A = K[free,free] and
+ * b_i = sum_T sum_q w_q phi_i(x_q) f - sum_{j not free} K_ij g_j.
+ *   gamma      kernel constant inside the ball (e.g. 15/(2 pi delta^5)).
+ *   f_const    constant source f.
+ *   g_nodal    [n_vert] nodal values of g (only collar nodes are read);
+ *              NULL means g = 0.  g_where: NL_HOST or NL_DEVICE.
+ *   precision  NL_FP64: every step in FP64 (decisions follow a fixed
+ *              operation order without fused multiply-add);
+ *              NL_FP32_COMP: the per-(pair, point) geometry, Monte Carlo
+ *              and moments run in FP32 in coordinates relative to x_q, and
+ *              every sum across points, pairs and elements is accumulated in
+ *              FP64; matrix entries are FP64.
+ * Deterministic: the same inputs give bitwise the same K and b (no floating-
+ * point atomics).  Errors: NL_EINVAL (strategy, precision, mc_points outside
+ * 1..4096 for fullcaps, gamma not finite), NL_ENOMEM, NL_ECUDA. */
+typedef struct {
+    int strategy;            /* nl_strategy */
+    int mc_points;           /* fullcaps samples per cap (ignored otherwise) */
+    uint64_t seed;           /* Philox key */
+    int precision;           /* nl_precision */
+    double gamma;
+    double f_const;
+    const double *g_nodal;
+    int g_where;
+} nl_assemble_opts;
+
+nl_status nl_assemble(nl_pairs *pairs, const nl_assemble_opts *opts, nl_system **out);
+void nl_system_destroy(nl_system *sys);
+
+/* Device views of an assembled matrix (no copy; valid until destroy).
+ * NL_MAT_K: full matrix over all nodes (rows/cols = node ids).
+ * NL_MAT_A: the free block, rows/cols numbered by increasing node id among
+ *           free nodes. */
+typedef struct {
+    int64_t n_rows, nnz;
+    const int64_t *rowptr;   /* device, n_rows+1 */
+    const int32_t *col;      /* device, nnz */
+    const double *val;       /* device, nnz */
+} nl_csr_view;
+nl_status nl_system_csr(const nl_system *sys, int which, nl_csr_view *out);
+
+/* Device pointer to b (n_free doubles) and to the free-node list (n_free int32
+ * node ids, increasing). */
+nl_status nl_system_rhs(const nl_system *sys, const double **b, const int32_t **free_nodes);
+
+typedef struct {
+    uint64_t pairs;            /* element pairs processed */
+    uint64_t cut_points;       /* (pair, q) with 1..3 vertices inside */
+    uint64_t inside_points;    /* (pair, q) with T' inside the ball */
+    uint64_t mc_samples;       /* Monte Carlo samples drawn */
+    uint64_t mc_accepted;
+    uint64_t hull_fallbacks;   /* approxcaps hulls that fell back to nocaps */
+} nl_assemble_stats;
+nl_status nl_system_stats(const nl_system *sys, nl_assemble_stats *out);
+
+/* ---------------------------------------------------------------------------
+ * nl_solve — conjugate gradients on A u = b from u = 0 (Alg. 5, last line),
+ * stopping when ||r||_2 / ||b||_2 <= rtol.
+ *   mixed = 0: FP64 CG.
+ *   mixed = 1: iterative refinement: r = b - A u in FP64, correction by an
+ *              FP32 CG on the FP32 copy of A to inner_rtol, u += d in FP64;
+ *              dot products and residuals are FP64 in both modes.
+ *   u_out      [n_vert] full nodal solution (free nodes solved, collar nodes
+ *              = g), or NULL; where: NL_HOST or NL_DEVICE.
+ * Errors: NL_ENOTCONV (info filled, u_out written with the last iterate),
+ * NL_EINVAL, NL_ENOMEM, NL_ECUDA. */
+typedef struct {
+    double rtol;           /* default 1e-12 when <= 0 */
+    int max_iter;          /* total inner iterations; default 20000 when <= 0 */
+    int mixed;
+    double inner_rtol;     /* default 1e-5 when <= 0 */
+    int check_every;       /* host polls the residual every k iterations; default 8 */
+} nl_solve_opts;
+
+typedef struct {
+    int iterations;        /* CG iterations (inner iterations for mixed) */
+    int refinements;       /* outer refinement steps (mixed) */
+    double rel_residual;   /* final ||b - A u|| / ||b|| in FP64 */
+} nl_solve_info;
+
+nl_status nl_solve(nl_system *sys, const nl_solve_opts *opts, double *u_out, int where,
+                   nl_solve_info *info);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostic entry points (not on the assembly path).  Host arrays in and
+ * out; they run on the default stream with their own temporary device
+ * buffers and synchronise before returning.
+ *
+ * nl_probe_moments — the inner moments of the approximate ball for n single
+ * cases (element T' with vertices tets_xyz[c][4][3], outer point x[c][3],
+ * Philox counter words ids[c] = (T, T', q)), computed by the same device code
+ * as nl_assemble.  moments[c][15] = (|R|, int_R lambda'_a (a=0..3),
+ * int_R lambda'_a lambda'_b for (a,b) = (0,0) (0,1) (0,2) (0,3) (1,1) (1,2)
+ * (1,3) (2,2) (2,3) (3,3)), lambda' the barycentric coordinates of T'.
+ * Definitions as for nl_assemble (Def. nocaps, Sec. 3.3, Sec. 4.3.2).
+ * Errors: NL_EINVAL, NL_ECUDA. */
+nl_status nl_probe_moments(const double *tets_xyz, const double *x, const uint32_t *ids, int64_t n,
+                           double delta, int strategy, int mc_points, uint64_t seed, int precision,
+                           double *moments);
+
+/* nl_probe_philox — Philox4x32-10 (Salmon et al., SC'11) of n counters
+ * ctr[n][4] under the key (key & 0xffffffff, key >> 32): the generator that
+ * draws the fullcaps Monte Carlo points.  out[n][4].  Errors: NL_EINVAL,
+ * NL_ECUDA. */
+nl_status nl_probe_philox(const uint32_t *ctr, uint64_t key, int64_t n, uint32_t *out);
+
+/* Thread-local message of the last failing call (empty string if none). */
+const char *nl_last_error(void);
+
+/* Library version string. */
+const char *nl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NLFEM_H */

@@ -62,7 +62,8 @@ def lib():
             L.or_dist2_point_tet.argtypes = [dp, dp]
             L.or_dist2_point_tet.restype = C.c_double
             L.or_pair_predicate.argtypes = [dp, dp, C.c_double]
-            L.or_pairs.argtypes = [dp, C.c_int64, i32p, C.c_int64, u8p, C.c_double, C.c_int, i64p, i32p, C.c_int64]
+            L.or_pairs.argtypes = [dp, C.c_int64, i32p, C.c_int64, u8p, C.c_double, C.c_int, i32p, C.c_int64, i64p, i32p,
+                                   C.c_int64]
             L.or_pairs.restype = C.c_int64
             L.or_hull_tets.argtypes = [C.c_int, dp, dp, C.c_int]
             L.or_mc_point.argtypes = [dp, C.c_int, u32p, dp, C.POINTER(C.c_int)]
@@ -167,22 +168,28 @@ def pair_block(vT, vTp, delta, gamma, tp_in_collar, strategy, nmc=0, seed=1, idT
 # --------------------------------------------------------------------------
 # Pairs, assembly, system, solve
 
-def pairs(mesh, delta, use_grid=True):
-    """(outer_ids, ptr, tp): outer_ids = Omega elements in increasing id,
-    partners of outer_ids[i] are tp[ptr[i]:ptr[i+1]] (sorted)."""
+def pairs(mesh, delta, use_grid=True, outer=None):
+    """(outer_ids, ptr, tp): outer_ids = Omega elements in increasing id (or
+    the given subset, in the given order); partners of outer_ids[i] are
+    tp[ptr[i]:ptr[i+1]] (sorted)."""
     L = lib()
     verts = _f64(mesh.verts)
     tets = np.ascontiguousarray(mesh.tets, dtype=np.int32)
     om = np.ascontiguousarray(mesh.tet_in_omega, dtype=np.uint8)
-    outer = np.nonzero(om)[0].astype(np.int32)
+    if outer is None:
+        outer = np.nonzero(om)[0].astype(np.int32)
+        lst, nl = None, 0
+    else:
+        outer = np.ascontiguousarray(outer, dtype=np.int32)
+        assert np.all(om[outer] == 1)
+        lst, nl = _p(outer, C.c_int32), outer.size
     ptr = np.zeros(outer.size + 1, dtype=np.int64)
-    cap = 0
     n = L.or_pairs(_p(verts, C.c_double), mesh.nv, _p(tets, C.c_int32), mesh.nt, _p(om, C.c_uint8),
-                   float(delta), int(use_grid), _p(ptr, C.c_int64), None, cap)
+                   float(delta), int(use_grid), lst, nl, _p(ptr, C.c_int64), None, 0)
     need = -n if n < 0 else n
     tp = np.zeros(max(need, 1), dtype=np.int32)
     n = L.or_pairs(_p(verts, C.c_double), mesh.nv, _p(tets, C.c_int32), mesh.nt, _p(om, C.c_uint8),
-                   float(delta), int(use_grid), _p(ptr, C.c_int64), _p(tp, C.c_int32), need)
+                   float(delta), int(use_grid), lst, nl, _p(ptr, C.c_int64), _p(tp, C.c_int32), need)
     assert n == need
     return outer, ptr, tp[:need]
 

@@ -221,6 +221,7 @@ static int cmp_i32(const void *a, const void *b)
 
 int64_t or_pairs(const double *verts, int64_t nv, const int32_t *tets, int64_t nt,
                  const uint8_t *in_omega, double delta, int use_grid,
+                 const int32_t *outer_list, int64_t n_list,
                  int64_t *ptr_out, int32_t *tp_out, int64_t cap)
 {
     (void)nv;
@@ -267,7 +268,9 @@ int64_t or_pairs(const double *verts, int64_t nv, const int32_t *tets, int64_t n
     int64_t np = 0, nouter = 0;
     int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * (size_t)nt);
     ptr_out[0] = 0;
-    for (int64_t t = 0; t < nt; ++t) {
+    int64_t nloop = outer_list ? n_list : nt;
+    for (int64_t li = 0; li < nloop; ++li) {
+        int64_t t = outer_list ? (int64_t)outer_list[li] : li;
         if (!in_omega[t]) continue;
         double vT[12];
         tet_coords(verts, tets, t, vT);

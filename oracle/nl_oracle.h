@@ -14,6 +14,7 @@ double or_dist2_point_tet(const double p[3], const double v[12]);
 int or_pair_predicate(const double vT[12], const double vTp[12], double delta);
 int64_t or_pairs(const double *verts, int64_t nv, const int32_t *tets, int64_t nt,
                  const uint8_t *in_omega, double delta, int use_grid,
+                 const int32_t *outer_list, int64_t n_list,
                  int64_t *ptr_out, int32_t *tp_out, int64_t cap);
 int or_hull_tets(int n, const double *p, double *out, int maxout);
 void or_mc_point(const double *S, int ns, const uint32_t u[4], double y[3], int *which);

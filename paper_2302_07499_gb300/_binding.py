@@ -1,0 +1,332 @@
+"""Thin ctypes binding of the nlfem C-ABI (argument marshalling only).
+
+Every step of the method runs in the CUDA kernels of ``libnlfem.so``; this
+module only converts arrays, passes PyTorch's caching allocator and current
+stream to the library, and wraps the returned handles.  If the shared
+library is missing the import fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnlfem.so")
+
+NL_OK, NL_EINVAL, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV, NL_ETIMEOUT, NL_EBUSY = range(7)
+NOCAPS, APPROXCAPS, FULLCAPS = 0, 1, 2
+FP64, FP32_COMP = 0, 1
+HOST, DEVICE = 0, 1
+MAT_K, MAT_A = 0, 1
+
+_STATUS = {0: "NL_OK", 1: "NL_EINVAL", 2: "NL_ENOMEM", 3: "NL_ECUDA", 4: "NL_ENOTCONV", 5: "NL_ETIMEOUT",
+           6: "NL_EBUSY"}
+
+
+class NlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class nl_device(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class nl_pairs_info(C.Structure):
+    _fields_ = [("n_vert", C.c_int64), ("n_tet", C.c_int64), ("n_outer", C.c_int64), ("n_pairs", C.c_int64),
+                ("nnz", C.c_int64), ("n_free", C.c_int64), ("nnz_a", C.c_int64), ("max_row", C.c_int32),
+                ("delta", C.c_double)]
+
+
+class nl_assemble_opts(C.Structure):
+    _fields_ = [("strategy", C.c_int), ("mc_points", C.c_int), ("seed", C.c_uint64), ("precision", C.c_int),
+                ("gamma", C.c_double), ("f_const", C.c_double), ("g_nodal", C.c_void_p), ("g_where", C.c_int)]
+
+
+class nl_csr_view(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+class nl_assemble_stats(C.Structure):
+    _fields_ = [("pairs", C.c_uint64), ("cut_points", C.c_uint64), ("inside_points", C.c_uint64),
+                ("mc_samples", C.c_uint64), ("mc_accepted", C.c_uint64), ("hull_fallbacks", C.c_uint64)]
+
+
+class nl_solve_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int), ("mixed", C.c_int), ("inner_rtol", C.c_double),
+                ("check_every", C.c_int)]
+
+
+class nl_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double)]
+
+
+# every symbol the header declares (checked by the CPU test suite)
+EXPORTED = ["nl_mesh_create", "nl_mesh_destroy", "nl_pairs_build", "nl_pairs_destroy", "nl_pairs_get_info",
+            "nl_pairs_export", "nl_assemble", "nl_system_destroy", "nl_system_csr", "nl_system_rhs",
+            "nl_system_stats", "nl_solve", "nl_probe_moments", "nl_probe_philox", "nl_last_error", "nl_version"]
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libnlfem.so is not built; run __graft_entry__.build() or "
+                          "python paper_2302_07499_gb300/build.py (nvcc, sm_103a)")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, dp = C.c_void_p, C.c_int64, C.c_double
+    L.nl_mesh_create.argtypes = [C.POINTER(nl_device), vp, i64, vp, i64, vp, vp, C.c_int, C.POINTER(vp)]
+    L.nl_mesh_destroy.argtypes = [vp]
+    L.nl_mesh_destroy.restype = None
+    L.nl_pairs_build.argtypes = [vp, dp, C.POINTER(vp)]
+    L.nl_pairs_destroy.argtypes = [vp]
+    L.nl_pairs_destroy.restype = None
+    L.nl_pairs_get_info.argtypes = [vp, C.POINTER(nl_pairs_info)]
+    L.nl_pairs_export.argtypes = [vp, vp, vp, vp, C.c_int]
+    L.nl_assemble.argtypes = [vp, C.POINTER(nl_assemble_opts), C.POINTER(vp)]
+    L.nl_system_destroy.argtypes = [vp]
+    L.nl_system_destroy.restype = None
+    L.nl_system_csr.argtypes = [vp, C.c_int, C.POINTER(nl_csr_view)]
+    L.nl_system_rhs.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
+    L.nl_system_stats.argtypes = [vp, C.POINTER(nl_assemble_stats)]
+    L.nl_solve.argtypes = [vp, C.POINTER(nl_solve_opts), vp, C.c_int, C.POINTER(nl_solve_info)]
+    L.nl_probe_moments.argtypes = [vp, vp, vp, i64, dp, C.c_int, C.c_int, C.c_uint64, C.c_int, vp]
+    L.nl_probe_philox.argtypes = [vp, C.c_uint64, i64, vp]
+    L.nl_last_error.restype = C.c_char_p
+    L.nl_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != NL_OK:
+        raise NlError(st, lib().nl_last_error().decode())
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor (data must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class Device:
+    """Allocator hooks bound to PyTorch's caching allocator and a CUDA stream."""
+
+    def __init__(self, stream=None, use_torch=True):
+        import torch
+        self.torch = torch
+        self.dev_index = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._live = {}
+        if use_torch:
+            def _alloc(n, ctx):
+                try:
+                    p = torch.cuda.caching_allocator_alloc(int(n), self.dev_index, self.stream)
+                except Exception:
+                    return None
+                return p
+
+            def _free(p, ctx):
+                torch.cuda.caching_allocator_delete(p)
+
+            self._a = ALLOC_FN(_alloc)
+            self._f = FREE_FN(_free)
+        else:
+            self._a = ALLOC_FN()
+            self._f = FREE_FN()
+        self.c = nl_device(self._a, self._f, None, C.c_void_p(self.stream.cuda_stream))
+
+
+class _CAI:
+    """__cuda_array_interface__ view of library-owned device memory."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 3, "strides": None}
+
+
+def _as_tensor(ptr, n, dtype):
+    import torch
+    ts = {torch.float64: "<f8", torch.int64: "<i8", torch.int32: "<i4", torch.float32: "<f4"}[dtype]
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_CAI(ptr, n, ts), device="cuda")
+
+
+class Mesh:
+    def __init__(self, verts, tets, tet_in_omega, node_free, device: Device | None = None):
+        import torch
+        self.device = device or Device()
+        self._keep = []
+        if isinstance(verts, torch.Tensor) and verts.is_cuda:
+            arrs = [verts.contiguous().double(), tets.contiguous().int(), tet_in_omega.contiguous().to(torch.uint8),
+                    node_free.contiguous().to(torch.uint8)]
+            where = DEVICE
+        else:
+            arrs = [np.ascontiguousarray(verts, dtype=np.float64), np.ascontiguousarray(tets, dtype=np.int32),
+                    np.ascontiguousarray(tet_in_omega, dtype=np.uint8),
+                    np.ascontiguousarray(node_free, dtype=np.uint8)]
+            where = HOST
+        self._keep = arrs
+        self.nv = int(arrs[0].shape[0])
+        self.nt = int(arrs[1].shape[0])
+        h = C.c_void_p()
+        _check(lib().nl_mesh_create(C.byref(self.device.c), _ptr(arrs[0]), self.nv, _ptr(arrs[1]), self.nt,
+                                    _ptr(arrs[2]), _ptr(arrs[3]), where, C.byref(h)))
+        self.h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nl_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pairs:
+    def __init__(self, mesh: Mesh, delta: float):
+        self.mesh = mesh
+        h = C.c_void_p()
+        _check(lib().nl_pairs_build(mesh.h, float(delta), C.byref(h)))
+        self.h = h
+        inf = nl_pairs_info()
+        _check(lib().nl_pairs_get_info(self.h, C.byref(inf)))
+        self.info = {k: getattr(inf, k) for k, _ in nl_pairs_info._fields_}
+
+    def export(self):
+        n_outer, npairs = self.info["n_outer"], self.info["n_pairs"]
+        outer = np.zeros(n_outer, dtype=np.int32)
+        ptr = np.zeros(n_outer + 1, dtype=np.int64)
+        tp = np.zeros(max(npairs, 1), dtype=np.int32)
+        _check(lib().nl_pairs_export(self.h, _ptr(outer), _ptr(ptr), _ptr(tp), HOST))
+        return outer, ptr, tp[:npairs]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nl_pairs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class System:
+    def __init__(self, pairs: Pairs, strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, gamma=1.0,
+                 f_const=0.0, g=None):
+        self.pairs = pairs
+        self._g = None
+        where = HOST
+        gp = None
+        if g is not None:
+            if isinstance(g, np.ndarray):
+                self._g = np.ascontiguousarray(g, dtype=np.float64)
+            else:
+                self._g = g.contiguous().double()
+                where = DEVICE
+            gp = _ptr(self._g)
+        o = nl_assemble_opts(int(strategy), int(mc_points), int(seed), int(precision), float(gamma), float(f_const),
+                             gp, where)
+        h = C.c_void_p()
+        _check(lib().nl_assemble(pairs.h, C.byref(o), C.byref(h)))
+        self.h = h
+        self._g = None
+
+    def csr(self, which=MAT_K):
+        """(rowptr, col, val) as torch CUDA tensors viewing library memory (valid until close)."""
+        import torch
+        v = nl_csr_view()
+        _check(lib().nl_system_csr(self.h, int(which), C.byref(v)))
+        return (_as_tensor(v.rowptr, v.n_rows + 1, torch.int64), _as_tensor(v.col, v.nnz, torch.int32),
+                _as_tensor(v.val, v.nnz, torch.float64))
+
+    def csr_numpy(self, which=MAT_K):
+        rp, c, v = self.csr(which)
+        return rp.cpu().numpy(), c.cpu().numpy(), v.cpu().numpy()
+
+    def scipy(self, which=MAT_K):
+        import scipy.sparse as sp
+        rp, c, v = self.csr_numpy(which)
+        n = rp.size - 1
+        return sp.csr_matrix((v, c, rp), shape=(n, n))
+
+    def rhs(self):
+        import torch
+        b = C.c_void_p()
+        fn = C.c_void_p()
+        _check(lib().nl_system_rhs(self.h, C.byref(b), C.byref(fn)))
+        nf = self.pairs.info["n_free"]
+        return _as_tensor(b.value, nf, torch.float64), _as_tensor(fn.value, nf, torch.int32)
+
+    def stats(self):
+        s = nl_assemble_stats()
+        _check(lib().nl_system_stats(self.h, C.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in nl_assemble_stats._fields_}
+
+    def solve(self, rtol=1e-12, max_iter=0, mixed=False, inner_rtol=0.0, check_every=0, out=None):
+        """Returns (u, info).  u: full nodal vector; numpy unless `out` is a CUDA tensor."""
+        o = nl_solve_opts(float(rtol), int(max_iter), int(bool(mixed)), float(inner_rtol), int(check_every))
+        inf = nl_solve_info()
+        if out is None:
+            u = np.zeros(self.pairs.info["n_vert"])
+            where = HOST
+        else:
+            u = out
+            where = DEVICE
+        st = lib().nl_solve(self.h, C.byref(o), _ptr(u), where, C.byref(inf))
+        info = {"iterations": inf.iterations, "refinements": inf.refinements, "rel_residual": inf.rel_residual,
+                "status": st}
+        if st not in (NL_OK, NL_ENOTCONV):
+            _check(st)
+        return u, info
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nl_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def probe_moments(tets_xyz, x, ids, delta, strategy, mc_points=0, seed=1, precision=FP64):
+    tv = np.ascontiguousarray(tets_xyz, dtype=np.float64).reshape(-1, 12)
+    xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    ii = np.ascontiguousarray(ids, dtype=np.uint32).reshape(-1, 3)
+    n = tv.shape[0]
+    out = np.zeros((n, 15))
+    _check(lib().nl_probe_moments(_ptr(tv), _ptr(xs), _ptr(ii), n, float(delta), int(strategy), int(mc_points),
+                                  int(seed), int(precision), _ptr(out)))
+    return out
+
+
+def probe_philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(c)
+    _check(lib().nl_probe_philox(_ptr(c), int(key), c.shape[0], _ptr(out)))
+    return out

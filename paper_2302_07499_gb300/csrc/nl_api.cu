@@ -1,0 +1,121 @@
+// C-ABI entry points for assembly and the system handle.
+#include <math.h>
+
+#include <algorithm>
+
+#include "nl_internal.h"
+
+namespace {
+
+__global__ void k_zero_collar_g(const uint8_t *__restrict__ node_free, double *g, int64_t nv)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nv && node_free[i]) g[i] = 0.0;    // only collar values are used
+}
+
+}  // namespace
+
+extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_system **out)
+{
+    nl_clear_error();
+    if (!P || !opts || !out) { nl_set_error("NULL argument"); return NL_EINVAL; }
+    *out = nullptr;
+    if (opts->strategy < NL_NOCAPS || opts->strategy > NL_FULLCAPS) { nl_set_error("bad strategy"); return NL_EINVAL; }
+    if (opts->precision != NL_FP64 && opts->precision != NL_FP32_COMP) { nl_set_error("bad precision"); return NL_EINVAL; }
+    if (opts->strategy == NL_FULLCAPS && (opts->mc_points < 1 || opts->mc_points > 4096)) {
+        nl_set_error("mc_points must be in 1..4096 for fullcaps");
+        return NL_EINVAL;
+    }
+    if (!isfinite(opts->gamma) || !isfinite(opts->f_const)) { nl_set_error("gamma and f_const must be finite"); return NL_EINVAL; }
+    if (opts->g_nodal && opts->g_where != NL_HOST && opts->g_where != NL_DEVICE) { nl_set_error("bad g_where"); return NL_EINVAL; }
+    nl_mesh *m = P->mesh;
+    nl_system *S = new nl_system();
+    S->arena.dev = P->arena.dev;
+    S->pairs = P;
+    S->opts = *opts;
+    S->opts.g_nodal = nullptr;
+    try {
+        cudaStream_t s = S->arena.stream();
+        S->K = S->arena.get<double>(P->nnz);
+        S->A = S->arena.get<double>(P->nnz_a);
+        S->A32 = S->arena.get<float>(P->nnz_a);
+        S->b = S->arena.get<double>(m->n_free);
+        S->g = S->arena.get<double>(m->nv);
+        S->F = S->arena.get<double>(m->nv);
+        if (opts->g_nodal) {
+            NL_CUDA(cudaMemcpyAsync(S->g, opts->g_nodal, sizeof(double) * m->nv,
+                                    opts->g_where == NL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+            k_zero_collar_g<<<(unsigned)nl_cdiv<int64_t>(m->nv, 256), 256, 0, s>>>(m->node_free, S->g, m->nv);
+            NL_CHECK_LAUNCH();
+        } else {
+            NL_CUDA(cudaMemsetAsync(S->g, 0, sizeof(double) * m->nv, s));
+        }
+        Scratch sc(&S->arena);
+        const bool f32 = opts->precision == NL_FP32_COMP;
+        void *D = f32 ? (void *)sc.get<float>(10 * P->npairs) : (void *)sc.get<double>(10 * P->npairs);
+        double *strips = sc.get<double>(P->strip_total);
+        double *TT = sc.get<double>(10 * m->n_outer);
+        uint64_t *st = sc.get<uint64_t>(8);
+        NL_CUDA(cudaMemsetAsync(st, 0, sizeof(uint64_t) * 8, s));
+        if (f32) nl_assemble_fp32(S, (float *)D, strips, TT, st);
+        else nl_assemble_fp64(S, (double *)D, strips, TT, st);
+        nl_reduce_system(S, D, f32 ? 1 : 0, strips, TT);
+        uint64_t hs[8];
+        NL_CUDA(cudaMemcpyAsync(hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        NL_CUDA(cudaStreamSynchronize(s));
+        S->stats.pairs = (uint64_t)P->npairs;
+        S->stats.cut_points = hs[0];
+        S->stats.inside_points = hs[1];
+        S->stats.mc_samples = hs[2];
+        S->stats.mc_accepted = hs[3];
+        S->stats.hull_fallbacks = hs[4];
+    } catch (NlError &e) {
+        S->arena.release_all();
+        delete S;
+        return e.st;
+    }
+    *out = S;
+    return NL_OK;
+}
+
+extern "C" void nl_system_destroy(nl_system *S)
+{
+    if (!S) return;
+    S->arena.release_all();
+    delete S;
+}
+
+extern "C" nl_status nl_system_csr(const nl_system *S, int which, nl_csr_view *out)
+{
+    nl_clear_error();
+    if (!S || !out) { nl_set_error("NULL argument"); return NL_EINVAL; }
+    const nl_pairs *P = S->pairs;
+    if (which == NL_MAT_K) {
+        out->n_rows = P->mesh->nv; out->nnz = P->nnz;
+        out->rowptr = P->rowptr; out->col = P->col; out->val = S->K;
+    } else if (which == NL_MAT_A) {
+        out->n_rows = P->mesh->n_free; out->nnz = P->nnz_a;
+        out->rowptr = P->a_rowptr; out->col = P->a_col; out->val = S->A;
+    } else {
+        nl_set_error("bad matrix selector");
+        return NL_EINVAL;
+    }
+    return NL_OK;
+}
+
+extern "C" nl_status nl_system_rhs(const nl_system *S, const double **b, const int32_t **free_nodes)
+{
+    nl_clear_error();
+    if (!S) { nl_set_error("NULL argument"); return NL_EINVAL; }
+    if (b) *b = S->b;
+    if (free_nodes) *free_nodes = S->pairs->mesh->free_nodes;
+    return NL_OK;
+}
+
+extern "C" nl_status nl_system_stats(const nl_system *S, nl_assemble_stats *out)
+{
+    nl_clear_error();
+    if (!S || !out) { nl_set_error("NULL argument"); return NL_EINVAL; }
+    *out = S->stats;
+    return NL_OK;
+}

@@ -1,0 +1,15 @@
+// FP32 assembly: per-(pair, point) geometry, Monte Carlo and moments in FP32
+// on coordinates relative to the outer point; every sum across points,
+// pairs and elements is accumulated in FP64 (strips, staged moments, V_q).
+#include "nl_assemble.cuh"
+
+void nl_assemble_fp32(nl_system *sys, float *D, double *strips, double *TT, uint64_t *stats)
+{
+    nla::launch_assemble<float>(sys, D, strips, TT, reinterpret_cast<unsigned long long *>(stats));
+}
+
+void nl_probe_fp32(const double *tv, const double *xs, const uint32_t *ids, int64_t n, double delta2, int strategy,
+                   int nmc, uint64_t seed, double *out)
+{
+    nla::launch_probe<float>(tv, xs, ids, n, delta2, strategy, nmc, seed, out);
+}

@@ -1,0 +1,16 @@
+// FP64 assembly.  Compiled with -fmad=false: every decision of the method
+// (inside test, edge/sphere points, diagonal, sampling volumes, Monte Carlo
+// points and acceptance) follows the fixed operation order of the arithmetic
+// specification, with no fused multiply-add.
+#include "nl_assemble.cuh"
+
+void nl_assemble_fp64(nl_system *sys, double *D, double *strips, double *TT, uint64_t *stats)
+{
+    nla::launch_assemble<double>(sys, D, strips, TT, reinterpret_cast<unsigned long long *>(stats));
+}
+
+void nl_probe_fp64(const double *tv, const double *xs, const uint32_t *ids, int64_t n, double delta2, int strategy,
+                   int nmc, uint64_t seed, double *out)
+{
+    nla::launch_probe<double>(tv, xs, ids, n, delta2, strategy, nmc, seed, out);
+}

@@ -1,0 +1,145 @@
+// Internal declarations of the nlfem CUDA library (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nlfem.h"
+
+// ---------------------------------------------------------------------------
+// error plumbing: every entry point returns nl_status; the message is kept
+// per thread.
+void nl_set_error(const char *fmt, ...);
+void nl_clear_error();
+
+struct NlError {
+    nl_status st;
+};
+
+#define NL_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t _e = (call);                                                       \
+        if (_e != cudaSuccess) {                                                       \
+            nl_set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(_e)); \
+            throw NlError{NL_ECUDA};                                                   \
+        }                                                                              \
+    } while (0)
+
+#define NL_CHECK_LAUNCH() NL_CUDA(cudaGetLastError())
+
+#define NL_REQUIRE(cond, ...)                                                          \
+    do {                                                                               \
+        if (!(cond)) {                                                                 \
+            nl_set_error(__VA_ARGS__);                                                 \
+            throw NlError{NL_EINVAL};                                                  \
+        }                                                                              \
+    } while (0)
+
+// Device allocations owned by a handle; released in reverse order.
+struct DevArena {
+    nl_device dev{};
+    std::vector<void *> ptrs;
+    void *raw(size_t bytes);
+    template <class T> T *get(size_t n) { return static_cast<T *>(raw(sizeof(T) * (n ? n : 1))); }
+    void release(void *p);
+    void release_all();
+    cudaStream_t stream() const { return static_cast<cudaStream_t>(dev.stream); }
+};
+
+// Scratch that lives for one call (freed on scope exit).
+struct Scratch {
+    DevArena *arena;
+    std::vector<void *> mine;
+    explicit Scratch(DevArena *a) : arena(a) {}
+    template <class T> T *get(size_t n) {
+        T *p = arena->get<T>(n);
+        mine.push_back(p);
+        return p;
+    }
+    ~Scratch() {
+        for (size_t i = mine.size(); i-- > 0;) arena->release(mine[i]);
+    }
+};
+
+struct nl_mesh {
+    DevArena arena;
+    int64_t nv = 0, nt = 0, n_outer = 0, n_free = 0;
+    double4 *verts = nullptr;      // x, y, z, 0
+    float4 *vhi = nullptr;         // float hi part of the coordinates
+    float4 *vlo = nullptr;         // float lo part (coordinate - hi, rounded)
+    int4 *tets = nullptr;
+    uint8_t *in_omega = nullptr;
+    uint8_t *node_free = nullptr;
+    double4 *tet_cr = nullptr;     // centroid xyz, bounding radius
+    double *tet_vol = nullptr;
+    int32_t *outer_ids = nullptr;  // Omega elements, increasing id
+    int32_t *outer_of = nullptr;   // element -> outer index or -1
+    double *xq = nullptr;          // [n_outer][4][3] quadrature points
+    int32_t *free_idx = nullptr;   // node -> free index or -1
+    int32_t *free_nodes = nullptr; // [n_free]
+    int64_t *ne_ptr = nullptr;     // node -> incident elements (sorted), packed elem<<2|local
+    int32_t *ne_ent = nullptr;
+    double rmax = 0.0;
+    double bbmin[3] = {0, 0, 0}, bbmax[3] = {0, 0, 0};
+};
+
+struct nl_pairs {
+    DevArena arena;
+    nl_mesh *mesh = nullptr;
+    double delta = 0.0;
+    int64_t npairs = 0;
+    int64_t *pair_ptr = nullptr;   // [n_outer+1]
+    int32_t *pair_tp = nullptr;    // [npairs]
+    int32_t *pair_T = nullptr;     // [npairs] element id of the outer element
+    int64_t *tp_ptr = nullptr;     // [nt+1] pairs having the element as T'
+    int32_t *tp_pair = nullptr;    // [npairs] pair ids, increasing
+    int64_t nnz = 0;
+    int64_t *rowptr = nullptr;     // [nv+1]
+    int32_t *col = nullptr;        // [nnz]
+    int32_t *perm = nullptr;       // [nnz] position of the transposed entry
+    int32_t *elem_pos = nullptr;   // [nt][16] positions of the element block, -1 if inactive
+    int64_t *strip_off = nullptr;  // [n_outer*4+1]
+    int64_t strip_total = 0;
+    int32_t max_row = 0;
+    int64_t max_pairs_per_outer = 0;
+    int64_t nnz_a = 0;
+    int64_t *a_rowptr = nullptr;   // [n_free+1]
+    int32_t *a_col = nullptr;      // [nnz_a]
+    int32_t *a_src = nullptr;      // [nnz_a] position in K
+};
+
+struct nl_system {
+    DevArena arena;
+    nl_pairs *pairs = nullptr;
+    nl_assemble_opts opts{};
+    double *K = nullptr;           // [nnz]
+    double *A = nullptr;           // [nnz_a]
+    float *A32 = nullptr;          // [nnz_a]
+    double *b = nullptr;           // [n_free]
+    double *g = nullptr;           // [nv]
+    double *F = nullptr;           // [nv]
+    nl_assemble_stats stats{};
+};
+
+// ---------------------------------------------------------------------------
+// shared device utilities (nl_util.cu)
+void nl_exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, DevArena *arena, cudaStream_t s);
+// out[i] = sum_{j<i} in[j] for i in [0,n], out has n+1 entries; returns out[n] (synchronises)
+int64_t nl_scan_counts(const int64_t *counts, int64_t *out, int64_t n, DevArena *arena, cudaStream_t s);
+// sort the int32 keys of each segment [ptr[i], ptr[i+1]) ascending; max_seg = longest segment
+void nl_segmented_sort_i32(int32_t *keys, const int64_t *ptr, int64_t nseg, int64_t max_seg,
+                           DevArena *arena, cudaStream_t s);
+int nl_num_sms();
+
+// kernels of other translation units
+nl_status nl_pairs_build_impl(nl_mesh *mesh, double delta, nl_pairs **out);
+void nl_assemble_fp64(nl_system *sys, double *D, double *strips, double *TT, uint64_t *stats);
+void nl_assemble_fp32(nl_system *sys, float *D, double *strips, double *TT, uint64_t *stats);
+void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT);
+nl_status nl_solve_impl(nl_system *sys, const nl_solve_opts *opts, double *u_out, int where,
+                        nl_solve_info *info);
+
+template <class T> static inline T nl_cdiv(T a, T b) { return (a + b - 1) / b; }

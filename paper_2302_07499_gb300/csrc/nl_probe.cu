@@ -1,0 +1,74 @@
+// Diagnostic entry points: the device geometry and the Philox stream on
+// caller-given cases (host arrays in, host arrays out; default stream,
+// cudaMalloc'd temporaries).  Used by tests to compare single cases with the
+// CPU reference; not on the assembly path.
+#include "nl_internal.h"
+#include "nl_quad.cuh"
+
+void nl_probe_fp64(const double *, const double *, const uint32_t *, int64_t, double, int, int, uint64_t, double *);
+void nl_probe_fp32(const double *, const double *, const uint32_t *, int64_t, double, int, int, uint64_t, double *);
+
+namespace {
+__global__ void k_philox(const uint4 *__restrict__ ctr, uint2 key, int64_t n, uint4 *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = nlq::philox4x32_10(ctr[i], key);
+}
+
+struct Tmp {
+    std::vector<void *> p;
+    template <class T> T *get(size_t n)
+    {
+        void *q = nullptr;
+        NL_CUDA(cudaMalloc(&q, sizeof(T) * (n ? n : 1)));
+        p.push_back(q);
+        return (T *)q;
+    }
+    ~Tmp() { for (void *q : p) cudaFree(q); }
+};
+}  // namespace
+
+extern "C" nl_status nl_probe_moments(const double *tets_xyz, const double *x, const uint32_t *ids, int64_t n,
+                                      double delta, int strategy, int mc_points, uint64_t seed, int precision,
+                                      double *moments)
+{
+    nl_clear_error();
+    if (!tets_xyz || !x || !ids || !moments || n < 0) { nl_set_error("bad argument"); return NL_EINVAL; }
+    if (strategy < 0 || strategy > 2 || (precision != NL_FP64 && precision != NL_FP32_COMP)) {
+        nl_set_error("bad strategy or precision");
+        return NL_EINVAL;
+    }
+    if (n == 0) return NL_OK;
+    try {
+        Tmp t;
+        double *dv = t.get<double>(12 * n), *dx = t.get<double>(3 * n), *dm = t.get<double>(15 * n);
+        uint32_t *di = t.get<uint32_t>(3 * n);
+        NL_CUDA(cudaMemcpy(dv, tets_xyz, sizeof(double) * 12 * n, cudaMemcpyHostToDevice));
+        NL_CUDA(cudaMemcpy(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+        NL_CUDA(cudaMemcpy(di, ids, sizeof(uint32_t) * 3 * n, cudaMemcpyHostToDevice));
+        if (precision == NL_FP64) nl_probe_fp64(dv, dx, di, n, delta * delta, strategy, mc_points, seed, dm);
+        else nl_probe_fp32(dv, dx, di, n, delta * delta, strategy, mc_points, seed, dm);
+        NL_CUDA(cudaMemcpy(moments, dm, sizeof(double) * 15 * n, cudaMemcpyDeviceToHost));
+    } catch (NlError &e) {
+        return e.st;
+    }
+    return NL_OK;
+}
+
+extern "C" nl_status nl_probe_philox(const uint32_t *ctr, uint64_t key, int64_t n, uint32_t *out)
+{
+    nl_clear_error();
+    if (!ctr || !out || n < 0) { nl_set_error("bad argument"); return NL_EINVAL; }
+    if (n == 0) return NL_OK;
+    try {
+        Tmp t;
+        uint4 *dc = t.get<uint4>(n), *doo = t.get<uint4>(n);
+        NL_CUDA(cudaMemcpy(dc, ctr, sizeof(uint4) * n, cudaMemcpyHostToDevice));
+        k_philox<<<(unsigned)((n + 255) / 256), 256>>>(dc, make_uint2((uint32_t)key, (uint32_t)(key >> 32)), n, doo);
+        NL_CHECK_LAUNCH();
+        NL_CUDA(cudaMemcpy(out, doo, sizeof(uint4) * n, cudaMemcpyDeviceToHost));
+    } catch (NlError &e) {
+        return e.st;
+    }
+    return NL_OK;
+}

@@ -1,0 +1,198 @@
+// Deterministic reduction of the assembly outputs into the CSR matrix K,
+// the free block A = K[free,free] and the right-hand side b (no floating-
+// point atomics: every sum runs in a fixed order).
+//
+//   G  = sum over outer elements of their cross strips (row gather)
+//   K  = G + G^T + sum over elements of their 4x4 element blocks
+//        (TT of the outer element plus the T'T' moments of every pair that
+//        has the element as T', scaled by omega (gamma/2)|T|/4)
+//   F_i = sum_T sum_q (|T|/4) lambda_i(x_q) f            (Alg. 5, last save)
+//   b  = F[free] - K[free, collar] g[collar]
+#include <algorithm>
+
+#include "nl_internal.h"
+
+namespace {
+
+// G row r = sum over outer elements T containing r (increasing id) of the
+// strip of T for r's local index.  One warp per row, lanes over columns.
+__global__ void k_strip_gather(const int64_t *__restrict__ rowptr, const int64_t *__restrict__ ne_ptr,
+                               const int32_t *__restrict__ ne_ent, const int32_t *__restrict__ outer_of,
+                               const int64_t *__restrict__ strip_off, const double *__restrict__ strips, int64_t nv,
+                               double *G)
+{
+    int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (r >= nv) return;
+    int64_t rb = rowptr[r];
+    int len = (int)(rowptr[r + 1] - rb);
+    for (int c0 = 0; c0 < len; c0 += 32 * 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t k = ne_ptr[r]; k < ne_ptr[r + 1]; ++k) {
+            int32_t ent = ne_ent[k];
+            int32_t o = outer_of[ent >> 2];
+            if (o < 0) continue;
+            const double *s = strips + strip_off[4 * (int64_t)o + (ent & 3)];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int c = c0 + u * 32 + lane;
+                if (c < len) acc[u] += s[c];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int c = c0 + u * 32 + lane;
+            if (c < len) G[rb + c] = acc[u];
+        }
+    }
+}
+
+// element blocks: warp per element; lanes take pairs lane, lane+32, ...;
+// fixed butterfly reduction.  Layout of the 10 values: (0,0) (0,1) (0,2)
+// (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3).
+template <class DT>
+__global__ void k_elem_blocks(const int64_t *__restrict__ tp_ptr, const int32_t *__restrict__ tp_pair,
+                              const int32_t *__restrict__ pair_T, const double *__restrict__ tet_vol,
+                              const uint8_t *__restrict__ in_omega, const int32_t *__restrict__ outer_of,
+                              const DT *__restrict__ D, const double *__restrict__ TT, double half_gamma, int64_t nt,
+                              double *E)
+{
+    int64_t el = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (el >= nt) return;
+    double omega = in_omega[el] ? 1.0 : 2.0;
+    double acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+    for (int64_t j = tp_ptr[el] + lane; j < tp_ptr[el + 1]; j += 32) {
+        int32_t p = tp_pair[j];
+        double w = omega * (half_gamma * (tet_vol[pair_T[p]] * 0.25));
+        const DT *d = D + 10 * (int64_t)p;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k] += w * (double)d[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 10; ++k)
+        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+    if (lane < 10) {
+        double v = acc[0];
+#pragma unroll
+        for (int k = 1; k < 10; ++k)
+            if (lane == k) v = acc[k];
+        int32_t o = outer_of[el];
+        if (o >= 0) v += TT[10 * (int64_t)o + lane];
+        E[10 * el + lane] = v;
+    }
+}
+
+__device__ __forceinline__ int sym10(int i, int j)
+{
+    int a = i < j ? i : j, b = i < j ? j : i;
+    // offsets of row a in the upper triangle: 0, 4, 7, 9
+    int base = (a == 0) ? 0 : (a == 1) ? 4 : (a == 2) ? 7 : 9;
+    return base + (b - a);
+}
+
+// K row r = G + G^T over the row, then the element blocks of the active
+// elements around r in increasing element id.
+__global__ void k_final_K(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ perm,
+                          const double *__restrict__ G, const int64_t *__restrict__ ne_ptr,
+                          const int32_t *__restrict__ ne_ent, const int32_t *__restrict__ elem_pos,
+                          const double *__restrict__ E, int64_t nv, double *K)
+{
+    int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (r >= nv) return;
+    for (int64_t e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32) K[e] = G[e] + G[perm[e]];
+    __syncwarp();
+    for (int64_t k = ne_ptr[r]; k < ne_ptr[r + 1]; ++k) {
+        int32_t ent = ne_ent[k];
+        int64_t el = ent >> 2;
+        int i = ent & 3;
+        if (lane < 4) {
+            int32_t pos = elem_pos[16 * el + 4 * i + lane];
+            if (pos >= 0) K[pos] += E[10 * el + sym10(i, lane)];
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_load_vector(const int64_t *__restrict__ ne_ptr, const int32_t *__restrict__ ne_ent,
+                              const int32_t *__restrict__ outer_of, const double *__restrict__ tet_vol, double fconst,
+                              int64_t nv, double *F)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nv) return;
+    const double qa = 0x1.2bbae2a27f931p-1, qb = 0x1.1b06d1d200913p-3;
+    double s = 0.0;
+    for (int64_t k = ne_ptr[r]; k < ne_ptr[r + 1]; ++k) {
+        int32_t ent = ne_ent[k];
+        int64_t el = ent >> 2;
+        if (outer_of[el] < 0) continue;
+        double w = tet_vol[el] * 0.25;
+        // sum over the four points: lambda_i = a at its own point, b at the others
+        s += ((w * qa * fconst + w * qb * fconst) + w * qb * fconst) + w * qb * fconst;
+    }
+    F[r] = s;
+}
+
+__global__ void k_system(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                         const double *__restrict__ K, const int32_t *__restrict__ free_nodes,
+                         const int32_t *__restrict__ free_idx, const int64_t *__restrict__ a_rowptr,
+                         const int32_t *__restrict__ a_src, const double *__restrict__ F,
+                         const double *__restrict__ g, int64_t n_free, double *Aval, float *A32, double *b)
+{
+    int64_t fr = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (fr >= n_free) return;
+    for (int64_t e = a_rowptr[fr] + lane; e < a_rowptr[fr + 1]; e += 32) {
+        double v = K[a_src[e]];
+        Aval[e] = v;
+        A32[e] = (float)v;
+    }
+    int32_t r = free_nodes[fr];
+    double s = 0.0;
+    for (int64_t e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32) {
+        int32_t c = col[e];
+        if (free_idx[c] < 0) s += K[e] * g[c];
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) b[fr] = F[r] - s;
+}
+
+unsigned wblocks(int64_t n) { return (unsigned)std::max<int64_t>(1, nl_cdiv<int64_t>(n * 32, 256)); }
+
+}  // namespace
+
+void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT)
+{
+    nl_pairs *P = sys->pairs;
+    nl_mesh *m = P->mesh;
+    cudaStream_t s = sys->arena.stream();
+    Scratch sc(&sys->arena);
+    double *G = sc.get<double>(P->nnz);
+    k_strip_gather<<<wblocks(m->nv), 256, 0, s>>>(P->rowptr, m->ne_ptr, m->ne_ent, m->outer_of, P->strip_off, strips,
+                                                 m->nv, G);
+    NL_CHECK_LAUNCH();
+    double *E = sc.get<double>(10 * m->nt);
+    if (d_is_float)
+        k_elem_blocks<float><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->in_omega,
+                                                           m->outer_of, (const float *)D, TT, sys->opts.gamma / 2.0,
+                                                           m->nt, E);
+    else
+        k_elem_blocks<double><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol,
+                                                            m->in_omega, m->outer_of, (const double *)D, TT,
+                                                            sys->opts.gamma / 2.0, m->nt, E);
+    NL_CHECK_LAUNCH();
+    k_final_K<<<wblocks(m->nv), 256, 0, s>>>(P->rowptr, P->perm, G, m->ne_ptr, m->ne_ent, P->elem_pos, E, m->nv,
+                                            sys->K);
+    NL_CHECK_LAUNCH();
+    k_load_vector<<<(unsigned)nl_cdiv<int64_t>(m->nv, 256), 256, 0, s>>>(m->ne_ptr, m->ne_ent, m->outer_of,
+                                                                       m->tet_vol, sys->opts.f_const, m->nv, sys->F);
+    NL_CHECK_LAUNCH();
+    k_system<<<wblocks(m->n_free), 256, 0, s>>>(P->rowptr, P->col, sys->K, m->free_nodes, m->free_idx, P->a_rowptr,
+                                               P->a_src, sys->F, sys->g, m->n_free, sys->A, sys->A32, sys->b);
+    NL_CHECK_LAUNCH();
+    // scratch is released (stream-ordered) when sc goes out of scope
+    NL_CUDA(cudaStreamSynchronize(s));
+}

@@ -1,0 +1,312 @@
+// Conjugate gradients on A u = b (Alg. 5, last line) with a CSR SpMV.
+// FP64 mode: all vectors and values in FP64.  Mixed mode: iterative
+// refinement with FP64 residuals r = b - A u and FP64 updates, the correction
+// solved by CG on the FP32 copy of A with FP32 vectors; dot products are
+// accumulated in FP64 in both modes.  Reductions use a fixed grid and a
+// fixed combination order, so results are bitwise reproducible.
+#include <math.h>
+
+#include <algorithm>
+
+#include "nl_internal.h"
+
+namespace {
+
+struct CgState {
+    double rr, pq, alpha, beta, tol2;
+    int done, it;
+};
+
+constexpr int RB = 256;   // threads per block in reductions
+
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    __syncthreads();
+    return s;   // valid in thread 0
+}
+
+// q = A p (warp per row) and per-block partial of p.q
+template <class VT, class XT>
+__global__ void k_spmv_dot(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const VT *__restrict__ val, const XT *__restrict__ p, XT *q, int64_t n,
+                           double *part, const CgState *st)
+{
+    __shared__ double sh[RB / 32];
+    if (st && st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double acc = 0.0;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        VT s = VT(0);
+        for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) s += val[e] * (VT)p[ci[e]];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            q[r] = (XT)s;
+            acc += (double)p[r] * (double)s;
+        }
+    }
+    double t = block_sum(acc, sh);
+    if (threadIdx.x == 0 && part) part[blockIdx.x] = t;
+}
+
+__global__ void k_alpha(const double *part, int nb, CgState *st)
+{
+    if (threadIdx.x != 0 || st->done) return;
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += part[i];
+    st->pq = s;
+    st->alpha = (s != 0.0) ? st->rr / s : 0.0;
+}
+
+template <class XT>
+__global__ void k_update_xr(XT *x, XT *r, const XT *p, const XT *q, int64_t n, double *part, const CgState *st)
+{
+    __shared__ double sh[RB / 32];
+    if (st->done) return;
+    const XT a = (XT)st->alpha;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += a * p[i];
+        XT ri = r[i] - a * q[i];
+        r[i] = ri;
+        acc += (double)ri * (double)ri;
+    }
+    double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_beta(const double *part, int nb, CgState *st)
+{
+    if (threadIdx.x != 0 || st->done) return;
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += part[i];
+    st->beta = (st->rr != 0.0) ? s / st->rr : 0.0;
+    st->rr = s;
+    st->it += 1;
+    if (s <= st->tol2 || !(s == s)) st->done = 1;
+}
+
+template <class XT>
+__global__ void k_update_p(XT *p, const XT *r, int64_t n, const CgState *st)
+{
+    if (st->done) return;
+    const XT b = (XT)st->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = r[i] + b * p[i];
+}
+
+template <class XT>
+__global__ void k_init(const double *b, XT *x, XT *r, XT *p, int64_t n, double scale, double *part)
+{
+    __shared__ double sh[RB / 32];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        XT v = (XT)(b[i] * scale);
+        x[i] = XT(0);
+        r[i] = v;
+        p[i] = v;
+        acc += (double)v * (double)v;
+    }
+    double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_start(const double *part, int nb, double rtol2, CgState *st)
+{
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += part[i];
+    st->rr = s;
+    st->tol2 = rtol2 * s;
+    st->done = (s == 0.0) ? 1 : 0;
+    st->it = 0;
+    st->alpha = st->beta = st->pq = 0.0;
+}
+
+// r = b - A x (FP64), partial |r|^2
+__global__ void k_residual(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ val, const double *__restrict__ x, const double *__restrict__ b,
+                           double *r, int64_t n, double *part)
+{
+    __shared__ double sh[RB / 32];
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double acc = 0.0;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += warps) {
+        double s = 0.0;
+        for (int64_t e = rp[row] + lane; e < rp[row + 1]; e += 32) s += val[e] * x[ci[e]];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            double ri = b[row] - s;
+            r[row] = ri;
+            acc += ri * ri;
+        }
+    }
+    double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_add_scaled(double *x, const float *d, double scale, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += scale * (double)d[i];
+}
+
+__global__ void k_scatter_u(const double *x, const int32_t *free_nodes, const double *g, const uint8_t *node_free,
+                            double *u, int64_t nv, int64_t nf)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nv && !node_free[i]) u[i] = g[i];
+    if (i < nf) u[free_nodes[i]] = x[i];
+}
+
+struct Cg {
+    int nb = 0;
+    double *part = nullptr;
+    CgState *st = nullptr;
+};
+
+// Run CG from x = 0 on A x = b*scale; returns iterations; converged flag in *conv.
+template <class VT, class XT>
+int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b, double scale, XT *x, XT *r, XT *p,
+           XT *q, int64_t n, double rtol, int max_it, int check_every, Cg &cg, cudaStream_t s, bool *conv)
+{
+    const int nb = cg.nb;
+    k_init<XT><<<nb, RB, 0, s>>>(b, x, r, p, n, scale, cg.part);
+    NL_CHECK_LAUNCH();
+    k_start<<<1, 32, 0, s>>>(cg.part, nb, rtol * rtol, cg.st);
+    NL_CHECK_LAUNCH();
+    CgState h{};
+    int launched = 0;
+    *conv = false;
+    while (launched < max_it) {
+        int k = std::min(check_every, max_it - launched);
+        for (int j = 0; j < k; ++j) {
+            k_spmv_dot<VT, XT><<<nb, RB, 0, s>>>(rp, ci, val, p, q, n, cg.part, cg.st);
+            k_alpha<<<1, 32, 0, s>>>(cg.part, nb, cg.st);
+            k_update_xr<XT><<<nb, RB, 0, s>>>(x, r, p, q, n, cg.part, cg.st);
+            k_beta<<<1, 32, 0, s>>>(cg.part, nb, cg.st);
+            k_update_p<XT><<<nb, RB, 0, s>>>(p, r, n, cg.st);
+        }
+        NL_CHECK_LAUNCH();
+        launched += k;
+        NL_CUDA(cudaMemcpyAsync(&h, cg.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        NL_CUDA(cudaStreamSynchronize(s));
+        if (h.done) break;
+    }
+    *conv = h.done && (h.rr == h.rr);
+    return h.it;
+}
+
+}  // namespace
+
+nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, int where, nl_solve_info *info)
+{
+    nl_pairs *P = S->pairs;
+    nl_mesh *m = P->mesh;
+    const int64_t n = m->n_free;
+    double rtol = (opts && opts->rtol > 0) ? opts->rtol : 1e-12;
+    int max_it = (opts && opts->max_iter > 0) ? opts->max_iter : 20000;
+    int mixed = opts ? opts->mixed : 0;
+    double inner = (opts && opts->inner_rtol > 0) ? opts->inner_rtol : 1e-5;
+    int check_every = (opts && opts->check_every > 0) ? opts->check_every : 8;
+    nl_solve_info inf{0, 0, 0.0};
+    nl_status ret = NL_OK;
+    try {
+        cudaStream_t s = S->arena.stream();
+        Scratch sc(&S->arena);
+        Cg cg;
+        cg.nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nl_num_sms() * 4, nl_cdiv<int64_t>(n * 32, RB)));
+        cg.part = sc.get<double>(cg.nb);
+        cg.st = sc.get<CgState>(1);
+        double *x = sc.get<double>(n);
+        double *rres = sc.get<double>(n);
+        // |b| (residual of u = 0)
+        double bb = 0.0;
+        {
+            double *z = sc.get<double>(n);
+            NL_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
+            k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, z, S->b, rres, n, cg.part);
+            NL_CHECK_LAUNCH();
+            std::vector<double> hp(cg.nb);
+            NL_CUDA(cudaMemcpyAsync(hp.data(), cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
+            NL_CUDA(cudaStreamSynchronize(s));
+            for (double v : hp) bb += v;
+        }
+        const double nb_ = sqrt(bb);
+        bool converged = false;
+        if (!mixed) {
+            double *r = sc.get<double>(n), *p = sc.get<double>(n), *q = sc.get<double>(n);
+            bool conv = false;
+            inf.iterations = run_cg<double, double>(P->a_rowptr, P->a_col, S->A, S->b, 1.0, x, r, p, q, n, rtol,
+                                                    max_it, check_every, cg, s, &conv);
+            converged = conv;
+        } else {
+            float *xf = sc.get<float>(n), *rf = sc.get<float>(n), *pf = sc.get<float>(n), *qf = sc.get<float>(n);
+            NL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+            int total = 0;
+            for (int outer = 0; outer < 100 && total < max_it; ++outer) {
+                k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part);
+                NL_CHECK_LAUNCH();
+                std::vector<double> hp(cg.nb);
+                NL_CUDA(cudaMemcpyAsync(hp.data(), cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
+                NL_CUDA(cudaStreamSynchronize(s));
+                double rr = 0.0;
+                for (double v : hp) rr += v;
+                if (sqrt(rr) <= rtol * nb_ || rr == 0.0) { converged = true; break; }
+                double rn = sqrt(rr);
+                bool conv = false;
+                int it = run_cg<float, float>(P->a_rowptr, P->a_col, S->A32, rres, 1.0 / rn, xf, rf, pf, qf, n,
+                                              inner, max_it - total, check_every, cg, s, &conv);
+                total += it;
+                inf.refinements += 1;
+                k_add_scaled<<<cg.nb, RB, 0, s>>>(x, xf, rn, n);
+                NL_CHECK_LAUNCH();
+                if (it == 0) break;
+            }
+            inf.iterations = total;
+        }
+        // true residual
+        k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part);
+        NL_CHECK_LAUNCH();
+        std::vector<double> hp(cg.nb);
+        NL_CUDA(cudaMemcpyAsync(hp.data(), cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
+        NL_CUDA(cudaStreamSynchronize(s));
+        double rr = 0.0;
+        for (double v : hp) rr += v;
+        inf.rel_residual = (nb_ > 0) ? sqrt(rr) / nb_ : 0.0;
+        if (mixed) converged = inf.rel_residual <= rtol * 1.0000001;
+        if (u_out) {
+            double *u = (where == NL_DEVICE) ? u_out : sc.get<double>(m->nv);
+            k_scatter_u<<<(unsigned)nl_cdiv<int64_t>(std::max(m->nv, n), 256), 256, 0, s>>>(
+                x, m->free_nodes, S->g, m->node_free, u, m->nv, n);
+            NL_CHECK_LAUNCH();
+            if (where == NL_HOST)
+                NL_CUDA(cudaMemcpyAsync(u_out, u, sizeof(double) * m->nv, cudaMemcpyDeviceToHost, s));
+            NL_CUDA(cudaStreamSynchronize(s));
+        }
+        if (!converged) {
+            nl_set_error("CG stopped after %d iterations at relative residual %.3e", inf.iterations, inf.rel_residual);
+            ret = NL_ENOTCONV;
+        }
+    } catch (NlError &e) {
+        ret = e.st;
+    }
+    if (info) *info = inf;
+    return ret;
+}
+
+extern "C" nl_status nl_solve(nl_system *S, const nl_solve_opts *opts, double *u_out, int where, nl_solve_info *info)
+{
+    nl_clear_error();
+    if (!S) { nl_set_error("NULL system"); return NL_EINVAL; }
+    if (u_out && where != NL_HOST && where != NL_DEVICE) { nl_set_error("bad where"); return NL_EINVAL; }
+    return nl_solve_impl(S, opts, u_out, where, info);
+}

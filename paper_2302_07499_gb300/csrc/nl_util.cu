@@ -1,0 +1,200 @@
+// Error plumbing, device allocation through the caller's hooks, prefix sums
+// and a segmented sort used when building pair lists and the sparsity pattern.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "nl_internal.h"
+
+static thread_local char g_err[1024] = {0};
+
+void nl_set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void nl_clear_error() { g_err[0] = 0; }
+
+extern "C" const char *nl_last_error(void) { return g_err; }
+extern "C" const char *nl_version(void) { return "nlfem 0.1 (sm_103a)"; }
+
+void *DevArena::raw(size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (dev.alloc) {
+        p = dev.alloc(bytes, dev.ctx);
+        if (!p) {
+            nl_set_error("device allocation of %zu bytes failed", bytes);
+            throw NlError{NL_ENOMEM};
+        }
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            nl_set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+            throw NlError{e == cudaErrorMemoryAllocation ? NL_ENOMEM : NL_ECUDA};
+        }
+    }
+    ptrs.push_back(p);
+    return p;
+}
+
+void DevArena::release(void *p)
+{
+    if (!p) return;
+    auto it = std::find(ptrs.begin(), ptrs.end(), p);
+    if (it == ptrs.end()) return;
+    ptrs.erase(it);
+    if (dev.free) {
+        // stream-ordered callers (e.g. a caching allocator) may reuse the block
+        // for later work on the same stream; other streams are not involved.
+        dev.free(p, dev.ctx);
+    } else {
+        cudaStreamSynchronize(stream());
+        cudaFree(p);
+    }
+}
+
+void DevArena::release_all()
+{
+    if (!ptrs.empty() && !dev.free) cudaStreamSynchronize(stream());
+    for (size_t i = ptrs.size(); i-- > 0;) {
+        if (dev.free) dev.free(ptrs[i], dev.ctx);
+        else cudaFree(ptrs[i]);
+    }
+    ptrs.clear();
+}
+
+int nl_num_sms()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int64 (three phases, recursive on the block sums)
+static constexpr int SCAN_BLOCK = 1024;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v)
+{
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) >= o) v += t;
+    }
+    return v;
+}
+
+__global__ void k_scan_block(const int64_t *in, int64_t *out, int64_t *bsum, int64_t n)
+{
+    __shared__ int64_t ws[32];
+    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    int64_t v = (i < n) ? in[i] : 0;
+    int64_t inc = warp_incl_scan(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = ws[lane];
+        t = warp_incl_scan(t);
+        ws[lane] = t;
+    }
+    __syncthreads();
+    int64_t base = (w > 0) ? ws[w - 1] : 0;
+    if (i < n) out[i] = base + inc - v;
+    if (threadIdx.x == SCAN_BLOCK - 1) bsum[blockIdx.x] = base + inc;
+}
+
+__global__ void k_scan_add(int64_t *out, const int64_t *boff, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * SCAN_BLOCK + threadIdx.x;
+    if (i < n) out[i] += boff[blockIdx.x];
+}
+
+void nl_exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, DevArena *arena, cudaStream_t s)
+{
+    if (n <= 0) return;
+    int64_t nb = nl_cdiv<int64_t>(n, SCAN_BLOCK);
+    Scratch sc(arena);
+    int64_t *bsum = sc.get<int64_t>(nb);
+    k_scan_block<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, bsum, n);
+    NL_CHECK_LAUNCH();
+    if (nb > 1) {
+        int64_t *boff = sc.get<int64_t>(nb);
+        nl_exclusive_scan_i64(bsum, boff, nb, arena, s);
+        k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(out, boff, n);
+        NL_CHECK_LAUNCH();
+    }
+}
+
+__global__ void k_set_last(int64_t *out, const int64_t *counts, int64_t n)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[n] = (n > 0 ? out[n - 1] + counts[n - 1] : 0);
+}
+
+int64_t nl_scan_counts(const int64_t *counts, int64_t *out, int64_t n, DevArena *arena, cudaStream_t s)
+{
+    nl_exclusive_scan_i64(counts, out, n, arena, s);
+    k_set_last<<<1, 32, 0, s>>>(out, counts, n);
+    NL_CHECK_LAUNCH();
+    int64_t total = 0;
+    NL_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    NL_CUDA(cudaStreamSynchronize(s));
+    return total;
+}
+
+// ---------------------------------------------------------------------------
+// segmented sort: one block per segment, bitonic sort in shared memory
+__global__ void k_seg_bitonic(int32_t *keys, const int64_t *ptr, int pow2)
+{
+    extern __shared__ int32_t sk[];
+    int64_t b = ptr[blockIdx.x], e = ptr[blockIdx.x + 1];
+    int n = (int)(e - b);
+    if (n <= 1) return;
+    int p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    for (int i = threadIdx.x; i < p2; i += blockDim.x) sk[i] = (i < n) ? keys[b + i] : 0x7fffffff;
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    int32_t a = sk[i], c = sk[ixj];
+                    bool up = ((i & k) == 0);
+                    if ((a > c) == up) { sk[i] = c; sk[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) keys[b + i] = sk[i];
+    (void)pow2;
+}
+
+void nl_segmented_sort_i32(int32_t *keys, const int64_t *ptr, int64_t nseg, int64_t max_seg,
+                           DevArena *arena, cudaStream_t s)
+{
+    (void)arena;
+    if (nseg <= 0 || max_seg <= 1) return;
+    NL_REQUIRE(max_seg <= 32768, "a segment of %lld entries exceeds the 32768 supported by the sort",
+               (long long)max_seg);
+    int p2 = 1;
+    while (p2 < max_seg) p2 <<= 1;
+    int threads = std::min(1024, std::max(32, p2 / 2));
+    size_t smem = sizeof(int32_t) * (size_t)p2;
+    if (smem > 48 * 1024)
+        NL_CUDA(cudaFuncSetAttribute(k_seg_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int64_t s0 = 0; s0 < nseg; s0 += 2147483647LL) {
+        int64_t cnt = std::min<int64_t>(nseg - s0, 2147483647LL);
+        k_seg_bitonic<<<(unsigned)cnt, threads, smem, s>>>(keys, ptr + s0, p2);
+        NL_CHECK_LAUNCH();
+    }
+}

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Bars: pair lists bit-exact; Philox words bit-identical; FP64 matrix entries
+within 1e-12 relative (per-entry metric with a floor for near-zero entries);
+FP32-compensated entries within 1e-5; right-hand side and solution checked
+against the oracle's system and dense Cholesky.
+"""
+import numpy as np
+import pytest
+
+import nl_inputs as I
+import oracle as O
+
+from _helpers import entry_rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2302_07499_gb300 as nl
+    from paper_2302_07499_gb300 import build
+    build.build()
+    return nl
+
+
+@pytest.fixture(scope="module")
+def dev(nl):
+    return nl.Device()
+
+
+def _gpu_system(nl, dev, mesh, delta, strategy, precision, nmc=64, seed=1, f=-6.0, g=None):
+    m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+    p = nl.Pairs(m, delta)
+    s = nl.System(p, strategy=strategy, mc_points=nmc, seed=seed, precision=precision,
+                  gamma=I.gamma_const(delta), f_const=f, g=g)
+    return m, p, s
+
+
+def _meshes():
+    return [("cube6", *I.config_mesh("cube6_d025")),
+            ("jit6", I.kuhn_box(-0.25, 1.25, 6, jitter_frac=0.2, seed=3), 0.25),
+            ("cube4r2", *I.cube_problem(4, 2)),
+            ("jit5r3", *I.cube_problem(5, 3, jitter_frac=0.2, seed=9))]
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_bitwise(nl):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(2000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344], [1, 2, 3, 4]]
+    for key in (0, 0xFFFFFFFFFFFFFFFF, 0x299f31d0a4093822, 12345):
+        got = nl.probe_philox(ctr, key)
+        for i in range(0, 2000, 97):
+            assert list(got[i]) == list(O.philox(ctr[i], [key & 0xFFFFFFFF, key >> 32]))
+    got = nl.probe_philox(ctr[2:3], 0x299f31d0a4093822)
+    assert [int(x) for x in got[0]] == [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]
+
+
+# ------------------------------------------------------------------ single cases
+def _cases(n, seed):
+    rng = np.random.default_rng(seed)
+    tv, xs, ids = [], [], []
+    while len(tv) < n:
+        v = rng.normal(size=(4, 3))
+        if np.linalg.det(v[1:] - v[0]) < 0.05:
+            continue
+        x = v[rng.integers(4)] + rng.normal(size=3) * 0.5 if rng.random() < 0.8 else v.mean(0) + rng.normal(size=3)
+        tv.append(v); xs.append(x); ids.append(rng.integers(0, 2 ** 31, size=3))
+    return np.array(tv), np.array(xs), np.array(ids, dtype=np.uint32)
+
+
+@pytest.mark.parametrize("strategy", [0, 2])
+def test_probe_moments_fp64_match_oracle(nl, strategy):
+    tv, xs, ids = _cases(600, 1 + strategy)
+    delta = 0.9
+    got = nl.probe_moments(tv, xs, ids, delta, strategy, mc_points=64, seed=7, precision=nl.FP64)
+    for c in range(len(tv)):
+        ref, _, _ = O.region_moments(tv[c], xs[c], delta, strategy, nmc=64, seed=7, idT=ids[c, 0], idTp=ids[c, 1],
+                                     q=ids[c, 2])
+        scale = O.tet_volume(tv[c])
+        assert np.abs(got[c] - ref).max() <= 1e-12 * scale, (c, got[c], ref)
+
+
+@pytest.mark.parametrize("strategy", [0, 2])
+def test_probe_moments_fp32_match_oracle(nl, strategy):
+    tv, xs, ids = _cases(600, 11 + strategy)
+    delta = 0.9
+    got = nl.probe_moments(tv, xs, ids, delta, strategy, mc_points=64, seed=7, precision=nl.FP32_COMP)
+    bad = 0
+    for c in range(len(tv)):
+        ref, _, _ = O.region_moments(tv[c], xs[c], delta, strategy, nmc=64, seed=7, idT=ids[c, 0], idTp=ids[c, 1],
+                                     q=ids[c, 2])
+        scale = O.tet_volume(tv[c])
+        err = np.abs(got[c] - ref).max() / scale
+        if strategy == 0:
+            assert err <= 1e-5, (c, err)
+        elif err > 1e-5:
+            bad += 1     # an FP32 acceptance flip moves one sample of 64
+    assert bad <= 0.02 * len(tv)
+
+
+# ------------------------------------------------------------------ pairs
+@pytest.mark.parametrize("name,mesh,delta", _meshes())
+def test_pairs_bit_exact(nl, dev, name, mesh, delta):
+    m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+    p = nl.Pairs(m, delta)
+    outer, ptr, tp = p.export()
+    o_outer, o_ptr, o_tp = O.pairs(mesh, delta)
+    assert np.array_equal(outer, o_outer)
+    assert np.array_equal(ptr, o_ptr)
+    assert np.array_equal(tp, o_tp)
+
+
+# ------------------------------------------------------------------ matrices
+@pytest.mark.parametrize("strategy", [0, 2])
+@pytest.mark.parametrize("name,mesh,delta", _meshes())
+def test_K_fp64_matches_oracle(nl, dev, name, mesh, delta, strategy):
+    g = I.quadratic_g(mesh.verts)
+    m, p, s = _gpu_system(nl, dev, mesh, delta, strategy, nl.FP64, g=g)
+    K = s.scipy(nl.MAT_K)
+    Kref = O.assemble_K(mesh, delta, I.gamma_const(delta), strategy, nmc=64, seed=1)
+    assert entry_rel_err(K, Kref) <= 1e-12
+    # symmetric, zero row sums
+    Kd = K.toarray()
+    assert np.abs(Kd - Kd.T).max() <= 1e-14 * np.abs(Kd).max()
+    assert np.abs(Kd.sum(1)).max() <= 1e-13 * np.abs(Kd).sum(1).max()
+    # right-hand side and A
+    A, b, free = O.system(mesh, Kref, O.load_vector(mesh, -6.0), g)
+    bg, fn = s.rhs()
+    assert np.array_equal(fn.cpu().numpy(), free)
+    assert np.abs(bg.cpu().numpy() - b).max() <= 1e-12 * np.abs(b).max()
+    assert entry_rel_err(s.scipy(nl.MAT_A), A) <= 1e-12
+
+
+@pytest.mark.parametrize("strategy", [0, 2])
+@pytest.mark.parametrize("name,mesh,delta", _meshes()[:3])
+def test_K_fp32_comp_matches_oracle(nl, dev, name, mesh, delta, strategy):
+    m, p, s = _gpu_system(nl, dev, mesh, delta, strategy, nl.FP32_COMP)
+    K = s.scipy(nl.MAT_K)
+    Kref = O.assemble_K(mesh, delta, I.gamma_const(delta), strategy, nmc=64, seed=1)
+    assert entry_rel_err(K, Kref) <= 1e-5
+
+
+def test_determinism_bitwise(nl, dev):
+    mesh, delta = I.cube_problem(4, 2, jitter_frac=0.2, seed=2)
+    for prec in (nl.FP64, nl.FP32_COMP):
+        vals = []
+        for _ in range(2):
+            _, _, s = _gpu_system(nl, dev, mesh, delta, nl.FULLCAPS, prec)
+            vals.append(s.csr_numpy()[2].copy())
+        assert np.array_equal(vals[0], vals[1])
+
+
+# ------------------------------------------------------------------ solve
+@pytest.mark.parametrize("mixed", [False, True])
+def test_solve_matches_cholesky(nl, dev, mixed):
+    mesh, delta = I.config_mesh("cube6_d025")
+    g = I.quadratic_g(mesh.verts)
+    m, p, s = _gpu_system(nl, dev, mesh, delta, nl.NOCAPS, nl.FP64, g=g)
+    u, info = s.solve(rtol=1e-12, mixed=mixed)
+    Kref = O.assemble_K(mesh, delta, I.gamma_const(delta), O.NOCAPS)
+    A, b, free = O.system(mesh, Kref, O.load_vector(mesh, -6.0), g)
+    x = O.cholesky_solve(A, b)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-12 * 1.01
+    assert np.abs(u[free] - x).max() <= 1e-10 * np.abs(x).max()
+    con = mesh.node_free == 0
+    assert np.array_equal(u[con], g[con])
+
+
+def test_manufactured_solution_converges(nl, dev):
+    """u = |x|^2, f = -6: fullcaps FP32-comp + mixed CG; the L2 error decreases ~h^2
+    and the mixed solution is as accurate as the FP64 one."""
+    errs = []
+    for inv_h in (4, 8):
+        mesh, delta = I.cube_problem(inv_h, 2)
+        g = I.quadratic_g(mesh.verts)
+        _, _, s64 = _gpu_system(nl, dev, mesh, delta, nl.FULLCAPS, nl.FP64, g=g)
+        u64, _ = s64.solve(rtol=1e-10)
+        _, _, s32 = _gpu_system(nl, dev, mesh, delta, nl.FULLCAPS, nl.FP32_COMP, g=g)
+        u32, inf = s32.solve(rtol=1e-10, mixed=True)
+        exact = lambda X: (X * X).sum(axis=1)
+        e64 = O.l2_error(mesh, u64, exact)
+        e32 = O.l2_error(mesh, u32, exact)
+        assert e32 <= 1.01 * e64 + 1e-12
+        errs.append(e64)
+    assert errs[1] < errs[0] / 3.0
+
+
+# ------------------------------------------------------------------ errors
+def test_errors_are_reported(nl, dev):
+    mesh, delta = I.config_mesh("cube6_d025")
+    bad = mesh.tets.copy()
+    bad[0, [2, 3]] = bad[0, [3, 2]]          # inverted element
+    with pytest.raises(nl.NlError, match="NL_EINVAL"):
+        nl.Mesh(mesh.verts, bad, mesh.tet_in_omega, mesh.node_free, dev)
+    bad = mesh.tets.copy()
+    bad[5, 0] = mesh.nv + 10
+    with pytest.raises(nl.NlError, match="NL_EINVAL"):
+        nl.Mesh(mesh.verts, bad, mesh.tet_in_omega, mesh.node_free, dev)
+    m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+    with pytest.raises(nl.NlError, match="NL_EINVAL"):
+        nl.Pairs(m, -1.0)
+    p = nl.Pairs(m, delta)
+    with pytest.raises(nl.NlError, match="NL_EINVAL"):
+        nl.System(p, strategy=nl.FULLCAPS, mc_points=0, gamma=1.0)
+    s = nl.System(p, strategy=nl.NOCAPS, gamma=I.gamma_const(delta), f_const=-6.0)
+    u, info = s.solve(rtol=1e-14, max_iter=2)
+    assert info["status"] == 4               # NL_ENOTCONV, last iterate returned
