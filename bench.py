@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the nonlocal P1 assembly + solve path on GB300.
+
+One step = the whole hot path on one synthetic problem: mesh upload and
+precompute, element-pair search and sparsity pattern, quadrature +
+deterministic reduction into K, A and b, and the CG solve.  The metric is
+element pairs per second of that step (plus p50/p99 step latency), for the
+FP32-compensated form, with the plain FP64 form of the same step reported
+beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun) runs independent replicas, one per GPU (weak scaling;
+the path has no exchange step on one box).  --impl reference times the CPU
+oracle (test infrastructure) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import nl_inputs as I  # noqa: E402
+
+METRIC = "assembly element-pairs/s; p50/p99 assemble+solve latency, FP32-comp vs FP64"
+UNIT = "element-pairs/s"
+
+WORKLOADS = {
+    # name: (mesh config, strategy, mc points, seed, CG rtol)
+    "cube24_d0125_fullcaps64": ("cube24_d0125", 2, 64, 1, 1e-10),
+    "cube6_d025_nocaps": ("cube6_d025", 0, 0, 1, 1e-12),
+    "jitter38_d3h_fullcaps128": ("jitter38_d3h", 2, 128, 1, 1e-10),
+}
+STRAT_NAME = {0: "nocaps", 1: "approxcaps", 2: "fullcaps"}
+
+# Algorithmic FP32 operations of the quadrature kernel (per unit, counted from
+# the arithmetic the method needs; see the design notes): classification per
+# (pair, point); closed-form moments per inside point; edge/sphere points,
+# cells and cap volumes per cut point; per Monte Carlo sample the point,
+# ball test and barycentrics, plus the moment update per accepted sample.
+FLOPS_PER_PAIR_POINT = 36
+FLOPS_PER_INSIDE = 16
+FLOPS_PER_CUT = 400
+FLOPS_PER_SAMPLE = 44
+FLOPS_PER_ACCEPTED = 53
+FP32_LANES_PER_SM = 128
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("nl_quad.cuh", "nl_assemble.cuh", "nl_assemble32.cu"):
+        with open(os.path.join(ROOT, "paper_2302_07499_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the quadrature kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha") != _kernel_source_sha():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def _algorithmic_flops(st):
+    pp = 4 * st["pairs"]
+    return (FLOPS_PER_PAIR_POINT * pp + FLOPS_PER_INSIDE * st["inside_points"] + FLOPS_PER_CUT * st["cut_points"]
+            + FLOPS_PER_SAMPLE * st["mc_samples"] + FLOPS_PER_ACCEPTED * st["mc_accepted"])
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2302_07499_gb300 as nl
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg, strategy, nmc, seed, rtol = WORKLOADS[args.workload]
+    mesh, delta = I.config_mesh(cfg)
+    gamma = I.gamma_const(delta)
+    g_host = I.quadratic_g(mesh.verts)
+    dev = nl.Device()
+    d_verts = torch.from_numpy(mesh.verts).cuda()
+    d_tets = torch.from_numpy(mesh.tets).cuda()
+    d_om = torch.from_numpy(mesh.tet_in_omega).cuda()
+    d_free = torch.from_numpy(mesh.node_free).cuda()
+    d_g = torch.from_numpy(g_host).cuda()
+    d_u = torch.empty(mesh.nv, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(precision, mixed, record=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        m = nl.Mesh(d_verts, d_tets, d_om, d_free, dev)
+        ev[1].record(stream)
+        p = nl.Pairs(m, delta)
+        ev[2].record(stream)
+        s = nl.System(p, strategy=strategy, mc_points=nmc, seed=seed, precision=precision, gamma=gamma,
+                      f_const=-6.0, g=d_g)
+        ev[3].record(stream)
+        _, info = s.solve(rtol=rtol, mixed=mixed, out=d_u)
+        ev[4].record(stream)
+        ev[4].synchronize()
+        t = [ev[0].elapsed_time(ev[i]) for i in range(1, 5)]
+        out = {"total_ms": t[3], "mesh_ms": t[0], "pairs_ms": t[1] - t[0], "assemble_ms": t[2] - t[1],
+               "solve_ms": t[3] - t[2], "npairs": p.info["n_pairs"], "stats": s.stats(), "cg": info,
+               "nnz_a": p.info["nnz_a"], "n_free": p.info["n_free"], "nnz": p.info["nnz"]}
+        s.close(); p.close(); m.close()
+        return out
+
+    def flush_l2():
+        flush.zero_()
+
+    # warm-up
+    for _ in range(args.warmup):
+        flush_l2()
+        step(nl.FP32_COMP, True)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = nl.kernel_launches()
+    barrier()
+    t_wall0 = time.perf_counter()
+    steps = []
+    for _ in range(args.steps):
+        flush_l2()
+        steps.append(step(nl.FP32_COMP, True))
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    launches = nl.kernel_launches() - launches0
+    clocks = sampler.stop()
+
+    ms = [s_["total_ms"] for s_ in steps]
+    ms_mean = float(np.mean(ms))
+    t_max = ms_mean
+    if dist is not None:
+        tt = torch.tensor([ms_mean], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    npairs = steps[0]["npairs"]
+    value = ws * npairs / (t_max / 1e3)
+
+    # FP64 form of the same step (fewer steps: the FP64 pipe is narrow on this part)
+    fp64 = None
+    if args.fp64_steps > 0:
+        for _ in range(1):
+            flush_l2()
+            step(nl.FP64, False)
+        r64 = []
+        for _ in range(args.fp64_steps):
+            flush_l2()
+            r64.append(step(nl.FP64, False))
+        m64 = float(np.mean([r["total_ms"] for r in r64]))
+        fp64 = {"value": npairs / (m64 / 1e3), "unit": UNIT, "ms_per_step": m64,
+                "assemble_ms": float(np.mean([r["assemble_ms"] for r in r64])),
+                "solve_ms": float(np.mean([r["solve_ms"] for r in r64])),
+                "cg_iterations": r64[0]["cg"]["iterations"], "steps": args.fp64_steps,
+                "p50_ms": float(np.percentile([r["total_ms"] for r in r64], 50)),
+                "p99_ms": float(np.percentile([r["total_ms"] for r in r64], 99))}
+
+    # end to end through the C-ABI with host buffers (H2D of the inputs and D2H
+    # of the solution inside the timed region)
+    e2e_ms = []
+    for k in range(max(2, min(args.steps, 5)) + 1):
+        flush_l2()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+        p = nl.Pairs(m, delta)
+        s = nl.System(p, strategy=strategy, mc_points=nmc, seed=seed, precision=nl.FP32_COMP, gamma=gamma,
+                      f_const=-6.0, g=g_host)
+        u, _ = s.solve(rtol=rtol, mixed=True)
+        t1 = time.perf_counter()
+        s.close(); p.close(); m.close()
+        if k > 0:
+            e2e_ms.append((t1 - t0) * 1e3)
+    h2d = mesh.verts.nbytes + mesh.tets.nbytes + mesh.tet_in_omega.nbytes + mesh.node_free.nbytes + g_host.nbytes
+    d2h = 8 * mesh.nv
+    e2e = {"value": npairs / (float(np.mean(e2e_ms)) / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.mean(e2e_ms))}
+
+    # roofline of the dominant kernel (quadrature): ALU-bound, FP32
+    st = steps[-1]["stats"]
+    qms = float(np.mean([s_["stats"]["quadrature_ms"] for s_ in steps]))
+    flops = _algorithmic_flops(st)
+    props = torch.cuda.get_device_properties(local)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (qms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_assemble<float,%s>" % STRAT_NAME[strategy],
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": _traffic_record(), "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz"
+                % (props.multi_processor_count, sm_max), "algorithmic_flops_per_launch": flops,
+                "kernel_ms": qms, "share_of_step": qms / ms_mean}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds)
+
+    phases = {k: float(np.mean([s_[k] for s_ in steps])) for k in ("mesh_ms", "pairs_ms", "assemble_ms", "solve_ms")}
+    phases["quadrature_kernel_ms"] = qms
+    phases["reduce_ms"] = float(np.mean([s_["stats"]["reduce_ms"] for s_ in steps]))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload,
+                   "mesh": "%s: Kuhn grid, %d tets, %d vertices, delta=%g, gamma=15/(2 pi delta^5)"
+                   % (cfg, mesh.nt, mesh.nv, delta),
+                   "strategy": STRAT_NAME[strategy], "mc_points": nmc, "seed": seed,
+                   "precision": "FP32 per-(pair,point) arithmetic, FP64 accumulation and entries",
+                   "solve": "mixed CG (FP32 inner, FP64 residual/updates) to rel. residual %g" % rtol,
+                   "element_pairs": npairs, "nnz_K": steps[0]["nnz"], "n_free": steps[0]["n_free"],
+                   "nnz_A": steps[0]["nnz_a"], "l2": "flushed before every step (256 MiB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "phases_ms": phases,
+        "cg": {"iterations": steps[-1]["cg"]["iterations"], "refinements": steps[-1]["cg"]["refinements"],
+               "rel_residual": steps[-1]["cg"]["rel_residual"]},
+        "fp64": fp64,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "wall_s": t_wall,
+        "stats": {k: (int(v) if isinstance(v, int) else v) for k, v in st.items()},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=15.0):
+    """The oracle as it stands, on the host cores, over a bounded contiguous
+    sample of outer elements of the same workload (pair search + per-pair
+    blocks + accumulation into K)."""
+    import oracle as O
+    outer_all = np.nonzero(mesh.tet_in_omega)[0].astype(np.int32)
+    cores = O.num_threads()
+
+    def run(outer):
+        t0 = time.perf_counter()
+        prs = O.pairs(mesh, delta, outer=outer)
+        pT, pTp = O.pair_arrays(*prs)
+        blocks, _ = O.assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads=cores)
+        O.blocks_to_matrix(mesh, pT, pTp, blocks)
+        return len(pT), time.perf_counter() - t0
+
+    n0 = min(len(outer_all), 64)
+    np0, t0 = run(outer_all[:n0])
+    n1 = int(min(len(outer_all), max(n0, n0 * budget_s / max(t0, 1e-3))))
+    npairs, t = run(outer_all[:n1])
+    return {"value": npairs / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of %d outer elements (%d element pairs), %.1f s" % (n1, len(outer_all), npairs, t)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    cfg, strategy, nmc, seed, rtol = WORKLOADS[args.workload]
+    mesh, delta = I.config_mesh(cfg)
+    gamma = I.gamma_const(delta)
+    outer_all = np.nonzero(mesh.tet_in_omega)[0].astype(np.int32)
+    cores = O.num_threads()
+    # size one step so that warm-up + steps stay within a few minutes
+    n_sample = int(os.environ.get("NL_REF_OUTER", "0")) or max(8, min(len(outer_all), 160))
+
+    def one(k):
+        sel = outer_all[(k * n_sample) % len(outer_all):][:n_sample]
+        t0 = time.perf_counter()
+        prs = O.pairs(mesh, delta, outer=sel)
+        pT, pTp = O.pair_arrays(*prs)
+        blocks, _ = O.assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads=cores)
+        O.blocks_to_matrix(mesh, pT, pTp, blocks)
+        return len(pT), time.perf_counter() - t0
+
+    for k in range(args.warmup):
+        one(k)
+    res = [one(args.warmup + k) for k in range(args.steps)]
+    npairs = sum(r[0] for r in res)
+    t = sum(r[1] for r in res)
+    value = npairs / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "mesh": cfg, "strategy": STRAT_NAME[strategy], "mc_points": nmc,
+                       "seed": seed},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d outer elements per step (%d element pairs over %d steps): pair search, "
+                                       "per-pair blocks, accumulation into K" % (n_sample, npairs, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube24_d0125_fullcaps64", choices=sorted(WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

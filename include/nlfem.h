@@ -184,6 +184,9 @@ typedef struct {
     uint64_t mc_samples;       /* Monte Carlo samples drawn */
     uint64_t mc_accepted;
     uint64_t hull_fallbacks;   /* approxcaps hulls that fell back to nocaps */
+    double quadrature_ms;      /* duration of the quadrature kernel (CUDA events
+                                  recorded on the assembly stream around its launch) */
+    double reduce_ms;          /* duration of the reduction into K, A and b */
 } nl_assemble_stats;
 nl_status nl_system_stats(const nl_system *sys, nl_assemble_stats *out);
 
@@ -240,6 +243,10 @@ nl_status nl_probe_philox(const uint32_t *ctr, uint64_t key, int64_t n, uint32_t
 
 /* Thread-local message of the last failing call (empty string if none). */
 const char *nl_last_error(void);
+
+/* Number of kernels this library has launched in this process (all entry
+ * points, all threads); for launch accounting around a timed region. */
+uint64_t nl_kernel_launches(void);
 
 /* Library version string. */
 const char *nl_version(void);

@@ -57,7 +57,8 @@ class nl_csr_view(C.Structure):
 
 class nl_assemble_stats(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("cut_points", C.c_uint64), ("inside_points", C.c_uint64),
-                ("mc_samples", C.c_uint64), ("mc_accepted", C.c_uint64), ("hull_fallbacks", C.c_uint64)]
+                ("mc_samples", C.c_uint64), ("mc_accepted", C.c_uint64), ("hull_fallbacks", C.c_uint64),
+                ("quadrature_ms", C.c_double), ("reduce_ms", C.c_double)]
 
 
 class nl_solve_opts(C.Structure):
@@ -72,7 +73,7 @@ class nl_solve_info(C.Structure):
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = ["nl_mesh_create", "nl_mesh_destroy", "nl_pairs_build", "nl_pairs_destroy", "nl_pairs_get_info",
             "nl_pairs_export", "nl_assemble", "nl_system_destroy", "nl_system_csr", "nl_system_rhs",
-            "nl_system_stats", "nl_solve", "nl_probe_moments", "nl_probe_philox", "nl_last_error", "nl_version"]
+            "nl_system_stats", "nl_solve", "nl_probe_moments", "nl_probe_philox", "nl_last_error", "nl_version", "nl_kernel_launches"]
 
 _lib = None
 
@@ -105,6 +106,7 @@ def lib():
     L.nl_probe_philox.argtypes = [vp, C.c_uint64, i64, vp]
     L.nl_last_error.restype = C.c_char_p
     L.nl_version.restype = C.c_char_p
+    L.nl_kernel_launches.restype = C.c_uint64
     _lib = L
     return L
 
@@ -283,7 +285,7 @@ class System:
     def stats(self):
         s = nl_assemble_stats()
         _check(lib().nl_system_stats(self.h, C.byref(s)))
-        return {k: int(getattr(s, k)) for k, _ in nl_assemble_stats._fields_}
+        return {k: getattr(s, k) for k, _ in nl_assemble_stats._fields_}
 
     def solve(self, rtol=1e-12, max_iter=0, mixed=False, inner_rtol=0.0, check_every=0, out=None):
         """Returns (u, info).  u: full nodal vector; numpy unless `out` is a CUDA tensor."""
@@ -312,6 +314,10 @@ class System:
             self.close()
         except Exception:
             pass
+
+
+def kernel_launches():
+    return int(lib().nl_kernel_launches())
 
 
 def probe_moments(tets_xyz, x, ids, delta, strategy, mc_points=0, seed=1, precision=FP64):

@@ -45,7 +45,7 @@ extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_s
         if (opts->g_nodal) {
             NL_CUDA(cudaMemcpyAsync(S->g, opts->g_nodal, sizeof(double) * m->nv,
                                     opts->g_where == NL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
-            k_zero_collar_g<<<(unsigned)nl_cdiv<int64_t>(m->nv, 256), 256, 0, s>>>(m->node_free, S->g, m->nv);
+            { k_zero_collar_g<<<(unsigned)nl_cdiv<int64_t>(m->nv, 256), 256, 0, s>>>(m->node_free, S->g, m->nv); nl_count_launch(); }
             NL_CHECK_LAUNCH();
         } else {
             NL_CUDA(cudaMemsetAsync(S->g, 0, sizeof(double) * m->nv, s));
@@ -57,9 +57,21 @@ extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_s
         double *TT = sc.get<double>(10 * m->n_outer);
         uint64_t *st = sc.get<uint64_t>(8);
         NL_CUDA(cudaMemsetAsync(st, 0, sizeof(uint64_t) * 8, s));
+        cudaEvent_t ev[3];
+        for (int i = 0; i < 3; ++i) NL_CUDA(cudaEventCreate(&ev[i]));
+        NL_CUDA(cudaEventRecord(ev[0], s));
         if (f32) nl_assemble_fp32(S, (float *)D, strips, TT, st);
         else nl_assemble_fp64(S, (double *)D, strips, TT, st);
+        NL_CUDA(cudaEventRecord(ev[1], s));
         nl_reduce_system(S, D, f32 ? 1 : 0, strips, TT);
+        NL_CUDA(cudaEventRecord(ev[2], s));
+        NL_CUDA(cudaEventSynchronize(ev[2]));
+        float ms0 = 0.f, ms1 = 0.f;
+        NL_CUDA(cudaEventElapsedTime(&ms0, ev[0], ev[1]));
+        NL_CUDA(cudaEventElapsedTime(&ms1, ev[1], ev[2]));
+        for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+        S->stats.quadrature_ms = ms0;
+        S->stats.reduce_ms = ms1;
         uint64_t hs[8];
         NL_CUDA(cudaMemcpyAsync(hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
         NL_CUDA(cudaStreamSynchronize(s));

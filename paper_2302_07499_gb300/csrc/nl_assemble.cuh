@@ -152,8 +152,18 @@ __global__ void __launch_bounds__(NT) k_assemble(AsmArgs A)
                                                 (R)((vh[k].z - xh[2]) + (vl[k].z - xl[2])));
                     }
                     Mom<R> M;
+                    nlq::Strict sx;
+                    if (sizeof(R) == 4) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            double4 g = A.verts[nodeP[k]];
+                            sx.v[k][0] = g.x; sx.v[k][1] = g.y; sx.v[k][2] = g.z;
+                        }
+                        sx.x[0] = xqd[q][0]; sx.x[1] = xqd[q][1]; sx.x[2] = xqd[q][2];
+                        sx.d2 = A.delta2;
+                    }
                     nlq::point_moments<R, STRAT>(vv, x, (R)A.delta2, volTp, A.nmc, A.key, (uint32_t)T, (uint32_t)Tp,
-                                                 (uint32_t)q, M, st);
+                                                 (uint32_t)q, M, st, sizeof(R) == 4 ? &sx : nullptr);
                     V[q] = M.m0;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) Y[q][k] = M.m1[k];
@@ -274,7 +284,7 @@ void launch_assemble(nl_system *sys, void *D, double *strips, double *TT, unsign
     per_sm = per_sm < 1 ? 1 : per_sm;
     int64_t grid = (int64_t)nl_num_sms() * per_sm;
     if (grid > m->n_outer) grid = m->n_outer;
-    kern<<<(unsigned)grid, NT, smem, sys->arena.stream()>>>(A);
+    { kern<<<(unsigned)grid, NT, smem, sys->arena.stream()>>>(A); nl_count_launch(); }
     NL_CHECK_LAUNCH();
 }
 
@@ -316,7 +326,12 @@ __global__ void k_probe(const double *__restrict__ tv, const double *__restrict_
     }
     Mom<R> M;
     nlq::Stats st{0, 0, 0, 0, 0};
-    nlq::point_moments<R, STRAT>(v, xx, (R)delta2, (R)vol, nmc, key, ids[3 * c], ids[3 * c + 1], ids[3 * c + 2], M, st);
+    nlq::Strict sx;
+    for (int k = 0; k < 4; ++k) { sx.v[k][0] = vd[k].x; sx.v[k][1] = vd[k].y; sx.v[k][2] = vd[k].z; }
+    for (int d = 0; d < 3; ++d) sx.x[d] = x[d];
+    sx.d2 = delta2;
+    nlq::point_moments<R, STRAT>(v, xx, (R)delta2, (R)vol, nmc, key, ids[3 * c], ids[3 * c + 1], ids[3 * c + 2], M, st,
+                                 sizeof(R) == 4 ? &sx : nullptr);
     out[15 * c] = (double)M.m0;
     for (int k = 0; k < 4; ++k) out[15 * c + 1 + k] = (double)M.m1[k];
     for (int k = 0; k < 10; ++k) out[15 * c + 5 + k] = (double)M.m2[k];
@@ -328,9 +343,9 @@ void launch_probe(const double *tv, const double *xs, const uint32_t *ids, int64
 {
     uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     unsigned blocks = (unsigned)((n + 127) / 128);
-    if (strategy == NL_NOCAPS) k_probe<R, 0><<<blocks, 128>>>(tv, xs, ids, n, delta2, 0, key, out);
-    else if (strategy == NL_APPROXCAPS) k_probe<R, 1><<<blocks, 128>>>(tv, xs, ids, n, delta2, 0, key, out);
-    else k_probe<R, 2><<<blocks, 128>>>(tv, xs, ids, n, delta2, nmc, key, out);
+    if (strategy == NL_NOCAPS) { k_probe<R, 0><<<blocks, 128>>>(tv, xs, ids, n, delta2, 0, key, out); nl_count_launch(); }
+    else if (strategy == NL_APPROXCAPS) { k_probe<R, 1><<<blocks, 128>>>(tv, xs, ids, n, delta2, 0, key, out); nl_count_launch(); }
+    else { k_probe<R, 2><<<blocks, 128>>>(tv, xs, ids, n, delta2, nmc, key, out); nl_count_launch(); }
     NL_CHECK_LAUNCH();
 }
 

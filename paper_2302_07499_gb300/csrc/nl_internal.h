@@ -14,6 +14,8 @@
 // per thread.
 void nl_set_error(const char *fmt, ...);
 void nl_clear_error();
+// process-wide count of kernels this library launched (nl_kernel_launches)
+void nl_count_launch();
 
 struct NlError {
     nl_status st;

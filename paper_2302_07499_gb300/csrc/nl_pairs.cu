@@ -708,7 +708,7 @@ extern "C" nl_status nl_mesh_create(const nl_device *dev, const double *verts, i
         NL_CUDA(cudaMemcpyAsync(m->tets, tets, sizeof(int4) * nt, kind, s));
         NL_CUDA(cudaMemcpyAsync(m->in_omega, tet_in_omega, nt, kind, s));
         NL_CUDA(cudaMemcpyAsync(m->node_free, node_free, nv, kind, s));
-        k_widen<<<blocks_for(nv, 256), 256, 0, s>>>(v3, m->verts, nv);
+        { k_widen<<<blocks_for(nv, 256), 256, 0, s>>>(v3, m->verts, nv); nl_count_launch(); }
         NL_CHECK_LAUNCH();
 
         m->tet_cr = m->arena.get<double4>(nt);
@@ -722,11 +722,11 @@ extern "C" nl_status nl_mesh_create(const nl_device *dev, const double *verts, i
         for (int i = 4; i <= 6; ++i) init[i] = 0ULL;
         init[7] = 0ULL;
         NL_CUDA(cudaMemcpyAsync(bb, init, sizeof(init), cudaMemcpyHostToDevice, s));
-        k_mesh_prep<<<blocks_for(nt, 256), 256, 0, s>>>(m->verts, m->tets, nv, nt, m->tet_cr, m->tet_vol, err, bb);
+        { k_mesh_prep<<<blocks_for(nt, 256), 256, 0, s>>>(m->verts, m->tets, nv, nt, m->tet_cr, m->tet_vol, err, bb); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         m->vhi = m->arena.get<float4>(nv);
         m->vlo = m->arena.get<float4>(nv);
-        k_split_coords<<<blocks_for(nv, 256), 256, 0, s>>>(m->verts, m->vhi, m->vlo, nv);
+        { k_split_coords<<<blocks_for(nv, 256), 256, 0, s>>>(m->verts, m->vhi, m->vlo, nv); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         int herr = 0;
         unsigned long long hbb[8];
@@ -741,40 +741,40 @@ extern "C" nl_status nl_mesh_create(const nl_device *dev, const double *verts, i
         // outer elements and free nodes
         int64_t *cnt = sc.get<int64_t>(std::max(nt, nv) + 1);
         int64_t *off = sc.get<int64_t>(std::max(nt, nv) + 1);
-        k_flag_counts<<<blocks_for(nt, 256), 256, 0, s>>>(m->in_omega, cnt, nt);
+        { k_flag_counts<<<blocks_for(nt, 256), 256, 0, s>>>(m->in_omega, cnt, nt); nl_count_launch(); }
         m->n_outer = nl_scan_counts(cnt, off, nt, &m->arena, s);
         NL_REQUIRE(m->n_outer > 0, "no element of Omega");
         m->outer_ids = m->arena.get<int32_t>(m->n_outer);
         m->outer_of = m->arena.get<int32_t>(nt);
-        k_compact_flags<<<blocks_for(nt, 256), 256, 0, s>>>(m->in_omega, off, m->outer_ids, m->outer_of, nt);
+        { k_compact_flags<<<blocks_for(nt, 256), 256, 0, s>>>(m->in_omega, off, m->outer_ids, m->outer_of, nt); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        k_flag_counts<<<blocks_for(nv, 256), 256, 0, s>>>(m->node_free, cnt, nv);
+        { k_flag_counts<<<blocks_for(nv, 256), 256, 0, s>>>(m->node_free, cnt, nv); nl_count_launch(); }
         m->n_free = nl_scan_counts(cnt, off, nv, &m->arena, s);
         NL_REQUIRE(m->n_free > 0, "no free node");
         m->free_nodes = m->arena.get<int32_t>(m->n_free);
         m->free_idx = m->arena.get<int32_t>(nv);
-        k_compact_flags<<<blocks_for(nv, 256), 256, 0, s>>>(m->node_free, off, m->free_nodes, m->free_idx, nv);
+        { k_compact_flags<<<blocks_for(nv, 256), 256, 0, s>>>(m->node_free, off, m->free_nodes, m->free_idx, nv); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         m->xq = m->arena.get<double>(12 * m->n_outer);
-        k_quad_points<<<blocks_for(m->n_outer, 128), 128, 0, s>>>(m->verts, m->tets, m->outer_ids, m->n_outer, m->xq);
+        { k_quad_points<<<blocks_for(m->n_outer, 128), 128, 0, s>>>(m->verts, m->tets, m->outer_ids, m->n_outer, m->xq); nl_count_launch(); }
         NL_CHECK_LAUNCH();
 
         // node -> incident elements, sorted by element id
         unsigned long long *ucnt = sc.get<unsigned long long>(nv);
         NL_CUDA(cudaMemsetAsync(ucnt, 0, sizeof(unsigned long long) * nv, s));
-        k_node_elem_count<<<blocks_for(nt, 256), 256, 0, s>>>(m->tets, nt, ucnt);
+        { k_node_elem_count<<<blocks_for(nt, 256), 256, 0, s>>>(m->tets, nt, ucnt); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        k_u64_to_i64<<<blocks_for(nv, 256), 256, 0, s>>>(ucnt, cnt, nv);
+        { k_u64_to_i64<<<blocks_for(nv, 256), 256, 0, s>>>(ucnt, cnt, nv); nl_count_launch(); }
         m->ne_ptr = m->arena.get<int64_t>(nv + 1);
         int64_t ninc = nl_scan_counts(cnt, m->ne_ptr, nv, &m->arena, s);
         m->ne_ent = m->arena.get<int32_t>(ninc);
-        k_u64_to_i64<<<blocks_for(nv, 256), 256, 0, s>>>(ucnt, cnt, nv);
+        { k_u64_to_i64<<<blocks_for(nv, 256), 256, 0, s>>>(ucnt, cnt, nv); nl_count_launch(); }
         NL_CUDA(cudaMemcpyAsync(ucnt, m->ne_ptr, sizeof(int64_t) * nv, cudaMemcpyDeviceToDevice, s));
-        k_node_elem_fill<<<blocks_for(nt, 256), 256, 0, s>>>(m->tets, nt, ucnt, m->ne_ent);
+        { k_node_elem_fill<<<blocks_for(nt, 256), 256, 0, s>>>(m->tets, nt, ucnt, m->ne_ent); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         unsigned long long *mx = sc.get<unsigned long long>(1);
         NL_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
-        k_max_seg<<<blocks_for(nv, 256), 256, 0, s>>>(m->ne_ptr, nv, mx);
+        { k_max_seg<<<blocks_for(nv, 256), 256, 0, s>>>(m->ne_ptr, nv, mx); nl_count_launch(); }
         unsigned long long hmx = 0;
         NL_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s));
         NL_CUDA(cudaStreamSynchronize(s));
@@ -830,19 +830,19 @@ nl_status nl_pairs_build_impl(nl_mesh *m, double delta, nl_pairs **out)
         unsigned long long *ucnt = sc.get<unsigned long long>(std::max(ncell, nt) + 1);
         int64_t *cnt = sc.get<int64_t>(std::max(std::max(ncell, nt), std::max(no, nv)) + 1);
         NL_CUDA(cudaMemsetAsync(ucnt, 0, sizeof(unsigned long long) * ncell, s));
-        k_cell_count<<<blocks_for(nt, 256), 256, 0, s>>>(m->tet_cr, nt, g, cell_of, ucnt);
+        { k_cell_count<<<blocks_for(nt, 256), 256, 0, s>>>(m->tet_cr, nt, g, cell_of, ucnt); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        k_u64_to_i64<<<blocks_for(ncell, 256), 256, 0, s>>>(ucnt, cnt, ncell);
+        { k_u64_to_i64<<<blocks_for(ncell, 256), 256, 0, s>>>(ucnt, cnt, ncell); nl_count_launch(); }
         int64_t *cell_ptr = sc.get<int64_t>(ncell + 1);
         nl_scan_counts(cnt, cell_ptr, ncell, &P->arena, s);
         int32_t *cell_ent = sc.get<int32_t>(nt);
         NL_CUDA(cudaMemcpyAsync(ucnt, cell_ptr, sizeof(int64_t) * ncell, cudaMemcpyDeviceToDevice, s));
-        k_cell_fill<<<blocks_for(nt, 256), 256, 0, s>>>(cell_of, nt, ucnt, cell_ent);
+        { k_cell_fill<<<blocks_for(nt, 256), 256, 0, s>>>(cell_of, nt, ucnt, cell_ent); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         unsigned long long *mx = sc.get<unsigned long long>(1);
         unsigned long long hmx = 0;
         NL_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
-        k_max_seg<<<blocks_for(ncell, 256), 256, 0, s>>>(cell_ptr, ncell, mx);
+        { k_max_seg<<<blocks_for(ncell, 256), 256, 0, s>>>(cell_ptr, ncell, mx); nl_count_launch(); }
         NL_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s));
         NL_CUDA(cudaStreamSynchronize(s));
         nl_segmented_sort_i32(cell_ent, cell_ptr, ncell, (int64_t)hmx, &P->arena, s);
@@ -855,37 +855,37 @@ nl_status nl_pairs_build_impl(nl_mesh *m, double delta, nl_pairs **out)
         A.d2_lo = (float)(A.d2 * (1.0 - 1e-4)); A.d2_hi = (float)(A.d2 * (1.0 + 1e-4));
         A.n_outer = no;
         unsigned pblocks = blocks_for(no * 32, 128);
-        k_pairs<0><<<pblocks, 128, 0, s>>>(A, cnt, nullptr, nullptr);
+        { k_pairs<0><<<pblocks, 128, 0, s>>>(A, cnt, nullptr, nullptr); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         P->pair_ptr = P->arena.get<int64_t>(no + 1);
         P->npairs = nl_scan_counts(cnt, P->pair_ptr, no, &P->arena, s);
         NL_REQUIRE(P->npairs < 0x7fffffffLL, "%lld pairs exceed the int32 pair index", (long long)P->npairs);
         P->pair_tp = P->arena.get<int32_t>(P->npairs);
-        k_pairs<1><<<pblocks, 128, 0, s>>>(A, nullptr, P->pair_ptr, P->pair_tp);
+        { k_pairs<1><<<pblocks, 128, 0, s>>>(A, nullptr, P->pair_ptr, P->pair_tp); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         NL_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
-        k_max_seg<<<blocks_for(no, 256), 256, 0, s>>>(P->pair_ptr, no, mx);
+        { k_max_seg<<<blocks_for(no, 256), 256, 0, s>>>(P->pair_ptr, no, mx); nl_count_launch(); }
         NL_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s));
         NL_CUDA(cudaStreamSynchronize(s));
         P->max_pairs_per_outer = (int64_t)hmx;
         nl_segmented_sort_i32(P->pair_tp, P->pair_ptr, no, (int64_t)hmx, &P->arena, s);
         P->pair_T = P->arena.get<int32_t>(P->npairs);
-        k_pair_T<<<(unsigned)no, 128, 0, s>>>(P->pair_ptr, m->outer_ids, no, P->pair_T);
+        { k_pair_T<<<(unsigned)no, 128, 0, s>>>(P->pair_ptr, m->outer_ids, no, P->pair_T); nl_count_launch(); }
         NL_CHECK_LAUNCH();
 
         // transposed pair list: pairs by T', increasing pair id
         NL_CUDA(cudaMemsetAsync(ucnt, 0, sizeof(unsigned long long) * nt, s));
-        k_tp_count<<<blocks_for(P->npairs, 256), 256, 0, s>>>(P->pair_tp, P->npairs, ucnt);
+        { k_tp_count<<<blocks_for(P->npairs, 256), 256, 0, s>>>(P->pair_tp, P->npairs, ucnt); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        k_u64_to_i64<<<blocks_for(nt, 256), 256, 0, s>>>(ucnt, cnt, nt);
+        { k_u64_to_i64<<<blocks_for(nt, 256), 256, 0, s>>>(ucnt, cnt, nt); nl_count_launch(); }
         P->tp_ptr = P->arena.get<int64_t>(nt + 1);
         nl_scan_counts(cnt, P->tp_ptr, nt, &P->arena, s);
         P->tp_pair = P->arena.get<int32_t>(P->npairs);
         NL_CUDA(cudaMemcpyAsync(ucnt, P->tp_ptr, sizeof(int64_t) * nt, cudaMemcpyDeviceToDevice, s));
-        k_tp_fill<<<blocks_for(P->npairs, 256), 256, 0, s>>>(P->pair_tp, P->npairs, ucnt, P->tp_pair);
+        { k_tp_fill<<<blocks_for(P->npairs, 256), 256, 0, s>>>(P->pair_tp, P->npairs, ucnt, P->tp_pair); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         NL_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
-        k_max_seg<<<blocks_for(nt, 256), 256, 0, s>>>(P->tp_ptr, nt, mx);
+        { k_max_seg<<<blocks_for(nt, 256), 256, 0, s>>>(P->tp_ptr, nt, mx); nl_count_launch(); }
         NL_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s));
         NL_CUDA(cudaStreamSynchronize(s));
         nl_segmented_sort_i32(P->tp_pair, P->tp_ptr, nt, (int64_t)hmx, &P->arena, s);
@@ -901,21 +901,21 @@ nl_status nl_pairs_build_impl(nl_mesh *m, double delta, nl_pairs **out)
         NL_CUDA(cudaFuncSetAttribute(k_elem_nodes<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
         NL_CUDA(cudaFuncSetAttribute(k_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
         NL_CUDA(cudaFuncSetAttribute(k_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-        k_elem_nodes<0><<<(unsigned)nt, GB, hsm, s>>>(N, cnt, nullptr, nullptr, ovf);
+        { k_elem_nodes<0><<<(unsigned)nt, GB, hsm, s>>>(N, cnt, nullptr, nullptr, ovf); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         int64_t *nn_ptr = sc.get<int64_t>(nt + 1);
         int64_t nn_total = nl_scan_counts(cnt, nn_ptr, nt, &P->arena, s);
         int32_t *nn_ent = sc.get<int32_t>(nn_total);
-        k_elem_nodes<1><<<(unsigned)nt, GB, hsm, s>>>(N, nullptr, nn_ptr, nn_ent, ovf);
+        { k_elem_nodes<1><<<(unsigned)nt, GB, hsm, s>>>(N, nullptr, nn_ptr, nn_ent, ovf); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        k_rows<0><<<(unsigned)nv, GB, hsm, s>>>(N, m->ne_ptr, m->ne_ent, nn_ptr, nn_ent, cnt, nullptr, nullptr, ovf);
+        { k_rows<0><<<(unsigned)nv, GB, hsm, s>>>(N, m->ne_ptr, m->ne_ent, nn_ptr, nn_ent, cnt, nullptr, nullptr, ovf); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         P->rowptr = P->arena.get<int64_t>(nv + 1);
         P->nnz = nl_scan_counts(cnt, P->rowptr, nv, &P->arena, s);
         NL_REQUIRE(P->nnz < 0x7fffffffLL, "nnz %lld exceeds the int32 position index", (long long)P->nnz);
         P->col = P->arena.get<int32_t>(P->nnz);
-        k_rows<1><<<(unsigned)nv, GB, hsm, s>>>(N, m->ne_ptr, m->ne_ent, nn_ptr, nn_ent, nullptr, P->rowptr, P->col,
-                                                 ovf);
+        { k_rows<1><<<(unsigned)nv, GB, hsm, s>>>(N, m->ne_ptr, m->ne_ent, nn_ptr, nn_ent, nullptr, P->rowptr, P->col,
+                                                 ovf); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         int hovf = 0;
         NL_CUDA(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -923,33 +923,33 @@ nl_status nl_pairs_build_impl(nl_mesh *m, double delta, nl_pairs **out)
         NL_REQUIRE(hovf == 0, "sparsity pattern overflow (more than %d columns in a row); delta/h too large", UCAP);
 
         NL_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
-        k_row_len_max<<<blocks_for(nv, 256), 256, 0, s>>>(P->rowptr, nv, mx);
+        { k_row_len_max<<<blocks_for(nv, 256), 256, 0, s>>>(P->rowptr, nv, mx); nl_count_launch(); }
         NL_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s));
 
         P->perm = P->arena.get<int32_t>(P->nnz);
         int *bad = sc.get<int>(1);
         NL_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-        k_perm<<<(unsigned)nv, 128, 0, s>>>(P->rowptr, P->col, nv, P->perm, bad);
+        { k_perm<<<(unsigned)nv, 128, 0, s>>>(P->rowptr, P->col, nv, P->perm, bad); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         P->elem_pos = P->arena.get<int32_t>(16 * nt);
-        k_elem_pos<<<blocks_for(nt, 128), 128, 0, s>>>(N, P->rowptr, P->col, P->elem_pos, bad);
+        { k_elem_pos<<<blocks_for(nt, 128), 128, 0, s>>>(N, P->rowptr, P->col, P->elem_pos, bad); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         int64_t *slen = sc.get<int64_t>(4 * no);
-        k_strip_len<<<blocks_for(no, 128), 128, 0, s>>>(m->tets, m->outer_ids, P->rowptr, no, slen);
+        { k_strip_len<<<blocks_for(no, 128), 128, 0, s>>>(m->tets, m->outer_ids, P->rowptr, no, slen); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         P->strip_off = P->arena.get<int64_t>(4 * no + 1);
         P->strip_total = nl_scan_counts(slen, P->strip_off, 4 * no, &P->arena, s);
 
         // A = K[free, free]
         const int64_t nf = m->n_free;
-        k_a_count<<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, cnt);
+        { k_a_count<<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, cnt); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         P->a_rowptr = P->arena.get<int64_t>(nf + 1);
         P->nnz_a = nl_scan_counts(cnt, P->a_rowptr, nf, &P->arena, s);
         P->a_col = P->arena.get<int32_t>(P->nnz_a);
         P->a_src = P->arena.get<int32_t>(P->nnz_a);
-        k_a_fill<<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, P->a_rowptr,
-                                                       P->a_col, P->a_src);
+        { k_a_fill<<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, P->a_rowptr,
+                                                       P->a_col, P->a_src); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         int hbad = 0;
         NL_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));

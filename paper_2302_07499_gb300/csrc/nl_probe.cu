@@ -64,7 +64,7 @@ extern "C" nl_status nl_probe_philox(const uint32_t *ctr, uint64_t key, int64_t 
         Tmp t;
         uint4 *dc = t.get<uint4>(n), *doo = t.get<uint4>(n);
         NL_CUDA(cudaMemcpy(dc, ctr, sizeof(uint4) * n, cudaMemcpyHostToDevice));
-        k_philox<<<(unsigned)((n + 255) / 256), 256>>>(dc, make_uint2((uint32_t)key, (uint32_t)(key >> 32)), n, doo);
+        { k_philox<<<(unsigned)((n + 255) / 256), 256>>>(dc, make_uint2((uint32_t)key, (uint32_t)(key >> 32)), n, doo); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         NL_CUDA(cudaMemcpy(out, doo, sizeof(uint4) * n, cudaMemcpyDeviceToHost));
     } catch (NlError &e) {

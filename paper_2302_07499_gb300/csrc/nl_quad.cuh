@@ -193,6 +193,62 @@ template <class R> __device__ R d2_point_tet(P3<R> p, const P3<R> v[4])
 //                    diagonal c2-d1: (c,c1,c2,d1) (c,c2,d2,d1)
 // m=3: (d, f1, f2, f3)
 
+// ---------------------------------------------------------------------------
+// Exact FP64 decisions for the FP32 path.  The FP32 kernel takes every
+// decision (inside test, m=2 diagonal, cap cell choice, sample acceptance) in
+// FP32 when it is clear by a wide margin, and otherwise recomputes it with the
+// FP64 operations of the specification, written with explicit round-to-
+// nearest intrinsics so that no multiply-add is fused.  The decisions of the
+// FP32 path therefore equal those of the FP64 path.
+struct Strict {
+    double v[4][3];   // global coordinates of T'
+    double x[3];      // outer point
+    double d2;        // delta^2
+};
+
+__device__ __forceinline__ double sadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ssub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double smul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double sdot(const double a[3], const double b[3])
+{
+    return sadd(sadd(smul(a[0], b[0]), smul(a[1], b[1])), smul(a[2], b[2]));
+}
+__device__ __forceinline__ double sdet3(const double a[3], const double b[3], const double c[3])
+{
+    double t0 = smul(a[0], ssub(smul(b[1], c[2]), smul(b[2], c[1])));
+    double t1 = smul(a[1], ssub(smul(b[2], c[0]), smul(b[0], c[2])));
+    double t2 = smul(a[2], ssub(smul(b[0], c[1]), smul(b[1], c[0])));
+    return sadd(sadd(t0, t1), t2);
+}
+__device__ __forceinline__ double sorient(const double p0[3], const double p1[3], const double p2[3],
+                                          const double p3[3])
+{
+    double e1[3], e2[3], e3[3];
+    for (int d = 0; d < 3; ++d) { e1[d] = ssub(p1[d], p0[d]); e2[d] = ssub(p2[d], p0[d]); e3[d] = ssub(p3[d], p0[d]); }
+    return sdet3(e1, e2, e3);
+}
+__device__ __forceinline__ double svol4(const double p0[3], const double p1[3], const double p2[3],
+                                        const double p3[3])
+{
+    return __ddiv_rn(fabs(sorient(p0, p1, p2, p3)), 6.0);
+}
+__device__ __forceinline__ double sr2(const double v[3], const double x[3])
+{
+    double w[3] = {ssub(v[0], x[0]), ssub(v[1], x[1]), ssub(v[2], x[2])};
+    return sdot(w, w);
+}
+// edge/sphere point between an inside vertex vi and an outside vertex vo
+__device__ __forceinline__ void sedge(const double vi[3], const double vo[3], const double x[3], double d2,
+                                      double p[3])
+{
+    double w[3], e[3];
+    for (int d = 0; d < 3; ++d) { w[d] = ssub(vi[d], x[d]); e[d] = ssub(vo[d], vi[d]); }
+    double A = sdot(e, e), B = sdot(e, w), C = ssub(sdot(w, w), d2);
+    double s = __dsqrt_rn(ssub(smul(B, B), smul(A, C)));
+    double t = (B >= 0.0) ? __ddiv_rn(-C, sadd(B, s)) : __ddiv_rn(ssub(s, B), A);
+    for (int d = 0; d < 3; ++d) p[d] = sadd(vi[d], smul(t, e[d]));
+}
+
 struct Stats {
     uint32_t cut, inside, mc, acc, fallback;
 };
@@ -203,8 +259,10 @@ struct Stats {
 //  volTp |T'|
 template <class R, int STRAT>
 __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, uint2 key, uint32_t idT,
-                              uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st)
+                              uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st, const Strict *sx = nullptr)
 {
+    constexpr bool F32 = sizeof(R) == 4;
+    const R MARGIN = R(1e-5);
     mom_zero(M);
     R r2[4];
     int inm = 0;
@@ -212,7 +270,9 @@ __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc,
     for (int k = 0; k < 4; ++k) {
         P3<R> w = sub(v[k], x);
         r2[k] = (w.x * w.x + w.y * w.y) + w.z * w.z;
-        if (r2[k] < d2) inm |= 1 << k;
+        bool in = r2[k] < d2;
+        if (F32 && sx && absr(r2[k] - d2) <= MARGIN * d2) in = sr2(sx->v[k], sx->x) < sx->d2;
+        if (in) inm |= 1 << k;
     }
     const int m = __popc(inm);
     if (m == 4) {
@@ -265,6 +325,22 @@ __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc,
     if (m == 2) {
         P3<R> c1 = pp[0], d1 = pp[1], c2 = pp[2], dd2 = pp[3];
         R o1 = orient(c1, c2, dd2, d1), o2 = orient(c1, c2, dd2, v[role[0]]);
+        if (F32 && sx) {
+            P3<R> e = sub(v[role[2]], v[role[0]]);
+            R L = (absr(e.x) + absr(e.y)) + absr(e.z);
+            R tol = R(1e-4) * L * L * L;
+            if (absr(o1) <= tol || absr(o2) <= tol) {
+                double P64[4][3];
+                sedge(sx->v[role[0]], sx->v[role[2]], sx->x, sx->d2, P64[0]);
+                sedge(sx->v[role[0]], sx->v[role[3]], sx->x, sx->d2, P64[1]);
+                sedge(sx->v[role[1]], sx->v[role[2]], sx->x, sx->d2, P64[2]);
+                sedge(sx->v[role[1]], sx->v[role[3]], sx->x, sx->d2, P64[3]);
+                double q1 = sorient(P64[0], P64[2], P64[3], P64[1]);
+                double q2 = sorient(P64[0], P64[2], P64[3], sx->v[role[0]]);
+                o1 = q1 > 0.0 ? R(1) : (q1 < 0.0 ? R(-1) : R(0));
+                o2 = q2 > 0.0 ? R(1) : (q2 < 0.0 ? R(-1) : R(0));
+            }
+        }
         diag_c2d1 = (o1 > R(0) && o2 < R(0)) || (o1 < R(0) && o2 > R(0));
     }
 
@@ -307,7 +383,15 @@ __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc,
 
     if (STRAT == 2 && nmc > 0) {
         bool run = (m > 0);
-        if (!run) run = d2_point_tet(x, v) <= d2;
+        if (!run) {
+            R dd = d2_point_tet(x, v);
+            run = dd <= d2;
+            if (F32 && sx && absr(dd - d2) <= R(1e-4) * d2) {
+                P3<double> vd[4];
+                for (int k = 0; k < 4; ++k) vd[k] = mk3<double>(sx->v[k][0], sx->v[k][1], sx->v[k][2]);
+                run = d2_point_tet(mk3<double>(sx->x[0], sx->x[1], sx->x[2]), vd) <= sx->d2;
+            }
+        }
         if (run) {
             int S[3][4];
             int ns;
@@ -352,13 +436,33 @@ __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc,
 #pragma unroll
             for (int k = 0; k < 10; ++k) a2[k] = R(0);
             uint32_t acc = 0;
+            // FP64 cap cells for samples whose FP32 decision is within the margin
+            bool have64 = false;
+            double s64[3][4][3], vol64[3], tot64 = 0.0;
+            auto build64 = [&]() {
+                double P64[4][3];
+                for (int n = 0; n < np; ++n)
+                    sedge(sx->v[pd[n].i], sx->v[pd[n].o], sx->x, sx->d2, P64[n]);
+                for (int jj = 0; jj < ns; ++jj) {
+                    for (int kk = 0; kk < 4; ++kk) {
+                        int pidx = S[jj][kk];
+                        for (int d = 0; d < 3; ++d) s64[jj][kk][d] = pidx < 4 ? sx->v[pidx][d] : P64[pidx - 4][d];
+                    }
+                    vol64[jj] = svol4(s64[jj][0], s64[jj][1], s64[jj][2], s64[jj][3]);
+                }
+                tot64 = 0.0;
+                for (int jj = 0; jj < ns; ++jj) tot64 = sadd(tot64, vol64[jj]);
+                have64 = true;
+            };
             for (int k = 0; k < nmc; ++k) {
                 uint4 u = philox4x32_10(make_uint4(idT, idTp, q, (uint32_t)k), key);
                 R r = unit_scale<R>(u.x) * tot;
                 int j = ns - 1;
                 R cum = R(0);
+                bool unsure = false;
                 for (int jj = 0; jj < ns; ++jj) {
                     cum += vol[jj];
+                    if (F32 && jj < ns - 1 && absr(r - cum) <= MARGIN * tot) unsure = true;
                     if (r < cum) { j = jj; break; }
                 }
                 R U0 = unif<R>(u.y), U1 = unif<R>(u.z), U2 = unif<R>(u.w), tmp;
@@ -372,7 +476,35 @@ __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc,
                                  ((be0 * s0.z + be1 * s1.z) + be2 * s2.z) + be3 * s3.z);
                 P3<R> w = sub(y, x);
                 R rr = (w.x * w.x + w.y * w.y) + w.z * w.z;
-                if (rr <= d2) {
+                bool inb = rr <= d2;
+                if (F32 && sx && (unsure || absr(rr - d2) <= MARGIN * d2)) {
+                    // the specification's FP64 sample: cell by cumulative volume, exact
+                    // spacings of the 32-bit uniforms, point and ball test
+                    if (!have64) build64();
+                    double rd = smul((double)u.x * 0x1p-32, tot64);
+                    int j64 = ns - 1;
+                    double c64 = 0.0;
+                    for (int jj = 0; jj < ns; ++jj) {
+                        c64 = sadd(c64, vol64[jj]);
+                        if (rd < c64) { j64 = jj; break; }
+                    }
+                    double V0 = ((double)u.y + 0.5) * 0x1p-32, V1 = ((double)u.z + 0.5) * 0x1p-32,
+                           V2 = ((double)u.w + 0.5) * 0x1p-32, tv;
+                    if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
+                    if (V1 > V2) { tv = V1; V1 = V2; V2 = tv; }
+                    if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
+                    double b0 = V0, b1 = ssub(V1, V0), b2 = ssub(V2, V1), b3 = ssub(1.0, V2);
+                    double wy[3];
+                    for (int d = 0; d < 3; ++d) {
+                        double yd = sadd(sadd(sadd(smul(b0, s64[j64][0][d]), smul(b1, s64[j64][1][d])),
+                                              smul(b2, s64[j64][2][d])),
+                                         smul(b3, s64[j64][3][d]));
+                        wy[d] = ssub(yd, sx->x[d]);
+                    }
+                    inb = sdot(wy, wy) <= sx->d2;
+                    j = j64;
+                }
+                if (inb) {
                     R lam[4];
 #pragma unroll
                     for (int aa = 0; aa < 4; ++aa)

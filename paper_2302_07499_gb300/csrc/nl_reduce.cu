@@ -171,27 +171,27 @@ void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const doubl
     cudaStream_t s = sys->arena.stream();
     Scratch sc(&sys->arena);
     double *G = sc.get<double>(P->nnz);
-    k_strip_gather<<<wblocks(m->nv), 256, 0, s>>>(P->rowptr, m->ne_ptr, m->ne_ent, m->outer_of, P->strip_off, strips,
-                                                 m->nv, G);
+    { k_strip_gather<<<wblocks(m->nv), 256, 0, s>>>(P->rowptr, m->ne_ptr, m->ne_ent, m->outer_of, P->strip_off, strips,
+                                                 m->nv, G); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     double *E = sc.get<double>(10 * m->nt);
     if (d_is_float)
-        k_elem_blocks<float><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->in_omega,
+        { k_elem_blocks<float><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->in_omega,
                                                            m->outer_of, (const float *)D, TT, sys->opts.gamma / 2.0,
-                                                           m->nt, E);
+                                                           m->nt, E); nl_count_launch(); }
     else
-        k_elem_blocks<double><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol,
+        { k_elem_blocks<double><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol,
                                                             m->in_omega, m->outer_of, (const double *)D, TT,
-                                                            sys->opts.gamma / 2.0, m->nt, E);
+                                                            sys->opts.gamma / 2.0, m->nt, E); nl_count_launch(); }
     NL_CHECK_LAUNCH();
-    k_final_K<<<wblocks(m->nv), 256, 0, s>>>(P->rowptr, P->perm, G, m->ne_ptr, m->ne_ent, P->elem_pos, E, m->nv,
-                                            sys->K);
+    { k_final_K<<<wblocks(m->nv), 256, 0, s>>>(P->rowptr, P->perm, G, m->ne_ptr, m->ne_ent, P->elem_pos, E, m->nv,
+                                            sys->K); nl_count_launch(); }
     NL_CHECK_LAUNCH();
-    k_load_vector<<<(unsigned)nl_cdiv<int64_t>(m->nv, 256), 256, 0, s>>>(m->ne_ptr, m->ne_ent, m->outer_of,
-                                                                       m->tet_vol, sys->opts.f_const, m->nv, sys->F);
+    { k_load_vector<<<(unsigned)nl_cdiv<int64_t>(m->nv, 256), 256, 0, s>>>(m->ne_ptr, m->ne_ent, m->outer_of,
+                                                                       m->tet_vol, sys->opts.f_const, m->nv, sys->F); nl_count_launch(); }
     NL_CHECK_LAUNCH();
-    k_system<<<wblocks(m->n_free), 256, 0, s>>>(P->rowptr, P->col, sys->K, m->free_nodes, m->free_idx, P->a_rowptr,
-                                               P->a_src, sys->F, sys->g, m->n_free, sys->A, sys->A32, sys->b);
+    { k_system<<<wblocks(m->n_free), 256, 0, s>>>(P->rowptr, P->col, sys->K, m->free_nodes, m->free_idx, P->a_rowptr,
+                                               P->a_src, sys->F, sys->g, m->n_free, sys->A, sys->A32, sys->b); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     // scratch is released (stream-ordered) when sc goes out of scope
     NL_CUDA(cudaStreamSynchronize(s));

@@ -179,9 +179,9 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b,
            XT *q, int64_t n, double rtol, int max_it, int check_every, Cg &cg, cudaStream_t s, bool *conv)
 {
     const int nb = cg.nb;
-    k_init<XT><<<nb, RB, 0, s>>>(b, x, r, p, n, scale, cg.part);
+    { k_init<XT><<<nb, RB, 0, s>>>(b, x, r, p, n, scale, cg.part); nl_count_launch(); }
     NL_CHECK_LAUNCH();
-    k_start<<<1, 32, 0, s>>>(cg.part, nb, rtol * rtol, cg.st);
+    { k_start<<<1, 32, 0, s>>>(cg.part, nb, rtol * rtol, cg.st); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     CgState h{};
     int launched = 0;
@@ -189,11 +189,11 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b,
     while (launched < max_it) {
         int k = std::min(check_every, max_it - launched);
         for (int j = 0; j < k; ++j) {
-            k_spmv_dot<VT, XT><<<nb, RB, 0, s>>>(rp, ci, val, p, q, n, cg.part, cg.st);
-            k_alpha<<<1, 32, 0, s>>>(cg.part, nb, cg.st);
-            k_update_xr<XT><<<nb, RB, 0, s>>>(x, r, p, q, n, cg.part, cg.st);
-            k_beta<<<1, 32, 0, s>>>(cg.part, nb, cg.st);
-            k_update_p<XT><<<nb, RB, 0, s>>>(p, r, n, cg.st);
+            { k_spmv_dot<VT, XT><<<nb, RB, 0, s>>>(rp, ci, val, p, q, n, cg.part, cg.st); nl_count_launch(); }
+            { k_alpha<<<1, 32, 0, s>>>(cg.part, nb, cg.st); nl_count_launch(); }
+            { k_update_xr<XT><<<nb, RB, 0, s>>>(x, r, p, q, n, cg.part, cg.st); nl_count_launch(); }
+            { k_beta<<<1, 32, 0, s>>>(cg.part, nb, cg.st); nl_count_launch(); }
+            { k_update_p<XT><<<nb, RB, 0, s>>>(p, r, n, cg.st); nl_count_launch(); }
         }
         NL_CHECK_LAUNCH();
         launched += k;
@@ -233,7 +233,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
         {
             double *z = sc.get<double>(n);
             NL_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
-            k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, z, S->b, rres, n, cg.part);
+            { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, z, S->b, rres, n, cg.part); nl_count_launch(); }
             NL_CHECK_LAUNCH();
             std::vector<double> hp(cg.nb);
             NL_CUDA(cudaMemcpyAsync(hp.data(), cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
@@ -253,7 +253,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
             NL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
             int total = 0;
             for (int outer = 0; outer < 100 && total < max_it; ++outer) {
-                k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part);
+                { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part); nl_count_launch(); }
                 NL_CHECK_LAUNCH();
                 std::vector<double> hp(cg.nb);
                 NL_CUDA(cudaMemcpyAsync(hp.data(), cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
@@ -267,14 +267,14 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
                                               inner, max_it - total, check_every, cg, s, &conv);
                 total += it;
                 inf.refinements += 1;
-                k_add_scaled<<<cg.nb, RB, 0, s>>>(x, xf, rn, n);
+                { k_add_scaled<<<cg.nb, RB, 0, s>>>(x, xf, rn, n); nl_count_launch(); }
                 NL_CHECK_LAUNCH();
                 if (it == 0) break;
             }
             inf.iterations = total;
         }
         // true residual
-        k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part);
+        { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         std::vector<double> hp(cg.nb);
         NL_CUDA(cudaMemcpyAsync(hp.data(), cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
@@ -285,8 +285,8 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
         if (mixed) converged = inf.rel_residual <= rtol * 1.0000001;
         if (u_out) {
             double *u = (where == NL_DEVICE) ? u_out : sc.get<double>(m->nv);
-            k_scatter_u<<<(unsigned)nl_cdiv<int64_t>(std::max(m->nv, n), 256), 256, 0, s>>>(
-                x, m->free_nodes, S->g, m->node_free, u, m->nv, n);
+            { k_scatter_u<<<(unsigned)nl_cdiv<int64_t>(std::max(m->nv, n), 256), 256, 0, s>>>(
+                x, m->free_nodes, S->g, m->node_free, u, m->nv, n); nl_count_launch(); }
             NL_CHECK_LAUNCH();
             if (where == NL_HOST)
                 NL_CUDA(cudaMemcpyAsync(u_out, u, sizeof(double) * m->nv, cudaMemcpyDeviceToHost, s));

@@ -8,7 +8,13 @@
 
 #include "nl_internal.h"
 
+#include <atomic>
+
 static thread_local char g_err[1024] = {0};
+static std::atomic<unsigned long long> g_launches{0};
+
+void nl_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" uint64_t nl_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 void nl_set_error(const char *fmt, ...)
 {
@@ -124,12 +130,12 @@ void nl_exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, DevArena 
     int64_t nb = nl_cdiv<int64_t>(n, SCAN_BLOCK);
     Scratch sc(arena);
     int64_t *bsum = sc.get<int64_t>(nb);
-    k_scan_block<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, bsum, n);
+    { k_scan_block<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, out, bsum, n); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     if (nb > 1) {
         int64_t *boff = sc.get<int64_t>(nb);
         nl_exclusive_scan_i64(bsum, boff, nb, arena, s);
-        k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(out, boff, n);
+        { k_scan_add<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(out, boff, n); nl_count_launch(); }
         NL_CHECK_LAUNCH();
     }
 }
@@ -142,7 +148,7 @@ __global__ void k_set_last(int64_t *out, const int64_t *counts, int64_t n)
 int64_t nl_scan_counts(const int64_t *counts, int64_t *out, int64_t n, DevArena *arena, cudaStream_t s)
 {
     nl_exclusive_scan_i64(counts, out, n, arena, s);
-    k_set_last<<<1, 32, 0, s>>>(out, counts, n);
+    { k_set_last<<<1, 32, 0, s>>>(out, counts, n); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     int64_t total = 0;
     NL_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -194,7 +200,7 @@ void nl_segmented_sort_i32(int32_t *keys, const int64_t *ptr, int64_t nseg, int6
         NL_CUDA(cudaFuncSetAttribute(k_seg_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int64_t s0 = 0; s0 < nseg; s0 += 2147483647LL) {
         int64_t cnt = std::min<int64_t>(nseg - s0, 2147483647LL);
-        k_seg_bitonic<<<(unsigned)cnt, threads, smem, s>>>(keys, ptr + s0, p2);
+        { k_seg_bitonic<<<(unsigned)cnt, threads, smem, s>>>(keys, ptr + s0, p2); nl_count_launch(); }
         NL_CHECK_LAUNCH();
     }
 }
