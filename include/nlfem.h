@@ -219,6 +219,30 @@ nl_status nl_solve(nl_system *sys, const nl_solve_opts *opts, double *u_out, int
                    nl_solve_info *info);
 
 /* ---------------------------------------------------------------------------
+ * nl_solve_static — the FP64 conjugate-gradient solve of nl_solve (mixed is
+ * ignored) without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory during
+ * the call, e.g. a latency-critical loop that cannot afford cudaMalloc or
+ * cudaFree (cudaFree synchronises the whole device), code that runs inside a
+ * fixed memory budget reserved up front by another framework, or a thread
+ * that holds a lock the caller's allocator may need.
+ *   Scratch: the CG vectors live in one fixed device array compiled into the
+ *   library (about 5.3 MB, held on every device that loads the library until
+ *   the process exits).  Limit: at most 131072 unknowns (n_free); larger
+ *   systems get NL_EINVAL with a message.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: every call uses the same array, which keeps the last call's
+ *   contents (each call clears or overwrites what it reads).  Calls whose GPU
+ *   work overlaps (other threads, other streams) race on the array; order
+ *   them, e.g. on one stream.
+ *   u_out: device pointer to n_vert doubles (required), written as by
+ *   nl_solve.  Work runs on the system's stream; the call synchronises it.
+ * Errors: NL_EINVAL, NL_ENOTCONV (u_out holds the last iterate), NL_ECUDA. */
+nl_status nl_solve_static(nl_system *sys, const nl_solve_opts *opts, double *u_out, nl_solve_info *info);
+
+/* ---------------------------------------------------------------------------
  * Diagnostic entry points (not on the assembly path).  Host arrays in and
  * out; they run on the default stream with their own temporary device
  * buffers and synchronise before returning.

@@ -73,7 +73,8 @@ class nl_solve_info(C.Structure):
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = ["nl_mesh_create", "nl_mesh_destroy", "nl_pairs_build", "nl_pairs_destroy", "nl_pairs_get_info",
             "nl_pairs_export", "nl_assemble", "nl_system_destroy", "nl_system_csr", "nl_system_rhs",
-            "nl_system_stats", "nl_solve", "nl_probe_moments", "nl_probe_philox", "nl_last_error", "nl_version", "nl_kernel_launches"]
+            "nl_system_stats", "nl_solve", "nl_probe_moments", "nl_probe_philox", "nl_last_error", "nl_version", "nl_kernel_launches",
+            "nl_solve_static"]
 
 _lib = None
 

@@ -310,3 +310,108 @@ extern "C" nl_status nl_solve(nl_system *S, const nl_solve_opts *opts, double *u
     if (u_out && where != NL_HOST && where != NL_DEVICE) { nl_set_error("bad where"); return NL_EINVAL; }
     return nl_solve_impl(S, opts, u_out, where, info);
 }
+
+// ===========================================================================
+// nl_solve_static: the FP64 CG solve with its scratch vectors in a fixed
+// device array compiled into the library, for callers that must not allocate
+// device memory during the call.  The array is shared by every call in the
+// process and keeps the last call's contents; each call overwrites what it
+// reads before reading it.
+namespace {
+
+constexpr int64_t kStaticMaxFree = 131072;        // unknowns (free nodes)
+constexpr int kStaticMaxBlocks = 4096;            // reduction partials
+constexpr size_t kStaticVecBytes = sizeof(double) * (size_t)kStaticMaxFree;
+constexpr size_t kStaticBytes = 5 * kStaticVecBytes + sizeof(double) * kStaticMaxBlocks + 256;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+static void *g_static_addr[kMaxDevices] = {nullptr};
+
+// Device address of the array on the current device (looked up once per
+// device; the host-side symbol is only a stand-in and is never dereferenced).
+void *static_scratch_address()
+{
+    int dev = 0;
+    NL_CUDA(cudaGetDevice(&dev));
+    NL_REQUIRE(dev >= 0 && dev < kMaxDevices, "device ordinal %d out of range", dev);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            nl_set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+            throw NlError{NL_ECUDA};
+        }
+        g_static_addr[dev] = p;
+    }
+    return g_static_addr[dev];
+}
+
+}  // namespace
+
+extern "C" nl_status nl_solve_static(nl_system *S, const nl_solve_opts *opts, double *u_out, nl_solve_info *info)
+{
+    nl_clear_error();
+    if (!S || !u_out) { nl_set_error("NULL system or output"); return NL_EINVAL; }
+    nl_pairs *P = S->pairs;
+    nl_mesh *m = P->mesh;
+    const int64_t n = m->n_free;
+    if (n > kStaticMaxFree) {
+        nl_set_error("nl_solve_static supports at most %lld unknowns, the system has %lld",
+                     (long long)kStaticMaxFree, (long long)n);
+        return NL_EINVAL;
+    }
+    double rtol = (opts && opts->rtol > 0) ? opts->rtol : 1e-12;
+    int max_it = (opts && opts->max_iter > 0) ? opts->max_iter : 20000;
+    int check_every = (opts && opts->check_every > 0) ? opts->check_every : 8;
+    nl_solve_info inf{0, 0, 0.0};
+    nl_status ret = NL_OK;
+    try {
+        cudaStream_t s = S->arena.stream();
+        unsigned char *base = static_cast<unsigned char *>(static_scratch_address());
+        double *x = reinterpret_cast<double *>(base);
+        double *r = reinterpret_cast<double *>(base + 1 * kStaticVecBytes);
+        double *p = reinterpret_cast<double *>(base + 2 * kStaticVecBytes);
+        double *q = reinterpret_cast<double *>(base + 3 * kStaticVecBytes);
+        double *rres = reinterpret_cast<double *>(base + 4 * kStaticVecBytes);
+        Cg cg;
+        cg.nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nl_num_sms() * 4, nl_cdiv<int64_t>(n * 32, RB)));
+        NL_REQUIRE(cg.nb <= kStaticMaxBlocks, "too many reduction blocks (%d)", cg.nb);
+        cg.part = reinterpret_cast<double *>(base + 5 * kStaticVecBytes);
+        cg.st = reinterpret_cast<CgState *>(base + 5 * kStaticVecBytes + sizeof(double) * kStaticMaxBlocks);
+        double hp[kStaticMaxBlocks];
+        // |b| from the residual of u = 0 (x starts at zero: clear it first)
+        NL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+        { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        NL_CUDA(cudaMemcpyAsync(hp, cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
+        NL_CUDA(cudaStreamSynchronize(s));
+        double bb = 0.0;
+        for (int i = 0; i < cg.nb; ++i) bb += hp[i];
+        const double nb_ = sqrt(bb);
+        bool conv = false;
+        inf.iterations = run_cg<double, double>(P->a_rowptr, P->a_col, S->A, S->b, 1.0, x, r, p, q, n, rtol, max_it,
+                                                check_every, cg, s, &conv);
+        { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        NL_CUDA(cudaMemcpyAsync(hp, cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
+        NL_CUDA(cudaStreamSynchronize(s));
+        double rr = 0.0;
+        for (int i = 0; i < cg.nb; ++i) rr += hp[i];
+        inf.rel_residual = (nb_ > 0) ? sqrt(rr) / nb_ : 0.0;
+        { k_scatter_u<<<(unsigned)nl_cdiv<int64_t>(std::max(m->nv, n), 256), 256, 0, s>>>(
+              x, m->free_nodes, S->g, m->node_free, u_out, m->nv, n); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        NL_CUDA(cudaStreamSynchronize(s));
+        if (!conv) {
+            nl_set_error("CG stopped after %d iterations at relative residual %.3e", inf.iterations, inf.rel_residual);
+            ret = NL_ENOTCONV;
+        }
+    } catch (NlError &e) {
+        ret = e.st;
+    }
+    if (info) *info = inf;
+    return ret;
+}
