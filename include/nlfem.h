@@ -187,6 +187,9 @@ typedef struct {
     double quadrature_ms;      /* duration of the quadrature kernel (CUDA events
                                   recorded on the assembly stream around its launch) */
     double reduce_ms;          /* duration of the reduction into K, A and b */
+    double classify_ms;        /* the three quadrature kernels, summed over the */
+    double events_ms;          /* chunks of pairs: classification, cut-point   */
+    double combine_ms;         /* moments (+ Monte Carlo), per-pair combination */
 } nl_assemble_stats;
 nl_status nl_system_stats(const nl_system *sys, nl_assemble_stats *out);
 

@@ -170,6 +170,8 @@ def config_mesh(name: str) -> tuple[Mesh, float]:
         return kuhn_box(-0.25, 1.25, 6), 0.25
     if name == "cube24_d0125":      # 24^3 cells, h = 1/16, delta = 1/8
         return kuhn_box(-0.25, 1.25, 24), 0.125
+    if name == "cube16_d016":       # 16^3 cells over [-1/6,7/6]^3, h = 1/12, delta = 1/6 (small profiling case)
+        return kuhn_box(-1.0 / 6.0, 7.0 / 6.0, 16), 1.0 / 6.0
     if name == "jitter38_d3h":      # 38^3 cells, h = 1/32, delta = 3h, jitter 0.2h seed 7
         return kuhn_box(-3.0 / 32.0, 1.0 + 3.0 / 32.0, 38, jitter_frac=0.2, seed=7), 3.0 / 32.0
     raise KeyError(name)

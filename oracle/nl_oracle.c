@@ -321,7 +321,198 @@ static void cross3(const double a[3], const double b[3], double c[3])
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-int or_hull_tets(int n, const double *pflat, double *outflat, int maxout)
+/* ------------------------------------------------------------------------- */
+/* Exact sign of orientation determinants (Shewchuk, "Adaptive precision
+ * floating-point arithmetic and fast robust geometric predicates", 1997):
+ * a floating-point evaluation with an error bound, and, when the bound does
+ * not decide, the exact value as a floating-point expansion (two_sum,
+ * two_product with fma, expansion sums and scalings).                       */
+#define EXP_MAX 512
+
+static void two_sum(double a, double b, double *x, double *y)
+{
+    double s = a + b, bv = s - a, av = s - bv;
+    *x = s;
+    *y = (a - av) + (b - bv);
+}
+
+static void two_prod(double a, double b, double *x, double *y)
+{
+    double p = a * b;
+    *x = p;
+    *y = fma(a, b, -p);
+}
+
+/* h = e + f (nonoverlapping expansions, zero components dropped) */
+static int exp_add(int elen, const double *e, int flen, const double *f, double *h)
+{
+    double tmp[EXP_MAX];
+    int hlen = elen;
+    for (int i = 0; i < elen; ++i) tmp[i] = e[i];
+    for (int j = 0; j < flen; ++j) {
+        double q = f[j];
+        int k = 0;
+        double out[EXP_MAX];
+        for (int i = 0; i < hlen; ++i) {
+            double x, y;
+            two_sum(q, tmp[i], &x, &y);
+            if (y != 0.0) out[k++] = y;
+            q = x;
+        }
+        if (q != 0.0 || k == 0) out[k++] = q;
+        for (int i = 0; i < k; ++i) tmp[i] = out[i];
+        hlen = k;
+    }
+    for (int i = 0; i < hlen; ++i) h[i] = tmp[i];
+    return hlen;
+}
+
+/* h = e * b */
+static int exp_scale(int elen, const double *e, double b, double *h)
+{
+    double acc[EXP_MAX];
+    int alen = 0;
+    for (int i = 0; i < elen; ++i) {
+        double p[2];
+        two_prod(e[i], b, &p[1], &p[0]);
+        alen = exp_add(alen, acc, 2, p, acc);
+    }
+    for (int i = 0; i < alen; ++i) h[i] = acc[i];
+    return alen;
+}
+
+/* h = e * f */
+static int exp_mul(int elen, const double *e, int flen, const double *f, double *h)
+{
+    double acc[EXP_MAX], t[EXP_MAX];
+    int alen = 0;
+    for (int j = 0; j < flen; ++j) {
+        int tl = exp_scale(elen, e, f[j], t);
+        alen = exp_add(alen, acc, tl, t, acc);
+    }
+    for (int i = 0; i < alen; ++i) h[i] = acc[i];
+    return alen;
+}
+
+static int exp_sign(int n, const double *e)
+{
+    /* components are nonoverlapping and increasing in magnitude: the last
+     * nonzero one carries the sign */
+    for (int i = n - 1; i >= 0; --i) if (e[i] != 0.0) return e[i] > 0.0 ? 1 : -1;
+    return 0;
+}
+
+/* sign of det[b-a; c-a; d-a] (the orientation of d against the plane abc) */
+static int orient3d_sign(const double a[3], const double b[3], const double c[3], const double d[3])
+{
+    double u[3], v[3], w[3];
+    for (int k = 0; k < 3; ++k) { u[k] = b[k] - a[k]; v[k] = c[k] - a[k]; w[k] = d[k] - a[k]; }
+    double t0 = v[1] * w[2] - v[2] * w[1], t1 = v[2] * w[0] - v[0] * w[2], t2 = v[0] * w[1] - v[1] * w[0];
+    double det = u[0] * t0 + u[1] * t1 + u[2] * t2;
+    double perm = fabs(u[0]) * (fabs(v[1] * w[2]) + fabs(v[2] * w[1])) +
+                  fabs(u[1]) * (fabs(v[2] * w[0]) + fabs(v[0] * w[2])) +
+                  fabs(u[2]) * (fabs(v[0] * w[1]) + fabs(v[1] * w[0]));
+    if (fabs(det) > 1e-14 * perm) return det > 0.0 ? 1 : -1;
+    /* exact: differences as 2-component expansions, then the cofactor sum */
+    double U[3][2], V[3][2], W[3][2];
+    for (int k = 0; k < 3; ++k) {
+        two_sum(b[k], -a[k], &U[k][1], &U[k][0]);
+        two_sum(c[k], -a[k], &V[k][1], &V[k][0]);
+        two_sum(d[k], -a[k], &W[k][1], &W[k][0]);
+    }
+    static const int cyc[3][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}};
+    double total[EXP_MAX];
+    int tl = 0;
+    for (int r = 0; r < 3; ++r) {
+        int i = cyc[r][0], j = cyc[r][1], k = cyc[r][2];
+        double p1[EXP_MAX], p2[EXP_MAX], cf[EXP_MAX], term[EXP_MAX];
+        int l1 = exp_mul(2, V[j], 2, W[k], p1);
+        int l2 = exp_mul(2, V[k], 2, W[j], p2);
+        for (int q = 0; q < l2; ++q) p2[q] = -p2[q];
+        int lc = exp_add(l1, p1, l2, p2, cf);
+        int lt = exp_mul(2, U[i], lc, cf, term);
+        tl = exp_add(tl, total, lt, term, total);
+    }
+    return exp_sign(tl, total);
+}
+
+/* the triple is collinear iff its cross product is exactly zero */
+static int collinear_exact(const double a[3], const double b[3], const double c[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        int i = (k + 1) % 3, j = (k + 2) % 3;
+        /* 2D orientation in the (i,j) coordinate plane */
+        double u0 = b[i] - a[i], u1 = b[j] - a[j], v0 = c[i] - a[i], v1 = c[j] - a[j];
+        double det = u0 * v1 - u1 * v0;
+        double perm = fabs(u0 * v1) + fabs(u1 * v0);
+        if (fabs(det) > 1e-14 * perm) return 0;
+        double U0[2], U1[2], V0[2], V1[2], p1[EXP_MAX], p2[EXP_MAX], tot[EXP_MAX];
+        two_sum(b[i], -a[i], &U0[1], &U0[0]);
+        two_sum(b[j], -a[j], &U1[1], &U1[0]);
+        two_sum(c[i], -a[i], &V0[1], &V0[0]);
+        two_sum(c[j], -a[j], &V1[1], &V1[0]);
+        int l1 = exp_mul(2, U0, 2, V1, p1);
+        int l2 = exp_mul(2, U1, 2, V0, p2);
+        for (int q = 0; q < l2; ++q) p2[q] = -p2[q];
+        int lt = exp_add(l1, p1, l2, p2, tot);
+        if (exp_sign(lt, tot) != 0) return 0;
+    }
+    return 1;
+}
+
+/* 2D convex hull (monotone chain) of the points idx[0..m) projected on the
+ * plane basis (u, w) through origin o; writes the polygon's point indices in
+ * order and returns their number. */
+static int polygon_2d(const double (*p)[3], const int *idx_in, int m, const double o[3], const double u[3],
+                      const double w2[3], double ctol, int *poly)
+{
+    int idx[16];
+    double px[16], py[16];
+    for (int a = 0; a < m; ++a) {
+        double r[3];
+        for (int d = 0; d < 3; ++d) r[d] = p[idx_in[a]][d] - o[d];
+        idx[a] = idx_in[a]; px[a] = dot3(r, u); py[a] = dot3(r, w2);
+    }
+    for (int a = 1; a < m; ++a) {             /* sort by (x, y) */
+        int ti = idx[a]; double tx = px[a], ty = py[a]; int b = a - 1;
+        while (b >= 0 && (px[b] > tx || (px[b] == tx && py[b] > ty))) {
+            idx[b + 1] = idx[b]; px[b + 1] = px[b]; py[b + 1] = py[b]; b--;
+        }
+        idx[b + 1] = ti; px[b + 1] = tx; py[b + 1] = ty;
+    }
+    int hull[34], hn = 0;
+    for (int a = 0; a < m; ++a) {             /* lower chain */
+        while (hn >= 2) {
+            int o2 = hull[hn - 2], b = hull[hn - 1];
+            double cr = (px[b] - px[o2]) * (py[a] - py[o2]) - (py[b] - py[o2]) * (px[a] - px[o2]);
+            if (cr <= ctol) hn--; else break;
+        }
+        hull[hn++] = a;
+    }
+    int lower = hn + 1;
+    for (int a = m - 2; a >= 0; --a) {         /* upper chain */
+        while (hn >= lower) {
+            int o2 = hull[hn - 2], b = hull[hn - 1];
+            double cr = (px[b] - px[o2]) * (py[a] - py[o2]) - (py[b] - py[o2]) * (px[a] - px[o2]);
+            if (cr <= ctol) hn--; else break;
+        }
+        hull[hn++] = a;
+    }
+    hn--;                                      /* last point repeats the first */
+    for (int a = 0; a < hn; ++a) poly[a] = idx[hull[a]];
+    return hn < 0 ? 0 : hn;
+}
+
+/* Convex hull of a few points, split into tetrahedra coned from the mean
+ * point.  `lab` (may be NULL) gives per point a bit set of known planes the
+ * point lies on by construction (for the approximate ball: the faces of T');
+ * a supporting plane through points sharing such a plane is that plane, with
+ * exactly the points that carry its bit.  Other supporting planes are found
+ * by brute force with exact orientation signs: every non-collinear triple
+ * whose plane has all points on one side (points with a zero sign lie on
+ * it).  The points of each facet are fan-triangulated along their 2D convex
+ * hull. */
+int or_hull_tets_labeled(int n, const double *pflat, const unsigned *lab, double *outflat, int maxout)
 {
     const double (*p)[3] = (const double (*)[3])pflat;
     double (*out)[4][3] = (double (*)[4][3])outflat;
@@ -329,43 +520,51 @@ int or_hull_tets(int n, const double *pflat, double *outflat, int maxout)
     double c[3] = {0, 0, 0};
     for (int i = 0; i < n; ++i) for (int d = 0; d < 3; ++d) c[d] += p[i][d];
     for (int d = 0; d < 3; ++d) c[d] /= (double)n;
-    double L = 0.0;
-    for (int i = 0; i < n; ++i) { double dd = sqrt(dist2(p[i], c)); if (dd > L) L = dd; }
+    double L = 0.0, Cabs = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double dd = sqrt(dist2(p[i], c));
+        if (dd > L) L = dd;
+        for (int d = 0; d < 3; ++d) if (fabs(p[i][d]) > Cabs) Cabs = fabs(p[i][d]);
+    }
     if (L == 0.0) return 0;
-    /* pass 1: the point sets of all supporting planes through a triple */
+    (void)Cabs;
     uint32_t masks[600];
     int fi[600], nmask = 0;
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j)
             for (int k = j + 1; k < n; ++k) {
+                uint32_t mask = 0;
+                unsigned shared = lab ? (lab[i] & lab[j] & lab[k]) : 0u;
                 double e1[3], e2[3], nr[3];
                 for (int d = 0; d < 3; ++d) { e1[d] = p[j][d] - p[i][d]; e2[d] = p[k][d] - p[i][d]; }
                 cross3(e1, e2, nr);
                 double nn = sqrt(dot3(nr, nr));
-                if (nn <= 1e-12 * L * L) continue;            /* degenerate triple */
-                double tol = 1e-10 * L * nn;
-                int pos = 0, neg = 0;
-                uint32_t mask = 0;
-                for (int l = 0; l < n; ++l) {
-                    double w[3];
-                    for (int d = 0; d < 3; ++d) w[d] = p[l][d] - p[i][d];
-                    double s = dot3(nr, w);
-                    if (fabs(s) <= tol) mask |= 1u << l;
-                    else if (s > 0) pos++;
-                    else neg++;
+                if (shared) {
+                    /* a known plane: its facet holds the points carrying that plane */
+                    int bit = 0;
+                    while (!(shared & (1u << bit))) bit++;
+                    for (int l = 0; l < n; ++l) if (lab[l] & (1u << bit)) mask |= 1u << l;
+                    if (nn <= 1e-14 * L * L) continue;        /* collinear triple */
+                } else {
+                    /* exact predicates: a collinear triple spans no plane */
+                    if (collinear_exact(p[i], p[j], p[k])) continue;
+                    int pos = 0, neg = 0;
+                    for (int l = 0; l < n; ++l) {
+                        int sg = (l == i || l == j || l == k) ? 0 : orient3d_sign(p[i], p[j], p[k], p[l]);
+                        if (sg == 0) mask |= 1u << l;
+                        else if (sg > 0) pos++;
+                        else neg++;
+                    }
+                    if (pos && neg) continue;
+                    if (!pos && !neg) return 0;                /* flat: zero volume */
                 }
-                if (pos && neg) continue;
-                if (!pos && !neg) return 0;                    /* flat: zero volume */
                 int seen = 0;
-                for (int m = 0; m < nmask; ++m) if (masks[m] == mask) { seen = 1; break; }
+                for (int m2 = 0; m2 < nmask; ++m2) if (masks[m2] == mask) { seen = 1; break; }
                 if (seen || nmask >= 600) continue;
                 masks[nmask] = mask;
                 fi[nmask] = (i << 8) | (j << 4) | k;
                 nmask++;
             }
-    /* pass 2: a point set contained in a larger one lies in the same plane
-     * (a near-collinear triple can tilt its computed plane); keep only the
-     * maximal sets, each as one facet.                                      */
     int nout = 0;
     for (int f = 0; f < nmask; ++f) {
         int sub = 0;
@@ -373,56 +572,22 @@ int or_hull_tets(int n, const double *pflat, double *outflat, int maxout)
             if (g != f && (masks[f] & masks[g]) == masks[f] && masks[g] != masks[f]) { sub = 1; break; }
         if (sub) continue;
         uint32_t mask = masks[f];
-        int i = fi[f] >> 8, j = (fi[f] >> 4) & 15;
-        int k = fi[f] & 15;
+        int i = fi[f] >> 8, j = (fi[f] >> 4) & 15, k = fi[f] & 15;
         double e1[3], e2[3], nr[3];
         for (int d = 0; d < 3; ++d) { e1[d] = p[j][d] - p[i][d]; e2[d] = p[k][d] - p[i][d]; }
         cross3(e1, e2, nr);
         double nn = sqrt(dot3(nr, nr));
-        /* 2D convex hull of the facet's points */
         double u[3], w2[3], nh[3];
         for (int d = 0; d < 3; ++d) nh[d] = nr[d] / nn;
         double lu = sqrt(dot3(e1, e1));
         for (int d = 0; d < 3; ++d) u[d] = e1[d] / lu;
         cross3(nh, u, w2);
-        int idx[16], m = 0;
-        double px[16], py[16];
-        for (int l = 0; l < n; ++l)
-            if (mask & (1u << l)) {
-                double r[3];
-                for (int d = 0; d < 3; ++d) r[d] = p[l][d] - p[i][d];
-                idx[m] = l; px[m] = dot3(r, u); py[m] = dot3(r, w2); m++;
-            }
-        for (int a = 1; a < m; ++a) {             /* sort by (x, y) */
-            int ti = idx[a]; double tx = px[a], ty = py[a]; int b = a - 1;
-            while (b >= 0 && (px[b] > tx || (px[b] == tx && py[b] > ty))) {
-                idx[b + 1] = idx[b]; px[b + 1] = px[b]; py[b + 1] = py[b]; b--;
-            }
-            idx[b + 1] = ti; px[b + 1] = tx; py[b + 1] = ty;
-        }
-        int hull[34], hn = 0;
-        double ctol = 1e-12 * L * L;
-        for (int a = 0; a < m; ++a) {             /* lower chain */
-            while (hn >= 2) {
-                int o = hull[hn - 2], b = hull[hn - 1];
-                double cr = (px[b] - px[o]) * (py[a] - py[o]) - (py[b] - py[o]) * (px[a] - px[o]);
-                if (cr <= ctol) hn--; else break;
-            }
-            hull[hn++] = a;
-        }
-        int lower = hn + 1;
-        for (int a = m - 2; a >= 0; --a) {         /* upper chain */
-            while (hn >= lower) {
-                int o = hull[hn - 2], b = hull[hn - 1];
-                double cr = (px[b] - px[o]) * (py[a] - py[o]) - (py[b] - py[o]) * (px[a] - px[o]);
-                if (cr <= ctol) hn--; else break;
-            }
-            hull[hn++] = a;
-        }
-        hn--;                                      /* last point repeats the first */
+        int idx[16], m = 0, poly[16];
+        for (int l = 0; l < n; ++l) if (mask & (1u << l)) idx[m++] = l;
+        int hn = polygon_2d(p, idx, m, p[i], u, w2, 1e-14 * L * L, poly);
         for (int a = 1; a + 1 < hn; ++a) {
             if (nout >= maxout) return -1;
-            const double *q0 = p[idx[hull[0]]], *q1 = p[idx[hull[a]]], *q2 = p[idx[hull[a + 1]]];
+            const double *q0 = p[poly[0]], *q1 = p[poly[a]], *q2 = p[poly[a + 1]];
             for (int d = 0; d < 3; ++d) {
                 out[nout][0][d] = c[d]; out[nout][1][d] = q0[d];
                 out[nout][2][d] = q1[d]; out[nout][3][d] = q2[d];
@@ -431,6 +596,11 @@ int or_hull_tets(int n, const double *pflat, double *outflat, int maxout)
         }
     }
     return nout;
+}
+
+int or_hull_tets(int n, const double *pflat, double *outflat, int maxout)
+{
+    return or_hull_tets_labeled(n, pflat, NULL, outflat, maxout);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -478,7 +648,7 @@ static void classify(const double v[4][3], const double x[3], double delta, clas
  * on the far side of the chord p1p2 from the face's inside vertex, on the
  * perpendicular bisector of the chord; dropped if it is not in the face.   */
 static int arc_midpoints(const double v[4][3], const double x[3], double delta, const classify_t *c,
-                         double mu[4][3])
+                         double mu[4][3], int face[4])
 {
     int inflag[4] = {0, 0, 0, 0};
     for (int a = 0; a < c->m; ++a) inflag[c->in[a]] = 1;
@@ -532,6 +702,7 @@ static int arc_midpoints(const double v[4][3], const double x[3], double delta, 
         double tol = -1e-12;
         if (ls < tol || lt < tol || 1.0 - ls - lt < tol) continue;
         for (int d = 0; d < 3; ++d) mu[nm][d] = m3[d];
+        face[nm] = o;
         nm++;
     }
     return nm;
@@ -547,17 +718,31 @@ static int region_cells(const double v[4][3], const double x[3], double delta, i
         return 1;
     }
     if (c->m == 0) return 0;
+    /* each point carries the faces of T' it lies on (face f = opposite vertex
+     * f): a vertex k lies on the faces f != k, an edge point (i,o) on the
+     * faces f not in {i,o}, an arc midpoint of face o on face o */
     double pts[16][3];
+    unsigned lab[16];
     int n = 0;
-    for (int a = 0; a < c->m; ++a) memcpy(pts[n++], v[c->in[a]], sizeof(double) * 3);
+    for (int a = 0; a < c->m; ++a) {
+        lab[n] = 15u & ~(1u << c->in[a]);
+        memcpy(pts[n++], v[c->in[a]], sizeof(double) * 3);
+    }
     for (int a = 0; a < c->m; ++a)
-        for (int b = 0; b < 4 - c->m; ++b) memcpy(pts[n++], c->P[c->in[a]][c->out[b]], sizeof(double) * 3);
+        for (int b = 0; b < 4 - c->m; ++b) {
+            lab[n] = 15u & ~((1u << c->in[a]) | (1u << c->out[b]));
+            memcpy(pts[n++], c->P[c->in[a]][c->out[b]], sizeof(double) * 3);
+        }
     if (strategy == OR_APPROXCAPS) {
         double mu[4][3];
-        int nm = arc_midpoints(v, x, delta, c, mu);
-        for (int a = 0; a < nm; ++a) memcpy(pts[n++], mu[a], sizeof(double) * 3);
+        int face[4];
+        int nm = arc_midpoints(v, x, delta, c, mu, face);
+        for (int a = 0; a < nm; ++a) {
+            lab[n] = 1u << face[a];
+            memcpy(pts[n++], mu[a], sizeof(double) * 3);
+        }
     }
-    int k = or_hull_tets(n, &pts[0][0], &cells[0][0][0], maxcells);
+    int k = or_hull_tets_labeled(n, &pts[0][0], lab, &cells[0][0][0], maxcells);
     return k < 0 ? 0 : k;
 }
 

@@ -17,6 +17,7 @@ int64_t or_pairs(const double *verts, int64_t nv, const int32_t *tets, int64_t n
                  const int32_t *outer_list, int64_t n_list,
                  int64_t *ptr_out, int32_t *tp_out, int64_t cap);
 int or_hull_tets(int n, const double *p, double *out, int maxout);
+int or_hull_tets_labeled(int n, const double *p, const unsigned *lab, double *out, int maxout);
 void or_mc_point(const double *S, int ns, const uint32_t u[4], double y[3], int *which);
 int or_region_moments(const double vTp[12], const double x[3], double delta, int strategy,
                       int nmc, uint64_t seed, uint32_t idT, uint32_t idTp, uint32_t q,

@@ -58,7 +58,8 @@ class nl_csr_view(C.Structure):
 class nl_assemble_stats(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("cut_points", C.c_uint64), ("inside_points", C.c_uint64),
                 ("mc_samples", C.c_uint64), ("mc_accepted", C.c_uint64), ("hull_fallbacks", C.c_uint64),
-                ("quadrature_ms", C.c_double), ("reduce_ms", C.c_double)]
+                ("quadrature_ms", C.c_double), ("reduce_ms", C.c_double), ("classify_ms", C.c_double),
+                ("events_ms", C.c_double), ("combine_ms", C.c_double)]
 
 
 class nl_solve_opts(C.Structure):

@@ -15,10 +15,19 @@
 #include "nl_internal.h"
 #include "nl_quad.cuh"
 
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 namespace nla {
 
 using nlq::Mom;
 using nlq::P3;
+
+// Work is cut into chunks of outer elements so that the per-(pair, point)
+// records stay bounded in size.
+constexpr int64_t kUnitsPerChunk = int64_t(1) << 25;
 
 struct AsmArgs {
     const double4 *verts;
@@ -27,25 +36,42 @@ struct AsmArgs {
     const uint8_t *in_omega;
     const double *tet_vol;
     const int32_t *outer_ids;
+    const int32_t *outer_of;
     const double *xq;
+    const float *xq_hl;      // [n_outer][4][6] outer points as float hi, lo parts
     const int64_t *pair_ptr;
     const int32_t *pair_tp;
+    const int32_t *pair_T;
     const int64_t *rowptr;
     const int32_t *col;
     const int64_t *strip_off;
-    int64_t n_outer;
+    int64_t o0, o1;          // outer elements of this chunk
+    int64_t p0, p1;          // pairs of this chunk
     int max_row;
     double delta2;
+    float delta2f;
     double half_gamma;
     int nmc;
-    uint2 key;
+    uint32_t rk[20];         // Philox round keys
+    // per-chunk work arrays
+    uint8_t *uinfo;          // [4*(p1-p0)] vertex-inside mask | 0x10 event | 0x20 zero
+    int32_t *slot;           // [4*(p1-p0)] class*units + index within the class, or -1
+    int32_t *evu;            // [4][units] unit of each event, per class (m = 0..3)
+    int *nev;                // [5] event count per class; nev[4] = deferred events
+    int32_t *fix;            // [units] FP32 approxcaps events deferred to the FP64 pass
+    void *Mq;                // [events][15] moments (R)
+    // outputs
     void *D;                 // [npairs][10] staged T'T' moments (R)
     double *strips;          // [strip_total]
     double *TT;              // [n_outer][10]
     unsigned long long *stats;  // [5]
 };
 
-constexpr int NT = 128;      // threads per block = pairs per chunk
+// barycentric weight lambda_i(x_q) of the 4-point rule: a on i == q, b elsewhere
+template <class R> __device__ __forceinline__ R qlam(int i, int q)
+{
+    return (i == q) ? R(0x1.2bbae2a27f931p-1) : R(0x1.1b06d1d200913p-3);
+}
 
 __device__ __forceinline__ int lower_bound_s(const int32_t *a, int n, int32_t key)
 {
@@ -57,30 +83,213 @@ __device__ __forceinline__ int lower_bound_s(const int32_t *a, int n, int32_t ke
     return lo;
 }
 
-// barycentric weight lambda_i(x_q) of the 4-point rule: a on i == q, b elsewhere
-template <class R> __device__ __forceinline__ R qlam(int i, int q)
+// T' vertex coordinates for the point x_q: global FP64 (R = double) or
+// relative to x_q as double-float differences (R = float), plus the FP64
+// context for the FP32 path's exact decisions.
+template <class R>
+__device__ __forceinline__ void load_point_geometry(const AsmArgs &A, int4 eP, int64_t o, int q, P3<R> v[4],
+                                                    P3<R> &x, nlq::Strict &sx)
 {
-    return (i == q) ? R(0x1.2bbae2a27f931p-1) : R(0x1.1b06d1d200913p-3);
+    const int ids[4] = {eP.x, eP.y, eP.z, eP.w};
+    const double *xq = A.xq + 12 * o + 3 * q;
+    if (sizeof(R) == 8) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double4 g = A.verts[ids[k]];
+            v[k] = nlq::mk3<R>((R)g.x, (R)g.y, (R)g.z);
+        }
+        x = nlq::mk3<R>((R)xq[0], (R)xq[1], (R)xq[2]);
+    } else {
+        const float *xh = A.xq_hl + 24 * o + 6 * q;   // hi xyz, lo xyz
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float4 h = A.vhi[ids[k]], l = A.vlo[ids[k]];
+            v[k] = nlq::mk3<R>((R)((h.x - xh[0]) + (l.x - xh[3])), (R)((h.y - xh[1]) + (l.y - xh[4])),
+                               (R)((h.z - xh[2]) + (l.z - xh[5])));
+        }
+        x = nlq::mk3<R>(R(0), R(0), R(0));
+        sx.verts = A.verts;
+        sx.e = eP;
+        sx.x = xq;
+        sx.d2 = A.delta2;
+    }
 }
 
+// ---------------------------------------------------------------------------
+// K1: classify every (pair, point) unit of the chunk; units with a cut (1..3
+// vertices inside, or a fullcaps cap without inside vertices) become events.
 template <class R, int STRAT>
-__global__ void __launch_bounds__(NT) k_assemble(AsmArgs A)
+__global__ void __launch_bounds__(256) k_classify(const __grid_constant__ AsmArgs A)
+{
+    const int64_t nu = 4 * (A.p1 - A.p0);
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nu; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = base + threadIdx.x;
+        bool ev = false;
+        uint8_t info = 0x20;
+        if (u < nu) {
+            const int64_t p = A.p0 + (u >> 2);
+            const int q = (int)(u & 3);
+            const int32_t T = A.pair_T[p], Tp = A.pair_tp[p];
+            const int32_t o = A.outer_of[T];
+            P3<R> v[4];
+            P3<R> x;
+            nlq::Strict sx;
+            load_point_geometry<R>(A, A.tets[Tp], o, q, v, x, sx);
+            const nlq::Strict *sp = (sizeof(R) == 4) ? &sx : nullptr;
+            const int inm = nlq::classify(v, x, (R)A.delta2f, sp);
+            info = (uint8_t)inm;
+            if (inm != 15) {
+                if (inm != 0) ev = true;
+                else if (STRAT == 2 && A.nmc > 0) ev = nlq::meets_ball(v, x, (R)A.delta2f, sp);
+                if (ev) info |= 0x10;
+                else info |= 0x20;
+            }
+        }
+        // warp-aggregated slot allocation within the event's class (number of
+        // inside vertices), so that each warp of K2 runs one geometry case
+        const int cls = __popc((unsigned)(info & 15));
+        int32_t sl = -1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const unsigned mm = __ballot_sync(0xffffffffu, ev && cls == c);
+            int basep = 0;
+            if (lane == 0 && mm) basep = atomicAdd(&A.nev[c], __popc(mm));
+            basep = __shfl_sync(0xffffffffu, basep, 0);
+            if (ev && cls == c) {
+                const int idx = basep + __popc(mm & ((1u << lane) - 1u));
+                sl = (int32_t)(c * nu + idx);
+                A.evu[c * nu + idx] = (int32_t)u;
+            }
+        }
+        if (u < nu) {
+            A.uinfo[u] = info;
+            A.slot[u] = sl;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2: one thread per event: cells of hull(I u P) and, for fullcaps, the
+// Monte Carlo loop over the cap (uniform trip count across the warp).
+template <class R> struct EvCfg {
+    static constexpr int threads = sizeof(R) == 4 ? 128 : 64;
+    static constexpr size_t smem = sizeof(R) * threads * 3 * nlq::CB_STRIDE;
+};
+
+template <class R, int STRAT>
+__global__ void __launch_bounds__(EvCfg<R>::threads, 6) k_events(const __grid_constant__ AsmArgs A)
+{
+    extern __shared__ __align__(16) unsigned char evsm[];
+    R *cb = reinterpret_cast<R *>(evsm) + 3 * nlq::CB_STRIDE * threadIdx.x;
+    nlq::Stats st{0, 0, 0, 0, 0};
+    const int64_t nu = 4 * (A.p1 - A.p0);
+    const int n0 = A.nev[0], n1 = A.nev[1], n2 = A.nev[2], n3 = A.nev[3];
+    const int nev = n0 + n1 + n2 + n3;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nev; e += gridDim.x * blockDim.x) {
+        // compact event index -> (class, index within the class)
+        int c = 0, idx = e;
+        if (idx >= n0) { idx -= n0; c = 1;
+            if (idx >= n1) { idx -= n1; c = 2;
+                if (idx >= n2) { idx -= n2; c = 3; } } }
+        const int32_t u = A.evu[c * nu + idx];
+        const int64_t p = A.p0 + (u >> 2);
+        const int q = u & 3;
+        const int32_t T = A.pair_T[p], Tp = A.pair_tp[p];
+        const int32_t o = A.outer_of[T];
+        P3<R> v[4];
+        P3<R> x;
+        nlq::Strict sx;
+        load_point_geometry<R>(A, A.tets[Tp], o, q, v, x, sx);
+        const int inm = A.uinfo[u] & 15;
+        R *out = reinterpret_cast<R *>(A.Mq) + 15 * (int64_t)e;
+        const bool deferred = nlq::event_moments<R, STRAT>(v, x, sizeof(R) == 4 ? (R)A.delta2f : (R)A.delta2, inm,
+                                                           A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q, out,
+                                                           st, (sizeof(R) == 4) ? &sx : nullptr, cb);
+        if (deferred) A.fix[atomicAdd(&A.nev[4], 1)] = e;
+    }
+    __shared__ unsigned long long sstat[4];
+    if (threadIdx.x < 4) sstat[threadIdx.x] = 0ULL;
+    __syncthreads();
+    if (st.cut) atomicAdd(&sstat[0], (unsigned long long)st.cut);
+    if (st.mc) atomicAdd(&sstat[1], (unsigned long long)st.mc);
+    if (st.acc) atomicAdd(&sstat[2], (unsigned long long)st.acc);
+    if (st.fallback) atomicAdd(&sstat[3], (unsigned long long)st.fallback);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (sstat[0]) atomicAdd(&A.stats[0], sstat[0]);
+        if (sstat[1]) atomicAdd(&A.stats[2], sstat[1]);
+        if (sstat[2]) atomicAdd(&A.stats[3], sstat[2]);
+        if (sstat[3]) atomicAdd(&A.stats[4], sstat[3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2b (FP32 approxcaps only): the events that K2 deferred are recomputed with
+// the FP64 event code on global coordinates (same classification), and the
+// moments stored in the event's FP32 record.
+template <int STRAT>
+__global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmArgs A)
+{
+    nlq::Stats st{0, 0, 0, 0, 0};
+    const int64_t nu = 4 * (A.p1 - A.p0);
+    const int n0 = A.nev[0], n1 = A.nev[1], n2 = A.nev[2], nf = A.nev[4];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+        const int e = A.fix[i];
+        int c = 0, idx = e;
+        if (idx >= n0) { idx -= n0; c = 1;
+            if (idx >= n1) { idx -= n1; c = 2;
+                if (idx >= n2) { idx -= n2; c = 3; } } }
+        const int32_t u = A.evu[c * nu + idx];
+        const int64_t p = A.p0 + (u >> 2);
+        const int q = u & 3;
+        const int32_t T = A.pair_T[p], Tp = A.pair_tp[p];
+        const int32_t o = A.outer_of[T];
+        P3<double> v[4];
+        P3<double> x;
+        nlq::Strict sx;
+        load_point_geometry<double>(A, A.tets[Tp], o, q, v, x, sx);
+        const int inm = A.uinfo[u] & 15;
+        double m15[15];
+        nlq::event_moments<double, STRAT>(v, x, A.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q,
+                                          m15, st, nullptr, nullptr);
+        float *out = reinterpret_cast<float *>(A.Mq) + 15 * (int64_t)e;
+#pragma unroll
+        for (int k = 0; k < 15; ++k) out[k] = (float)m15[k];
+    }
+    if (st.fallback) atomicAdd(&A.stats[4], (unsigned long long)st.fallback);
+}
+
+// ---------------------------------------------------------------------------
+// K3: one block per outer element T (persistent over the chunk's outer
+// elements), one thread per pair: combine the four points of each pair into
+// the staged T'T' moments, the TT sums and the cross strips:
+//   TT   += c omega lambda(x_q) lambda(x_q)^T m0     (V_q summed per T)
+//   TT'  -= c omega lambda(x_q) m1^T                  (strip rows of T's nodes)
+//   T'T' += c omega m2                                 (staged per pair)
+// with c = (gamma/2)|T|/4 and omega = 2 for collar elements T'.  Strips are
+// accumulated by one warp per row in pair order (deterministic).
+constexpr int NT = 128;
+
+template <class R>
+__global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int mr = A.max_row;
-    int32_t *cols = reinterpret_cast<int32_t *>(smem);                       // [4][mr]
+    int32_t *cols = reinterpret_cast<int32_t *>(smem);                                        // [4][mr]
     double *strip = reinterpret_cast<double *>(smem + sizeof(int32_t) * 4 * ((mr + 1) & ~1));  // [4][mr]
-    R *Xs = reinterpret_cast<R *>(strip + 4 * mr);                            // [NT][16]
-    int32_t *offs = reinterpret_cast<int32_t *>(Xs + NT * 16);                // [NT][16]
-    double *wsc = reinterpret_cast<double *>(offs + NT * 16);                 // [NT]
-    double *red = wsc + NT;                                                   // [NT/32][4]
+    R *Xs = reinterpret_cast<R *>(strip + 4 * mr);                                             // [NT][16]
+    int32_t *offs = reinterpret_cast<int32_t *>(Xs + NT * 16);                                 // [NT][16]
+    double *wsc = reinterpret_cast<double *>(offs + NT * 16);                                  // [NT]
+    double *red = wsc + NT;                                                                    // [NT/32][4]
     __shared__ int lens[4];
-    __shared__ unsigned long long sstat[5];
-
+    __shared__ unsigned long long sin_;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    nlq::Stats st{0, 0, 0, 0, 0};
+    unsigned long long inside = 0;
+    const int64_t nu = 4 * (A.p1 - A.p0);
+    const int cpre[4] = {0, A.nev[0], A.nev[0] + A.nev[1], A.nev[0] + A.nev[1] + A.nev[2]};
 
-    for (int64_t o = blockIdx.x; o < A.n_outer; o += gridDim.x) {
+    for (int64_t o = A.o0 + blockIdx.x; o < A.o1; o += gridDim.x) {
         const int32_t T = A.outer_ids[o];
         const int4 eT = A.tets[T];
         const int nodeT[4] = {eT.x, eT.y, eT.z, eT.w};
@@ -93,15 +302,9 @@ __global__ void __launch_bounds__(NT) k_assemble(AsmArgs A)
                 strip[i * mr + c] = 0.0;
             }
         }
-        double xqd[4][3];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) xqd[q][d] = A.xq[12 * o + 3 * q + d];
         const double cT = A.half_gamma * (A.tet_vol[T] * 0.25);
         double vq[4] = {0.0, 0.0, 0.0, 0.0};
         __syncthreads();
-
         const int64_t pb = A.pair_ptr[o], pe = A.pair_ptr[o + 1];
         for (int64_t base = pb; base < pe; base += NT) {
             const int cnt = (int)((pe - base) < (int64_t)NT ? (pe - base) : (int64_t)NT);
@@ -115,84 +318,54 @@ __global__ void __launch_bounds__(NT) k_assemble(AsmArgs A)
                 R Y[4][4], V[4], Dp[10];
 #pragma unroll
                 for (int k = 0; k < 10; ++k) Dp[k] = R(0);
-                P3<R> v[4];
-                if (sizeof(R) == 8) {
+                const int64_t u0 = 4 * (p - A.p0);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        double4 g = A.verts[nodeP[k]];
-                        v[k] = nlq::mk3<R>((R)g.x, (R)g.y, (R)g.z);
-                    }
-                }
-                float4 vh[4], vl[4];
-                if (sizeof(R) == 4) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) { vh[k] = A.vhi[nodeP[k]]; vl[k] = A.vlo[nodeP[k]]; }
-                }
-#pragma unroll 1
                 for (int q = 0; q < 4; ++q) {
-                    P3<R> x;
-                    P3<R> vv[4];
-                    if (sizeof(R) == 8) {
-                        x = nlq::mk3<R>((R)xqd[q][0], (R)xqd[q][1], (R)xqd[q][2]);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) vv[k] = v[k];
-                    } else {
-                        // coordinates relative to x_q as double-float differences
-                        float xh[3], xl[3];
-#pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            xh[d] = (float)xqd[q][d];
-                            xl[d] = (float)(xqd[q][d] - (double)xh[d]);
-                        }
-                        x = nlq::mk3<R>(R(0), R(0), R(0));
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            vv[k] = nlq::mk3<R>((R)((vh[k].x - xh[0]) + (vl[k].x - xl[0])),
-                                                (R)((vh[k].y - xh[1]) + (vl[k].y - xl[1])),
-                                                (R)((vh[k].z - xh[2]) + (vl[k].z - xl[2])));
-                    }
+                    const uint8_t info = A.uinfo[u0 + q];
                     Mom<R> M;
-                    nlq::Strict sx;
-                    if (sizeof(R) == 4) {
+                    if ((info & 15) == 15) {
+                        nlq::closed_form_inside(M, volTp);
+                        inside++;
+                    } else if (info & 0x10) {
+                        const int32_t sl = A.slot[u0 + q];
+                        const int cls = (int)(sl / nu), idx = (int)(sl - (int64_t)cls * nu);
+                        const int64_t ev = (int64_t)cpre[cls] + idx;
+                        const R *mq = reinterpret_cast<const R *>(A.Mq) + 15 * ev;
+                        M.m0 = mq[0];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            double4 g = A.verts[nodeP[k]];
-                            sx.v[k][0] = g.x; sx.v[k][1] = g.y; sx.v[k][2] = g.z;
-                        }
-                        sx.x[0] = xqd[q][0]; sx.x[1] = xqd[q][1]; sx.x[2] = xqd[q][2];
-                        sx.d2 = A.delta2;
+                        for (int k = 0; k < 4; ++k) M.m1[k] = mq[1 + k];
+#pragma unroll
+                        for (int k = 0; k < 10; ++k) M.m2[k] = mq[5 + k];
+                    } else {
+                        nlq::mom_zero(M);
                     }
-                    nlq::point_moments<R, STRAT>(vv, x, (R)A.delta2, volTp, A.nmc, A.key, (uint32_t)T, (uint32_t)Tp,
-                                                 (uint32_t)q, M, st, sizeof(R) == 4 ? &sx : nullptr);
                     V[q] = M.m0;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) Y[q][k] = M.m1[k];
 #pragma unroll
                     for (int k = 0; k < 10; ++k) Dp[k] += M.m2[k];
                 }
-                // staged T'T' moments (scaled later by c * omega)
                 R *Dst = reinterpret_cast<R *>(A.D) + 10 * p;
 #pragma unroll
                 for (int k = 0; k < 10; ++k) Dst[k] = Dp[k];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) vq[q] += omega * (double)V[q];
-                // cross: X[i][k] = sum_q lambda_i(x_q) m1_k(q)
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        R s = ((qlam<R>(i, 0) * Y[0][k] + qlam<R>(i, 1) * Y[1][k]) + qlam<R>(i, 2) * Y[2][k]) +
-                              qlam<R>(i, 3) * Y[3][k];
-                        Xs[tid * 16 + 4 * i + k] = s;
+                        R sum = ((qlam<R>(i, 0) * Y[0][k] + qlam<R>(i, 1) * Y[1][k]) + qlam<R>(i, 2) * Y[2][k]) +
+                                qlam<R>(i, 3) * Y[3][k];
+                        Xs[tid * 16 + 4 * i + k] = sum;
                     }
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) offs[tid * 16 + 4 * i + k] = lower_bound_s(cols + i * mr, lens[i], nodeP[k]);
+                    for (int k = 0; k < 4; ++k)
+                        offs[tid * 16 + 4 * i + k] = lower_bound_s(cols + i * mr, lens[i], nodeP[k]);
                 wsc[tid] = -(omega * cT);
             }
             __syncthreads();
-            // deterministic strip accumulation: warp i owns row i; pairs in order
             {
                 const int i = warp;
                 for (int t = 0; t < cnt; ++t) {
@@ -205,12 +378,11 @@ __global__ void __launch_bounds__(NT) k_assemble(AsmArgs A)
             }
             __syncthreads();
         }
-        // TT block: c * sum_q lambda(x_q) lambda(x_q)^T V_q, with V_q summed over the block in fixed order
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            double s = vq[q];
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == 0) red[warp * 4 + q] = s;
+            double sum = vq[q];
+            for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+            if (lane == 0) red[warp * 4 + q] = sum;
         }
         __syncthreads();
         if (tid < 10) {
@@ -220,31 +392,25 @@ __global__ void __launch_bounds__(NT) k_assemble(AsmArgs A)
             const int ia[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
             const int ib[10] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
             const int i = ia[tid], j = ib[tid];
-            double s = 0.0;
+            double sum = 0.0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) s += qlam<double>(i, q) * qlam<double>(j, q) * V[q];
-            A.TT[10 * o + tid] = cT * s;
+            for (int q = 0; q < 4; ++q) sum += qlam<double>(i, q) * qlam<double>(j, q) * V[q];
+            A.TT[10 * o + tid] = cT * sum;
         }
-        // strips out
         for (int i = 0; i < 4; ++i) {
             const int64_t so = A.strip_off[4 * o + i];
             for (int c = tid; c < lens[i]; c += NT) A.strips[so + c] = strip[i * mr + c];
         }
         __syncthreads();
     }
-    // statistics (integer atomics)
-    if (tid < 5) sstat[tid] = 0ULL;
+    if (tid == 0) sin_ = 0ULL;
     __syncthreads();
-    atomicAdd(&sstat[0], (unsigned long long)st.cut);
-    atomicAdd(&sstat[1], (unsigned long long)st.inside);
-    atomicAdd(&sstat[2], (unsigned long long)st.mc);
-    atomicAdd(&sstat[3], (unsigned long long)st.acc);
-    atomicAdd(&sstat[4], (unsigned long long)st.fallback);
+    if (inside) atomicAdd(&sin_, inside);
     __syncthreads();
-    if (tid < 5 && sstat[tid]) atomicAdd(&A.stats[tid], sstat[tid]);
+    if (tid == 0 && sin_) atomicAdd(&A.stats[1], sin_);
 }
 
-inline size_t asm_smem_bytes(int max_row, size_t real_size)
+inline size_t combine_smem_bytes(int max_row, size_t real_size)
 {
     size_t b = sizeof(int32_t) * 4 * (size_t)((max_row + 1) & ~1);
     b += sizeof(double) * 4 * (size_t)max_row;
@@ -255,37 +421,127 @@ inline size_t asm_smem_bytes(int max_row, size_t real_size)
     return b;
 }
 
+inline void philox_round_keys(uint64_t seed, uint32_t rk[20])
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+}
+
+template <class R, int STRAT>
+void run_chunks(nl_system *sys, AsmArgs &A)
+{
+    nl_pairs *P = sys->pairs;
+    nl_mesh *m = P->mesh;
+    cudaStream_t s = sys->arena.stream();
+    // chunk sizes
+    std::vector<int64_t> hp(m->n_outer + 1);
+    NL_CUDA(cudaMemcpyAsync(hp.data(), P->pair_ptr, sizeof(int64_t) * (m->n_outer + 1), cudaMemcpyDeviceToHost, s));
+    NL_CUDA(cudaStreamSynchronize(s));
+    int64_t max_units = 0;
+    std::vector<std::pair<int64_t, int64_t>> chunks;
+    for (int64_t o = 0; o < m->n_outer;) {
+        int64_t o1 = o + 1;
+        while (o1 < m->n_outer && 4 * (hp[o1 + 1] - hp[o]) <= kUnitsPerChunk) ++o1;
+        chunks.push_back({o, o1});
+        max_units = std::max<int64_t>(max_units, 4 * (hp[o1] - hp[o]));
+        o = o1;
+    }
+    Scratch sc(&sys->arena);
+    A.uinfo = sc.get<uint8_t>(max_units);
+    A.slot = sc.get<int32_t>(max_units);
+    A.evu = sc.get<int32_t>(4 * max_units);
+    A.nev = sc.get<int>(5);
+    constexpr bool kDefer = sizeof(R) == 4 && STRAT == 1;
+    A.fix = kDefer ? sc.get<int32_t>(max_units) : nullptr;
+    A.Mq = (void *)sc.get<R>(15 * max_units);
+    const size_t smem = combine_smem_bytes(P->max_row, sizeof(R));
+    NL_REQUIRE(smem <= 220 * 1024, "rows of %d columns need %zu bytes of shared memory", P->max_row, smem);
+    NL_CUDA(cudaFuncSetAttribute(k_combine<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<R>, NT, smem));
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    int ev_per_sm = 0;
+    constexpr int ET = EvCfg<R>::threads;
+    constexpr size_t ESM = EvCfg<R>::smem;
+    NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
+    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, k_events<R, STRAT>, ET, ESM));
+    ev_per_sm = ev_per_sm < 1 ? 1 : ev_per_sm;
+    const int sms = nl_num_sms();
+    // per-kernel durations (CUDA events on the assembly stream)
+    std::vector<cudaEvent_t> ev(4 * chunks.size());
+    for (auto &e : ev) NL_CUDA(cudaEventCreate(&e));
+    size_t ci = 0;
+    for (auto &c : chunks) {
+        A.o0 = c.first; A.o1 = c.second;
+        A.p0 = hp[c.first]; A.p1 = hp[c.second];
+        const int64_t nu = 4 * (A.p1 - A.p0);
+        NL_CUDA(cudaMemsetAsync(A.nev, 0, 5 * sizeof(int), s));
+        unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, 256), (int64_t)sms * 32));
+        NL_CUDA(cudaEventRecord(ev[4 * ci], s));
+        { k_classify<R, STRAT><<<g1, 256, 0, s>>>(A); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        NL_CUDA(cudaEventRecord(ev[4 * ci + 1], s));
+        // enough resident threads for the largest possible event count; the
+        // kernel reads the actual count from device memory
+        unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, ET), (int64_t)sms * ev_per_sm));
+        { k_events<R, STRAT><<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        if constexpr (kDefer) {
+            { k_events_fp64<STRAT><<<(unsigned)(2 * sms), 64, 0, s>>>(A); nl_count_launch(); }
+            NL_CHECK_LAUNCH();
+        }
+        NL_CUDA(cudaEventRecord(ev[4 * ci + 2], s));
+        int64_t no = A.o1 - A.o0;
+        unsigned g3 = (unsigned)std::min<int64_t>(no, (int64_t)sms * per_sm);
+        { k_combine<R><<<g3, NT, smem, s>>>(A); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        NL_CUDA(cudaEventRecord(ev[4 * ci + 3], s));
+        ++ci;
+    }
+    NL_CUDA(cudaStreamSynchronize(s));
+    double t[3] = {0.0, 0.0, 0.0};
+    for (size_t k = 0; k < chunks.size(); ++k)
+        for (int j = 0; j < 3; ++j) {
+            float ms = 0.f;
+            NL_CUDA(cudaEventElapsedTime(&ms, ev[4 * k + j], ev[4 * k + j + 1]));
+            t[j] += ms;
+        }
+    for (auto &e : ev) cudaEventDestroy(e);
+    sys->stats.classify_ms = t[0];
+    sys->stats.events_ms = t[1];
+    sys->stats.combine_ms = t[2];
+}
+
 template <class R>
 void launch_assemble(nl_system *sys, void *D, double *strips, double *TT, unsigned long long *stats)
 {
     nl_pairs *P = sys->pairs;
     nl_mesh *m = P->mesh;
     AsmArgs A;
+    memset(&A, 0, sizeof(A));
     A.verts = m->verts; A.vhi = m->vhi; A.vlo = m->vlo; A.tets = m->tets; A.in_omega = m->in_omega;
-    A.tet_vol = m->tet_vol; A.outer_ids = m->outer_ids; A.xq = m->xq; A.pair_ptr = P->pair_ptr;
-    A.pair_tp = P->pair_tp; A.rowptr = P->rowptr; A.col = P->col; A.strip_off = P->strip_off;
-    A.n_outer = m->n_outer; A.max_row = P->max_row;
+    A.tet_vol = m->tet_vol; A.outer_ids = m->outer_ids; A.outer_of = m->outer_of; A.xq = m->xq;
+    A.xq_hl = m->xq_hl;
+    A.pair_ptr = P->pair_ptr; A.pair_tp = P->pair_tp; A.pair_T = P->pair_T;
+    A.rowptr = P->rowptr; A.col = P->col; A.strip_off = P->strip_off;
+    A.max_row = P->max_row;
     A.delta2 = P->delta * P->delta;
+    A.delta2f = (float)A.delta2;
     A.half_gamma = sys->opts.gamma / 2.0;
     A.nmc = sys->opts.strategy == NL_FULLCAPS ? sys->opts.mc_points : 0;
-    A.key = make_uint2((uint32_t)sys->opts.seed, (uint32_t)(sys->opts.seed >> 32));
+    philox_round_keys(sys->opts.seed, A.rk);
     A.D = D; A.strips = strips; A.TT = TT; A.stats = stats;
-    size_t smem = asm_smem_bytes(P->max_row, sizeof(R));
-    NL_REQUIRE(smem <= 220 * 1024, "rows of %d columns need %zu bytes of shared memory", P->max_row, smem);
-    void (*kern)(AsmArgs) = nullptr;
+    NL_REQUIRE(A.verts && A.vhi && A.vlo && A.tets && A.xq && A.xq_hl && A.pair_ptr && A.pair_tp && A.pair_T &&
+                   A.rowptr && A.col && A.strip_off && A.outer_of && A.outer_ids,
+               "internal: an input array of the assembly is missing");
     switch (sys->opts.strategy) {
-    case NL_NOCAPS: kern = k_assemble<R, 0>; break;
-    case NL_APPROXCAPS: kern = k_assemble<R, 1>; break;
-    default: kern = k_assemble<R, 2>; break;
+    case NL_NOCAPS: run_chunks<R, 0>(sys, A); break;
+    case NL_APPROXCAPS: run_chunks<R, 1>(sys, A); break;
+    default: run_chunks<R, 2>(sys, A); break;
     }
-    NL_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-    per_sm = per_sm < 1 ? 1 : per_sm;
-    int64_t grid = (int64_t)nl_num_sms() * per_sm;
-    if (grid > m->n_outer) grid = m->n_outer;
-    { kern<<<(unsigned)grid, NT, smem, sys->arena.stream()>>>(A); nl_count_launch(); }
-    NL_CHECK_LAUNCH();
 }
 
 }  // namespace nla
@@ -296,9 +552,14 @@ namespace nla {
 // device code (and, per translation unit, the same compiler flags) as the
 // assembly kernel.  For float, coordinates are made relative to x as
 // double-float differences exactly as in the assembly.
+struct RoundKeys {
+    uint32_t k[20];
+};
+
 template <class R, int STRAT>
-__global__ void k_probe(const double *__restrict__ tv, const double *__restrict__ xs, const uint32_t *__restrict__ ids,
-                        int64_t n, double delta2, int nmc, uint2 key, double *out)
+__global__ void k_probe(const double *__restrict__ tv, const double4 *__restrict__ tv4, const double *__restrict__ xs,
+                        const uint32_t *__restrict__ ids, int64_t n, double delta2, int nmc,
+                        const __grid_constant__ RoundKeys rk, double *out, int *defer)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
@@ -327,26 +588,55 @@ __global__ void k_probe(const double *__restrict__ tv, const double *__restrict_
     Mom<R> M;
     nlq::Stats st{0, 0, 0, 0, 0};
     nlq::Strict sx;
-    for (int k = 0; k < 4; ++k) { sx.v[k][0] = vd[k].x; sx.v[k][1] = vd[k].y; sx.v[k][2] = vd[k].z; }
-    for (int d = 0; d < 3; ++d) sx.x[d] = x[d];
+    sx.verts = tv4;
+    sx.e = make_int4((int)(4 * c), (int)(4 * c + 1), (int)(4 * c + 2), (int)(4 * c + 3));
+    sx.x = xs + 3 * c;
     sx.d2 = delta2;
-    nlq::point_moments<R, STRAT>(v, xx, (R)delta2, (R)vol, nmc, key, ids[3 * c], ids[3 * c + 1], ids[3 * c + 2], M, st,
-                                 sizeof(R) == 4 ? &sx : nullptr);
+    R cb[3 * nlq::CB_STRIDE];
+    const int d = nlq::point_moments<R, STRAT>(v, xx, (R)delta2, (R)vol, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
+                                               ids[3 * c + 2], M, st, sizeof(R) == 4 ? &sx : nullptr, cb);
+    defer[c] = d;
+    if (d) return;
     out[15 * c] = (double)M.m0;
     for (int k = 0; k < 4; ++k) out[15 * c + 1 + k] = (double)M.m1[k];
     for (int k = 0; k < 10; ++k) out[15 * c + 5 + k] = (double)M.m2[k];
 }
 
-template <class R>
-void launch_probe(const double *tv, const double *xs, const uint32_t *ids, int64_t n, double delta2, int strategy,
-                  int nmc, uint64_t seed, double *out)
+// The deferred FP32 cases (defer[c] = classification + 1), recomputed with
+// the FP64 event code and rounded through float as in the assembly's records.
+template <int STRAT>
+__global__ void k_probe_fp64(const double *__restrict__ tv, const double *__restrict__ xs,
+                             const uint32_t *__restrict__ ids, int64_t n, double delta2, int nmc,
+                             const __grid_constant__ RoundKeys rk, double *out, const int *defer)
 {
-    uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n || defer[c] == 0) return;
+    const double *t = tv + 12 * c;
+    P3<double> v[4];
+    for (int k = 0; k < 4; ++k) v[k] = nlq::mk3<double>(t[3 * k], t[3 * k + 1], t[3 * k + 2]);
+    P3<double> x = nlq::mk3<double>(xs[3 * c], xs[3 * c + 1], xs[3 * c + 2]);
+    nlq::Stats st{0, 0, 0, 0, 0};
+    double m15[15];
+    nlq::event_moments<double, STRAT>(v, x, delta2, defer[c] - 1, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
+                                      ids[3 * c + 2], m15, st, nullptr, nullptr);
+    for (int k = 0; k < 15; ++k) out[15 * c + k] = (double)(float)m15[k];
+}
+
+template <class R>
+void launch_probe(const double *tv, const double4 *tv4, const double *xs, const uint32_t *ids, int64_t n,
+                  double delta2, int strategy, int nmc, uint64_t seed, double *out, int *defer)
+{
+    RoundKeys key;
+    philox_round_keys(seed, key.k);
     unsigned blocks = (unsigned)((n + 127) / 128);
-    if (strategy == NL_NOCAPS) { k_probe<R, 0><<<blocks, 128>>>(tv, xs, ids, n, delta2, 0, key, out); nl_count_launch(); }
-    else if (strategy == NL_APPROXCAPS) { k_probe<R, 1><<<blocks, 128>>>(tv, xs, ids, n, delta2, 0, key, out); nl_count_launch(); }
-    else { k_probe<R, 2><<<blocks, 128>>>(tv, xs, ids, n, delta2, nmc, key, out); nl_count_launch(); }
+    if (strategy == NL_NOCAPS) { k_probe<R, 0><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
+    else if (strategy == NL_APPROXCAPS) { k_probe<R, 1><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
+    else { k_probe<R, 2><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, nmc, key, out, defer); nl_count_launch(); }
     NL_CHECK_LAUNCH();
+    if (sizeof(R) == 4 && strategy == NL_APPROXCAPS) {
+        { k_probe_fp64<1><<<blocks, 64 * 2>>>(tv, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+    }
 }
 
 }  // namespace nla

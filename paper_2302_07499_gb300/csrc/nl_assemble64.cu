@@ -9,8 +9,8 @@ void nl_assemble_fp64(nl_system *sys, double *D, double *strips, double *TT, uin
     nla::launch_assemble<double>(sys, D, strips, TT, reinterpret_cast<unsigned long long *>(stats));
 }
 
-void nl_probe_fp64(const double *tv, const double *xs, const uint32_t *ids, int64_t n, double delta2, int strategy,
-                   int nmc, uint64_t seed, double *out)
+void nl_probe_fp64(const double *tv, const double4 *tv4, const double *xs, const uint32_t *ids, int64_t n, double delta2, int strategy,
+                   int nmc, uint64_t seed, double *out, int *defer)
 {
-    nla::launch_probe<double>(tv, xs, ids, n, delta2, strategy, nmc, seed, out);
+    nla::launch_probe<double>(tv, tv4, xs, ids, n, delta2, strategy, nmc, seed, out, defer);
 }

@@ -80,6 +80,7 @@ struct nl_mesh {
     int32_t *outer_ids = nullptr;  // Omega elements, increasing id
     int32_t *outer_of = nullptr;   // element -> outer index or -1
     double *xq = nullptr;          // [n_outer][4][3] quadrature points
+    float *xq_hl = nullptr;        // [n_outer][4][6] the same as float hi xyz, lo xyz
     int32_t *free_idx = nullptr;   // node -> free index or -1
     int32_t *free_nodes = nullptr; // [n_free]
     int64_t *ne_ptr = nullptr;     // node -> incident elements (sorted), packed elem<<2|local

@@ -112,7 +112,7 @@ __global__ void k_compact_flags(const uint8_t *__restrict__ f, const int64_t *__
 }
 
 __global__ void k_quad_points(const double4 *__restrict__ verts, const int4 *__restrict__ tets,
-                              const int32_t *__restrict__ outer_ids, int64_t n_outer, double *xq)
+                              const int32_t *__restrict__ outer_ids, int64_t n_outer, double *xq, float *xq_hl)
 {
     int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= n_outer) return;
@@ -124,6 +124,12 @@ __global__ void k_quad_points(const double4 *__restrict__ verts, const int4 *__r
         xq[12 * o + 3 * q + 0] = kQB * s[0] + kQAB * v[q].x;
         xq[12 * o + 3 * q + 1] = kQB * s[1] + kQAB * v[q].y;
         xq[12 * o + 3 * q + 2] = kQB * s[2] + kQAB * v[q].z;
+        for (int d = 0; d < 3; ++d) {
+            double x = xq[12 * o + 3 * q + d];
+            float h = (float)x;
+            xq_hl[24 * o + 6 * q + d] = h;
+            xq_hl[24 * o + 6 * q + 3 + d] = (float)(x - (double)h);
+        }
     }
 }
 
@@ -756,7 +762,8 @@ extern "C" nl_status nl_mesh_create(const nl_device *dev, const double *verts, i
         { k_compact_flags<<<blocks_for(nv, 256), 256, 0, s>>>(m->node_free, off, m->free_nodes, m->free_idx, nv); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         m->xq = m->arena.get<double>(12 * m->n_outer);
-        { k_quad_points<<<blocks_for(m->n_outer, 128), 128, 0, s>>>(m->verts, m->tets, m->outer_ids, m->n_outer, m->xq); nl_count_launch(); }
+        m->xq_hl = m->arena.get<float>(24 * m->n_outer);
+        { k_quad_points<<<blocks_for(m->n_outer, 128), 128, 0, s>>>(m->verts, m->tets, m->outer_ids, m->n_outer, m->xq, m->xq_hl); nl_count_launch(); }
         NL_CHECK_LAUNCH();
 
         // node -> incident elements, sorted by element id

@@ -5,8 +5,10 @@
 #include "nl_internal.h"
 #include "nl_quad.cuh"
 
-void nl_probe_fp64(const double *, const double *, const uint32_t *, int64_t, double, int, int, uint64_t, double *);
-void nl_probe_fp32(const double *, const double *, const uint32_t *, int64_t, double, int, int, uint64_t, double *);
+void nl_probe_fp64(const double *, const double4 *, const double *, const uint32_t *, int64_t, double, int, int,
+                   uint64_t, double *, int *);
+void nl_probe_fp32(const double *, const double4 *, const double *, const uint32_t *, int64_t, double, int, int,
+                   uint64_t, double *, int *);
 
 namespace {
 __global__ void k_philox(const uint4 *__restrict__ ctr, uint2 key, int64_t n, uint4 *out)
@@ -46,8 +48,15 @@ extern "C" nl_status nl_probe_moments(const double *tets_xyz, const double *x, c
         NL_CUDA(cudaMemcpy(dv, tets_xyz, sizeof(double) * 12 * n, cudaMemcpyHostToDevice));
         NL_CUDA(cudaMemcpy(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
         NL_CUDA(cudaMemcpy(di, ids, sizeof(uint32_t) * 3 * n, cudaMemcpyHostToDevice));
-        if (precision == NL_FP64) nl_probe_fp64(dv, dx, di, n, delta * delta, strategy, mc_points, seed, dm);
-        else nl_probe_fp32(dv, dx, di, n, delta * delta, strategy, mc_points, seed, dm);
+        // the same coordinates as a vertex table (4 vertices per case) for the exact decisions
+        std::vector<double4> h4(4 * n);
+        for (int64_t i = 0; i < 4 * n; ++i)
+            h4[i] = make_double4(tets_xyz[3 * i], tets_xyz[3 * i + 1], tets_xyz[3 * i + 2], 0.0);
+        double4 *dv4 = t.get<double4>(4 * n);
+        NL_CUDA(cudaMemcpy(dv4, h4.data(), sizeof(double4) * 4 * n, cudaMemcpyHostToDevice));
+        int *dd = t.get<int>(n);
+        if (precision == NL_FP64) nl_probe_fp64(dv, dv4, dx, di, n, delta * delta, strategy, mc_points, seed, dm, dd);
+        else nl_probe_fp32(dv, dv4, dx, di, n, delta * delta, strategy, mc_points, seed, dm, dd);
         NL_CUDA(cudaMemcpy(moments, dm, sizeof(double) * 15 * n, cudaMemcpyDeviceToHost));
     } catch (NlError &e) {
         return e.st;

@@ -53,13 +53,24 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
-// uniforms in (0,1): FP64 (u + 0.5) 2^-32 (exact); FP32 ((u >> 8) + 0.5) 2^-24 (exact)
+// Uniforms.  FP64: U = (u + 0.5) 2^-32 in (0,1) and u 2^-32 in [0,1), both
+// exact.  FP32: the top 23 bits, U = (k + 0.5) 2^-23 and k 2^-23 with
+// k = u >> 9, built from the bit pattern of 1 + k 2^-23 (exact, and no
+// integer-to-float conversion instruction).  The FP32 values differ from the
+// FP64 ones by less than 2^-23; decisions within the FP32 margins are
+// retaken with the FP64 values.
 template <class R> __device__ __forceinline__ R unif(uint32_t u);
 template <> __device__ __forceinline__ double unif<double>(uint32_t u) { return ((double)u + 0.5) * 0x1p-32; }
-template <> __device__ __forceinline__ float unif<float>(uint32_t u) { return ((float)(u >> 8) + 0.5f) * 0x1p-24f; }
+template <> __device__ __forceinline__ float unif<float>(uint32_t u)
+{
+    return __uint_as_float(0x3f800000u | (u >> 9)) - (1.0f - 0x1p-24f);
+}
 template <class R> __device__ __forceinline__ R unit_scale(uint32_t u);
 template <> __device__ __forceinline__ double unit_scale<double>(uint32_t u) { return (double)u * 0x1p-32; }
-template <> __device__ __forceinline__ float unit_scale<float>(uint32_t u) { return (float)(u >> 8) * 0x1p-24f; }
+template <> __device__ __forceinline__ float unit_scale<float>(uint32_t u)
+{
+    return __uint_as_float(0x3f800000u | (u >> 9)) - 1.0f;
+}
 
 // ---------------------------------------------------------------------------
 template <class R> struct Mom {
@@ -201,9 +212,10 @@ template <class R> __device__ R d2_point_tet(P3<R> p, const P3<R> v[4])
 // nearest intrinsics so that no multiply-add is fused.  The decisions of the
 // FP32 path therefore equal those of the FP64 path.
 struct Strict {
-    double v[4][3];   // global coordinates of T'
-    double x[3];      // outer point
-    double d2;        // delta^2
+    const double4 *verts;   // global vertex table (FP64)
+    int4 e;                 // vertex ids of T'
+    const double *x;        // outer point, 3 doubles
+    double d2;              // delta^2
 };
 
 __device__ __forceinline__ double sadd(double a, double b) { return __dadd_rn(a, b); }
@@ -249,43 +261,439 @@ __device__ __forceinline__ void sedge(const double vi[3], const double vo[3], co
     for (int d = 0; d < 3; ++d) p[d] = sadd(vi[d], smul(t, e[d]));
 }
 
+__device__ __forceinline__ void strict_load(const Strict *sx, double v[4][3], double x[3])
+{
+    const int ids[4] = {sx->e.x, sx->e.y, sx->e.z, sx->e.w};
+    for (int k = 0; k < 4; ++k) {
+        double4 g = sx->verts[ids[k]];
+        v[k][0] = g.x; v[k][1] = g.y; v[k][2] = g.z;
+    }
+    x[0] = sx->x[0]; x[1] = sx->x[1]; x[2] = sx->x[2];
+}
+
+// FP64 inside test of vertex k (specification order).
+static __device__ __noinline__ bool strict_inside(const Strict *sx, int k)
+{
+    double v[4][3], x[3];
+    strict_load(sx, v, x);
+    return sr2(v[k], x) < sx->d2;
+}
+
+// FP64 m=2 diagonal: true for the c2-d1 diagonal.
+static __device__ __noinline__ bool strict_diag(const Strict *sx, int r0, int r1, int r2, int r3)
+{
+    double v[4][3], x[3];
+    strict_load(sx, v, x);
+    double P64[4][3];
+    sedge(v[r0], v[r2], x, sx->d2, P64[0]);
+    sedge(v[r0], v[r3], x, sx->d2, P64[1]);
+    sedge(v[r1], v[r2], x, sx->d2, P64[2]);
+    sedge(v[r1], v[r3], x, sx->d2, P64[3]);
+    double q1 = sorient(P64[0], P64[2], P64[3], P64[1]);
+    double q2 = sorient(P64[0], P64[2], P64[3], v[r0]);
+    return (q1 > 0.0 && q2 < 0.0) || (q1 < 0.0 && q2 > 0.0);
+}
+
+// FP64 data of one event's cap built on the first exact decision: the edge
+// points and the cell volumes (local memory; used only on that rare path).
+struct StrictCap {
+    int ready;
+    double P[4][3];
+    double vol[3];
+    double tot;
+};
+
+// The specification's FP64 sample for the Philox words u.  The cap cells are
+// described by their packed point indices (3 bits per point, 4 points per
+// cell, ns cells) and the edge points (2+2 bits: inside, outside vertex).
+static __device__ __noinline__ int strict_sample(const Strict *sx, StrictCap *cap, unsigned long long spack, int ns,
+                                                 uint32_t pdpack, int np, uint4 u, int *jout)
+{
+    double v[4][3], x[3];
+    strict_load(sx, v, x);
+    if (!cap->ready) {
+        for (int n = 0; n < np; ++n) {
+            int i = (pdpack >> (4 * n)) & 3, o = (pdpack >> (4 * n + 2)) & 3;
+            sedge(v[i], v[o], x, sx->d2, cap->P[n]);
+        }
+        double tot = 0.0;
+        for (int jj = 0; jj < ns; ++jj) {
+            const double *c[4];
+            for (int kk = 0; kk < 4; ++kk) {
+                int pidx = (int)((spack >> (3 * (4 * jj + kk))) & 7);
+                c[kk] = pidx < 4 ? v[pidx] : cap->P[pidx - 4];
+            }
+            cap->vol[jj] = svol4(c[0], c[1], c[2], c[3]);
+            tot = sadd(tot, cap->vol[jj]);
+        }
+        cap->tot = tot;
+        cap->ready = 1;
+    }
+    double rd = smul((double)u.x * 0x1p-32, cap->tot);
+    int j64 = ns - 1;
+    double c64 = 0.0;
+    for (int jj = 0; jj < ns; ++jj) {
+        c64 = sadd(c64, cap->vol[jj]);
+        if (rd < c64) { j64 = jj; break; }
+    }
+    double V0 = ((double)u.y + 0.5) * 0x1p-32, V1 = ((double)u.z + 0.5) * 0x1p-32, V2 = ((double)u.w + 0.5) * 0x1p-32,
+           tv;
+    if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
+    if (V1 > V2) { tv = V1; V1 = V2; V2 = tv; }
+    if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
+    double b0 = V0, b1 = ssub(V1, V0), b2 = ssub(V2, V1), b3 = ssub(1.0, V2);
+    const double *c[4];
+    for (int kk = 0; kk < 4; ++kk) {
+        int pidx = (int)((spack >> (3 * (4 * j64 + kk))) & 7);
+        c[kk] = pidx < 4 ? v[pidx] : cap->P[pidx - 4];
+    }
+    double wy[3];
+    for (int d = 0; d < 3; ++d) {
+        double yd = sadd(sadd(sadd(smul(b0, c[0][d]), smul(b1, c[1][d])), smul(b2, c[2][d])), smul(b3, c[3][d]));
+        wy[d] = ssub(yd, x[d]);
+    }
+    *jout = j64;
+    return sdot(wy, wy) <= sx->d2 ? 1 : 0;
+}
+
+static __device__ __noinline__ bool strict_meets(const Strict *sx)
+{
+    double v[4][3], x[3];
+    strict_load(sx, v, x);
+    P3<double> vd[4];
+    for (int k = 0; k < 4; ++k) vd[k] = mk3<double>(v[k][0], v[k][1], v[k][2]);
+    return d2_point_tet(mk3<double>(x[0], x[1], x[2]), vd) <= sx->d2;
+}
+
 struct Stats {
     uint32_t cut, inside, mc, acc, fallback;
 };
 
-// Approximate-ball moments for one element T' and one outer point x.
-//  v[4]  vertex coordinates (global for double, relative to x for float)
-//  x     outer point (global for double, zero for float)
-//  volTp |T'|
-template <class R, int STRAT>
-__device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, uint2 key, uint32_t idT,
-                              uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st, const Strict *sx = nullptr)
+// ---------------------------------------------------------------------------
+// Classification of the four vertices of T' against the open ball around x
+// (Def. simplex's dividing strategy): bit k of the result is set when
+// |v_k - x|^2 < delta^2.  The FP32 path decides within a 1e-5 relative margin
+// of the sphere with the FP64 specification (sx).
+template <class R>
+__device__ __forceinline__ int classify(const P3<R> v[4], P3<R> x, R d2, const Strict *sx)
 {
     constexpr bool F32 = sizeof(R) == 4;
-    const R MARGIN = R(1e-5);
-    mom_zero(M);
-    R r2[4];
     int inm = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         P3<R> w = sub(v[k], x);
-        r2[k] = (w.x * w.x + w.y * w.y) + w.z * w.z;
-        bool in = r2[k] < d2;
-        if (F32 && sx && absr(r2[k] - d2) <= MARGIN * d2) in = sr2(sx->v[k], sx->x) < sx->d2;
+        R r2 = (w.x * w.x + w.y * w.y) + w.z * w.z;
+        bool in = r2 < d2;
+        if (F32 && sx && absr(r2 - d2) <= R(1e-5) * d2) in = strict_inside(sx, k);
         if (in) inm |= 1 << k;
     }
-    const int m = __popc(inm);
-    if (m == 4) {
-        st.inside++;
-        M.m0 = volTp;
-        R q4 = volTp * R(0.25), q20 = volTp * R(0.05), q10 = volTp * R(0.1);
+    return inm;
+}
+
+// Whether T' meets the closed ball when no vertex is inside (the fullcaps
+// cap of Alg. 4 exists only then).
+template <class R>
+__device__ __forceinline__ bool meets_ball(const P3<R> v[4], P3<R> x, R d2, const Strict *sx)
+{
+    constexpr bool F32 = sizeof(R) == 4;
+    R dd = d2_point_tet(x, v);
+    bool run = dd <= d2;
+    if (F32 && sx && absr(dd - d2) <= R(1e-4) * d2) run = strict_meets(sx);
+    return run;
+}
+
+template <class R> __device__ __forceinline__ void closed_form_inside(Mom<R> &M, R volTp)
+{
+    M.m0 = volTp;
+    R q4 = volTp * R(0.25), q20 = volTp * R(0.05), q10 = volTp * R(0.1);
 #pragma unroll
-        for (int a = 0; a < 4; ++a) M.m1[a] = q4;
-        M.m2[0] = q10; M.m2[1] = q20; M.m2[2] = q20; M.m2[3] = q20; M.m2[4] = q10;
-        M.m2[5] = q20; M.m2[6] = q20; M.m2[7] = q10; M.m2[8] = q20; M.m2[9] = q10;
-        return;
+    for (int a = 0; a < 4; ++a) M.m1[a] = q4;
+    M.m2[0] = q10; M.m2[1] = q20; M.m2[2] = q20; M.m2[3] = q20; M.m2[4] = q10;
+    M.m2[5] = q20; M.m2[6] = q20; M.m2[7] = q10; M.m2[8] = q20; M.m2[9] = q10;
+}
+
+// Philox with the per-round keys precomputed (rk[2r], rk[2r+1] = key + r*Weyl).
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
     }
-    // roles
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// approxcaps (Sec. 3.3): the convex hull of the inside vertices, the
+// edge/sphere points and, on every face of T' crossed by the sphere between
+// two edge points, the midpoint of the sphere's arc on that face.  The hull
+// is grown from the nocaps polytope hull(I u P) by inserting the arc
+// midpoints one at a time (beneath-beyond: faces that see the new point are
+// replaced by the cone from the point to their horizon), then coned from the
+// mean of its points.  Returns false when a hull could not be completed
+// (face capacity); the caller then keeps the nocaps cells.
+// The arc midpoint of face (f0,f1,f2) computed in FP64 for the FP32 path
+// (used when the chord between the two edge points is short or the in-face
+// decision is close).  Returns whether it lies in the face; its position
+// relative to x (rounded to float) and its barycentric coordinates in the
+// face go to pos[3] and lam[3].
+static __device__ __noinline__ bool exact_mu(const Strict *sx, int f0, int f1, int f2, int iA, int oA, int iB, int oB,
+                                             int vin, float pos[3], float lam[3])
+{
+    double v[4][3], x[3], pa[3], pb[3];
+    strict_load(sx, v, x);
+    sedge(v[iA], v[oA], x, sx->d2, pa);
+    sedge(v[iB], v[oB], x, sx->d2, pb);
+    double e1[3], e2[3], nr[3], xw[3];
+    for (int d = 0; d < 3; ++d) { e1[d] = v[f1][d] - v[f0][d]; e2[d] = v[f2][d] - v[f0][d]; xw[d] = x[d] - v[f0][d]; }
+    nr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    nr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    nr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    double sf = (xw[0] * nr[0] + xw[1] * nr[1] + xw[2] * nr[2]) / (nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+    double cf[3], xc[3];
+    for (int d = 0; d < 3; ++d) { cf[d] = x[d] - sf * nr[d]; xc[d] = x[d] - cf[d]; }
+    double r2 = sx->d2 - (xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]);
+    if (!(r2 > 0.0)) return false;
+    double mid[3], ch[3], w[3];
+    for (int d = 0; d < 3; ++d) { mid[d] = 0.5 * (pa[d] + pb[d]); ch[d] = pb[d] - pa[d]; w[d] = mid[d] - v[vin][d]; }
+    double cc = ch[0] * ch[0] + ch[1] * ch[1] + ch[2] * ch[2];
+    if (!(cc > 0.0)) return false;
+    double pr = (w[0] * ch[0] + w[1] * ch[1] + w[2] * ch[2]) / cc;
+    for (int d = 0; d < 3; ++d) w[d] -= pr * ch[d];
+    double lw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (!(lw > 0.0)) return false;
+    double rr = sqrt(r2) / lw, mu[3], g[3];
+    for (int d = 0; d < 3; ++d) { mu[d] = cf[d] + rr * w[d]; g[d] = mu[d] - v[f0][d]; }
+    double a11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2], a12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+    double a22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    double b1 = e1[0] * g[0] + e1[1] * g[1] + e1[2] * g[2], b2 = e2[0] * g[0] + e2[1] * g[1] + e2[2] * g[2];
+    double det = a11 * a22 - a12 * a12;
+    double ls = (b1 * a22 - b2 * a12) / det, lt = (a11 * b2 - a12 * b1) / det;
+    for (int d = 0; d < 3; ++d) pos[d] = (float)(mu[d] - x[d]);
+    lam[0] = (float)(1.0 - ls - lt); lam[1] = (float)ls; lam[2] = (float)lt;
+    return !(ls < -1e-12 || lt < -1e-12 || 1.0 - ls - lt < -1e-12);
+}
+
+constexpr int HULL_MAXP = 12;
+constexpr int HULL_MAXF = 24;
+
+template <class R>
+__device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, const int role[4], const P3<R> pp[4],
+                                    const R pt[4], const PDesc pd[4], bool diag_c2d1, Mom<R> &M, const Strict *sx)
+{
+    constexpr bool F32 = sizeof(R) == 4;
+    P3<R> X[HULL_MAXP];
+    R Lr[HULL_MAXP][4];
+    int n = 0;
+    // table: T' vertices 0..3, edge points 4..7, arc midpoints 8..
+    for (int k = 0; k < 4; ++k) {
+        X[k] = v[k];
+        for (int a = 0; a < 4; ++a) Lr[k][a] = (a == k) ? R(1) : R(0);
+    }
+    const int np = m * (4 - m);
+    for (int k = 0; k < np; ++k) {
+        X[4 + k] = pp[k];
+        for (int a = 0; a < 4; ++a)
+            Lr[4 + k][a] = (a == pd[k].i) ? (R(1) - pt[k]) : ((a == pd[k].o) ? pt[k] : R(0));
+    }
+    n = 4 + 4;
+    // scale for tolerances
+    // initial faces of hull(I u P) (point indices), oriented outward below
+    uint8_t F[HULL_MAXF][3];
+    int nf = 0;
+    const int a = role[0];
+    auto add = [&](int i, int j, int k) { F[nf][0] = (uint8_t)i; F[nf][1] = (uint8_t)j; F[nf][2] = (uint8_t)k; nf++; };
+    if (m == 1) {
+        add(a, 4, 5); add(a, 5, 6); add(a, 6, 4); add(4, 6, 5);
+    } else if (m == 2) {
+        const int b = role[1];
+        add(a, 4, 5); add(b, 6, 7); add(a, b, 6); add(a, 6, 4); add(a, b, 7); add(a, 7, 5);
+        if (!diag_c2d1) { add(4, 6, 7); add(4, 7, 5); }
+        else { add(4, 6, 5); add(6, 7, 5); }
+    } else {
+        const int b = role[1], c = role[2];
+        add(a, b, c); add(4, 5, 6); add(a, b, 5); add(a, 5, 4); add(b, c, 6); add(b, 6, 5); add(a, c, 6);
+        add(a, 6, 4);
+    }
+    {
+        // interior reference: mean of the hull(I u P) points
+        P3<R> ci = mk3<R>(R(0), R(0), R(0));
+        int cnt = 0;
+        for (int k = 0; k < 4; ++k)
+            if (k < m) { ci.x += v[role[k]].x; ci.y += v[role[k]].y; ci.z += v[role[k]].z; cnt++; }
+        for (int k = 0; k < np; ++k) { ci.x += pp[k].x; ci.y += pp[k].y; ci.z += pp[k].z; cnt++; }
+        R inv = R(1) / R(cnt);
+        ci = mk3<R>(ci.x * inv, ci.y * inv, ci.z * inv);
+        for (int f = 0; f < nf; ++f)
+            if (orient(X[F[f][0]], X[F[f][1]], X[F[f][2]], ci) > R(0)) {
+                uint8_t t = F[f][1]; F[f][1] = F[f][2]; F[f][2] = t;
+            }
+    }
+    // arc midpoints
+    int inrank[4], outrank[4];
+    {
+        int ni = 0, no = 0;
+        for (int k = 0; k < 4; ++k) { inrank[k] = -1; outrank[k] = -1; }
+        for (int k = 0; k < m; ++k) inrank[role[k]] = ni++;
+        for (int k = m; k < 4; ++k) outrank[role[k]] = no++;
+    }
+    int used = 4 + np;   // points in the hull so far (all of I u P; unused T' vertices are never referenced)
+    (void)used;
+    for (int o = 0; o < 4; ++o) {
+        int fv[3], k3 = 0;
+        for (int k = 0; k < 4; ++k) if (k != o) fv[k3++] = k;
+        int pA = -1, pB = -1, vin = -1;
+        for (int aa = 0; aa < 3; ++aa)
+            for (int bb = aa + 1; bb < 3; ++bb) {
+                int i = fv[aa], j = fv[bb];
+                int pi = -1;
+                if (inrank[i] >= 0 && outrank[j] >= 0) pi = 4 + inrank[i] * (4 - m) + outrank[j];
+                else if (inrank[j] >= 0 && outrank[i] >= 0) pi = 4 + inrank[j] * (4 - m) + outrank[i];
+                if (pi >= 0) { if (pA < 0) pA = pi; else pB = pi; }
+            }
+        for (int aa = 0; aa < 3; ++aa) if (inrank[fv[aa]] >= 0) { vin = fv[aa]; break; }
+        if (pA < 0 || pB < 0 || vin < 0) continue;
+        P3<R> e1 = sub(v[fv[1]], v[fv[0]]), e2 = sub(v[fv[2]], v[fv[0]]);
+        P3<R> nr = mk3<R>(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+        P3<R> xw = sub(x, v[fv[0]]);
+        R sfac = dot(xw, nr) / dot(nr, nr);
+        P3<R> cf = mk3<R>(x.x - sfac * nr.x, x.y - sfac * nr.y, x.z - sfac * nr.z);
+        P3<R> xc = sub(x, cf);
+        R r2 = d2 - dot(xc, xc);
+        if (!(r2 > R(0))) continue;
+        P3<R> mid = mk3<R>(R(0.5) * (X[pA].x + X[pB].x), R(0.5) * (X[pA].y + X[pB].y), R(0.5) * (X[pA].z + X[pB].z));
+        P3<R> ch = sub(X[pB], X[pA]);
+        R cc = dot(ch, ch);
+        P3<R> mu;
+        R l0, ls, lt;
+        bool keep = false, exact = false;
+        if (F32 && sx && cc < R(1e-6) * d2) {
+            exact = true;        // short chord: its direction is ill-conditioned in FP32
+        } else {
+            if (!(cc > R(0))) continue;
+            P3<R> w = sub(mid, v[vin]);
+            R pr = dot(w, ch) / cc;
+            w = mk3<R>(w.x - pr * ch.x, w.y - pr * ch.y, w.z - pr * ch.z);
+            R lw = sqrt(dot(w, w));
+            if (!(lw > R(0))) continue;
+            R rr = sqrt(r2) / lw;
+            mu = mk3<R>(cf.x + rr * w.x, cf.y + rr * w.y, cf.z + rr * w.z);
+            // barycentric coordinates in the face; keep mu only inside the face
+            P3<R> g = sub(mu, v[fv[0]]);
+            R a11 = dot(e1, e1), a12 = dot(e1, e2), a22 = dot(e2, e2), b1 = dot(e1, g), b2 = dot(e2, g);
+            R det = a11 * a22 - a12 * a12;
+            ls = (b1 * a22 - b2 * a12) / det;
+            lt = (a11 * b2 - a12 * b1) / det;
+            l0 = R(1) - ls - lt;
+            const R tl = R(-1e-12);
+            keep = !(ls < tl || lt < tl || l0 < tl);
+            if (F32 && sx && (absr(ls) < R(1e-4) || absr(lt) < R(1e-4) || absr(l0) < R(1e-4))) exact = true;
+        }
+        if (exact) {
+            const int iA = pd[pA - 4].i, oA = pd[pA - 4].o, iB = pd[pB - 4].i, oB = pd[pB - 4].o;
+            float pos[3], lm[3];
+            keep = exact_mu(sx, fv[0], fv[1], fv[2], iA, oA, iB, oB, vin, pos, lm);
+            mu = mk3<R>((R)pos[0], (R)pos[1], (R)pos[2]);
+            l0 = (R)lm[0]; ls = (R)lm[1]; lt = (R)lm[2];
+        }
+        if (!keep) continue;
+        if (n >= HULL_MAXP) return false;
+        X[n] = mu;
+        for (int aa = 0; aa < 4; ++aa) Lr[n][aa] = R(0);
+        Lr[n][fv[0]] = l0; Lr[n][fv[1]] = ls; Lr[n][fv[2]] = lt;
+        // insert: faces that see mu
+        bool vis[HULL_MAXF];
+        int nvis = 0;
+        for (int f = 0; f < nf; ++f) {
+            const int i0 = F[f][0], i1 = F[f][1], i2 = F[f][2];
+            // faces in the plane of T''s face o (zero o-th barycentric coordinate
+            // at all three points, exact by construction) hold mu in their plane
+            if (Lr[i0][o] == R(0) && Lr[i1][o] == R(0) && Lr[i2][o] == R(0)) { vis[f] = false; continue; }
+            vis[f] = orient(X[i0], X[i1], X[i2], mu) > R(0);
+            nvis += vis[f] ? 1 : 0;
+        }
+        if (nvis == 0) continue;              // inside (or on) the hull already
+        // horizon: edges of visible faces whose neighbour across is not visible
+        uint8_t hz[HULL_MAXF * 3][2];
+        int nh = 0;
+        for (int f = 0; f < nf; ++f) {
+            if (!vis[f]) continue;
+            for (int e = 0; e < 3; ++e) {
+                int i0 = F[f][e], i1 = F[f][(e + 1) % 3];
+                bool other_vis = false, found = false;
+                for (int g2 = 0; g2 < nf && !found; ++g2) {
+                    if (g2 == f) continue;
+                    for (int e2i = 0; e2i < 3; ++e2i)
+                        if (F[g2][e2i] == i1 && F[g2][(e2i + 1) % 3] == i0) { found = true; other_vis = vis[g2]; break; }
+                }
+                if (!found) return false;       // not a closed surface
+                if (!other_vis) { hz[nh][0] = (uint8_t)i0; hz[nh][1] = (uint8_t)i1; nh++; }
+            }
+        }
+        if (nf - nvis + nh > HULL_MAXF) return false;
+        int w2 = 0;
+        for (int f = 0; f < nf; ++f)
+            if (!vis[f]) { F[w2][0] = F[f][0]; F[w2][1] = F[f][1]; F[w2][2] = F[f][2]; w2++; }
+        nf = w2;
+        for (int h = 0; h < nh; ++h) { F[nf][0] = hz[h][0]; F[nf][1] = hz[h][1]; F[nf][2] = (uint8_t)n; nf++; }
+        n++;
+    }
+    // cone from the mean of the hull's points
+    bool inh[HULL_MAXP];
+    for (int k = 0; k < HULL_MAXP; ++k) inh[k] = false;
+    for (int f = 0; f < nf; ++f) { inh[F[f][0]] = true; inh[F[f][1]] = true; inh[F[f][2]] = true; }
+    P3<R> c = mk3<R>(R(0), R(0), R(0));
+    R Lc[4] = {R(0), R(0), R(0), R(0)};
+    int cnt = 0;
+    for (int k = 0; k < n; ++k)
+        if (inh[k]) {
+            c.x += X[k].x; c.y += X[k].y; c.z += X[k].z;
+            for (int aa = 0; aa < 4; ++aa) Lc[aa] += Lr[k][aa];
+            cnt++;
+        }
+    if (cnt < 4) return false;
+    const R inv = R(1) / R(cnt);
+    c = mk3<R>(c.x * inv, c.y * inv, c.z * inv);
+    for (int aa = 0; aa < 4; ++aa) Lc[aa] *= inv;
+    for (int f = 0; f < nf; ++f) {
+        const int i0 = F[f][0], i1 = F[f][1], i2 = F[f][2];
+        R vol = vol4(c, X[i0], X[i1], X[i2]);
+        add_cell(M, vol, Lc, Lr[i0], Lr[i1], Lr[i2]);
+    }
+    return true;
+}
+
+// Per-thread scratch for the cap cells: per cell the 4 vertices (12 values)
+// and their barycentric rows with respect to T' (16 values).
+constexpr int CB_STRIDE = 28;
+
+// Moments of the approximate ball inside T' for a point x whose
+// classification inm has 1..3 vertices inside, or 0 vertices for a fullcaps
+// cap that meets the ball.
+//   nocaps/fullcaps: exact moments of the cells of hull(I u P);
+//   fullcaps:        plus the Monte Carlo estimate over S = T' \ hull(I u P)
+//                    with nmc Philox samples (cell by cumulative volume,
+//                    uniform point from the spacings of three sorted
+//                    uniforms, acceptance |y-x|^2 <= delta^2).  Accepted
+//                    samples are accumulated as count, sum of z and sum of
+//                    z z^T with z = y - centroid(T'); the barycentric moments
+//                    follow from the affine map lambda'(y) = 1/4 + G z.
+//   cb: per-thread scratch of 36 values for the sampling cells.
+//   Returns true (and writes nothing) when the FP32 path defers the event to
+//   the FP64 pass: approxcaps with a vertex of T' within 1e-3 (relative) of
+//   the sphere, where the arc midpoints are ill-conditioned in FP32.
+template <class R, int STRAT>
+__device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
+                              uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb)
+{
+    Mom<R> M;
+    constexpr bool F32 = sizeof(R) == 4;
+    // FP32 decision margins (relative): the FP32 sample point differs from the
+    // FP64 one by a few 1e-7 of the cell size, far inside these margins
+    const R MARGIN = R(4e-6);
+    mom_zero(M);
+    const int m = __popc(inm);
     int role[4];
     {
         int ni = 0, no = m;
@@ -295,8 +703,8 @@ __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc,
             else role[no++] = k;
         }
     }
-    P3<R> pp[4];     // edge/sphere points
-    R pt[4];         // their parameters
+    P3<R> pp[4];
+    R pt[4];
     PDesc pd[4];
     int np = 0;
     if (m > 0) {
@@ -308,7 +716,7 @@ __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc,
                 P3<R> e = sub(v[o], v[i]);
                 R A = (e.x * e.x + e.y * e.y) + e.z * e.z;
                 R B = (e.x * w.x + e.y * w.y) + e.z * w.z;
-                R C = r2[i] - d2;
+                R C = ((w.x * w.x + w.y * w.y) + w.z * w.z) - d2;
                 R s = sqrt(B * B - A * C);
                 R t = (B >= R(0)) ? (-C) / (B + s) : (s - B) / A;
                 pp[np] = mk3<R>(v[i].x + t * e.x, v[i].y + t * e.y, v[i].z + t * e.z);
@@ -318,34 +726,46 @@ __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc,
                 np++;
             }
     }
-    // point lookup: p < 4 -> vertex by local index, else edge point
     auto P = [&](int p) -> P3<R> { return p < 4 ? v[p] : pp[p - 4]; };
 
     bool diag_c2d1 = false;
     if (m == 2) {
         P3<R> c1 = pp[0], d1 = pp[1], c2 = pp[2], dd2 = pp[3];
         R o1 = orient(c1, c2, dd2, d1), o2 = orient(c1, c2, dd2, v[role[0]]);
+        bool exact = false;
         if (F32 && sx) {
             P3<R> e = sub(v[role[2]], v[role[0]]);
             R L = (absr(e.x) + absr(e.y)) + absr(e.z);
             R tol = R(1e-4) * L * L * L;
             if (absr(o1) <= tol || absr(o2) <= tol) {
-                double P64[4][3];
-                sedge(sx->v[role[0]], sx->v[role[2]], sx->x, sx->d2, P64[0]);
-                sedge(sx->v[role[0]], sx->v[role[3]], sx->x, sx->d2, P64[1]);
-                sedge(sx->v[role[1]], sx->v[role[2]], sx->x, sx->d2, P64[2]);
-                sedge(sx->v[role[1]], sx->v[role[3]], sx->x, sx->d2, P64[3]);
-                double q1 = sorient(P64[0], P64[2], P64[3], P64[1]);
-                double q2 = sorient(P64[0], P64[2], P64[3], sx->v[role[0]]);
-                o1 = q1 > 0.0 ? R(1) : (q1 < 0.0 ? R(-1) : R(0));
-                o2 = q2 > 0.0 ? R(1) : (q2 < 0.0 ? R(-1) : R(0));
+                diag_c2d1 = strict_diag(sx, role[0], role[1], role[2], role[3]);
+                exact = true;
             }
         }
-        diag_c2d1 = (o1 > R(0) && o2 < R(0)) || (o1 < R(0) && o2 > R(0));
+        if (!exact) diag_c2d1 = (o1 > R(0) && o2 < R(0)) || (o1 < R(0) && o2 > R(0));
     }
 
-    // deterministic cells: hull(I u P)
-    if (m > 0) {
+    // approxcaps: the hull with the arc midpoints (falls back to nocaps cells)
+    bool done_hull = false;
+    if (STRAT == 1 && m > 0) {
+        Mom<R> H;
+        mom_zero(H);
+        bool near = false;
+        if (F32 && sx) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                P3<R> w = sub(v[k], x);
+                R r2 = (w.x * w.x + w.y * w.y) + w.z * w.z;
+                near |= absr(r2 - d2) < R(1e-3) * d2;
+            }
+        }
+        if (near) return true;
+        done_hull = approx_hull_moments<R>(v, x, d2, m, role, pp, pt, pd, diag_c2d1, H, sx);
+        if (done_hull) M = H;
+        else st.fallback++;
+    }
+    // deterministic cells: hull(I u P), coned from the first inside vertex
+    if (m > 0 && !done_hull) {
         int cells[3][4];
         int nc = 0;
         const int a = role[0];
@@ -381,155 +801,152 @@ __device__ void point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc,
         }
     }
 
-    if (STRAT == 2 && nmc > 0) {
-        bool run = (m > 0);
-        if (!run) {
-            R dd = d2_point_tet(x, v);
-            run = dd <= d2;
-            if (F32 && sx && absr(dd - d2) <= R(1e-4) * d2) {
-                P3<double> vd[4];
-                for (int k = 0; k < 4; ++k) vd[k] = mk3<double>(sx->v[k][0], sx->v[k][1], sx->v[k][2]);
-                run = d2_point_tet(mk3<double>(sx->x[0], sx->x[1], sx->x[2]), vd) <= sx->d2;
-            }
+    // the deterministic part goes out first (its registers are free during sampling)
+    out[0] = M.m0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[1 + k] = M.m1[k];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) out[5 + k] = M.m2[k];
+    if (STRAT != 2 || nmc <= 0) return false;
+
+    // cap cells S = T' \ hull(I u P) in the specification's order
+    int S[3][4];
+    int ns;
+    if (m == 0) {
+        S[0][0] = 0; S[0][1] = 1; S[0][2] = 2; S[0][3] = 3;
+        ns = 1;
+    } else if (m == 1) {
+        const int b = role[1], c = role[2], d = role[3];
+        S[0][0] = b; S[0][1] = NLQ_P(0); S[0][2] = NLQ_P(1); S[0][3] = NLQ_P(2);
+        S[1][0] = b; S[1][1] = c; S[1][2] = d; S[1][3] = NLQ_P(2);
+        S[2][0] = b; S[2][1] = c; S[2][2] = NLQ_P(2); S[2][3] = NLQ_P(1);
+        ns = 3;
+    } else if (m == 2) {
+        const int c = role[2], d = role[3];
+        S[0][0] = c; S[0][1] = d; S[0][2] = NLQ_P(1); S[0][3] = NLQ_P(3);
+        if (!diag_c2d1) {
+            S[1][0] = c; S[1][1] = NLQ_P(0); S[1][2] = NLQ_P(2); S[1][3] = NLQ_P(3);
+            S[2][0] = c; S[2][1] = NLQ_P(0); S[2][2] = NLQ_P(3); S[2][3] = NLQ_P(1);
+        } else {
+            S[1][0] = c; S[1][1] = NLQ_P(0); S[1][2] = NLQ_P(2); S[1][3] = NLQ_P(1);
+            S[2][0] = c; S[2][1] = NLQ_P(2); S[2][2] = NLQ_P(3); S[2][3] = NLQ_P(1);
         }
-        if (run) {
-            int S[3][4];
-            int ns;
-            if (m == 0) {
-                S[0][0] = 0; S[0][1] = 1; S[0][2] = 2; S[0][3] = 3;
-                ns = 1;
-            } else if (m == 1) {
-                const int b = role[1], c = role[2], d = role[3];
-                S[0][0] = b; S[0][1] = NLQ_P(0); S[0][2] = NLQ_P(1); S[0][3] = NLQ_P(2);
-                S[1][0] = b; S[1][1] = c; S[1][2] = d; S[1][3] = NLQ_P(2);
-                S[2][0] = b; S[2][1] = c; S[2][2] = NLQ_P(2); S[2][3] = NLQ_P(1);
-                ns = 3;
-            } else if (m == 2) {
-                const int c = role[2], d = role[3];
-                S[0][0] = c; S[0][1] = d; S[0][2] = NLQ_P(1); S[0][3] = NLQ_P(3);
-                if (!diag_c2d1) {
-                    S[1][0] = c; S[1][1] = NLQ_P(0); S[1][2] = NLQ_P(2); S[1][3] = NLQ_P(3);
-                    S[2][0] = c; S[2][1] = NLQ_P(0); S[2][2] = NLQ_P(3); S[2][3] = NLQ_P(1);
-                } else {
-                    S[1][0] = c; S[1][1] = NLQ_P(0); S[1][2] = NLQ_P(2); S[1][3] = NLQ_P(1);
-                    S[2][0] = c; S[2][1] = NLQ_P(2); S[2][2] = NLQ_P(3); S[2][3] = NLQ_P(1);
-                }
-                ns = 3;
-            } else {
-                const int d = role[3];
-                S[0][0] = d; S[0][1] = NLQ_P(0); S[0][2] = NLQ_P(1); S[0][3] = NLQ_P(2);
-                ns = 1;
-            }
-            P3<R> sp[3][4];
-            R sl[3][4][4];
-            R vol[3];
-            R tot = R(0);
-            for (int j = 0; j < ns; ++j) {
-                for (int k = 0; k < 4; ++k) {
-                    sp[j][k] = P(S[j][k]);
-                    lam_row<R>(S[j][k], pd, pt, sl[j][k]);
-                }
-                vol[j] = vol4(sp[j][0], sp[j][1], sp[j][2], sp[j][3]);
-            }
-            for (int j = 0; j < ns; ++j) tot += vol[j];
-            R a0 = R(0), a1[4] = {R(0), R(0), R(0), R(0)}, a2[10];
-#pragma unroll
-            for (int k = 0; k < 10; ++k) a2[k] = R(0);
-            uint32_t acc = 0;
-            // FP64 cap cells for samples whose FP32 decision is within the margin
-            bool have64 = false;
-            double s64[3][4][3], vol64[3], tot64 = 0.0;
-            auto build64 = [&]() {
-                double P64[4][3];
-                for (int n = 0; n < np; ++n)
-                    sedge(sx->v[pd[n].i], sx->v[pd[n].o], sx->x, sx->d2, P64[n]);
-                for (int jj = 0; jj < ns; ++jj) {
-                    for (int kk = 0; kk < 4; ++kk) {
-                        int pidx = S[jj][kk];
-                        for (int d = 0; d < 3; ++d) s64[jj][kk][d] = pidx < 4 ? sx->v[pidx][d] : P64[pidx - 4][d];
-                    }
-                    vol64[jj] = svol4(s64[jj][0], s64[jj][1], s64[jj][2], s64[jj][3]);
-                }
-                tot64 = 0.0;
-                for (int jj = 0; jj < ns; ++jj) tot64 = sadd(tot64, vol64[jj]);
-                have64 = true;
-            };
-            for (int k = 0; k < nmc; ++k) {
-                uint4 u = philox4x32_10(make_uint4(idT, idTp, q, (uint32_t)k), key);
-                R r = unit_scale<R>(u.x) * tot;
-                int j = ns - 1;
-                R cum = R(0);
-                bool unsure = false;
-                for (int jj = 0; jj < ns; ++jj) {
-                    cum += vol[jj];
-                    if (F32 && jj < ns - 1 && absr(r - cum) <= MARGIN * tot) unsure = true;
-                    if (r < cum) { j = jj; break; }
-                }
-                R U0 = unif<R>(u.y), U1 = unif<R>(u.z), U2 = unif<R>(u.w), tmp;
-                if (U0 > U1) { tmp = U0; U0 = U1; U1 = tmp; }
-                if (U1 > U2) { tmp = U1; U1 = U2; U2 = tmp; }
-                if (U0 > U1) { tmp = U0; U0 = U1; U1 = tmp; }
-                R be0 = U0, be1 = U1 - U0, be2 = U2 - U1, be3 = R(1) - U2;
-                P3<R> s0 = sp[j][0], s1 = sp[j][1], s2 = sp[j][2], s3 = sp[j][3];
-                P3<R> y = mk3<R>(((be0 * s0.x + be1 * s1.x) + be2 * s2.x) + be3 * s3.x,
-                                 ((be0 * s0.y + be1 * s1.y) + be2 * s2.y) + be3 * s3.y,
-                                 ((be0 * s0.z + be1 * s1.z) + be2 * s2.z) + be3 * s3.z);
-                P3<R> w = sub(y, x);
-                R rr = (w.x * w.x + w.y * w.y) + w.z * w.z;
-                bool inb = rr <= d2;
-                if (F32 && sx && (unsure || absr(rr - d2) <= MARGIN * d2)) {
-                    // the specification's FP64 sample: cell by cumulative volume, exact
-                    // spacings of the 32-bit uniforms, point and ball test
-                    if (!have64) build64();
-                    double rd = smul((double)u.x * 0x1p-32, tot64);
-                    int j64 = ns - 1;
-                    double c64 = 0.0;
-                    for (int jj = 0; jj < ns; ++jj) {
-                        c64 = sadd(c64, vol64[jj]);
-                        if (rd < c64) { j64 = jj; break; }
-                    }
-                    double V0 = ((double)u.y + 0.5) * 0x1p-32, V1 = ((double)u.z + 0.5) * 0x1p-32,
-                           V2 = ((double)u.w + 0.5) * 0x1p-32, tv;
-                    if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
-                    if (V1 > V2) { tv = V1; V1 = V2; V2 = tv; }
-                    if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
-                    double b0 = V0, b1 = ssub(V1, V0), b2 = ssub(V2, V1), b3 = ssub(1.0, V2);
-                    double wy[3];
-                    for (int d = 0; d < 3; ++d) {
-                        double yd = sadd(sadd(sadd(smul(b0, s64[j64][0][d]), smul(b1, s64[j64][1][d])),
-                                              smul(b2, s64[j64][2][d])),
-                                         smul(b3, s64[j64][3][d]));
-                        wy[d] = ssub(yd, sx->x[d]);
-                    }
-                    inb = sdot(wy, wy) <= sx->d2;
-                    j = j64;
-                }
-                if (inb) {
-                    R lam[4];
-#pragma unroll
-                    for (int aa = 0; aa < 4; ++aa)
-                        lam[aa] = ((be0 * sl[j][0][aa] + be1 * sl[j][1][aa]) + be2 * sl[j][2][aa]) + be3 * sl[j][3][aa];
-                    acc++;
-                    a0 += R(1);
-#pragma unroll
-                    for (int aa = 0; aa < 4; ++aa) a1[aa] += lam[aa];
-                    int kk = 0;
-#pragma unroll
-                    for (int aa = 0; aa < 4; ++aa)
-#pragma unroll
-                        for (int bb = aa; bb < 4; ++bb) a2[kk++] += lam[aa] * lam[bb];
-                }
-            }
-            st.mc += (uint32_t)nmc;
-            st.acc += acc;
-            R wgt = tot / R(nmc);
-            M.m0 += wgt * a0;
-#pragma unroll
-            for (int aa = 0; aa < 4; ++aa) M.m1[aa] += wgt * a1[aa];
-#pragma unroll
-            for (int kk = 0; kk < 10; ++kk) M.m2[kk] += wgt * a2[kk];
+        ns = 3;
+    } else {
+        const int d = role[3];
+        S[0][0] = d; S[0][1] = NLQ_P(0); S[0][2] = NLQ_P(1); S[0][3] = NLQ_P(2);
+        ns = 1;
+    }
+    unsigned long long spack = 0ULL;
+    uint32_t pdpack = 0u;
+    R vol[3] = {R(0), R(0), R(0)};
+    for (int j = 0; j < ns; ++j) {
+        P3<R> c0 = P(S[j][0]), c1 = P(S[j][1]), c2 = P(S[j][2]), c3 = P(S[j][3]);
+        vol[j] = vol4(c0, c1, c2, c3);
+        R *o = cb + CB_STRIDE * j;
+        o[0] = c0.x; o[1] = c0.y; o[2] = c0.z; o[3] = c1.x; o[4] = c1.y; o[5] = c1.z;
+        o[6] = c2.x; o[7] = c2.y; o[8] = c2.z; o[9] = c3.x; o[10] = c3.y; o[11] = c3.z;
+        for (int kk = 0; kk < 4; ++kk) {
+            lam_row<R>(S[j][kk], pd, pt, o + 12 + 4 * kk);
+            spack |= (unsigned long long)S[j][kk] << (3 * (4 * j + kk));
         }
     }
+    for (int n = 0; n < np; ++n) pdpack |= (uint32_t)(pd[n].i | (pd[n].o << 2)) << (4 * n);
+    R tot = R(0);
+    for (int j = 0; j < ns; ++j) tot += vol[j];
+    const R BIG = R(3.0e38);
+    R cum0 = vol[0];
+    R cum1 = (ns > 1) ? cum0 + vol[1] : BIG;
+    if (ns == 1) cum0 = BIG;
+    // margins of the FP32 decisions
+    const R c0lo = cum0 - MARGIN * tot, c0hi = cum0 + MARGIN * tot;
+    const R c1lo = cum1 - MARGIN * tot, c1hi = cum1 + MARGIN * tot;
+    const R d2lo = d2 * (R(1) - MARGIN), d2hi = d2 * (R(1) + MARGIN);
+    R cnt = R(0), a1[4] = {R(0), R(0), R(0), R(0)}, a2[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) a2[k] = R(0);
+    uint32_t acc = 0;
+    StrictCap scap;
+    scap.ready = 0;
+    for (int k = 0; k < nmc; ++k) {
+        uint4 u = philox_rk(make_uint4(idT, idTp, q, (uint32_t)k), rk);
+        R r = unit_scale<R>(u.x) * tot;
+        int j = (r >= cum0 ? 1 : 0) + (r >= cum1 ? 1 : 0);
+        R U0 = unif<R>(u.y), U1 = unif<R>(u.z), U2 = unif<R>(u.w);
+        R lo = U0 < U1 ? U0 : U1, hi = U0 < U1 ? U1 : U0;
+        R s0 = lo < U2 ? lo : U2;
+        R mid0 = lo < U2 ? U2 : lo;
+        R s2 = hi < mid0 ? mid0 : hi;
+        R s1 = hi < mid0 ? hi : mid0;
+        R be0 = s0, be1 = s1 - s0, be2 = s2 - s1, be3 = R(1) - s2;
+        const R *c = cb + CB_STRIDE * j;
+        P3<R> y = mk3<R>(((be0 * c[0] + be1 * c[3]) + be2 * c[6]) + be3 * c[9],
+                         ((be0 * c[1] + be1 * c[4]) + be2 * c[7]) + be3 * c[10],
+                         ((be0 * c[2] + be1 * c[5]) + be2 * c[8]) + be3 * c[11]);
+        P3<R> w = F32 ? y : sub(y, x);   // the FP32 path works relative to x
+        R rr = (w.x * w.x + w.y * w.y) + w.z * w.z;
+        bool inb = rr <= d2;
+        if (F32 && sx) {
+            const bool unsure = (r > c0lo && r < c0hi) || (r > c1lo && r < c1hi) || (rr > d2lo && rr < d2hi);
+            if (unsure) {
+                int j64 = j;
+                inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64) != 0;
+                c = cb + CB_STRIDE * j64;
+            }
+        }
+        // branch-free accumulation of the accepted sample
+        const R f = inb ? R(1) : R(0);
+        const R *L = c + 12;
+        R lam[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            lam[a] = f * (((be0 * L[a] + be1 * L[4 + a]) + be2 * L[8 + a]) + be3 * L[12 + a]);
+        acc += inb ? 1u : 0u;
+        cnt += f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) a1[a] += lam[a];
+        {
+            int kk = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = a; b < 4; ++b) a2[kk++] += lam[a] * lam[b];
+        }
+    }
+    st.mc += (uint32_t)nmc;
+    st.acc += acc;
+    const R wgt = tot / R(nmc);
+    out[0] += wgt * cnt;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) out[1 + a] += wgt * a1[a];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) out[5 + k] += wgt * a2[k];
+    return false;
+}
+
+// Moments for one (T', x) including classification: used by the diagnostic
+// probe; the assembly splits the two steps across kernels.
+template <class R, int STRAT>
+// Returns the classification + 1 when the event is deferred to FP64, else 0.
+__device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, const uint32_t *rk, uint32_t idT,
+                             uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st, const Strict *sx, R *cb)
+{
+    int inm = classify(v, x, d2, sx);
+    if (inm == 15) {
+        st.inside++;
+        closed_form_inside(M, volTp);
+        return 0;
+    }
+    if (inm == 0 && !(STRAT == 2 && nmc > 0 && meets_ball(v, x, d2, sx))) {
+        mom_zero(M);
+        return 0;
+    }
+    R o[15];
+    if (event_moments<R, STRAT>(v, x, d2, inm, nmc, rk, idT, idTp, q, o, st, sx, cb)) return inm + 1;
+    M.m0 = o[0];
+    for (int k = 0; k < 4; ++k) M.m1[k] = o[1 + k];
+    for (int k = 0; k < 10; ++k) M.m2[k] = o[5 + k];
+    return 0;
 }
 
 }  // namespace nlq
