@@ -475,6 +475,40 @@ static __device__ __noinline__ bool exact_mu(const Strict *sx, int f0, int f1, i
     return !(ls < -1e-12 || lt < -1e-12 || 1.0 - ls - lt < -1e-12);
 }
 
+// Orientation of four FP32 points in FP64 (the rare branch of the filter below).
+static __device__ __noinline__ int orient_sign_fp64(float ax, float ay, float az, float bx, float by, float bz,
+                                                    float cx, float cy, float cz, float dx, float dy, float dz)
+{
+    const double e1x = (double)bx - ax, e1y = (double)by - ay, e1z = (double)bz - az;
+    const double e2x = (double)cx - ax, e2y = (double)cy - ay, e2z = (double)cz - az;
+    const double e3x = (double)dx - ax, e3y = (double)dy - ay, e3z = (double)dz - az;
+    const double o = (e1x * (e2y * e3z - e2z * e3y) + e1y * (e2z * e3x - e2x * e3z)) + e1z * (e2x * e3y - e2y * e3x);
+    return (o > 0.0) - (o < 0.0);
+}
+
+// Sign of orient(a, b, c, d), consistent across the decisions of one hull:
+// in FP32 the determinant is trusted when it exceeds 1e-5 of its permanent
+// (some 160 times its rounding error bound), otherwise the same FP32 points
+// are taken to FP64, where the differences are exact and the determinant's
+// error is far below any gap the FP32 coordinates can express.  Without it,
+// an arc midpoint a few 1e-7 beyond a short chord can be seen as visible
+// from one face and not from its neighbour, and the hull folds.
+template <class R> __device__ __forceinline__ int orient_sign(P3<R> a, P3<R> b, P3<R> c, P3<R> d)
+{
+    if constexpr (sizeof(R) == 8) {
+        const R o = orient(a, b, c, d);
+        return (o > R(0)) - (o < R(0));
+    } else {
+        const P3<R> e1 = sub(b, a), e2 = sub(c, a), e3 = sub(d, a);
+        const R o = det3(e1, e2, e3);
+        const R perm = absr(e1.x) * (absr(e2.y * e3.z) + absr(e2.z * e3.y)) +
+                       absr(e1.y) * (absr(e2.z * e3.x) + absr(e2.x * e3.z)) +
+                       absr(e1.z) * (absr(e2.x * e3.y) + absr(e2.y * e3.x));
+        if (absr(o) > R(1e-5) * perm) return (o > R(0)) - (o < R(0));
+        return orient_sign_fp64(a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z, d.x, d.y, d.z);
+    }
+}
+
 constexpr int HULL_MAXP = 12;
 constexpr int HULL_MAXF = 24;
 
@@ -526,7 +560,7 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
         R inv = R(1) / R(cnt);
         ci = mk3<R>(ci.x * inv, ci.y * inv, ci.z * inv);
         for (int f = 0; f < nf; ++f)
-            if (orient(X[F[f][0]], X[F[f][1]], X[F[f][2]], ci) > R(0)) {
+            if (orient_sign(X[F[f][0]], X[F[f][1]], X[F[f][2]], ci) > 0) {
                 uint8_t t = F[f][1]; F[f][1] = F[f][2]; F[f][2] = t;
             }
     }
@@ -610,7 +644,7 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
             // faces in the plane of T''s face o (zero o-th barycentric coordinate
             // at all three points, exact by construction) hold mu in their plane
             if (Lr[i0][o] == R(0) && Lr[i1][o] == R(0) && Lr[i2][o] == R(0)) { vis[f] = false; continue; }
-            vis[f] = orient(X[i0], X[i1], X[i2], mu) > R(0);
+            vis[f] = orient_sign(X[i0], X[i1], X[i2], mu) > 0;
             nvis += vis[f] ? 1 : 0;
         }
         if (nvis == 0) continue;              // inside (or on) the hull already
