@@ -367,12 +367,27 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
             }
             __syncthreads();
             {
+                // warp i adds row i's contributions of 8 pairs at a time (lane =
+                // 4 * pair + k); lanes that hit the same column are summed by
+                // the lowest of them in ascending lane order, so the sum order
+                // is fixed by the pair order alone
                 const int i = warp;
-                for (int t = 0; t < cnt; ++t) {
-                    if (lane < 4) {
-                        const int c = offs[t * 16 + 4 * i + lane];
-                        strip[i * mr + c] += wsc[t] * (double)Xs[t * 16 + 4 * i + lane];
+                for (int g0 = 0; g0 < cnt; g0 += 8) {
+                    const int t = g0 + (lane >> 2), k = lane & 3;
+                    const bool act = t < cnt;
+                    const int c = act ? offs[t * 16 + 4 * i + k] : -1 - lane;
+                    const double v = act ? wsc[t] * (double)Xs[t * 16 + 4 * i + k] : 0.0;
+                    const unsigned peers = __match_any_sync(0xffffffffu, c);
+                    const int leader = __ffs(peers) - 1;
+                    const int maxn = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
+                    double sum = v;
+                    unsigned rest = (lane == leader) ? (peers & (peers - 1u)) : 0u;
+                    for (int j = 1; j < maxn; ++j) {
+                        const int src = rest ? __ffs(rest) - 1 : lane;
+                        const double w = __shfl_sync(0xffffffffu, v, src);
+                        if (rest) { sum += w; rest &= rest - 1u; }
                     }
+                    if (act && lane == leader) strip[i * mr + c] += sum;
                     __syncwarp();
                 }
             }

@@ -308,6 +308,7 @@ struct PairArgs {
     const float4 *vhi, *vlo;
     const int4 *tets;
     const double4 *tet_cr;
+    const float4 *tet_cf;   // centroid and bounding radius in FP32 (conservative filters only)
     const int32_t *outer_ids;
     const double *xq;
     const int32_t *cell_of;
@@ -317,8 +318,24 @@ struct PairArgs {
     int ks;                 // stencil radius in cells
     double delta, d2;
     float d2_lo, d2_hi;     // FP32 sure-accept / sure-reject bounds on d^2
+    float deltaf;
     int64_t n_outer;
 };
+
+// Conservative FP32 reach: a candidate is dropped only when its FP32 distance
+// exceeds the exact limit by far more than the FP32 rounding of coordinates
+// of magnitude <= 4 (relative 1e-5 plus 1e-5 absolute), so no pair of the
+// exact predicate is ever lost.
+__device__ __forceinline__ float reach_f(float lim) { return lim * 1.00001f + 1e-5f; }
+
+__global__ void k_tet_cf(const double4 *__restrict__ cr, int64_t nt, float4 *cf)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) {
+        double4 c = cr[t];
+        cf[t] = make_float4((float)c.x, (float)c.y, (float)c.z, (float)c.w);
+    }
+}
 
 // Exact predicate min_q d^2(x_q, T') <= delta^2, with an FP32 fast path on
 // coordinates relative to x_q (double-float differences) and the FP64
@@ -357,29 +374,33 @@ __device__ bool pair_predicate(const PairArgs &A, const double3 xq[4], const flo
     return false;
 }
 
-// One warp per outer element: scan the stencil of grid cells, test each
-// candidate; pass 0 counts, pass 1 writes the survivors in scan order.
+// One warp per outer element: scan the stencil of grid cells and test each
+// candidate T'.  PASS 0 only bounds the number of candidates (centroid
+// filter); PASS 1 applies the filters and the exact predicate once and writes
+// the survivors, in scan order, into the outer element's bounded slot.
 template <int PASS>
-__global__ void k_pairs(PairArgs A, int64_t *counts, const int64_t *ptr, int32_t *out)
+__global__ void k_pairs(PairArgs A, const int64_t *bptr, int64_t *counts, int32_t *out)
 {
     int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (warp >= A.n_outer) return;
     int32_t T = A.outer_ids[warp];
-    double4 cT = A.tet_cr[T];
+    const float4 cT = A.tet_cf[T];
     double3 xq[4];
     float3 xh[4], xl[4];
-    for (int q = 0; q < 4; ++q) {
-        xq[q] = make_double3(A.xq[12 * (int64_t)warp + 3 * q], A.xq[12 * (int64_t)warp + 3 * q + 1],
-                             A.xq[12 * (int64_t)warp + 3 * q + 2]);
-        xh[q] = make_float3((float)xq[q].x, (float)xq[q].y, (float)xq[q].z);
-        xl[q] = make_float3((float)(xq[q].x - (double)xh[q].x), (float)(xq[q].y - (double)xh[q].y),
-                            (float)(xq[q].z - (double)xh[q].z));
+    if (PASS == 1) {
+        for (int q = 0; q < 4; ++q) {
+            xq[q] = make_double3(A.xq[12 * (int64_t)warp + 3 * q], A.xq[12 * (int64_t)warp + 3 * q + 1],
+                                 A.xq[12 * (int64_t)warp + 3 * q + 2]);
+            xh[q] = make_float3((float)xq[q].x, (float)xq[q].y, (float)xq[q].z);
+            xl[q] = make_float3((float)(xq[q].x - (double)xh[q].x), (float)(xq[q].y - (double)xh[q].y),
+                                (float)(xq[q].z - (double)xh[q].z));
+        }
     }
     int cell = A.cell_of[T];
     int cx = cell % A.g.n[0], cy = (cell / A.g.n[0]) % A.g.n[1], cz = cell / (A.g.n[0] * A.g.n[1]);
     int64_t n = 0;
-    int64_t base = (PASS == 1) ? ptr[warp] : 0;
+    int64_t base = (PASS == 1) ? bptr[warp] : 0;
     for (int dz = -A.ks; dz <= A.ks; ++dz) {
         int z = cz + dz;
         if (z < 0 || z >= A.g.n[2]) continue;
@@ -396,11 +417,21 @@ __global__ void k_pairs(PairArgs A, int64_t *counts, const int64_t *ptr, int32_t
                     int32_t Tp = -1;
                     if (s + lane < e) {
                         Tp = A.cell_ent[s + lane];
-                        double4 cp = A.tet_cr[Tp];
-                        double dx_ = cT.x - cp.x, dy_ = cT.y - cp.y, dz_ = cT.z - cp.z;
-                        double lim = (A.delta + cT.w + cp.w) * (1.0 + 1e-9);
-                        if ((dx_ * dx_ + dy_ * dy_) + dz_ * dz_ <= lim * lim)
-                            keep = pair_predicate(A, xq, xh, xl, A.tets[Tp]);
+                        const float4 cp = A.tet_cf[Tp];
+                        const float ex = cT.x - cp.x, ey = cT.y - cp.y, ez = cT.z - cp.z;
+                        const float lim = reach_f(A.deltaf + cT.w + cp.w);
+                        keep = (ex * ex + ey * ey) + ez * ez <= lim * lim;
+                        if (PASS == 1 && keep) {
+                            // some outer point must reach the bounding ball of T'
+                            const float lq = reach_f(A.deltaf + cp.w);
+                            bool any = false;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float qx = xh[q].x - cp.x, qy = xh[q].y - cp.y, qz = xh[q].z - cp.z;
+                                any |= (qx * qx + qy * qy) + qz * qz <= lq * lq;
+                            }
+                            keep = any && pair_predicate(A, xq, xh, xl, A.tets[Tp]);
+                        }
                     }
                     unsigned m = __ballot_sync(0xffffffffu, keep);
                     if (PASS == 1 && keep) out[base + n + __popc(m & ((1u << lane) - 1u))] = Tp;
@@ -409,7 +440,17 @@ __global__ void k_pairs(PairArgs A, int64_t *counts, const int64_t *ptr, int32_t
             }
         }
     }
-    if (PASS == 0 && lane == 0) counts[warp] = n;
+    if (lane == 0) counts[warp] = n;
+}
+
+// Move each outer element's survivors from its bounded slot to the pair list.
+__global__ void k_pairs_compact(const int64_t *__restrict__ bptr, const int64_t *__restrict__ ptr,
+                                const int32_t *__restrict__ tmp, int64_t n_outer, int32_t *out)
+{
+    int64_t o = blockIdx.x;
+    if (o >= n_outer) return;
+    const int64_t b = bptr[o], p = ptr[o], n = ptr[o + 1] - ptr[o];
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) out[p + k] = tmp[b + k];
 }
 
 __global__ void k_pair_T(const int64_t *__restrict__ ptr, const int32_t *__restrict__ outer_ids, int64_t n_outer,
@@ -856,19 +897,28 @@ nl_status nl_pairs_build_impl(nl_mesh *m, double delta, nl_pairs **out)
 
         // pairs
         PairArgs A;
-        A.verts = m->verts; A.vhi = m->vhi; A.vlo = m->vlo; A.tets = m->tets; A.tet_cr = m->tet_cr;
+        float4 *tet_cf = sc.get<float4>(nt);
+        { k_tet_cf<<<blocks_for(nt, 256), 256, 0, s>>>(m->tet_cr, nt, tet_cf); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        A.verts = m->verts; A.vhi = m->vhi; A.vlo = m->vlo; A.tets = m->tets; A.tet_cr = m->tet_cr; A.tet_cf = tet_cf;
         A.outer_ids = m->outer_ids; A.xq = m->xq; A.cell_of = cell_of; A.cell_ptr = cell_ptr; A.cell_ent = cell_ent;
         A.g = g; A.ks = ks; A.delta = delta; A.d2 = delta * delta;
         A.d2_lo = (float)(A.d2 * (1.0 - 1e-4)); A.d2_hi = (float)(A.d2 * (1.0 + 1e-4));
+        A.deltaf = (float)delta;
         A.n_outer = no;
         unsigned pblocks = blocks_for(no * 32, 128);
-        { k_pairs<0><<<pblocks, 128, 0, s>>>(A, cnt, nullptr, nullptr); nl_count_launch(); }
+        { k_pairs<0><<<pblocks, 128, 0, s>>>(A, nullptr, cnt, nullptr); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        int64_t *bptr = sc.get<int64_t>(no + 1);
+        const int64_t nbound = nl_scan_counts(cnt, bptr, no, &P->arena, s);
+        int32_t *tmp = sc.get<int32_t>(nbound);
+        { k_pairs<1><<<pblocks, 128, 0, s>>>(A, bptr, cnt, tmp); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         P->pair_ptr = P->arena.get<int64_t>(no + 1);
         P->npairs = nl_scan_counts(cnt, P->pair_ptr, no, &P->arena, s);
         NL_REQUIRE(P->npairs < 0x7fffffffLL, "%lld pairs exceed the int32 pair index", (long long)P->npairs);
         P->pair_tp = P->arena.get<int32_t>(P->npairs);
-        { k_pairs<1><<<pblocks, 128, 0, s>>>(A, nullptr, P->pair_ptr, P->pair_tp); nl_count_launch(); }
+        { k_pairs_compact<<<(unsigned)no, 128, 0, s>>>(bptr, P->pair_ptr, tmp, no, P->pair_tp); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         NL_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
         { k_max_seg<<<blocks_for(no, 256), 256, 0, s>>>(P->pair_ptr, no, mx); nl_count_launch(); }
