@@ -175,10 +175,13 @@ __global__ void __launch_bounds__(256) k_classify(const __grid_constant__ AsmArg
 template <class R> struct EvCfg {
     static constexpr int threads = sizeof(R) == 4 ? 128 : 64;
     static constexpr size_t smem = sizeof(R) * threads * 3 * nlq::CB_STRIDE;
+    // resident blocks per SM allowed by the cap-cell scratch (228 KB of shared
+    // memory per SM, 1 KB reserved per block); the register budget follows
+    static constexpr int min_blocks = (int)((228 * 1024) / (smem + 1024));
 };
 
 template <class R, int STRAT>
-__global__ void __launch_bounds__(EvCfg<R>::threads, 6) k_events(const __grid_constant__ AsmArgs A)
+__global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_events(const __grid_constant__ AsmArgs A)
 {
     extern __shared__ __align__(16) unsigned char evsm[];
     R *cb = reinterpret_cast<R *>(evsm) + 3 * nlq::CB_STRIDE * threadIdx.x;
@@ -261,6 +264,38 @@ __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmA
 }
 
 // ---------------------------------------------------------------------------
+// Double-float (hi + lo) arithmetic for the FP32 path's sums: error-free
+// transformations (Knuth's TwoSum, and the exact product by fused
+// multiply-add), so that strip sums keep about 44 bits without touching the
+// narrow FP64 pipe.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return DF{h, e - (h - s)};
+}
+__device__ __forceinline__ DF df_mul(DF a, float x)
+{
+    const float p = a.hi * x;
+    float e = __fmaf_rn(a.hi, x, -p);
+    e = __fmaf_rn(a.lo, x, e);
+    const float h = p + e;
+    return DF{h, e - (h - p)};
+}
+__device__ __forceinline__ DF df_from(double d)
+{
+    const float h = (float)d;
+    return DF{h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
+
+// ---------------------------------------------------------------------------
 // K3: one block per outer element T (persistent over the chunk's outer
 // elements), one thread per pair: combine the four points of each pair into
 // the staged T'T' moments, the TT sums and the cross strips:
@@ -284,6 +319,8 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
     double *red = wsc + NT;                                                                    // [NT/32][4]
     __shared__ int lens[4];
     __shared__ unsigned long long sin_;
+    constexpr bool F32 = sizeof(R) == 4;
+    static_assert(sizeof(DF) == sizeof(double), "strip and weight slots hold a double or a double-float");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long inside = 0;
     const int64_t nu = 4 * (A.p1 - A.p0);
@@ -299,11 +336,12 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
             const int64_t rb = A.rowptr[nodeT[i]];
             for (int c = tid; c < lens[i]; c += NT) {
                 cols[i * mr + c] = A.col[rb + c];
-                strip[i * mr + c] = 0.0;
+                strip[i * mr + c] = 0.0;     // also DF{0, 0} for the FP32 path
             }
         }
         const double cT = A.half_gamma * (A.tet_vol[T] * 0.25);
         double vq[4] = {0.0, 0.0, 0.0, 0.0};
+        DF vqf[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         __syncthreads();
         const int64_t pb = A.pair_ptr[o], pe = A.pair_ptr[o + 1];
         for (int64_t base = pb; base < pe; base += NT) {
@@ -348,8 +386,13 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                 R *Dst = reinterpret_cast<R *>(A.D) + 10 * p;
 #pragma unroll
                 for (int k = 0; k < 10; ++k) Dst[k] = Dp[k];
+                if constexpr (F32) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) vq[q] += omega * (double)V[q];
+                    for (int q = 0; q < 4; ++q) vqf[q] = df_add(vqf[q], DF{(float)omega * (float)V[q], 0.f});
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) vq[q] += omega * (double)V[q];
+                }
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -363,7 +406,8 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         offs[tid * 16 + 4 * i + k] = lower_bound_s(cols + i * mr, lens[i], nodeP[k]);
-                wsc[tid] = -(omega * cT);
+                if constexpr (F32) reinterpret_cast<DF *>(wsc)[tid] = df_from(-(omega * cT));
+                else wsc[tid] = -(omega * cT);
             }
             __syncthreads();
             {
@@ -376,18 +420,32 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                     const int t = g0 + (lane >> 2), k = lane & 3;
                     const bool act = t < cnt;
                     const int c = act ? offs[t * 16 + 4 * i + k] : -1 - lane;
-                    const double v = act ? wsc[t] * (double)Xs[t * 16 + 4 * i + k] : 0.0;
                     const unsigned peers = __match_any_sync(0xffffffffu, c);
                     const int leader = __ffs(peers) - 1;
                     const int maxn = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
-                    double sum = v;
                     unsigned rest = (lane == leader) ? (peers & (peers - 1u)) : 0u;
-                    for (int j = 1; j < maxn; ++j) {
-                        const int src = rest ? __ffs(rest) - 1 : lane;
-                        const double w = __shfl_sync(0xffffffffu, v, src);
-                        if (rest) { sum += w; rest &= rest - 1u; }
+                    if constexpr (F32) {
+                        const DF v = act ? df_mul(reinterpret_cast<const DF *>(wsc)[t], (float)Xs[t * 16 + 4 * i + k])
+                                         : DF{0.f, 0.f};
+                        DF sum = v;
+                        for (int j = 1; j < maxn; ++j) {
+                            const int src = rest ? __ffs(rest) - 1 : lane;
+                            const float wh = __shfl_sync(0xffffffffu, v.hi, src);
+                            const float wl = __shfl_sync(0xffffffffu, v.lo, src);
+                            if (rest) { sum = df_add(sum, DF{wh, wl}); rest &= rest - 1u; }
+                        }
+                        DF *sp = reinterpret_cast<DF *>(strip);
+                        if (act && lane == leader) sp[i * mr + c] = df_add(sp[i * mr + c], sum);
+                    } else {
+                        const double v = act ? wsc[t] * (double)Xs[t * 16 + 4 * i + k] : 0.0;
+                        double sum = v;
+                        for (int j = 1; j < maxn; ++j) {
+                            const int src = rest ? __ffs(rest) - 1 : lane;
+                            const double w = __shfl_sync(0xffffffffu, v, src);
+                            if (rest) { sum += w; rest &= rest - 1u; }
+                        }
+                        if (act && lane == leader) strip[i * mr + c] += sum;
                     }
-                    if (act && lane == leader) strip[i * mr + c] += sum;
                     __syncwarp();
                 }
             }
@@ -395,9 +453,17 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            double sum = vq[q];
-            for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-            if (lane == 0) red[warp * 4 + q] = sum;
+            if constexpr (F32) {
+                DF sum = vqf[q];
+                for (int off = 16; off > 0; off >>= 1)
+                    sum = df_add(sum, DF{__shfl_xor_sync(0xffffffffu, sum.hi, off),
+                                         __shfl_xor_sync(0xffffffffu, sum.lo, off)});
+                if (lane == 0) red[warp * 4 + q] = df_to(sum);
+            } else {
+                double sum = vq[q];
+                for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+                if (lane == 0) red[warp * 4 + q] = sum;
+            }
         }
         __syncthreads();
         if (tid < 10) {
@@ -414,7 +480,8 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
         }
         for (int i = 0; i < 4; ++i) {
             const int64_t so = A.strip_off[4 * o + i];
-            for (int c = tid; c < lens[i]; c += NT) A.strips[so + c] = strip[i * mr + c];
+            for (int c = tid; c < lens[i]; c += NT)
+                A.strips[so + c] = F32 ? df_to(reinterpret_cast<const DF *>(strip)[i * mr + c]) : strip[i * mr + c];
         }
         __syncthreads();
     }
@@ -607,7 +674,7 @@ __global__ void k_probe(const double *__restrict__ tv, const double4 *__restrict
     sx.e = make_int4((int)(4 * c), (int)(4 * c + 1), (int)(4 * c + 2), (int)(4 * c + 3));
     sx.x = xs + 3 * c;
     sx.d2 = delta2;
-    R cb[3 * nlq::CB_STRIDE];
+    __align__(16) R cb[3 * nlq::CB_STRIDE];   // 16-byte aligned: the sampler reads it with 16-byte loads
     const int d = nlq::point_moments<R, STRAT>(v, xx, (R)delta2, (R)vol, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
                                                ids[3 * c + 2], M, st, sizeof(R) == 4 ? &sx : nullptr, cb);
     defer[c] = d;

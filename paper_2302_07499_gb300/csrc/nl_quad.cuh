@@ -699,8 +699,11 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
 }
 
 // Per-thread scratch for the cap cells: per cell the 4 vertices (12 values)
-// and their barycentric rows with respect to T' (16 values).
+// and their barycentric rows with respect to T' (16 values).  The FP32
+// sampler reads it with 16-byte loads, so the scratch must be 16-byte aligned
+// (28 floats per cell keep every cell and every row on a 16-byte boundary).
 constexpr int CB_STRIDE = 28;
+static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16 == 0, "cap scratch alignment");
 
 // Moments of the approximate ball inside T' for a point x whose
 // classification inm has 1..3 vertices inside, or 0 vertices for a fullcaps
@@ -914,9 +917,21 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         R s1 = hi < mid0 ? hi : mid0;
         R be0 = s0, be1 = s1 - s0, be2 = s2 - s1, be3 = R(1) - s2;
         const R *c = cb + CB_STRIDE * j;
-        P3<R> y = mk3<R>(((be0 * c[0] + be1 * c[3]) + be2 * c[6]) + be3 * c[9],
-                         ((be0 * c[1] + be1 * c[4]) + be2 * c[7]) + be3 * c[10],
-                         ((be0 * c[2] + be1 * c[5]) + be2 * c[8]) + be3 * c[11]);
+        R cc[12];
+        if constexpr (F32) {
+            // 16-byte loads: the per-thread stride of 336 bytes makes them
+            // conflict-free, where 4-byte loads would conflict 4 ways
+            const float4 *c4 = reinterpret_cast<const float4 *>(c);
+            const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
+            cc[0] = q0.x; cc[1] = q0.y; cc[2] = q0.z; cc[3] = q0.w; cc[4] = q1.x; cc[5] = q1.y;
+            cc[6] = q1.z; cc[7] = q1.w; cc[8] = q2.x; cc[9] = q2.y; cc[10] = q2.z; cc[11] = q2.w;
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < 12; ++kk) cc[kk] = c[kk];
+        }
+        P3<R> y = mk3<R>(((be0 * cc[0] + be1 * cc[3]) + be2 * cc[6]) + be3 * cc[9],
+                         ((be0 * cc[1] + be1 * cc[4]) + be2 * cc[7]) + be3 * cc[10],
+                         ((be0 * cc[2] + be1 * cc[5]) + be2 * cc[8]) + be3 * cc[11]);
         P3<R> w = F32 ? y : sub(y, x);   // the FP32 path works relative to x
         R rr = (w.x * w.x + w.y * w.y) + w.z * w.z;
         bool inb = rr <= d2;
@@ -930,7 +945,19 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         }
         // branch-free accumulation of the accepted sample
         const R f = inb ? R(1) : R(0);
-        const R *L = c + 12;
+        R Lr[16];
+        if constexpr (F32) {
+            const float4 *l4 = reinterpret_cast<const float4 *>(c + 12);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const float4 t4 = l4[kk];
+                Lr[4 * kk] = t4.x; Lr[4 * kk + 1] = t4.y; Lr[4 * kk + 2] = t4.z; Lr[4 * kk + 3] = t4.w;
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) Lr[kk] = c[12 + kk];
+        }
+        const R *L = Lr;
         R lam[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
