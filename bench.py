@@ -45,17 +45,21 @@ WORKLOADS = {
 }
 STRAT_NAME = {0: "nocaps", 1: "approxcaps", 2: "fullcaps"}
 
-# Algorithmic FP32 operations of the quadrature kernel (per unit, counted from
-# the arithmetic the method needs; see the design notes): classification per
-# (pair, point); closed-form moments per inside point; edge/sphere points,
-# cells and cap volumes per cut point; per Monte Carlo sample the point,
-# ball test and barycentrics, plus the moment update per accepted sample.
-FLOPS_PER_PAIR_POINT = 36
-FLOPS_PER_INSIDE = 16
-FLOPS_PER_CUT = 400
-FLOPS_PER_SAMPLE = 44
-FLOPS_PER_ACCEPTED = 53
-FP32_LANES_PER_SM = 128
+# Algorithmic ALU operations of the quadrature kernels per unit, counted from
+# the arithmetic the method prescribes (each 32-bit add, multiply, fused
+# multiply-add, compare, min/max, shift or logic operation counts once):
+#   per Monte Carlo sample: Philox4x32-10 (10 rounds x (2 mul.lo + 2 mul.hi +
+#     4 xor) = 80), the cell choice (6), three uniforms (9), their sort (6),
+#     the spacings (4), the point (12) and the ball test (4) = 121;
+#   per accepted sample: the barycentrics (16) and the 15 moments (15) = 31;
+#   per cut point (1..3 vertices inside): the edge/sphere points, the cells
+#     of hull(I u P) with their moments and the cap cell volumes, about 300;
+#   per (pair, point): the classification, 4 x 7 = 28.
+OPS_PER_SAMPLE = 121
+OPS_PER_ACCEPTED = 31
+OPS_PER_CUT = 300
+OPS_PER_PAIR_POINT = 28
+ALU_LANES_PER_SM = 128
 
 
 def _dist():
@@ -141,16 +145,14 @@ def _traffic_record():
     return rec.get("dram_bytes_per_launch")
 
 
-def _algorithmic_flops(st):
-    """FP32 operations of the whole quadrature (all three kernels)."""
-    pp = 4 * st["pairs"]
-    return (FLOPS_PER_PAIR_POINT * pp + FLOPS_PER_INSIDE * st["inside_points"] + _event_flops(st))
+def _event_ops(st):
+    """ALU operations of the cut-point kernel k_events (cells, caps, samples)."""
+    return OPS_PER_CUT * st["cut_points"] + OPS_PER_SAMPLE * st["mc_samples"] + OPS_PER_ACCEPTED * st["mc_accepted"]
 
 
-def _event_flops(st):
-    """FP32 operations of the cut-point kernel alone (cells, caps, samples)."""
-    return (FLOPS_PER_CUT * st["cut_points"] + FLOPS_PER_SAMPLE * st["mc_samples"]
-            + FLOPS_PER_ACCEPTED * st["mc_accepted"])
+def _quadrature_ops(st):
+    """ALU operations of the three quadrature kernels."""
+    return OPS_PER_PAIR_POINT * 4 * st["pairs"] + _event_ops(st)
 
 
 # ---------------------------------------------------------------------------
@@ -275,26 +277,27 @@ def run_ours(args, ws, rank, local):
            "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.mean(e2e_ms))}
 
     # roofline of the dominant kernel (the cut-point kernel k_events, which
-    # holds the cells, caps and Monte Carlo samples): ALU-bound, FP32.  Its
-    # duration is the sum over the assembly's chunks of CUDA events recorded
-    # on the assembly stream around its launches.
+    # holds the cells, caps and Monte Carlo samples): ALU-bound.  Its duration
+    # is the sum over the assembly's chunks of CUDA events recorded on the
+    # assembly stream around its launches; the peak is one 32-bit operation
+    # per lane per clock on the 128 lanes of every SM at the maximum clock.
     st = steps[-1]["stats"]
     ems = float(np.mean([s_["stats"]["events_ms"] for s_ in steps]))
     qms = float(np.mean([s_["stats"]["quadrature_ms"] for s_ in steps]))
-    flops = _event_flops(st)
+    ops = _event_ops(st)
     props = torch.cuda.get_device_properties(local)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = flops / (ems / 1e3) / 1e12
+    peak = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12
+    achieved = ops / (ems / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_events<float,%s>" % STRAT_NAME[strategy],
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _traffic_record(), "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flops x %.0f MHz"
-                % (props.multi_processor_count, sm_max), "algorithmic_flops_per_step": flops,
-                "kernel_ms_per_step": ems, "share_of_step": ems / ms_mean,
+                "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": _traffic_record(),
+                "peak_source": "derived: %d SMs x %d lanes x 1 op/clk x %.0f MHz (no measured ALU peak)"
+                % (props.multi_processor_count, ALU_LANES_PER_SM, sm_max),
+                "algorithmic_ops_per_step": ops, "kernel_ms_per_step": ems, "share_of_step": ems / ms_mean,
                 "quadrature": {"kernels": "k_classify + k_events + k_combine", "ms": qms,
-                               "algorithmic_flops": _algorithmic_flops(st),
-                               "achieved_tflops": _algorithmic_flops(st) / (qms / 1e3) / 1e12}}
-
+                               "algorithmic_ops": _quadrature_ops(st),
+                               "achieved_tops": _quadrature_ops(st) / (qms / 1e3) / 1e12}}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds)

@@ -246,6 +246,59 @@ nl_status nl_solve(nl_system *sys, const nl_solve_opts *opts, double *u_out, int
 nl_status nl_solve_static(nl_system *sys, const nl_solve_opts *opts, double *u_out, nl_solve_info *info);
 
 /* ---------------------------------------------------------------------------
+ * Batched assembly (a system layer; the paper has none).  n independent
+ * problems, each an nl_pairs with its own options, assembled by shared
+ * launches: problems with the same precision, strategy, Monte Carlo count and
+ * seed form a group whose (pair, point) units run in one classification, one
+ * cut-point and one combination launch per chunk; the reductions into K, A and
+ * b follow per problem.  Every unit's arithmetic and every sum's order are
+ * those of the problem alone, so each problem's K, A and b are bitwise equal
+ * to nl_assemble's.
+ *
+ * nl_batch_create builds the plan: per problem an nl_system (owned by the
+ * batch; nl_batch_system lends it out, valid until nl_batch_destroy), the
+ * group maps, and work arrays for the largest chunk.
+ *   autotune   1: time candidate launch shapes (units per chunk 2^23, 2^24,
+ *              2^25 x classification block 128, 256 threads) on the batch
+ *              itself, one run each after a warm-up run, and keep the fastest
+ *              (the candidates' timings are in nl_batch_info).  The results of
+ *              every run are identical whatever the shape.
+ *   use_graph  1: capture one whole run in a CUDA graph that nl_batch_run
+ *              replays (the batch's buffers stay fixed).
+ * All pairs must share one stream (their nl_device's).  opts: n entries, as
+ * for nl_assemble (g_nodal is copied at creation).
+ * Errors: NL_EINVAL, NL_ENOMEM, NL_ECUDA. */
+typedef struct nl_batch nl_batch;
+typedef struct {
+    int autotune;
+    int use_graph;
+} nl_batch_opts;
+nl_status nl_batch_create(nl_pairs *const *pairs, const nl_assemble_opts *opts, int n, const nl_batch_opts *bopts,
+                          nl_batch **out);
+
+/* Assemble every problem of the batch (replays the graph when there is one);
+ * synchronises the stream before returning.  Errors: NL_EINVAL, NL_ECUDA. */
+nl_status nl_batch_run(nl_batch *batch);
+
+/* The system of problem i (the caller's order), owned by the batch. */
+nl_status nl_batch_system(nl_batch *batch, int i, nl_system **out);
+
+typedef struct {
+    int n_problems, n_groups, graph;
+    uint64_t launches_per_run;     /* kernels one run launches */
+    double last_run_ms;            /* device time of the last nl_batch_run (CUDA events) */
+    int64_t units_per_chunk;       /* the shape in use */
+    int classify_threads;
+    int n_tried;                   /* autotuner candidates and their run times */
+    int64_t tried_units_per_chunk[16];
+    int tried_classify_threads[16];
+    double tried_ms[16];
+    uint64_t pairs, cut_points, inside_points, mc_samples, mc_accepted, hull_fallbacks;   /* last run, summed */
+} nl_batch_info;
+nl_status nl_batch_get_info(const nl_batch *batch, nl_batch_info *info);
+void nl_batch_destroy(nl_batch *batch);
+
+/* ---------------------------------------------------------------------------
  * Diagnostic entry points (not on the assembly path).  Host arrays in and
  * out; they run on the default stream with their own temporary device
  * buffers and synchronise before returning.

@@ -62,6 +62,19 @@ class nl_assemble_stats(C.Structure):
                 ("events_ms", C.c_double), ("combine_ms", C.c_double)]
 
 
+class nl_batch_opts(C.Structure):
+    _fields_ = [("autotune", C.c_int), ("use_graph", C.c_int)]
+
+
+class nl_batch_info(C.Structure):
+    _fields_ = [("n_problems", C.c_int), ("n_groups", C.c_int), ("graph", C.c_int),
+                ("launches_per_run", C.c_uint64), ("last_run_ms", C.c_double), ("units_per_chunk", C.c_int64),
+                ("classify_threads", C.c_int), ("n_tried", C.c_int), ("tried_units_per_chunk", C.c_int64 * 16),
+                ("tried_classify_threads", C.c_int * 16), ("tried_ms", C.c_double * 16), ("pairs", C.c_uint64),
+                ("cut_points", C.c_uint64), ("inside_points", C.c_uint64), ("mc_samples", C.c_uint64),
+                ("mc_accepted", C.c_uint64), ("hull_fallbacks", C.c_uint64)]
+
+
 class nl_solve_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int), ("mixed", C.c_int), ("inner_rtol", C.c_double),
                 ("check_every", C.c_int)]
@@ -75,7 +88,8 @@ class nl_solve_info(C.Structure):
 EXPORTED = ["nl_mesh_create", "nl_mesh_destroy", "nl_pairs_build", "nl_pairs_destroy", "nl_pairs_get_info",
             "nl_pairs_export", "nl_assemble", "nl_system_destroy", "nl_system_csr", "nl_system_rhs",
             "nl_system_stats", "nl_solve", "nl_probe_moments", "nl_probe_philox", "nl_last_error", "nl_version", "nl_kernel_launches",
-            "nl_solve_static"]
+            "nl_solve_static", "nl_batch_create", "nl_batch_run", "nl_batch_system", "nl_batch_get_info",
+            "nl_batch_destroy"]
 
 _lib = None
 
@@ -109,6 +123,12 @@ def lib():
     L.nl_last_error.restype = C.c_char_p
     L.nl_version.restype = C.c_char_p
     L.nl_kernel_launches.restype = C.c_uint64
+    L.nl_batch_create.argtypes = [vp, vp, C.c_int, C.POINTER(nl_batch_opts), C.POINTER(vp)]
+    L.nl_batch_run.argtypes = [vp]
+    L.nl_batch_system.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    L.nl_batch_get_info.argtypes = [vp, C.POINTER(nl_batch_info)]
+    L.nl_batch_destroy.argtypes = [vp]
+    L.nl_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -309,6 +329,84 @@ class System:
     def close(self):
         if getattr(self, "h", None):
             lib().nl_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _assemble_opts(strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, gamma=1.0, f_const=0.0, g=None):
+    """nl_assemble_opts and the array that must stay alive while the call runs."""
+    keep = None
+    where = HOST
+    gp = None
+    if g is not None:
+        if isinstance(g, np.ndarray):
+            keep = np.ascontiguousarray(g, dtype=np.float64)
+        else:
+            keep = g.contiguous().double()
+            where = DEVICE
+        gp = _ptr(keep)
+    o = nl_assemble_opts(int(strategy), int(mc_points), int(seed), int(precision), float(gamma), float(f_const),
+                         gp, where)
+    return o, keep
+
+
+class _BorrowedSystem(System):
+    """A system owned by a batch (closing it does nothing)."""
+
+    def __init__(self, pairs, h):
+        self.pairs = pairs
+        self.h = h
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Batched assembly of independent problems (nl_batch_*).
+
+    problems: list of (Pairs, dict of System options).  Each problem's system
+    is bitwise equal to System(pairs, **options)."""
+
+    def __init__(self, problems, autotune=True, use_graph=True):
+        self.pairs = [p for p, _ in problems]
+        n = len(problems)
+        arr = (nl_assemble_opts * n)()
+        keep = []
+        for i, (_, kw) in enumerate(problems):
+            o, k = _assemble_opts(**kw)
+            arr[i] = o
+            keep.append(k)
+        hp = (C.c_void_p * n)(*[p.h for p in self.pairs])
+        bo = nl_batch_opts(int(bool(autotune)), int(bool(use_graph)))
+        h = C.c_void_p()
+        _check(lib().nl_batch_create(C.cast(hp, C.c_void_p), C.cast(arr, C.c_void_p), n, C.byref(bo), C.byref(h)))
+        self.h = h
+        del keep
+
+    def run(self):
+        _check(lib().nl_batch_run(self.h))
+
+    def system(self, i):
+        h = C.c_void_p()
+        _check(lib().nl_batch_system(self.h, int(i), C.byref(h)))
+        return _BorrowedSystem(self.pairs[i], h)
+
+    def info(self):
+        inf = nl_batch_info()
+        _check(lib().nl_batch_get_info(self.h, C.byref(inf)))
+        d = {k: getattr(inf, k) for k, _ in nl_batch_info._fields_ if not k.startswith("tried")}
+        d["tried"] = [(int(inf.tried_units_per_chunk[k]), int(inf.tried_classify_threads[k]), float(inf.tried_ms[k]))
+                      for k in range(inf.n_tried)]
+        return d
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nl_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

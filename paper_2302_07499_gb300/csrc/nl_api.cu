@@ -15,11 +15,8 @@ __global__ void k_zero_collar_g(const uint8_t *__restrict__ node_free, double *g
 
 }  // namespace
 
-extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_system **out)
+nl_status nl_check_assemble_opts(const nl_assemble_opts *opts)
 {
-    nl_clear_error();
-    if (!P || !opts || !out) { nl_set_error("NULL argument"); return NL_EINVAL; }
-    *out = nullptr;
     if (opts->strategy < NL_NOCAPS || opts->strategy > NL_FULLCAPS) { nl_set_error("bad strategy"); return NL_EINVAL; }
     if (opts->precision != NL_FP64 && opts->precision != NL_FP32_COMP) { nl_set_error("bad precision"); return NL_EINVAL; }
     if (opts->strategy == NL_FULLCAPS && (opts->mc_points < 1 || opts->mc_points > 4096)) {
@@ -28,6 +25,13 @@ extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_s
     }
     if (!isfinite(opts->gamma) || !isfinite(opts->f_const)) { nl_set_error("gamma and f_const must be finite"); return NL_EINVAL; }
     if (opts->g_nodal && opts->g_where != NL_HOST && opts->g_where != NL_DEVICE) { nl_set_error("bad g_where"); return NL_EINVAL; }
+    return NL_OK;
+}
+
+// A system handle with K, A, b, F and the collar values g allocated (g set,
+// stream-ordered); throws NlError.
+nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts)
+{
     nl_mesh *m = P->mesh;
     nl_system *S = new nl_system();
     S->arena.dev = P->arena.dev;
@@ -50,6 +54,29 @@ extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_s
         } else {
             NL_CUDA(cudaMemsetAsync(S->g, 0, sizeof(double) * m->nv, s));
         }
+    } catch (NlError &) {
+        S->arena.release_all();
+        delete S;
+        throw;
+    }
+    return S;
+}
+
+extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_system **out)
+{
+    nl_clear_error();
+    if (!P || !opts || !out) { nl_set_error("NULL argument"); return NL_EINVAL; }
+    *out = nullptr;
+    if (nl_status st = nl_check_assemble_opts(opts)) return st;
+    nl_mesh *m = P->mesh;
+    nl_system *S = nullptr;
+    try {
+        S = nl_system_alloc(P, opts);
+    } catch (NlError &e) {
+        return e.st;
+    }
+    try {
+        cudaStream_t s = S->arena.stream();
         Scratch sc(&S->arena);
         const bool f32 = opts->precision == NL_FP32_COMP;
         void *D = f32 ? (void *)sc.get<float>(10 * P->npairs) : (void *)sc.get<double>(10 * P->npairs);

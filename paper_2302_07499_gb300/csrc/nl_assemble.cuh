@@ -12,6 +12,7 @@
 // per row in pair order; everything else is written to its own slot.
 #pragma once
 
+#include "nl_asm_types.h"
 #include "nl_internal.h"
 #include "nl_quad.cuh"
 
@@ -25,47 +26,33 @@ namespace nla {
 using nlq::Mom;
 using nlq::P3;
 
-// Work is cut into chunks of outer elements so that the per-(pair, point)
-// records stay bounded in size.
-constexpr int64_t kUnitsPerChunk = int64_t(1) << 25;
+// The problem of pair pg (launch index space) and the pair's own index in it.
+template <bool B>
+__device__ __forceinline__ const Prob &prob_of_pair(const AsmArgs &A, int64_t pg, int64_t &p)
+{
+    if constexpr (B) {
+        const Prob &P = A.probs[A.pair_prob[pg]];
+        p = pg - P.pair_base;
+        return P;
+    } else {
+        p = pg;
+        return A.self;
+    }
+}
 
-struct AsmArgs {
-    const double4 *verts;
-    const float4 *vhi, *vlo;
-    const int4 *tets;
-    const uint8_t *in_omega;
-    const double *tet_vol;
-    const int32_t *outer_ids;
-    const int32_t *outer_of;
-    const double *xq;
-    const float *xq_hl;      // [n_outer][4][6] outer points as float hi, lo parts
-    const int64_t *pair_ptr;
-    const int32_t *pair_tp;
-    const int32_t *pair_T;
-    const int64_t *rowptr;
-    const int32_t *col;
-    const int64_t *strip_off;
-    int64_t o0, o1;          // outer elements of this chunk
-    int64_t p0, p1;          // pairs of this chunk
-    int max_row;
-    double delta2;
-    float delta2f;
-    double half_gamma;
-    int nmc;
-    uint32_t rk[20];         // Philox round keys
-    // per-chunk work arrays
-    uint8_t *uinfo;          // [4*(p1-p0)] vertex-inside mask | 0x10 event | 0x20 zero
-    int32_t *slot;           // [4*(p1-p0)] class*units + index within the class, or -1
-    int32_t *evu;            // [4][units] unit of each event, per class (m = 0..3)
-    int *nev;                // [5] event count per class; nev[4] = deferred events
-    int32_t *fix;            // [units] FP32 approxcaps events deferred to the FP64 pass
-    void *Mq;                // [events][15] moments (R)
-    // outputs
-    void *D;                 // [npairs][10] staged T'T' moments (R)
-    double *strips;          // [strip_total]
-    double *TT;              // [n_outer][10]
-    unsigned long long *stats;  // [5]
-};
+// The problem of outer element og (launch index space) and its own index.
+template <bool B>
+__device__ __forceinline__ const Prob &prob_of_outer(const AsmArgs &A, int64_t og, int64_t &o)
+{
+    if constexpr (B) {
+        const Prob &P = A.probs[A.outer_prob[og]];
+        o = og - P.outer_base;
+        return P;
+    } else {
+        o = og;
+        return A.self;
+    }
+}
 
 // barycentric weight lambda_i(x_q) of the 4-point rule: a on i == q, b elsewhere
 template <class R> __device__ __forceinline__ R qlam(int i, int q)
@@ -87,7 +74,7 @@ __device__ __forceinline__ int lower_bound_s(const int32_t *a, int n, int32_t ke
 // relative to x_q as double-float differences (R = float), plus the FP64
 // context for the FP32 path's exact decisions.
 template <class R>
-__device__ __forceinline__ void load_point_geometry(const AsmArgs &A, int4 eP, int64_t o, int q, P3<R> v[4],
+__device__ __forceinline__ void load_point_geometry(const Prob &A, int4 eP, int64_t o, int q, P3<R> v[4],
                                                     P3<R> &x, nlq::Strict &sx)
 {
     const int ids[4] = {eP.x, eP.y, eP.z, eP.w};
@@ -118,7 +105,7 @@ __device__ __forceinline__ void load_point_geometry(const AsmArgs &A, int4 eP, i
 // ---------------------------------------------------------------------------
 // K1: classify every (pair, point) unit of the chunk; units with a cut (1..3
 // vertices inside, or a fullcaps cap without inside vertices) become events.
-template <class R, int STRAT>
+template <class R, int STRAT, bool B>
 __global__ void __launch_bounds__(256) k_classify(const __grid_constant__ AsmArgs A)
 {
     const int64_t nu = 4 * (A.p1 - A.p0);
@@ -128,20 +115,22 @@ __global__ void __launch_bounds__(256) k_classify(const __grid_constant__ AsmArg
         bool ev = false;
         uint8_t info = 0x20;
         if (u < nu) {
-            const int64_t p = A.p0 + (u >> 2);
+            int64_t p;
+            const Prob &P = prob_of_pair<B>(A, A.p0 + (u >> 2), p);
             const int q = (int)(u & 3);
-            const int32_t T = A.pair_T[p], Tp = A.pair_tp[p];
-            const int32_t o = A.outer_of[T];
+            const int32_t T = P.pair_T[p], Tp = P.pair_tp[p];
+            const int32_t o = P.outer_of[T];
             P3<R> v[4];
             P3<R> x;
             nlq::Strict sx;
-            load_point_geometry<R>(A, A.tets[Tp], o, q, v, x, sx);
+            load_point_geometry<R>(P, P.tets[Tp], o, q, v, x, sx);
             const nlq::Strict *sp = (sizeof(R) == 4) ? &sx : nullptr;
-            const int inm = nlq::classify(v, x, (R)A.delta2f, sp);
+            const R d2 = (sizeof(R) == 4) ? (R)P.delta2f : (R)P.delta2;
+            const int inm = nlq::classify(v, x, d2, sp);
             info = (uint8_t)inm;
             if (inm != 15) {
                 if (inm != 0) ev = true;
-                else if (STRAT == 2 && A.nmc > 0) ev = nlq::meets_ball(v, x, (R)A.delta2f, sp);
+                else if (STRAT == 2 && A.nmc > 0) ev = nlq::meets_ball(v, x, d2, sp);
                 if (ev) info |= 0x10;
                 else info |= 0x20;
             }
@@ -180,7 +169,7 @@ template <class R> struct EvCfg {
     static constexpr int min_blocks = (int)((228 * 1024) / (smem + 1024));
 };
 
-template <class R, int STRAT>
+template <class R, int STRAT, bool B>
 __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_events(const __grid_constant__ AsmArgs A)
 {
     extern __shared__ __align__(16) unsigned char evsm[];
@@ -196,17 +185,18 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
             if (idx >= n1) { idx -= n1; c = 2;
                 if (idx >= n2) { idx -= n2; c = 3; } } }
         const int32_t u = A.evu[c * nu + idx];
-        const int64_t p = A.p0 + (u >> 2);
+        int64_t p;
+        const Prob &P = prob_of_pair<B>(A, A.p0 + (u >> 2), p);
         const int q = u & 3;
-        const int32_t T = A.pair_T[p], Tp = A.pair_tp[p];
-        const int32_t o = A.outer_of[T];
+        const int32_t T = P.pair_T[p], Tp = P.pair_tp[p];
+        const int32_t o = P.outer_of[T];
         P3<R> v[4];
         P3<R> x;
         nlq::Strict sx;
-        load_point_geometry<R>(A, A.tets[Tp], o, q, v, x, sx);
+        load_point_geometry<R>(P, P.tets[Tp], o, q, v, x, sx);
         const int inm = A.uinfo[u] & 15;
         R *out = reinterpret_cast<R *>(A.Mq) + 15 * (int64_t)e;
-        const bool deferred = nlq::event_moments<R, STRAT>(v, x, sizeof(R) == 4 ? (R)A.delta2f : (R)A.delta2, inm,
+        const bool deferred = nlq::event_moments<R, STRAT>(v, x, sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2, inm,
                                                            A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q, out,
                                                            st, (sizeof(R) == 4) ? &sx : nullptr, cb);
         if (deferred) A.fix[atomicAdd(&A.nev[4], 1)] = e;
@@ -231,7 +221,7 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
 // K2b (FP32 approxcaps only): the events that K2 deferred are recomputed with
 // the FP64 event code on global coordinates (same classification), and the
 // moments stored in the event's FP32 record.
-template <int STRAT>
+template <int STRAT, bool B>
 __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmArgs A)
 {
     nlq::Stats st{0, 0, 0, 0, 0};
@@ -244,17 +234,18 @@ __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmA
             if (idx >= n1) { idx -= n1; c = 2;
                 if (idx >= n2) { idx -= n2; c = 3; } } }
         const int32_t u = A.evu[c * nu + idx];
-        const int64_t p = A.p0 + (u >> 2);
+        int64_t p;
+        const Prob &P = prob_of_pair<B>(A, A.p0 + (u >> 2), p);
         const int q = u & 3;
-        const int32_t T = A.pair_T[p], Tp = A.pair_tp[p];
-        const int32_t o = A.outer_of[T];
+        const int32_t T = P.pair_T[p], Tp = P.pair_tp[p];
+        const int32_t o = P.outer_of[T];
         P3<double> v[4];
         P3<double> x;
         nlq::Strict sx;
-        load_point_geometry<double>(A, A.tets[Tp], o, q, v, x, sx);
+        load_point_geometry<double>(P, P.tets[Tp], o, q, v, x, sx);
         const int inm = A.uinfo[u] & 15;
         double m15[15];
-        nlq::event_moments<double, STRAT>(v, x, A.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q,
+        nlq::event_moments<double, STRAT>(v, x, P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q,
                                           m15, st, nullptr, nullptr);
         float *out = reinterpret_cast<float *>(A.Mq) + 15 * (int64_t)e;
 #pragma unroll
@@ -306,7 +297,7 @@ __device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.
 // accumulated by one warp per row in pair order (deterministic).
 constexpr int NT = 128;
 
-template <class R>
+template <class R, bool B>
 __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -326,37 +317,39 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
     const int64_t nu = 4 * (A.p1 - A.p0);
     const int cpre[4] = {0, A.nev[0], A.nev[0] + A.nev[1], A.nev[0] + A.nev[1] + A.nev[2]};
 
-    for (int64_t o = A.o0 + blockIdx.x; o < A.o1; o += gridDim.x) {
-        const int32_t T = A.outer_ids[o];
-        const int4 eT = A.tets[T];
+    for (int64_t og = A.o0 + blockIdx.x; og < A.o1; og += gridDim.x) {
+        int64_t o;
+        const Prob &P = prob_of_outer<B>(A, og, o);
+        const int32_t T = P.outer_ids[o];
+        const int4 eT = P.tets[T];
         const int nodeT[4] = {eT.x, eT.y, eT.z, eT.w};
-        if (tid < 4) lens[tid] = (int)(A.rowptr[nodeT[tid] + 1] - A.rowptr[nodeT[tid]]);
+        if (tid < 4) lens[tid] = (int)(P.rowptr[nodeT[tid] + 1] - P.rowptr[nodeT[tid]]);
         __syncthreads();
         for (int i = 0; i < 4; ++i) {
-            const int64_t rb = A.rowptr[nodeT[i]];
+            const int64_t rb = P.rowptr[nodeT[i]];
             for (int c = tid; c < lens[i]; c += NT) {
-                cols[i * mr + c] = A.col[rb + c];
+                cols[i * mr + c] = P.col[rb + c];
                 strip[i * mr + c] = 0.0;     // also DF{0, 0} for the FP32 path
             }
         }
-        const double cT = A.half_gamma * (A.tet_vol[T] * 0.25);
+        const double cT = P.half_gamma * (P.tet_vol[T] * 0.25);
         double vq[4] = {0.0, 0.0, 0.0, 0.0};
         DF vqf[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         __syncthreads();
-        const int64_t pb = A.pair_ptr[o], pe = A.pair_ptr[o + 1];
+        const int64_t pb = P.pair_ptr[o], pe = P.pair_ptr[o + 1];
         for (int64_t base = pb; base < pe; base += NT) {
             const int cnt = (int)((pe - base) < (int64_t)NT ? (pe - base) : (int64_t)NT);
             const int64_t p = base + tid;
             if (tid < cnt) {
-                const int32_t Tp = A.pair_tp[p];
-                const int4 eP = A.tets[Tp];
+                const int32_t Tp = P.pair_tp[p];
+                const int4 eP = P.tets[Tp];
                 const int nodeP[4] = {eP.x, eP.y, eP.z, eP.w};
-                const double omega = A.in_omega[Tp] ? 1.0 : 2.0;
-                const R volTp = (R)A.tet_vol[Tp];
+                const double omega = P.in_omega[Tp] ? 1.0 : 2.0;
+                const R volTp = (R)P.tet_vol[Tp];
                 R Y[4][4], V[4], Dp[10];
 #pragma unroll
                 for (int k = 0; k < 10; ++k) Dp[k] = R(0);
-                const int64_t u0 = 4 * (p - A.p0);
+                const int64_t u0 = 4 * (P.pair_base + p - A.p0);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const uint8_t info = A.uinfo[u0 + q];
@@ -383,7 +376,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
 #pragma unroll
                     for (int k = 0; k < 10; ++k) Dp[k] += M.m2[k];
                 }
-                R *Dst = reinterpret_cast<R *>(A.D) + 10 * p;
+                R *Dst = reinterpret_cast<R *>(P.D) + 10 * p;
 #pragma unroll
                 for (int k = 0; k < 10; ++k) Dst[k] = Dp[k];
                 if constexpr (F32) {
@@ -476,12 +469,12 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
             double sum = 0.0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) sum += qlam<double>(i, q) * qlam<double>(j, q) * V[q];
-            A.TT[10 * o + tid] = cT * sum;
+            P.TT[10 * o + tid] = cT * sum;
         }
         for (int i = 0; i < 4; ++i) {
-            const int64_t so = A.strip_off[4 * o + i];
+            const int64_t so = P.strip_off[4 * o + i];
             for (int c = tid; c < lens[i]; c += NT)
-                A.strips[so + c] = F32 ? df_to(reinterpret_cast<const DF *>(strip)[i * mr + c]) : strip[i * mr + c];
+                P.strips[so + c] = F32 ? df_to(reinterpret_cast<const DF *>(strip)[i * mr + c]) : strip[i * mr + c];
         }
         __syncthreads();
     }
@@ -503,86 +496,88 @@ inline size_t combine_smem_bytes(int max_row, size_t real_size)
     return b;
 }
 
-inline void philox_round_keys(uint64_t seed, uint32_t rk[20])
-{
-    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    for (int r = 0; r < 10; ++r) {
-        rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
-        rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
-    }
-}
-
+// Work arrays of one chunk (reused by every chunk of a launch).
 template <class R, int STRAT>
-void run_chunks(nl_system *sys, AsmArgs &A)
+void alloc_work(AsmArgs &A, Scratch &sc, int64_t max_units)
 {
-    nl_pairs *P = sys->pairs;
-    nl_mesh *m = P->mesh;
-    cudaStream_t s = sys->arena.stream();
-    // chunk sizes
-    std::vector<int64_t> hp(m->n_outer + 1);
-    NL_CUDA(cudaMemcpyAsync(hp.data(), P->pair_ptr, sizeof(int64_t) * (m->n_outer + 1), cudaMemcpyDeviceToHost, s));
-    NL_CUDA(cudaStreamSynchronize(s));
-    int64_t max_units = 0;
-    std::vector<std::pair<int64_t, int64_t>> chunks;
-    for (int64_t o = 0; o < m->n_outer;) {
-        int64_t o1 = o + 1;
-        while (o1 < m->n_outer && 4 * (hp[o1 + 1] - hp[o]) <= kUnitsPerChunk) ++o1;
-        chunks.push_back({o, o1});
-        max_units = std::max<int64_t>(max_units, 4 * (hp[o1] - hp[o]));
-        o = o1;
-    }
-    Scratch sc(&sys->arena);
+    constexpr bool kDefer = sizeof(R) == 4 && STRAT == 1;
     A.uinfo = sc.get<uint8_t>(max_units);
     A.slot = sc.get<int32_t>(max_units);
     A.evu = sc.get<int32_t>(4 * max_units);
     A.nev = sc.get<int>(5);
-    constexpr bool kDefer = sizeof(R) == 4 && STRAT == 1;
     A.fix = kDefer ? sc.get<int32_t>(max_units) : nullptr;
     A.Mq = (void *)sc.get<R>(15 * max_units);
-    const size_t smem = combine_smem_bytes(P->max_row, sizeof(R));
-    NL_REQUIRE(smem <= 220 * 1024, "rows of %d columns need %zu bytes of shared memory", P->max_row, smem);
-    NL_CUDA(cudaFuncSetAttribute(k_combine<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+}
+
+// The three quadrature kernels over every chunk, stream-ordered, no host
+// synchronisation (capturable in a CUDA graph).  ev, when given, receives 4
+// events per chunk around the kernels.
+template <class R, int STRAT, bool B>
+void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vector<std::pair<int64_t, int64_t>> &chunks,
+                   const Shape &sh, cudaStream_t s, cudaEvent_t *ev)
+{
+    constexpr bool kDefer = sizeof(R) == 4 && STRAT == 1;
+    const size_t smem = combine_smem_bytes(A.max_row, sizeof(R));
+    NL_REQUIRE(smem <= 220 * 1024, "rows of %d columns need %zu bytes of shared memory", A.max_row, smem);
+    NL_CUDA(cudaFuncSetAttribute(k_combine<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<R>, NT, smem));
+    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<R, B>, NT, smem));
     per_sm = per_sm < 1 ? 1 : per_sm;
     int ev_per_sm = 0;
     constexpr int ET = EvCfg<R>::threads;
     constexpr size_t ESM = EvCfg<R>::smem;
-    NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
-    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, k_events<R, STRAT>, ET, ESM));
+    NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
+    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, k_events<R, STRAT, B>, ET, ESM));
     ev_per_sm = ev_per_sm < 1 ? 1 : ev_per_sm;
+    if (sh.events_blocks_per_sm > 0) ev_per_sm = std::min(ev_per_sm, sh.events_blocks_per_sm);
     const int sms = nl_num_sms();
-    // per-kernel durations (CUDA events on the assembly stream)
-    std::vector<cudaEvent_t> ev(4 * chunks.size());
-    for (auto &e : ev) NL_CUDA(cudaEventCreate(&e));
+    const int ct = sh.classify_threads;
     size_t ci = 0;
     for (auto &c : chunks) {
         A.o0 = c.first; A.o1 = c.second;
-        A.p0 = hp[c.first]; A.p1 = hp[c.second];
+        A.p0 = gptr[c.first]; A.p1 = gptr[c.second];
         const int64_t nu = 4 * (A.p1 - A.p0);
         NL_CUDA(cudaMemsetAsync(A.nev, 0, 5 * sizeof(int), s));
-        unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, 256), (int64_t)sms * 32));
-        NL_CUDA(cudaEventRecord(ev[4 * ci], s));
-        { k_classify<R, STRAT><<<g1, 256, 0, s>>>(A); nl_count_launch(); }
+        unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, ct), (int64_t)sms * (8192 / ct)));
+        if (ev) NL_CUDA(cudaEventRecord(ev[4 * ci], s));
+        { k_classify<R, STRAT, B><<<g1, ct, 0, s>>>(A); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        NL_CUDA(cudaEventRecord(ev[4 * ci + 1], s));
+        if (ev) NL_CUDA(cudaEventRecord(ev[4 * ci + 1], s));
         // enough resident threads for the largest possible event count; the
         // kernel reads the actual count from device memory
         unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, ET), (int64_t)sms * ev_per_sm));
-        { k_events<R, STRAT><<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
+        { k_events<R, STRAT, B><<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         if constexpr (kDefer) {
-            { k_events_fp64<STRAT><<<(unsigned)(2 * sms), 64, 0, s>>>(A); nl_count_launch(); }
+            { k_events_fp64<STRAT, B><<<(unsigned)(2 * sms), 64, 0, s>>>(A); nl_count_launch(); }
             NL_CHECK_LAUNCH();
         }
-        NL_CUDA(cudaEventRecord(ev[4 * ci + 2], s));
+        if (ev) NL_CUDA(cudaEventRecord(ev[4 * ci + 2], s));
         int64_t no = A.o1 - A.o0;
         unsigned g3 = (unsigned)std::min<int64_t>(no, (int64_t)sms * per_sm);
-        { k_combine<R><<<g3, NT, smem, s>>>(A); nl_count_launch(); }
+        { k_combine<R, B><<<g3, NT, smem, s>>>(A); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        NL_CUDA(cudaEventRecord(ev[4 * ci + 3], s));
+        if (ev) NL_CUDA(cudaEventRecord(ev[4 * ci + 3], s));
         ++ci;
     }
+}
+
+template <class R, int STRAT>
+void run_single(nl_system *sys, AsmArgs &A)
+{
+    nl_pairs *P = sys->pairs;
+    nl_mesh *m = P->mesh;
+    cudaStream_t s = sys->arena.stream();
+    std::vector<int64_t> hp(m->n_outer + 1);
+    NL_CUDA(cudaMemcpyAsync(hp.data(), P->pair_ptr, sizeof(int64_t) * (m->n_outer + 1), cudaMemcpyDeviceToHost, s));
+    NL_CUDA(cudaStreamSynchronize(s));
+    int64_t max_units = 0;
+    auto chunks = plan_chunks(hp, kUnitsPerChunk, &max_units);
+    Scratch sc(&sys->arena);
+    alloc_work<R, STRAT>(A, sc, max_units);
+    std::vector<cudaEvent_t> ev(4 * chunks.size());
+    for (auto &e : ev) NL_CUDA(cudaEventCreate(&e));
+    launch_chunks<R, STRAT, false>(A, hp, chunks, Shape(), s, ev.data());
     NL_CUDA(cudaStreamSynchronize(s));
     double t[3] = {0.0, 0.0, 0.0};
     for (size_t k = 0; k < chunks.size(); ++k)
@@ -597,33 +592,45 @@ void run_chunks(nl_system *sys, AsmArgs &A)
     sys->stats.combine_ms = t[2];
 }
 
+
 template <class R>
 void launch_assemble(nl_system *sys, void *D, double *strips, double *TT, unsigned long long *stats)
 {
-    nl_pairs *P = sys->pairs;
-    nl_mesh *m = P->mesh;
     AsmArgs A;
     memset(&A, 0, sizeof(A));
-    A.verts = m->verts; A.vhi = m->vhi; A.vlo = m->vlo; A.tets = m->tets; A.in_omega = m->in_omega;
-    A.tet_vol = m->tet_vol; A.outer_ids = m->outer_ids; A.outer_of = m->outer_of; A.xq = m->xq;
-    A.xq_hl = m->xq_hl;
-    A.pair_ptr = P->pair_ptr; A.pair_tp = P->pair_tp; A.pair_T = P->pair_T;
-    A.rowptr = P->rowptr; A.col = P->col; A.strip_off = P->strip_off;
-    A.max_row = P->max_row;
-    A.delta2 = P->delta * P->delta;
-    A.delta2f = (float)A.delta2;
-    A.half_gamma = sys->opts.gamma / 2.0;
-    A.nmc = sys->opts.strategy == NL_FULLCAPS ? sys->opts.mc_points : 0;
-    philox_round_keys(sys->opts.seed, A.rk);
-    A.D = D; A.strips = strips; A.TT = TT; A.stats = stats;
-    NL_REQUIRE(A.verts && A.vhi && A.vlo && A.tets && A.xq && A.xq_hl && A.pair_ptr && A.pair_tp && A.pair_T &&
-                   A.rowptr && A.col && A.strip_off && A.outer_of && A.outer_ids,
-               "internal: an input array of the assembly is missing");
+    A.self = make_prob(sys, D, strips, TT);
+    init_group_args(A, sys->opts, stats, sys->pairs->max_row);
     switch (sys->opts.strategy) {
-    case NL_NOCAPS: run_chunks<R, 0>(sys, A); break;
-    case NL_APPROXCAPS: run_chunks<R, 1>(sys, A); break;
-    default: run_chunks<R, 2>(sys, A); break;
+    case NL_NOCAPS: run_single<R, 0>(sys, A); break;
+    case NL_APPROXCAPS: run_single<R, 1>(sys, A); break;
+    default: run_single<R, 2>(sys, A); break;
     }
+}
+
+template <class R>
+void launch_group(const BatchGroup &g, const Shape &sh, cudaStream_t s)
+{
+    int64_t mu = 0;
+    auto chunks = plan_chunks(g.gptr, sh.units_per_chunk, &mu);
+    switch (g.strategy) {
+    case NL_NOCAPS: launch_chunks<R, 0, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
+    case NL_APPROXCAPS: launch_chunks<R, 1, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
+    default: launch_chunks<R, 2, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
+    }
+}
+
+// Work arrays for the largest chunk any candidate shape can form.
+template <class R>
+void alloc_group_work(BatchGroup &g, DevArena &arena, int64_t max_units, std::vector<void *> &owned)
+{
+    Scratch sc(&arena);
+    switch (g.strategy) {
+    case NL_NOCAPS: alloc_work<R, 0>(g.A, sc, max_units); break;
+    case NL_APPROXCAPS: alloc_work<R, 1>(g.A, sc, max_units); break;
+    default: alloc_work<R, 2>(g.A, sc, max_units); break;
+    }
+    owned.insert(owned.end(), sc.mine.begin(), sc.mine.end());
+    sc.mine.clear();    // kept by the batch
 }
 
 }  // namespace nla

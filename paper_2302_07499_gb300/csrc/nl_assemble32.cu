@@ -13,3 +13,13 @@ void nl_probe_fp32(const double *tv, const double4 *tv4, const double *xs, const
 {
     nla::launch_probe<float>(tv, tv4, xs, ids, n, delta2, strategy, nmc, seed, out, defer);
 }
+
+void nl_batch_alloc_work_fp32(nla::BatchGroup &g, DevArena &arena, int64_t max_units, std::vector<void *> &owned)
+{
+    nla::alloc_group_work<float>(g, arena, max_units, owned);
+}
+
+void nl_batch_launch_fp32(const nla::BatchGroup &g, const nla::Shape &sh, cudaStream_t s)
+{
+    nla::launch_group<float>(g, sh, s);
+}

@@ -142,6 +142,17 @@ nl_status nl_pairs_build_impl(nl_mesh *mesh, double delta, nl_pairs **out);
 void nl_assemble_fp64(nl_system *sys, double *D, double *strips, double *TT, uint64_t *stats);
 void nl_assemble_fp32(nl_system *sys, float *D, double *strips, double *TT, uint64_t *stats);
 void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT);
+void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT,
+                           double *G, double *E, cudaStream_t s);
+nl_status nl_check_assemble_opts(const nl_assemble_opts *opts);
+nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts);
+void nl_count_launches(uint64_t n);
+void nl_uncount_launches(uint64_t n);
+namespace nla { struct BatchGroup; struct Shape; }
+void nl_batch_alloc_work_fp32(nla::BatchGroup &g, DevArena &arena, int64_t max_units, std::vector<void *> &owned);
+void nl_batch_alloc_work_fp64(nla::BatchGroup &g, DevArena &arena, int64_t max_units, std::vector<void *> &owned);
+void nl_batch_launch_fp32(const nla::BatchGroup &g, const nla::Shape &sh, cudaStream_t s);
+void nl_batch_launch_fp64(const nla::BatchGroup &g, const nla::Shape &sh, cudaStream_t s);
 nl_status nl_solve_impl(nl_system *sys, const nl_solve_opts *opts, double *u_out, int where,
                         nl_solve_info *info);
 

@@ -164,17 +164,16 @@ unsigned wblocks(int64_t n) { return (unsigned)std::max<int64_t>(1, nl_cdiv<int6
 
 }  // namespace
 
-void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT)
+// The reduction into K, A, b with caller-given scratch G [nnz] and E [10 nt]
+// (stream-ordered, no synchronisation: capturable in a CUDA graph).
+void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT,
+                           double *G, double *E, cudaStream_t s)
 {
     nl_pairs *P = sys->pairs;
     nl_mesh *m = P->mesh;
-    cudaStream_t s = sys->arena.stream();
-    Scratch sc(&sys->arena);
-    double *G = sc.get<double>(P->nnz);
     { k_strip_gather<<<wblocks(m->nv), 256, 0, s>>>(P->rowptr, m->ne_ptr, m->ne_ent, m->outer_of, P->strip_off, strips,
                                                  m->nv, G); nl_count_launch(); }
     NL_CHECK_LAUNCH();
-    double *E = sc.get<double>(10 * m->nt);
     if (d_is_float)
         { k_elem_blocks<float><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->in_omega,
                                                            m->outer_of, (const float *)D, TT, sys->opts.gamma / 2.0,
@@ -193,6 +192,16 @@ void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const doubl
     { k_system<<<wblocks(m->n_free), 256, 0, s>>>(P->rowptr, P->col, sys->K, m->free_nodes, m->free_idx, P->a_rowptr,
                                                P->a_src, sys->F, sys->g, m->n_free, sys->A, sys->A32, sys->b); nl_count_launch(); }
     NL_CHECK_LAUNCH();
+}
+
+void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT)
+{
+    nl_pairs *P = sys->pairs;
+    nl_mesh *m = P->mesh;
+    Scratch sc(&sys->arena);
+    double *G = sc.get<double>(P->nnz);
+    double *E = sc.get<double>(10 * m->nt);
+    nl_reduce_system_into(sys, D, d_is_float, strips, TT, G, E, sys->arena.stream());
     // scratch is released (stream-ordered) when sc goes out of scope
-    NL_CUDA(cudaStreamSynchronize(s));
+    NL_CUDA(cudaStreamSynchronize(sys->arena.stream()));
 }

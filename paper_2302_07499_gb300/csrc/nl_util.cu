@@ -14,6 +14,8 @@ static thread_local char g_err[1024] = {0};
 static std::atomic<unsigned long long> g_launches{0};
 
 void nl_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void nl_count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void nl_uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 extern "C" uint64_t nl_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 void nl_set_error(const char *fmt, ...)
