@@ -62,6 +62,15 @@ OPS_PER_PAIR_POINT = 28
 ALU_LANES_PER_SM = 128
 
 
+def _measured_peak(key, fallback):
+    """(value, source) from the measured peaks file, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key]), "measured"
+    except (OSError, ValueError, KeyError):
+        return fallback, "fallback"
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -276,6 +285,23 @@ def run_ours(args, ws, rank, local):
     e2e = {"value": npairs / (float(np.mean(e2e_ms)) / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": float(np.mean(e2e_ms))}
 
+    # SpMV of the CG on this workload's A (HBM-bound when A exceeds L2)
+    m = nl.Mesh(d_verts, d_tets, d_om, d_free, dev)
+    p = nl.Pairs(m, delta)
+    s = nl.System(p, strategy=strategy, mc_points=nmc, seed=seed, precision=nl.FP32_COMP, gamma=gamma,
+                  f_const=-6.0, g=d_g)
+    hbm = _measured_peak("hbm_gbs", 6800.0)
+    spmv = {}
+    for name, prec in (("fp64", nl.FP64), ("fp32", nl.FP32_COMP)):
+        ms_, by = s.spmv_time(prec, reps=50)
+        spmv[name] = {"ms": ms_, "bytes": by, "achieved_gbs": by / (ms_ / 1e3) / 1e9,
+                      "frac_of_measured_hbm": by / (ms_ / 1e3) / 1e9 / hbm[0]}
+    spmv["peak_gbs"] = hbm[0]
+    spmv["peak_source"] = hbm[1]
+    spmv["a_bytes_fp64"] = int(steps[0]["nnz_a"] * 12)
+    spmv["l2_bytes"] = getattr(torch.cuda.get_device_properties(local), "L2_cache_size", None)
+    s.close(); p.close(); m.close()
+
     # roofline of the dominant kernel (the cut-point kernel k_events, which
     # holds the cells, caps and Monte Carlo samples): ALU-bound.  Its duration
     # is the sum over the assembly's chunks of CUDA events recorded on the
@@ -326,6 +352,7 @@ def run_ours(args, ws, rank, local):
                "rel_residual": steps[-1]["cg"]["rel_residual"]},
         "fp64": fp64,
         "roofline": roofline,
+        "spmv": spmv,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clocks,
@@ -361,6 +388,191 @@ def cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=15.0):
     npairs, t = run(outer_all[:n1])
     return {"value": npairs / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "first %d of %d outer elements (%d element pairs), %.1f s" % (n1, len(outer_all), npairs, t)}
+
+
+def run_batch(args, ws, rank, local):
+    """Batched assembly of the 256-problem set (1/h ~ U{8..20}, delta/h ~
+    U{1,2,3}, strategy ~ U{nocaps, approxcaps, fullcaps-64}, seed 3; FP32-comp
+    assembly).  The problems run as consecutive sub-batches of at most
+    --batch-pairs element pairs (device memory), each an nl_batch whose launch
+    shape is autotuned on the first sub-batch and whose run is a CUDA graph.
+    value = all pairs / the summed device time of the batched runs; the same
+    problems assembled one by one (nl_assemble) give the solo figure.  The
+    first problem of every sub-batch is checked bitwise against its solo
+    assembly."""
+    import torch
+    import paper_2302_07499_gb300 as nl
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    dev = nl.Device()
+    spec = I.batch_problems(256, 3)
+    problems = []
+    for inv_h, ratio, strat in spec:
+        mesh, delta = I.cube_problem(inv_h, ratio)
+        kw = dict(strategy=strat, mc_points=64, seed=1, precision=nl.FP32_COMP, gamma=I.gamma_const(delta),
+                  f_const=-6.0, g=I.quadratic_g(mesh.verts))
+        problems.append((mesh, delta, kw))
+
+    def build(i):
+        mesh, delta, _ = problems[i]
+        m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+        return m, nl.Pairs(m, delta)
+
+    # solo: each problem alone (pairs built outside the timed call)
+    solo_ms, npairs, first_vals = [], [], {}
+    for w in range(2):          # one warm-up pass over a few problems, then the timed pass
+        rng = range(4) if w == 0 else range(len(problems))
+        for i in rng:
+            m, p = build(i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sys_ = nl.System(p, **problems[i][2])
+            e1.record(stream)
+            e1.synchronize()
+            if w == 1:
+                solo_ms.append(e0.elapsed_time(e1))
+                npairs.append(p.info["n_pairs"])
+                first_vals[i] = sys_.csr_numpy(nl.MAT_K)[2].copy()
+            sys_.close(); p.close(); m.close()
+    # sub-batches of consecutive problems under the pair budget
+    groups, cur, acc = [], [], 0
+    for i, n_ in enumerate(npairs):
+        if cur and acc + n_ > args.batch_pairs:
+            groups.append(cur)
+            cur, acc = [], 0
+        cur.append(i)
+        acc += n_
+    if cur:
+        groups.append(cur)
+    batch_ms, shape, checked, equal, launches, tried = [], None, 0, True, 0, None
+    l0 = nl.kernel_launches()
+    for gi, ids in enumerate(groups):
+        built = [build(i) for i in ids]
+        b = nl.Batch([(p, problems[i][2]) for i, (m, p) in zip(ids, built)], autotune=(shape is None),
+                     use_graph=True, shape=shape)
+        info = b.info()
+        if shape is None:
+            shape = (info["units_per_chunk"], info["classify_threads"])
+            tried = info["tried"]
+        b.run()                  # warm-up replay
+        t = []
+        for _ in range(args.steps):
+            b.run()
+            t.append(b.info()["last_run_ms"])
+        batch_ms.append(float(np.mean(t)))
+        launches += b.info()["launches_per_run"]
+        got = b.system(0).csr_numpy(nl.MAT_K)[2]
+        equal &= bool(np.array_equal(got, first_vals[ids[0]]))
+        checked += 1
+        b.close()
+        for m, p in built:
+            p.close(); m.close()
+    total_pairs = int(sum(npairs))
+    value = total_pairs / (sum(batch_ms) / 1e3)
+    solo_value = total_pairs / (sum(solo_ms) / 1e3)
+    tets = [6 * (inv_h + 2 * r) ** 3 for inv_h, r, _ in spec]
+    line = {"metric": "batched assembly element-pairs/s (256 problems)", "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": 1, "ms_per_step": float(sum(batch_ms)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch256_seed3", "problems": len(spec), "tets_min": min(tets),
+                       "tets_max": max(tets), "tets_total": int(sum(tets)), "element_pairs": total_pairs,
+                       "strategies": {STRAT_NAME[k]: sum(1 for x in spec if x[2] == k) for k in range(3)},
+                       "precision": "FP32-comp", "mc_points": 64, "seed": 1,
+                       "sub_batches": len(groups), "batch_pairs_budget": args.batch_pairs,
+                       "shape": {"units_per_chunk": shape[0], "classify_threads": shape[1]},
+                       "autotuner": tried, "graph": True},
+            "solo": {"value": solo_value, "ms": float(sum(solo_ms))},
+            "speedup_vs_solo": value / solo_value,
+            "parity": {"bitwise_equal_to_solo": equal, "problems_checked": checked},
+            "gpu_launches": int(launches)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def _serve_stream(nl, reqs, precision, mixed, workers, budget):
+    """Replay the arrivals in real time against a fresh server; per request
+    (latency, queue delay, service, pairs, status)."""
+    srv = nl.Server(budget_bytes=budget, workers=workers, cache=True)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        dt = r["arrival"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        req = nl.Server.box_request(r["inv_h"], r["ratio"], strategy=r["strategy"], mc_points=max(1, r["mc"]),
+                                    seed=1, precision=precision, mixed=mixed, rtol=1e-10)
+        tickets.append(srv.submit(req))
+    out = []
+    for t in tickets:
+        res, _ = srv.wait(t)
+        out.append(res)
+        srv.release(t)
+    srv.close()
+    return out
+
+
+def _serve_summary(res, arrivals_span):
+    ok = [r for r in res if r["status"] in (0, 4)]
+    lat = np.array([r["t_done"] - r["t_submit"] for r in ok]) * 1e3
+    qd = np.array([r["t_start"] - r["t_submit"] for r in ok]) * 1e3
+    svc = np.array([r["t_done"] - r["t_start"] for r in ok]) * 1e3
+    t_first = min(r["t_submit"] for r in res)
+    t_last = max(r["t_done"] for r in res)
+    pairs = int(sum(r["n_pairs"] for r in ok))
+    makespan = t_last - t_first
+    return {"requests": len(res), "completed": len(ok), "failed": len(res) - len(ok),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_queue_ms": float(qd.mean()), "p50_service_ms": float(np.percentile(svc, 50)),
+            "element_pairs": pairs, "makespan_s": makespan, "pairs_per_s": pairs / makespan,
+            "requests_per_s": len(ok) / makespan, "arrival_span_s": arrivals_span,
+            "offered_load": float(svc.sum() / 1e3 / max(arrivals_span, 1e-9)),
+            "max_queue_depth": int(max(r["queue_depth_at_start"] for r in ok)),
+            "cache_hits": int(sum(r["cache_hit"] for r in ok)),
+            "failures": sorted({"%d: %s" % (r["status"], r["message"]) for r in res if r["status"] not in (0, 4)})}
+
+
+def run_serve(args, ws, rank, local):
+    """The request stream (Poisson arrivals at 20/s, sizes log-uniform in
+    10k..400k elements, delta/h ~ U[1,4], 40% fullcaps-128 / 30% approxcaps /
+    30% nocaps, seed 5) replayed in real time against the server (150 GB
+    budget, --workers concurrent streams): the first --requests requests in
+    FP32-comp with mixed CG, and the first --fp64-requests of them again in
+    plain FP64 (the same requests).  Latency = completion - submission."""
+    import torch
+    import paper_2302_07499_gb300 as nl
+
+    torch.cuda.set_device(local)
+    reqs = I.request_stream(2000, 20.0, 5)[:args.requests]
+    span = reqs[-1]["arrival"] - reqs[0]["arrival"]
+    budget = 150 * 10 ** 9
+    # warm-up: a few small requests (module load, pools)
+    warm = [dict(r, arrival=0.0) for r in sorted(reqs, key=lambda r: r["inv_h"])[:3]]
+    _serve_stream(nl, warm, nl.FP32_COMP, True, args.workers, budget)
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = nl.kernel_launches()
+    res32 = _serve_stream(nl, reqs, nl.FP32_COMP, True, args.workers, budget)
+    launches = nl.kernel_launches() - l0
+    nf = min(args.fp64_requests, len(reqs))
+    res64 = _serve_stream(nl, reqs[:nf], nl.FP64, False, args.workers, budget) if nf > 0 else []
+    clocks = sampler.stop()
+    s32 = _serve_summary(res32, span)
+    s32_prefix = _serve_summary(res32[:nf], reqs[nf - 1]["arrival"] - reqs[0]["arrival"]) if nf > 1 else None
+    s64 = _serve_summary(res64, reqs[nf - 1]["arrival"] - reqs[0]["arrival"]) if nf > 1 else None
+    line = {"metric": "served assemble+solve: element-pairs/s and p50/p99 latency, FP32-comp vs FP64",
+            "value": s32["pairs_per_s"], "unit": UNIT, "n_gpus": ws, "steps": len(reqs), "warmup": len(warm),
+            "ms_per_step": s32["makespan_s"] * 1e3 / max(1, s32["completed"]), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve_stream_seed5", "requests": len(reqs), "rate_per_s": 20.0,
+                       "tets": "log-uniform 1e4..4e5", "delta_over_h": "U[1,4]",
+                       "strategies": "40% fullcaps-128 / 30% approxcaps / 30% nocaps", "budget_bytes": budget,
+                       "workers": args.workers, "cache": True, "solve": "mixed CG to 1e-10 (FP64: plain CG)"},
+            "fp32_comp": s32, "fp32_comp_same_prefix_as_fp64": s32_prefix, "fp64": s64,
+            "clocks": clocks, "gpu_launches": int(launches)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_reference(args, ws, rank):
@@ -408,14 +620,23 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cube24_d0125_fullcaps64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cube24_d0125_fullcaps64", choices=sorted(WORKLOADS) + ["batch256_seed3", "serve_stream_seed5"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=300, help="workload serve_stream_seed5: requests replayed")
+    ap.add_argument("--fp64-requests", type=int, default=60, help="workload serve_stream_seed5: FP64 prefix")
+    ap.add_argument("--workers", type=int, default=4, help="workload serve_stream_seed5: server workers")
+    ap.add_argument("--batch-pairs", type=float, default=6e8,
+                    help="element-pair budget of one sub-batch (workload batch256_seed3)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batch256_seed3":
+        run_batch(args, ws, rank, local)
+    elif args.workload == "serve_stream_seed5":
+        run_serve(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -88,6 +88,21 @@ nl_status nl_mesh_create(const nl_device *dev, const double *verts, int64_t nv,
                          const uint8_t *node_free, int where, nl_mesh **out);
 void nl_mesh_destroy(nl_mesh *mesh);
 
+/* nl_mesh_create_box — the Kuhn (Freudenthal) grid of [lo,hi]^3 with `cells`
+ * cubes per side and 6 tetrahedra per cube (Sec. 5 uses tetrahedral meshes of
+ * Omega-hat = Omega plus its interaction collar), generated on the device:
+ * vertex i + (n+1)(j + (n+1)k) at lo + (i,j,k) h with h = (hi-lo)/cells;
+ * element 6*cell + p for the p-th permutation of the axes in lexicographic
+ * order, vertices (c, c+e_p1, c+e_p1+e_p2, c+(1,1,1)), the last two swapped
+ * for the odd permutations so that every element is positively oriented.
+ * Omega = [omega_lo, omega_hi]^3, whose bounds must be grid planes: an
+ * element belongs to Omega when its cube does, a node is free when it lies
+ * strictly inside.  The result is an nl_mesh as from nl_mesh_create.
+ * Errors: NL_EINVAL (cells outside 1..1000, hi <= lo, Omega bounds not on
+ * grid planes), NL_ENOMEM, NL_ECUDA. */
+nl_status nl_mesh_create_box(const nl_device *dev, double lo, double hi, int32_t cells, double omega_lo,
+                             double omega_hi, nl_mesh **out);
+
 /* ---------------------------------------------------------------------------
  * nl_pairs_build — element pairs and the fixed sparsity pattern for a horizon
  * delta.  A pair (T, T') has T in Omega and T' any element with
@@ -272,6 +287,8 @@ typedef struct nl_batch nl_batch;
 typedef struct {
     int autotune;
     int use_graph;
+    int64_t units_per_chunk;   /* with autotune = 0: the shape to use (0: defaults 2^25 and 256) */
+    int classify_threads;
 } nl_batch_opts;
 nl_status nl_batch_create(nl_pairs *const *pairs, const nl_assemble_opts *opts, int n, const nl_batch_opts *bopts,
                           nl_batch **out);
@@ -299,6 +316,68 @@ nl_status nl_batch_get_info(const nl_batch *batch, nl_batch_info *info);
 void nl_batch_destroy(nl_batch *batch);
 
 /* ---------------------------------------------------------------------------
+ * Request server (a system layer; the paper has none): assemble-and-solve
+ * requests on Kuhn box meshes, served continuously.  `workers` threads, each
+ * with its own stream, take requests first come first served; up to
+ * `workers` requests run on the device at once and their kernels overlap.
+ * The head of the queue starts when a worker is free and the estimated
+ * device footprint of the running requests plus the resident cache plus its
+ * own fits budget_bytes (least recently used cache entries that no running
+ * request holds are evicted first; a request whose estimate alone exceeds
+ * the budget fails with NL_ENOMEM).  With cache = 1 the mesh, pairs and
+ * sparsity pattern of a (box, delta) key stay resident between requests.
+ * Device memory is stream-ordered (cudaMallocAsync on the worker's stream);
+ * the server does not use any nl_device.  Every request runs the
+ * single-problem code path, so its result does not depend on what else runs.
+ * Times are seconds since nl_server_create (host steady clock). */
+typedef struct nl_server nl_server;
+typedef struct {
+    int64_t budget_bytes;
+    int workers;               /* 1..16 */
+    int queue_capacity;        /* pending requests; submit beyond it returns NL_EBUSY */
+    int cache;
+} nl_server_opts;
+typedef struct {
+    double lo, hi;             /* the box [lo,hi]^3 and its cells per side */
+    int32_t cells;
+    double omega_lo, omega_hi; /* Omega = [omega_lo, omega_hi]^3 (grid planes) */
+    double delta;
+    nl_assemble_opts assemble; /* g_nodal must be NULL */
+    int g_quadratic;           /* 1: volume constraint g = |x|^2 at the collar nodes; 0: g = 0 */
+    nl_solve_opts solve;
+} nl_request;
+enum { NL_REQ_QUEUED = 0, NL_REQ_RUNNING = 1, NL_REQ_DONE = 2 };
+typedef struct {
+    int state;                 /* NL_REQ_* */
+    nl_status status;          /* when done: NL_OK, NL_ENOTCONV (u = last iterate) or the error */
+    double t_submit, t_start, t_done;
+    double assemble_ms, solve_ms;   /* device time of the assembly and of the solve */
+    int64_t n_pairs, n_free, n_vert, est_bytes;
+    int iterations, refinements, cache_hit, queue_depth_at_start;
+    double rel_residual;
+    char message[160];         /* error message when status is an error */
+} nl_result;
+typedef struct {
+    int queued, running, cache_entries;
+    int64_t cache_bytes, running_bytes;
+} nl_server_load;
+nl_status nl_server_create(const nl_server_opts *opts, nl_server **out);
+/* Queue a request (copied); the ticket names it until nl_server_release. */
+nl_status nl_server_submit(nl_server *server, const nl_request *req, uint64_t *ticket);
+/* The request's state and result so far (never blocks). */
+nl_status nl_server_poll(nl_server *server, uint64_t ticket, nl_result *res);
+/* Wait until the request is done (timeout_s <= 0: no limit; NL_ETIMEOUT
+ * otherwise), then copy its result and, when u_out is not NULL, its nodal
+ * solution (n_vert doubles, host memory of n_u >= n_vert entries). */
+nl_status nl_server_wait(nl_server *server, uint64_t ticket, double timeout_s, nl_result *res, double *u_out,
+                         int64_t n_u);
+/* Forget a finished request (NL_EBUSY while it is queued or running). */
+nl_status nl_server_release(nl_server *server, uint64_t ticket);
+nl_status nl_server_get_load(nl_server *server, nl_server_load *out);
+/* Stops the workers after their current requests; queued ones are dropped. */
+void nl_server_destroy(nl_server *server);
+
+/* ---------------------------------------------------------------------------
  * Diagnostic entry points (not on the assembly path).  Host arrays in and
  * out; they run on the default stream with their own temporary device
  * buffers and synchronise before returning.
@@ -320,6 +399,14 @@ nl_status nl_probe_moments(const double *tets_xyz, const double *x, const uint32
  * draws the fullcaps Monte Carlo points.  out[n][4].  Errors: NL_EINVAL,
  * NL_ECUDA. */
 nl_status nl_probe_philox(const uint32_t *ctr, uint64_t key, int64_t n, uint32_t *out);
+
+/* nl_spmv_time — device time of one SpMV y = A x of the CG (warp per row,
+ * the kernel nl_solve runs) on the system's free block A, FP64 values or the
+ * FP32 copy, averaged over `reps` back-to-back launches after one untimed
+ * launch (CUDA events on the system's stream).  bytes_per_spmv (optional):
+ * the algorithmic traffic nnz (value + column index) + rowptr + x + y.
+ * Errors: NL_EINVAL, NL_ECUDA. */
+nl_status nl_spmv_time(nl_system *sys, int precision, int reps, double *ms_per_spmv, double *bytes_per_spmv);
 
 /* Thread-local message of the last failing call (empty string if none). */
 const char *nl_last_error(void);

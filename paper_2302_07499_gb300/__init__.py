@@ -10,4 +10,4 @@ package is the Python binding.
 """
 from ._binding import (APPROXCAPS, DEVICE, FP32_COMP, FP64, FULLCAPS, HOST, MAT_A, MAT_K, NOCAPS, Device,  # noqa
                        Mesh, NlError, Pairs, System, lib, probe_moments, probe_philox, EXPORTED, LIB_PATH,
-                       kernel_launches, Batch)
+                       kernel_launches, Batch, Server, mesh_box)

@@ -63,7 +63,8 @@ class nl_assemble_stats(C.Structure):
 
 
 class nl_batch_opts(C.Structure):
-    _fields_ = [("autotune", C.c_int), ("use_graph", C.c_int)]
+    _fields_ = [("autotune", C.c_int), ("use_graph", C.c_int), ("units_per_chunk", C.c_int64),
+                ("classify_threads", C.c_int)]
 
 
 class nl_batch_info(C.Structure):
@@ -80,6 +81,29 @@ class nl_solve_opts(C.Structure):
                 ("check_every", C.c_int)]
 
 
+class nl_server_opts(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("workers", C.c_int), ("queue_capacity", C.c_int), ("cache", C.c_int)]
+
+
+class nl_request(C.Structure):
+    _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("cells", C.c_int32), ("omega_lo", C.c_double),
+                ("omega_hi", C.c_double), ("delta", C.c_double), ("assemble", nl_assemble_opts),
+                ("g_quadratic", C.c_int), ("solve", nl_solve_opts)]
+
+
+class nl_result(C.Structure):
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double), ("assemble_ms", C.c_double), ("solve_ms", C.c_double),
+                ("n_pairs", C.c_int64), ("n_free", C.c_int64), ("n_vert", C.c_int64), ("est_bytes", C.c_int64),
+                ("iterations", C.c_int), ("refinements", C.c_int), ("cache_hit", C.c_int),
+                ("queue_depth_at_start", C.c_int), ("rel_residual", C.c_double), ("message", C.c_char * 160)]
+
+
+class nl_server_load(C.Structure):
+    _fields_ = [("queued", C.c_int), ("running", C.c_int), ("cache_entries", C.c_int), ("cache_bytes", C.c_int64),
+                ("running_bytes", C.c_int64)]
+
+
 class nl_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double)]
 
@@ -89,7 +113,8 @@ EXPORTED = ["nl_mesh_create", "nl_mesh_destroy", "nl_pairs_build", "nl_pairs_des
             "nl_pairs_export", "nl_assemble", "nl_system_destroy", "nl_system_csr", "nl_system_rhs",
             "nl_system_stats", "nl_solve", "nl_probe_moments", "nl_probe_philox", "nl_last_error", "nl_version", "nl_kernel_launches",
             "nl_solve_static", "nl_batch_create", "nl_batch_run", "nl_batch_system", "nl_batch_get_info",
-            "nl_batch_destroy"]
+            "nl_batch_destroy", "nl_mesh_create_box", "nl_server_create", "nl_server_submit", "nl_server_poll",
+            "nl_server_wait", "nl_server_release", "nl_server_get_load", "nl_server_destroy", "nl_spmv_time"]
 
 _lib = None
 
@@ -129,6 +154,16 @@ def lib():
     L.nl_batch_get_info.argtypes = [vp, C.POINTER(nl_batch_info)]
     L.nl_batch_destroy.argtypes = [vp]
     L.nl_batch_destroy.restype = None
+    L.nl_mesh_create_box.argtypes = [C.POINTER(nl_device), dp, dp, C.c_int32, dp, dp, C.POINTER(vp)]
+    L.nl_server_create.argtypes = [C.POINTER(nl_server_opts), C.POINTER(vp)]
+    L.nl_server_submit.argtypes = [vp, C.POINTER(nl_request), C.POINTER(C.c_uint64)]
+    L.nl_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(nl_result)]
+    L.nl_server_wait.argtypes = [vp, C.c_uint64, dp, C.POINTER(nl_result), vp, i64]
+    L.nl_server_release.argtypes = [vp, C.c_uint64]
+    L.nl_server_get_load.argtypes = [vp, C.POINTER(nl_server_load)]
+    L.nl_server_destroy.argtypes = [vp]
+    L.nl_server_destroy.restype = None
+    L.nl_spmv_time.argtypes = [vp, C.c_int, C.c_int, C.POINTER(dp), C.POINTER(dp)]
     _lib = L
     return L
 
@@ -214,6 +249,12 @@ class Mesh:
                                     _ptr(arrs[2]), _ptr(arrs[3]), where, C.byref(h)))
         self.h = h
         self._keep = None
+
+    @classmethod
+    def from_handle(cls, h, device, nv, nt):
+        m = cls.__new__(cls)
+        m.device, m._keep, m.h, m.nv, m.nt = device, None, h, int(nv), int(nt)
+        return m
 
     def close(self):
         if getattr(self, "h", None):
@@ -326,6 +367,12 @@ class System:
             _check(st)
         return u, info
 
+    def spmv_time(self, precision=FP64, reps=50):
+        """(ms per SpMV of the CG on A, algorithmic bytes per SpMV)."""
+        ms, by = C.c_double(), C.c_double()
+        _check(lib().nl_spmv_time(self.h, int(precision), int(reps), C.byref(ms), C.byref(by)))
+        return ms.value, by.value
+
     def close(self):
         if getattr(self, "h", None):
             lib().nl_system_destroy(self.h)
@@ -372,7 +419,7 @@ class Batch:
     problems: list of (Pairs, dict of System options).  Each problem's system
     is bitwise equal to System(pairs, **options)."""
 
-    def __init__(self, problems, autotune=True, use_graph=True):
+    def __init__(self, problems, autotune=True, use_graph=True, shape=None):
         self.pairs = [p for p, _ in problems]
         n = len(problems)
         arr = (nl_assemble_opts * n)()
@@ -382,7 +429,8 @@ class Batch:
             arr[i] = o
             keep.append(k)
         hp = (C.c_void_p * n)(*[p.h for p in self.pairs])
-        bo = nl_batch_opts(int(bool(autotune)), int(bool(use_graph)))
+        up, ct = shape if shape else (0, 0)
+        bo = nl_batch_opts(int(bool(autotune)), int(bool(use_graph)), int(up), int(ct))
         h = C.c_void_p()
         _check(lib().nl_batch_create(C.cast(hp, C.c_void_p), C.cast(arr, C.c_void_p), n, C.byref(bo), C.byref(h)))
         self.h = h
@@ -414,6 +462,94 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _result_dict(r):
+    d = {k: getattr(r, k) for k, _ in nl_result._fields_ if k != "message"}
+    d["message"] = r.message.decode(errors="replace")
+    return d
+
+
+class Server:
+    """Request server (nl_server_*): assemble-and-solve requests on Kuhn box
+    meshes, served by `workers` concurrent device streams under an admission
+    budget, with mesh / pairs / pattern residency between requests."""
+
+    def __init__(self, budget_bytes=150 * 10 ** 9, workers=4, queue_capacity=100000, cache=True):
+        o = nl_server_opts(int(budget_bytes), int(workers), int(queue_capacity), int(bool(cache)))
+        h = C.c_void_p()
+        _check(lib().nl_server_create(C.byref(o), C.byref(h)))
+        self.h = h
+
+    @staticmethod
+    def box_request(inv_h, ratio, strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, f_const=-6.0,
+                    g_quadratic=True, rtol=1e-10, mixed=False, max_iter=0, gamma=None):
+        """The unit-cube problem with h = 1/inv_h, delta = ratio*h and a collar
+        of ceil(ratio) cells (the box of the inputs module's cube_problem)."""
+        import math
+        h = 1.0 / inv_h
+        collar = int(math.ceil(ratio - 1e-12))
+        lo, hi = -collar * h, 1.0 + collar * h
+        delta = ratio * h
+        if gamma is None:
+            gamma = 15.0 / (2.0 * math.pi * delta ** 5)
+        a = nl_assemble_opts(int(strategy), int(mc_points), int(seed), int(precision), float(gamma), float(f_const),
+                             None, HOST)
+        sv = nl_solve_opts(float(rtol), int(max_iter), int(bool(mixed)), 0.0, 0)
+        return nl_request(lo, hi, inv_h + 2 * collar, 0.0, 1.0, delta, a, int(bool(g_quadratic)), sv)
+
+    def submit(self, req):
+        t = C.c_uint64()
+        _check(lib().nl_server_submit(self.h, C.byref(req), C.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket):
+        r = nl_result()
+        _check(lib().nl_server_poll(self.h, int(ticket), C.byref(r)))
+        return _result_dict(r)
+
+    def wait(self, ticket, timeout_s=0.0, want_u=False):
+        """(result dict, u or None); does not release the ticket."""
+        r = nl_result()
+        _check(lib().nl_server_poll(self.h, int(ticket), C.byref(r)))
+        u = None
+        if want_u:
+            st = lib().nl_server_wait(self.h, int(ticket), float(timeout_s), C.byref(r), None, 0)
+            if st != NL_OK:
+                _check(st)
+            u = np.zeros(r.n_vert)
+            _check(lib().nl_server_wait(self.h, int(ticket), float(timeout_s), C.byref(r), u.ctypes.data, u.size))
+        else:
+            _check(lib().nl_server_wait(self.h, int(ticket), float(timeout_s), C.byref(r), None, 0))
+        return _result_dict(r), u
+
+    def release(self, ticket):
+        _check(lib().nl_server_release(self.h, int(ticket)))
+
+    def load(self):
+        o = nl_server_load()
+        _check(lib().nl_server_get_load(self.h, C.byref(o)))
+        return {k: getattr(o, k) for k, _ in nl_server_load._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nl_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mesh_box(lo, hi, cells, omega_lo=0.0, omega_hi=1.0, device=None):
+    """nl_mesh_create_box: a Kuhn box mesh generated on the device."""
+    device = device or Device()
+    h = C.c_void_p()
+    _check(lib().nl_mesh_create_box(C.byref(device.c), float(lo), float(hi), int(cells), float(omega_lo),
+                                    float(omega_hi), C.byref(h)))
+    return Mesh.from_handle(h, device, (cells + 1) ** 3, 6 * cells ** 3)
 
 
 def kernel_launches():

@@ -30,11 +30,11 @@ nl_status nl_check_assemble_opts(const nl_assemble_opts *opts)
 
 // A system handle with K, A, b, F and the collar values g allocated (g set,
 // stream-ordered); throws NlError.
-nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts)
+nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts, const nl_device *dev)
 {
     nl_mesh *m = P->mesh;
     nl_system *S = new nl_system();
-    S->arena.dev = P->arena.dev;
+    S->arena.dev = dev ? *dev : P->arena.dev;
     S->pairs = P;
     S->opts = *opts;
     S->opts.g_nodal = nullptr;
@@ -62,7 +62,9 @@ nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts)
     return S;
 }
 
-extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_system **out)
+// nl_assemble with the system's work on the given device / stream (the
+// pairs' own when dev is NULL).
+nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_device *dev, nl_system **out)
 {
     nl_clear_error();
     if (!P || !opts || !out) { nl_set_error("NULL argument"); return NL_EINVAL; }
@@ -71,7 +73,7 @@ extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_s
     nl_mesh *m = P->mesh;
     nl_system *S = nullptr;
     try {
-        S = nl_system_alloc(P, opts);
+        S = nl_system_alloc(P, opts, dev);
     } catch (NlError &e) {
         return e.st;
     }
@@ -115,6 +117,11 @@ extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_s
     }
     *out = S;
     return NL_OK;
+}
+
+extern "C" nl_status nl_assemble(nl_pairs *P, const nl_assemble_opts *opts, nl_system **out)
+{
+    return nl_assemble_on(P, opts, nullptr, out);
 }
 
 extern "C" void nl_system_destroy(nl_system *S)

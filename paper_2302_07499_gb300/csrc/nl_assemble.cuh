@@ -1,15 +1,23 @@
-// Assembly kernel: one thread block per outer element T (persistent loop),
-// one thread per pair (T, T').  Per pair and outer point x_q the inner
-// moments of the approximate ball inside T' are computed (nl_quad.cuh) and
-// turned into the local block of Eq. (replaceBasis):
-//   TT   += c * omega * lambda(x_q) lambda(x_q)^T m0      (summed per T)
-//   TT'  -= c * omega * lambda(x_q) m1^T                   (cross strip of T)
-//   T'T' += c * omega * m2                                  (staged per pair)
-// with c = (gamma/2) |T|/4 and omega = 2 for collar elements T'.
+// Quadrature of the nonlocal assembly, three kernels per chunk of
+// (pair, point) units:
+//   K1 k_classify  one thread per unit (pair, outer point x_q): classifies
+//                  the vertices of T' against the ball around x_q and lists
+//                  the units with a cut (1..3 vertices inside, or a fullcaps
+//                  cap without inside vertices) per class;
+//   K2 k_events    one thread per listed unit, warps of one class: the inner
+//                  moments of the approximate ball inside T' (nl_quad.cuh);
+//   K3 k_combine   one block per outer element T: the local block of
+//                  Eq. (replaceBasis) from the moments of its pairs,
+//     TT   += c * omega * lambda(x_q) lambda(x_q)^T m0      (summed per T)
+//     TT'  -= c * omega * lambda(x_q) m1^T                   (cross strip of T)
+//     T'T' += c * omega * m2                                  (staged per pair)
+//   with c = (gamma/2) |T|/4 and omega = 2 for collar elements T'.
 //
-// Determinism: the cross contributions of a chunk of pairs are added into
-// the strips (the four CSR rows of T's nodes, in shared memory) by one warp
-// per row in pair order; everything else is written to its own slot.
+// Determinism: the cross contributions are added into the strips (the four
+// CSR rows of T's nodes, in shared memory) in an order fixed by the pair
+// order alone; everything else is written to its own slot.  A launch serves
+// one problem or, through the pair -> problem map, a group of problems of a
+// batch, with the same arithmetic per unit.
 #pragma once
 
 #include "nl_asm_types.h"

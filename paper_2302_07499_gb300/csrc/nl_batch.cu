@@ -222,7 +222,14 @@ extern "C" nl_status nl_batch_create(nl_pairs *const *pairs, const nl_assemble_o
                     cands.push_back(sh);
                 }
         } else {
-            cands.push_back(nla::Shape());
+            nla::Shape sh;
+            if (bopts && bopts->units_per_chunk > 0) sh.units_per_chunk = bopts->units_per_chunk;
+            if (bopts && bopts->classify_threads > 0) sh.classify_threads = bopts->classify_threads;
+            NL_REQUIRE(sh.units_per_chunk >= 4096 && sh.units_per_chunk <= (int64_t(1) << 28) &&
+                           (sh.classify_threads == 128 || sh.classify_threads == 256),
+                       "bad launch shape (units per chunk %lld, classification block %d)",
+                       (long long)sh.units_per_chunk, sh.classify_threads);
+            cands.push_back(sh);
         }
         for (auto &g : b->groups) {
             int64_t mu = 0;

@@ -145,7 +145,8 @@ void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const doubl
 void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT,
                            double *G, double *E, cudaStream_t s);
 nl_status nl_check_assemble_opts(const nl_assemble_opts *opts);
-nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts);
+nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts, const nl_device *dev = nullptr);
+nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_device *dev, nl_system **out);
 void nl_count_launches(uint64_t n);
 void nl_uncount_launches(uint64_t n);
 namespace nla { struct BatchGroup; struct Shape; }

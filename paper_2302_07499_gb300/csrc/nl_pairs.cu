@@ -718,6 +718,88 @@ unsigned blocks_for(int64_t n, int threads) { return (unsigned)std::max<int64_t>
 }  // namespace
 
 // ===========================================================================
+// ---------------------------------------------------------------------------
+// Kuhn (Freudenthal) box mesh generated on the device: the same vertex and
+// element numbering, coordinates and orientation as the host generator of
+// the inputs module.  Vertex id = i + (n+1)(j + (n+1)k), coordinate lo + i*h
+// with h = (hi - lo)/n; element id = 6*cell + p for the p-th axis permutation
+// in lexicographic order, vertices (c, c+e_p1, c+e_p1+e_p2, c+(1,1,1)) with
+// the last two swapped for the odd permutations (their signed volume is
+// negative otherwise).  Omega = the cells inside [olo, ohi)^3 (grid
+// indices); a node is free when strictly inside.
+__global__ void k_box_verts(int n, double lo, double h, int olo, int ohi, double *v3, uint8_t *node_free)
+{
+    const int64_t m = n + 1;
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= m * m * m) return;
+    const int i = (int)(id % m), j = (int)((id / m) % m), k = (int)(id / (m * m));
+    v3[3 * id] = lo + (double)i * h;
+    v3[3 * id + 1] = lo + (double)j * h;
+    v3[3 * id + 2] = lo + (double)k * h;
+    node_free[id] = (i > olo && i < ohi && j > olo && j < ohi && k > olo && k < ohi) ? 1 : 0;
+}
+
+__global__ void k_box_tets(int n, int olo, int ohi, int4 *tets, uint8_t *in_omega)
+{
+    const int64_t m = n + 1;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 6 * (int64_t)n * n * n) return;
+    const int64_t cell = t / 6;
+    const int p = (int)(t % 6);
+    const int ci = (int)(cell % n), cj = (int)((cell / n) % n), ck = (int)(cell / ((int64_t)n * n));
+    // lexicographic permutations of (0, 1, 2)
+    const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    int c[3] = {ci, cj, ck};
+    int vid[4];
+    for (int s = 0; s < 4; ++s) {
+        if (s > 0) c[P[p][s - 1]] += 1;
+        vid[s] = (int)(c[0] + m * (c[1] + m * c[2]));
+    }
+    const bool odd = (p == 1 || p == 2 || p == 5);
+    tets[t] = odd ? make_int4(vid[0], vid[1], vid[3], vid[2]) : make_int4(vid[0], vid[1], vid[2], vid[3]);
+    in_omega[t] = (ci >= olo && ci < ohi && cj >= olo && cj < ohi && ck >= olo && ck < ohi) ? 1 : 0;
+}
+
+extern "C" nl_status nl_mesh_create_box(const nl_device *dev, double lo, double hi, int32_t cells, double omega_lo,
+                                        double omega_hi, nl_mesh **out)
+{
+    nl_clear_error();
+    if (!out) { nl_set_error("out is NULL"); return NL_EINVAL; }
+    *out = nullptr;
+    if (cells < 1 || cells > 1000 || !(hi > lo) || !isfinite(lo) || !isfinite(hi)) {
+        nl_set_error("bad box (cells %d, [%g, %g])", cells, lo, hi);
+        return NL_EINVAL;
+    }
+    const double h = (hi - lo) / cells;
+    const double fo = (omega_lo - lo) / h, fe = (omega_hi - lo) / h;
+    if (fabs(fo - nearbyint(fo)) > 1e-9 || fabs(fe - nearbyint(fe)) > 1e-9 || nearbyint(fo) < 0 ||
+        nearbyint(fe) > cells || !(fe > fo)) {
+        nl_set_error("Omega bounds must lie on grid planes inside the box");
+        return NL_EINVAL;
+    }
+    const int olo = (int)nearbyint(fo), ohi = (int)nearbyint(fe);
+    const int64_t m = cells + 1, nv = m * m * m, nt = 6 * (int64_t)cells * cells * cells;
+    DevArena tmp;
+    if (dev) tmp.dev = *dev;
+    nl_status st = NL_OK;
+    try {
+        cudaStream_t s = tmp.stream();
+        double *v3 = tmp.get<double>(3 * nv);
+        int4 *t4 = tmp.get<int4>(nt);
+        uint8_t *om = tmp.get<uint8_t>(nt), *nf = tmp.get<uint8_t>(nv);
+        { k_box_verts<<<blocks_for(nv, 256), 256, 0, s>>>(cells, lo, h, olo, ohi, v3, nf); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        { k_box_tets<<<blocks_for(nt, 256), 256, 0, s>>>(cells, olo, ohi, t4, om); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        st = nl_mesh_create(dev, v3, nv, reinterpret_cast<const int32_t *>(t4), nt, om, nf, NL_DEVICE, out);
+        NL_CUDA(cudaStreamSynchronize(s));
+    } catch (NlError &e) {
+        st = e.st;
+    }
+    tmp.release_all();
+    return st;
+}
+
 extern "C" nl_status nl_mesh_create(const nl_device *dev, const double *verts, int64_t nv, const int32_t *tets,
                                     int64_t nt, const uint8_t *tet_in_omega, const uint8_t *node_free, int where,
                                     nl_mesh **out)

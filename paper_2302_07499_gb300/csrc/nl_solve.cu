@@ -303,6 +303,59 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
     return ret;
 }
 
+namespace {
+__global__ void k_fill_ones(double *a, float *b, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { a[i] = 1.0; b[i] = 1.0f; }
+}
+}  // namespace
+
+extern "C" nl_status nl_spmv_time(nl_system *S, int precision, int reps, double *ms_per_spmv, double *bytes_per_spmv)
+{
+    nl_clear_error();
+    if (!S || !ms_per_spmv || reps < 1 || (precision != NL_FP64 && precision != NL_FP32_COMP)) {
+        nl_set_error("bad argument");
+        return NL_EINVAL;
+    }
+    try {
+        const nl_pairs *P = S->pairs;
+        const int64_t n = P->mesh->n_free, nnz = P->nnz_a;
+        cudaStream_t s = S->arena.stream();
+        Scratch sc(&S->arena);
+        double *xd = sc.get<double>(n), *yd = sc.get<double>(n);
+        float *xf = sc.get<float>(n), *yf = sc.get<float>(n);
+        { k_fill_ones<<<(unsigned)nl_cdiv<int64_t>(n, 256), 256, 0, s>>>(xd, xf, n); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        const int nb = std::max(1, std::min<int>(nl_num_sms() * 8, (int)nl_cdiv<int64_t>(n * 32, RB)));
+        cudaEvent_t e0, e1;
+        NL_CUDA(cudaEventCreate(&e0));
+        NL_CUDA(cudaEventCreate(&e1));
+        for (int w = 0; w < 2; ++w) {
+            NL_CUDA(cudaEventRecord(e0, s));
+            for (int k = 0; k < (w ? reps : 1); ++k) {
+                if (precision == NL_FP64)
+                    { k_spmv_dot<double, double><<<nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, xd, yd, n, nullptr, nullptr); nl_count_launch(); }
+                else
+                    { k_spmv_dot<float, float><<<nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A32, xf, yf, n, nullptr, nullptr); nl_count_launch(); }
+            }
+            NL_CUDA(cudaEventRecord(e1, s));
+        }
+        NL_CHECK_LAUNCH();
+        NL_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *ms_per_spmv = ms / reps;
+        const double vb = precision == NL_FP64 ? 8.0 : 4.0;
+        if (bytes_per_spmv) *bytes_per_spmv = (double)nnz * (vb + 4.0) + (double)(n + 1) * 8.0 + 2.0 * n * vb;
+    } catch (NlError &e) {
+        return e.st;
+    }
+    return NL_OK;
+}
+
 extern "C" nl_status nl_solve(nl_system *S, const nl_solve_opts *opts, double *u_out, int where, nl_solve_info *info)
 {
     nl_clear_error();
