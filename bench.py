@@ -151,7 +151,7 @@ def _traffic_record():
         return None
     if rec.get("source_sha") != _kernel_source_sha():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec.get("dram_bytes_per_step")
 
 
 def _event_ops(st):

@@ -527,7 +527,9 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
     constexpr bool kDefer = sizeof(R) == 4 && STRAT == 1;
     const size_t smem = combine_smem_bytes(A.max_row, sizeof(R));
     NL_REQUIRE(smem <= 220 * 1024, "rows of %d columns need %zu bytes of shared memory", A.max_row, smem);
-    NL_CUDA(cudaFuncSetAttribute(k_combine<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the attribute is per function and process-wide: always the same limit,
+    // so concurrent launches of other sizes (other threads) never lower it
+    NL_CUDA(cudaFuncSetAttribute(k_combine<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     int per_sm = 0;
     NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<R, B>, NT, smem));
     per_sm = per_sm < 1 ? 1 : per_sm;

@@ -376,14 +376,20 @@ __device__ bool pair_predicate(const PairArgs &A, const double3 xq[4], const flo
 
 // One warp per outer element: scan the stencil of grid cells and test each
 // candidate T'.  PASS 0 only bounds the number of candidates (centroid
-// filter); PASS 1 applies the filters and the exact predicate once and writes
-// the survivors, in scan order, into the outer element's bounded slot.
+// filter).  PASS 1 applies the cheap filters to 32 candidates at a time,
+// queues the survivors per warp in shared memory, and runs the exact
+// predicate on full warps of queued candidates (the order of the output does
+// not matter: every element's list is sorted afterwards); the survivors go to
+// the outer element's bounded slot.
 template <int PASS>
-__global__ void k_pairs(PairArgs A, const int64_t *bptr, int64_t *counts, int32_t *out)
+__global__ void __launch_bounds__(128) k_pairs(PairArgs A, const int64_t *bptr, int64_t *counts, int32_t *out)
 {
+    __shared__ int32_t wq[4][64];
     int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (warp >= A.n_outer) return;
+    int32_t *Q = wq[threadIdx.x >> 5];
+    const unsigned lt = (1u << lane) - 1u;
     int32_t T = A.outer_ids[warp];
     const float4 cT = A.tet_cf[T];
     double3 xq[4];
@@ -400,7 +406,22 @@ __global__ void k_pairs(PairArgs A, const int64_t *bptr, int64_t *counts, int32_
     int cell = A.cell_of[T];
     int cx = cell % A.g.n[0], cy = (cell / A.g.n[0]) % A.g.n[1], cz = cell / (A.g.n[0] * A.g.n[1]);
     int64_t n = 0;
+    int nq = 0;     // queued candidates (warp-uniform, below 64)
     int64_t base = (PASS == 1) ? bptr[warp] : 0;
+    // exact predicate on the last cnt queued candidates (cnt <= 32)
+    auto drain = [&](int cnt) {
+        bool keep = false;
+        int32_t Tp = -1;
+        if (lane < cnt) {
+            Tp = Q[nq - cnt + lane];
+            keep = pair_predicate(A, xq, xh, xl, A.tets[Tp]);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) out[base + n + __popc(m & lt)] = Tp;
+        n += __popc(m);
+        nq -= cnt;
+        __syncwarp();
+    };
     for (int dz = -A.ks; dz <= A.ks; ++dz) {
         int z = cz + dz;
         if (z < 0 || z >= A.g.n[2]) continue;
@@ -430,16 +451,24 @@ __global__ void k_pairs(PairArgs A, const int64_t *bptr, int64_t *counts, int32_
                                 const float qx = xh[q].x - cp.x, qy = xh[q].y - cp.y, qz = xh[q].z - cp.z;
                                 any |= (qx * qx + qy * qy) + qz * qz <= lq * lq;
                             }
-                            keep = any && pair_predicate(A, xq, xh, xl, A.tets[Tp]);
+                            keep = any;
                         }
                     }
-                    unsigned m = __ballot_sync(0xffffffffu, keep);
-                    if (PASS == 1 && keep) out[base + n + __popc(m & ((1u << lane) - 1u))] = Tp;
-                    n += __popc(m);
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (PASS == 0) {
+                        n += __popc(m);
+                    } else {
+                        if (keep) Q[nq + __popc(m & lt)] = Tp;
+                        nq += __popc(m);
+                        __syncwarp();
+                        if (nq >= 32) drain(32);
+                    }
                 }
             }
         }
     }
+    if (PASS == 1)
+        while (nq > 0) drain(nq < 32 ? nq : 32);
     if (lane == 0) counts[warp] = n;
 }
 

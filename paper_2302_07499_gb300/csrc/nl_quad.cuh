@@ -771,9 +771,15 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         R o1 = orient(c1, c2, dd2, d1), o2 = orient(c1, c2, dd2, v[role[0]]);
         bool exact = false;
         if (F32 && sx) {
-            P3<R> e = sub(v[role[2]], v[role[0]]);
-            R L = (absr(e.x) + absr(e.y)) + absr(e.z);
-            R tol = R(1e-4) * L * L * L;
+            // The FP32 points and determinants err by less than about
+            // (3 delta/L + 6) 2^-24 L^3 (coordinates of size delta relative to
+            // x, quad of size L); decisions within 1e-5 L^2 max(L, delta) of
+            // zero, nine times that bound or more, are retaken in FP64.
+            const P3<R> e1 = sub(v[role[2]], v[role[0]]), e2 = sub(v[role[3]], v[role[1]]);
+            const R L1 = (absr(e1.x) + absr(e1.y)) + absr(e1.z), L2 = (absr(e2.x) + absr(e2.y)) + absr(e2.z);
+            const R L = L1 > L2 ? L1 : L2;
+            const R dl = sqrt(d2);
+            const R tol = R(1e-5) * L * L * (L > dl ? L : dl);
             if (absr(o1) <= tol || absr(o2) <= tol) {
                 diag_c2d1 = strict_diag(sx, role[0], role[1], role[2], role[3]);
                 exact = true;

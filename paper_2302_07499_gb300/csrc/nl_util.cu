@@ -198,8 +198,10 @@ void nl_segmented_sort_i32(int32_t *keys, const int64_t *ptr, int64_t nseg, int6
     while (p2 < max_seg) p2 <<= 1;
     int threads = std::min(1024, std::max(32, p2 / 2));
     size_t smem = sizeof(int32_t) * (size_t)p2;
+    // one process-wide limit for every size (concurrent callers never lower it)
     if (smem > 48 * 1024)
-        NL_CUDA(cudaFuncSetAttribute(k_seg_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NL_CUDA(cudaFuncSetAttribute(k_seg_bitonic, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(int32_t) * 32768)));
     for (int64_t s0 = 0; s0 < nseg; s0 += 2147483647LL) {
         int64_t cnt = std::min<int64_t>(nseg - s0, 2147483647LL);
         { k_seg_bitonic<<<(unsigned)cnt, threads, smem, s>>>(keys, ptr + s0, p2); nl_count_launch(); }
