@@ -29,6 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 NOCAPS, APPROXCAPS, FULLCAPS = 0, 1, 2
+BARYCENTER, OVERLAP, INSIDE = 3, 4, 5     # element-level strategies (Sec. 4.3)
 
 
 def build(force: bool = False) -> str:

@@ -708,11 +708,32 @@ static int arc_midpoints(const double v[4][3], const double x[3], double delta, 
     return nm;
 }
 
+/* Element-level approximate balls (Sec. 4.3: the element is taken whole or
+ * not at all): barycenter - T' when its barycenter lies in the closed ball;
+ * overlap - T' when it meets the closed ball; inside - T' when all four
+ * vertices lie in the open ball.                                          */
+static int element_level_full(const double v[4][3], const double x[3], double delta, int strategy,
+                              const classify_t *c)
+{
+    const double d2 = delta * delta;
+    if (strategy == OR_INSIDE) return c->m == 4;
+    if (strategy == OR_OVERLAP) return or_dist2_point_tet(x, &v[0][0]) <= d2;
+    double w[3];
+    for (int d = 0; d < 3; ++d) w[d] = 0.25 * ((v[0][d] + v[1][d]) + (v[2][d] + v[3][d])) - x[d];
+    return (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2] <= d2;
+}
+
 /* Deterministic cells of the approximate ball inside T' (nocaps/approxcaps,
- * and the nocaps part of fullcaps).  Returns the number of tetrahedra.      */
+ * the nocaps part of fullcaps, and T' itself or nothing for the
+ * element-level strategies).  Returns the number of tetrahedra.            */
 static int region_cells(const double v[4][3], const double x[3], double delta, int strategy,
                         const classify_t *c, double cells[][4][3], int maxcells)
 {
+    if (strategy >= OR_BARYCENTER) {
+        if (!element_level_full(v, x, delta, strategy, c)) return 0;
+        memcpy(cells[0], v, sizeof(double) * 12);
+        return 1;
+    }
     if (c->m == 4) {
         memcpy(cells[0], v, sizeof(double) * 12);
         return 1;

@@ -6,6 +6,9 @@
 #define OR_NOCAPS 0
 #define OR_APPROXCAPS 1
 #define OR_FULLCAPS 2
+#define OR_BARYCENTER 3
+#define OR_OVERLAP 4
+#define OR_INSIDE 5
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double or_tet_volume(const double v[12]);

@@ -323,6 +323,67 @@ def test_ball_volume_bounds_and_fullcaps_moments():
     assert abs(lap - 6.0) < 4 * I.gamma_const(delta) * seconds.std(ddof=1) / math.sqrt(seconds.size)
 
 
+def test_element_level_strategies():
+    """barycenter / overlap / inside (Sec. 4.3) take T' whole or not at all:
+    the moments are those of T' (closed forms) or zero, and the decision is
+    the centroid in the closed ball / T' meeting the closed ball (distance by
+    constrained minimisation) / every vertex in the open ball."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(21)
+    n_full = {O.BARYCENTER: 0, O.OVERLAP: 0, O.INSIDE: 0}
+    for _ in range(60):
+        v = rand_tet(rng)
+        x = v.mean(axis=0) + rng.normal(size=3) * 0.8
+        delta = rng.uniform(0.4, 2.0)
+        vol = O.tet_volume(v)
+        full_form = np.concatenate([[vol], [vol / 4] * 4,
+                                    [vol * (2 if a == b else 1) / 20 for a in range(4) for b in range(a, 4)]])
+        f = lambda lam: float(np.sum((lam @ v - x) ** 2))
+        best = np.inf
+        for start in np.eye(4).tolist() + [[0.25] * 4]:
+            res = minimize(f, start, method="SLSQP", bounds=[(0, 1)] * 4,
+                           constraints=[{"type": "eq", "fun": lambda l: l.sum() - 1}],
+                           options={"ftol": 1e-15, "maxiter": 500})
+            best = min(best, res.fun)
+        expect = {O.BARYCENTER: np.sum((v.mean(axis=0) - x) ** 2) <= delta ** 2,
+                  O.OVERLAP: best <= delta ** 2,
+                  O.INSIDE: bool(np.all(np.sum((v - x) ** 2, axis=1) < delta ** 2))}
+        margin = {O.BARYCENTER: abs(np.sum((v.mean(axis=0) - x) ** 2) - delta ** 2),
+                  O.OVERLAP: abs(best - delta ** 2),
+                  O.INSIDE: np.min(np.abs(np.sum((v - x) ** 2, axis=1) - delta ** 2))}
+        for strat in (O.BARYCENTER, O.OVERLAP, O.INSIDE):
+            M, acc, _ = O.region_moments(v, x, delta, strat)
+            full = M[0] > 0
+            if margin[strat] > 1e-6 * delta ** 2:
+                assert full == expect[strat], (strat, margin[strat])
+            ref = full_form if full else np.zeros(15)
+            assert np.abs(M - ref).max() <= 1e-14 * vol
+            n_full[strat] += int(full)
+    assert all(0 < k < 60 for k in n_full.values()), n_full
+
+
+def test_element_level_ball_volumes():
+    """Around an interior point: inside <= nocaps <= overlap element by
+    element, so sum(inside) <= 4 pi delta^3/3 <= sum(overlap); the barycenter
+    ball is within a few element volumes of the exact one."""
+    mesh, delta = I.cube_problem(4, 2)
+    x = np.array([0.47, 0.52, 0.49])
+    ball = 4 * math.pi * delta ** 3 / 3
+    vin, vov, vba = 0.0, 0.0, 0.0
+    for t in range(mesh.nt):
+        v = mesh.verts[mesh.tets[t]]
+        if O.dist2_point_tet(x, v) > delta * delta:
+            continue
+        mi = O.region_moments(v, x, delta, O.INSIDE)[0][0]
+        mn = O.region_moments(v, x, delta, O.NOCAPS)[0][0]
+        mo = O.region_moments(v, x, delta, O.OVERLAP)[0][0]
+        mb = O.region_moments(v, x, delta, O.BARYCENTER)[0][0]
+        assert mi <= mn * (1 + 1e-14) and mn <= mo * (1 + 1e-14)
+        vin += mi; vov += mo; vba += mb
+    assert vin < ball < vov
+    assert abs(vba - ball) < 0.1 * ball
+
+
 # ---------------------------------------------------------------- mesh and pairs
 def test_kuhn_mesh_is_a_conforming_triangulation():
     for jit in (0.0, 0.2):
@@ -355,9 +416,11 @@ def test_pairs_grid_equals_brute_force():
 
 
 # ---------------------------------------------------------------- assembly and solve
-@pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS])
+@pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS, O.BARYCENTER, O.OVERLAP, O.INSIDE])
 def test_stiffness_symmetric_zero_row_sums_psd(strat):
-    m, delta = I.config_mesh("cube6_d025")
+    # delta = h leaves no element wholly inside a ball; the element-level
+    # strategies use delta = 2h
+    m, delta = I.config_mesh("cube6_d025") if strat <= O.FULLCAPS else I.cube_problem(4, 2)
     K = O.assemble_K(m, delta, I.gamma_const(delta), strat, nmc=64, seed=1)
     Kd = K.toarray()
     scale = np.abs(Kd).sum(axis=1)
