@@ -15,7 +15,9 @@
  *   - per quadrature point, the approximate ball restricted to T'
  *     (Def. "simplex's dividing strategy", Def. "nocaps", Alg. 3; the
  *     simplified 3D approxcaps of Sec. 3.3; fullcaps = nocaps cells plus a
- *     Monte Carlo estimate over the cap region, Sec. 4.3.2 and Alg. 4);
+ *     Monte Carlo estimate over the cap region, Sec. 4.3.2 and Alg. 4;
+ *     the element-level balls of Sec. 4.3: barycenter, overlap, inside,
+ *     which take T' whole or not at all);
  *   - the local 8x8 contribution of Eqs. (notreplaced)/(replaceBasis):
  *     the integrand (phi_j(y)-phi_j(x))(phi_i(y)-phi_i(x)) psi evaluated at
  *     every inner quadrature point / accepted MC sample, with psi = gamma/2
