@@ -71,6 +71,22 @@ def _measured_peak(key, fallback):
         return fallback, "fallback"
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (the slowest replica sets the step time)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ws, units_per_rank, t_max_ms):
+    """Whole-job throughput of ws independent replicas, each processing
+    units_per_rank units, timed by the slowest rank (weak scaling)."""
+    return ws * units_per_rank / (t_max_ms / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -238,13 +254,9 @@ def run_ours(args, ws, rank, local):
 
     ms = [s_["total_ms"] for s_ in steps]
     ms_mean = float(np.mean(ms))
-    t_max = ms_mean
-    if dist is not None:
-        tt = torch.tensor([ms_mean], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(ms_mean, dist, "cuda")
     npairs = steps[0]["npairs"]
-    value = ws * npairs / (t_max / 1e3)
+    value = replica_throughput(ws, npairs, t_max)
 
     # FP64 form of the same step (fewer steps: the FP64 pipe is narrow on this part)
     fp64 = None

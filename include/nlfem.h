@@ -49,7 +49,18 @@ typedef enum {
     NL_EBUSY = 6        /* resource limit reached (server queue full) */
 } nl_status;
 
-typedef enum { NL_NOCAPS = 0, NL_APPROXCAPS = 1, NL_FULLCAPS = 2 } nl_strategy;
+/* Ball strategies: the three of Sec. 3.3 / 4.3.2 and the element-level ones of
+ * Sec. 4.3 (T' whole or not at all: barycenter - its centroid in the closed
+ * ball; overlap - it meets the closed ball; inside - all vertices in the open
+ * ball). */
+typedef enum {
+    NL_NOCAPS = 0,
+    NL_APPROXCAPS = 1,
+    NL_FULLCAPS = 2,
+    NL_BARYCENTER = 3,
+    NL_OVERLAP = 4,
+    NL_INSIDE = 5
+} nl_strategy;
 typedef enum { NL_FP64 = 0, NL_FP32_COMP = 1 } nl_precision;
 typedef enum { NL_HOST = 0, NL_DEVICE = 1 } nl_where;
 typedef enum { NL_MAT_K = 0, NL_MAT_A = 1 } nl_matrix;

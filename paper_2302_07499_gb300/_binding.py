@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libnlfem.so")
 
 NL_OK, NL_EINVAL, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV, NL_ETIMEOUT, NL_EBUSY = range(7)
 NOCAPS, APPROXCAPS, FULLCAPS = 0, 1, 2
+BARYCENTER, OVERLAP, INSIDE = 3, 4, 5
 FP64, FP32_COMP = 0, 1
 HOST, DEVICE = 0, 1
 MAT_K, MAT_A = 0, 1

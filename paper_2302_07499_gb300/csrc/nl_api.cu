@@ -17,7 +17,7 @@ __global__ void k_zero_collar_g(const uint8_t *__restrict__ node_free, double *g
 
 nl_status nl_check_assemble_opts(const nl_assemble_opts *opts)
 {
-    if (opts->strategy < NL_NOCAPS || opts->strategy > NL_FULLCAPS) { nl_set_error("bad strategy"); return NL_EINVAL; }
+    if (opts->strategy < NL_NOCAPS || opts->strategy > NL_INSIDE) { nl_set_error("bad strategy"); return NL_EINVAL; }
     if (opts->precision != NL_FP64 && opts->precision != NL_FP32_COMP) { nl_set_error("bad precision"); return NL_EINVAL; }
     if (opts->strategy == NL_FULLCAPS && (opts->mc_points < 1 || opts->mc_points > 4096)) {
         nl_set_error("mc_points must be in 1..4096 for fullcaps");
@@ -84,15 +84,16 @@ nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_dev
         void *D = f32 ? (void *)sc.get<float>(10 * P->npairs) : (void *)sc.get<double>(10 * P->npairs);
         double *strips = sc.get<double>(P->strip_total);
         double *TT = sc.get<double>(10 * m->n_outer);
+        uint8_t *nfull = f32 ? sc.get<uint8_t>(P->npairs) : nullptr;
         uint64_t *st = sc.get<uint64_t>(8);
         NL_CUDA(cudaMemsetAsync(st, 0, sizeof(uint64_t) * 8, s));
         cudaEvent_t ev[3];
         for (int i = 0; i < 3; ++i) NL_CUDA(cudaEventCreate(&ev[i]));
         NL_CUDA(cudaEventRecord(ev[0], s));
-        if (f32) nl_assemble_fp32(S, (float *)D, strips, TT, st);
-        else nl_assemble_fp64(S, (double *)D, strips, TT, st);
+        if (f32) nl_assemble_fp32(S, (float *)D, strips, TT, nfull, st);
+        else nl_assemble_fp64(S, (double *)D, strips, TT, nullptr, st);
         NL_CUDA(cudaEventRecord(ev[1], s));
-        nl_reduce_system(S, D, f32 ? 1 : 0, strips, TT);
+        nl_reduce_system(S, D, f32 ? 1 : 0, nfull, strips, TT);
         NL_CUDA(cudaEventRecord(ev[2], s));
         NL_CUDA(cudaEventSynchronize(ev[2]));
         float ms0 = 0.f, ms1 = 0.f;

@@ -43,6 +43,7 @@ struct Prob {
     double half_gamma;
     int64_t pair_base, outer_base;
     void *D;                 // [npairs][10] staged T'T' moments (R)
+    uint8_t *nfull;          // FP32: [npairs] points at which T' is whole (their T'T' part is added in FP64)
     double *strips;          // [strip_total]
     double *TT;              // [n_outer][10]
 };
@@ -113,7 +114,7 @@ inline void philox_round_keys(uint64_t seed, uint32_t rk[20])
     }
 }
 
-inline Prob make_prob(nl_system *sys, void *D, double *strips, double *TT)
+inline Prob make_prob(nl_system *sys, void *D, double *strips, double *TT, uint8_t *nfull)
 {
     nl_pairs *P = sys->pairs;
     nl_mesh *m = P->mesh;
@@ -127,7 +128,7 @@ inline Prob make_prob(nl_system *sys, void *D, double *strips, double *TT)
     r.delta2 = P->delta * P->delta;
     r.delta2f = (float)r.delta2;
     r.half_gamma = sys->opts.gamma / 2.0;
-    r.D = D; r.strips = strips; r.TT = TT;
+    r.D = D; r.strips = strips; r.TT = TT; r.nfull = nfull;
     NL_REQUIRE(r.verts && r.vhi && r.vlo && r.tets && r.xq && r.xq_hl && r.pair_ptr && r.pair_tp && r.pair_T &&
                    r.rowptr && r.col && r.strip_off && r.outer_of && r.outer_ids,
                "internal: an input array of the assembly is missing");

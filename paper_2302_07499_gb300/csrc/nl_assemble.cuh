@@ -114,7 +114,7 @@ __device__ __forceinline__ void load_point_geometry(const Prob &A, int4 eP, int6
 // K1: classify every (pair, point) unit of the chunk; units with a cut (1..3
 // vertices inside, or a fullcaps cap without inside vertices) become events.
 template <class R, int STRAT, bool B>
-__global__ void __launch_bounds__(256) k_classify(const __grid_constant__ AsmArgs A)
+__global__ void __launch_bounds__(256, 3) k_classify(const __grid_constant__ AsmArgs A)
 {
     const int64_t nu = 4 * (A.p1 - A.p0);
     const int lane = threadIdx.x & 31;
@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(256) k_classify(const __grid_constant__ AsmArg
             const R d2 = (sizeof(R) == 4) ? (R)P.delta2f : (R)P.delta2;
             const int inm = nlq::classify(v, x, d2, sp);
             info = (uint8_t)inm;
-            if (inm != 15) {
+            if constexpr (STRAT >= 3) {
+                // element-level strategies: T' whole (closed form) or nothing
+                info = nlq::element_full<R, STRAT>(v, x, d2, inm, sp) ? (uint8_t)15 : (uint8_t)0x20;
+            } else if (inm != 15) {
                 if (inm != 0) ev = true;
                 else if (STRAT == 2 && A.nmc > 0) ev = nlq::meets_ball(v, x, d2, sp);
                 if (ev) info |= 0x10;
@@ -287,6 +290,17 @@ __device__ __forceinline__ DF df_mul(DF a, float x)
     const float h = p + e;
     return DF{h, e - (h - p)};
 }
+// double-float times double-float (the products' low parts by fused
+// multiply-add; the lo x lo term is below the result's precision)
+__device__ __forceinline__ DF df_mul2(DF a, DF b)
+{
+    const float p = a.hi * b.hi;
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float h = p + e;
+    return DF{h, e - (h - p)};
+}
 __device__ __forceinline__ DF df_from(double d)
 {
     const float h = (float)d;
@@ -312,7 +326,8 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
     const int mr = A.max_row;
     int32_t *cols = reinterpret_cast<int32_t *>(smem);                                        // [4][mr]
     double *strip = reinterpret_cast<double *>(smem + sizeof(int32_t) * 4 * ((mr + 1) & ~1));  // [4][mr]
-    R *Xs = reinterpret_cast<R *>(strip + 4 * mr);                                             // [NT][16]
+    // [NT][16] cross coefficients: R for FP64, double-float for FP32 (8 bytes either way)
+    double *Xs = strip + 4 * mr;
     int32_t *offs = reinterpret_cast<int32_t *>(Xs + NT * 16);                                 // [NT][16]
     double *wsc = reinterpret_cast<double *>(offs + NT * 16);                                  // [NT]
     double *red = wsc + NT;                                                                    // [NT/32][4]
@@ -358,12 +373,20 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
 #pragma unroll
                 for (int k = 0; k < 10; ++k) Dp[k] = R(0);
                 const int64_t u0 = 4 * (P.pair_base + p - A.p0);
+                // FP32: points where T' is whole enter in double (their moments
+                // are closed forms of |T'|), the others from their FP32 records
+                int fullmask = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const uint8_t info = A.uinfo[u0 + q];
                     Mom<R> M;
                     if ((info & 15) == 15) {
-                        nlq::closed_form_inside(M, volTp);
+                        if constexpr (F32) {
+                            nlq::mom_zero(M);
+                            fullmask |= 1 << q;
+                        } else {
+                            nlq::closed_form_inside(M, volTp);
+                        }
                         inside++;
                     } else if (info & 0x10) {
                         const int32_t sl = A.slot[u0 + q];
@@ -388,20 +411,41 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
 #pragma unroll
                 for (int k = 0; k < 10; ++k) Dst[k] = Dp[k];
                 if constexpr (F32) {
+                    const int nfull = __popc(fullmask);
+                    P.nfull[p] = (uint8_t)nfull;
+                    const double Vd = P.tet_vol[Tp];
+                    const DF wV = df_from(omega * Vd);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) vqf[q] = df_add(vqf[q], DF{(float)omega * (float)V[q], 0.f});
+                    for (int q = 0; q < 4; ++q) {
+                        vqf[q] = df_add(vqf[q], DF{(float)omega * (float)V[q], 0.f});
+                        if ((fullmask >> q) & 1) vqf[q] = df_add(vqf[q], wV);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        // whole-T' points: sum over them of lambda_i(x_q) |T'| / 4
+                        const int own = (fullmask >> i) & 1;
+                        const DF xc = nfull ? df_from(0.25 * Vd * (own * qlam<double>(i, i) +
+                                                                   (nfull - own) * qlam<double>(i, (i + 1) & 3)))
+                                            : DF{0.f, 0.f};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float ev = ((qlam<float>(i, 0) * (float)Y[0][k] + qlam<float>(i, 1) * (float)Y[1][k]) +
+                                              qlam<float>(i, 2) * (float)Y[2][k]) + qlam<float>(i, 3) * (float)Y[3][k];
+                            reinterpret_cast<DF *>(Xs)[tid * 16 + 4 * i + k] = df_add(xc, DF{ev, 0.f});
+                        }
+                    }
                 } else {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) vq[q] += omega * (double)V[q];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            R sum = ((qlam<R>(i, 0) * Y[0][k] + qlam<R>(i, 1) * Y[1][k]) + qlam<R>(i, 2) * Y[2][k]) +
+                                    qlam<R>(i, 3) * Y[3][k];
+                            Xs[tid * 16 + 4 * i + k] = (double)sum;
+                        }
                 }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        R sum = ((qlam<R>(i, 0) * Y[0][k] + qlam<R>(i, 1) * Y[1][k]) + qlam<R>(i, 2) * Y[2][k]) +
-                                qlam<R>(i, 3) * Y[3][k];
-                        Xs[tid * 16 + 4 * i + k] = sum;
-                    }
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -426,7 +470,8 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                     const int maxn = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
                     unsigned rest = (lane == leader) ? (peers & (peers - 1u)) : 0u;
                     if constexpr (F32) {
-                        const DF v = act ? df_mul(reinterpret_cast<const DF *>(wsc)[t], (float)Xs[t * 16 + 4 * i + k])
+                        const DF v = act ? df_mul2(reinterpret_cast<const DF *>(wsc)[t],
+                                                   reinterpret_cast<const DF *>(Xs)[t * 16 + 4 * i + k])
                                          : DF{0.f, 0.f};
                         DF sum = v;
                         for (int j = 1; j < maxn; ++j) {
@@ -438,7 +483,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         DF *sp = reinterpret_cast<DF *>(strip);
                         if (act && lane == leader) sp[i * mr + c] = df_add(sp[i * mr + c], sum);
                     } else {
-                        const double v = act ? wsc[t] * (double)Xs[t * 16 + 4 * i + k] : 0.0;
+                        const double v = act ? wsc[t] * Xs[t * 16 + 4 * i + k] : 0.0;
                         double sum = v;
                         for (int j = 1; j < maxn; ++j) {
                             const int src = rest ? __ffs(rest) - 1 : lane;
@@ -497,7 +542,8 @@ inline size_t combine_smem_bytes(int max_row, size_t real_size)
 {
     size_t b = sizeof(int32_t) * 4 * (size_t)((max_row + 1) & ~1);
     b += sizeof(double) * 4 * (size_t)max_row;
-    b += real_size * NT * 16;
+    b += sizeof(double) * NT * 16;     // cross coefficients (double or double-float)
+    (void)real_size;
     b += sizeof(int32_t) * NT * 16;
     b += sizeof(double) * NT;
     b += sizeof(double) * (NT / 32) * 4;
@@ -536,8 +582,10 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
     int ev_per_sm = 0;
     constexpr int ET = EvCfg<R>::threads;
     constexpr size_t ESM = EvCfg<R>::smem;
-    NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
-    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, k_events<R, STRAT, B>, ET, ESM));
+    if constexpr (STRAT <= 2) {
+        NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
+        NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, k_events<R, STRAT, B>, ET, ESM));
+    }
     ev_per_sm = ev_per_sm < 1 ? 1 : ev_per_sm;
     if (sh.events_blocks_per_sm > 0) ev_per_sm = std::min(ev_per_sm, sh.events_blocks_per_sm);
     const int sms = nl_num_sms();
@@ -556,8 +604,10 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
         // enough resident threads for the largest possible event count; the
         // kernel reads the actual count from device memory
         unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, ET), (int64_t)sms * ev_per_sm));
-        { k_events<R, STRAT, B><<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
-        NL_CHECK_LAUNCH();
+        if constexpr (STRAT <= 2) {
+            { k_events<R, STRAT, B><<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
+            NL_CHECK_LAUNCH();
+        }
         if constexpr (kDefer) {
             { k_events_fp64<STRAT, B><<<(unsigned)(2 * sms), 64, 0, s>>>(A); nl_count_launch(); }
             NL_CHECK_LAUNCH();
@@ -604,16 +654,19 @@ void run_single(nl_system *sys, AsmArgs &A)
 
 
 template <class R>
-void launch_assemble(nl_system *sys, void *D, double *strips, double *TT, unsigned long long *stats)
+void launch_assemble(nl_system *sys, void *D, double *strips, double *TT, uint8_t *nfull, unsigned long long *stats)
 {
     AsmArgs A;
     memset(&A, 0, sizeof(A));
-    A.self = make_prob(sys, D, strips, TT);
+    A.self = make_prob(sys, D, strips, TT, nfull);
     init_group_args(A, sys->opts, stats, sys->pairs->max_row);
     switch (sys->opts.strategy) {
     case NL_NOCAPS: run_single<R, 0>(sys, A); break;
     case NL_APPROXCAPS: run_single<R, 1>(sys, A); break;
-    default: run_single<R, 2>(sys, A); break;
+    case NL_FULLCAPS: run_single<R, 2>(sys, A); break;
+    case NL_BARYCENTER: run_single<R, 3>(sys, A); break;
+    case NL_OVERLAP: run_single<R, 4>(sys, A); break;
+    default: run_single<R, 5>(sys, A); break;
     }
 }
 
@@ -625,7 +678,10 @@ void launch_group(const BatchGroup &g, const Shape &sh, cudaStream_t s)
     switch (g.strategy) {
     case NL_NOCAPS: launch_chunks<R, 0, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
     case NL_APPROXCAPS: launch_chunks<R, 1, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
-    default: launch_chunks<R, 2, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
+    case NL_FULLCAPS: launch_chunks<R, 2, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
+    case NL_BARYCENTER: launch_chunks<R, 3, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
+    case NL_OVERLAP: launch_chunks<R, 4, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
+    default: launch_chunks<R, 5, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
     }
 }
 
@@ -730,7 +786,10 @@ void launch_probe(const double *tv, const double4 *tv4, const double *xs, const 
     unsigned blocks = (unsigned)((n + 127) / 128);
     if (strategy == NL_NOCAPS) { k_probe<R, 0><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
     else if (strategy == NL_APPROXCAPS) { k_probe<R, 1><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
-    else { k_probe<R, 2><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, nmc, key, out, defer); nl_count_launch(); }
+    else if (strategy == NL_FULLCAPS) { k_probe<R, 2><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, nmc, key, out, defer); nl_count_launch(); }
+    else if (strategy == NL_BARYCENTER) { k_probe<R, 3><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
+    else if (strategy == NL_OVERLAP) { k_probe<R, 4><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
+    else { k_probe<R, 5><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     if (sizeof(R) == 4 && strategy == NL_APPROXCAPS) {
         { k_probe_fp64<1><<<blocks, 64 * 2>>>(tv, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }

@@ -4,9 +4,9 @@
 // specification, with no fused multiply-add.
 #include "nl_assemble.cuh"
 
-void nl_assemble_fp64(nl_system *sys, double *D, double *strips, double *TT, uint64_t *stats)
+void nl_assemble_fp64(nl_system *sys, double *D, double *strips, double *TT, uint8_t *nfull, uint64_t *stats)
 {
-    nla::launch_assemble<double>(sys, D, strips, TT, reinterpret_cast<unsigned long long *>(stats));
+    nla::launch_assemble<double>(sys, D, strips, TT, nfull, reinterpret_cast<unsigned long long *>(stats));
 }
 
 void nl_probe_fp64(const double *tv, const double4 *tv4, const double *xs, const uint32_t *ids, int64_t n, double delta2, int strategy,

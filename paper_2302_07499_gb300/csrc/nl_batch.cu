@@ -40,6 +40,7 @@ struct nl_batch {
     std::vector<nl_system *> sys;         // one per problem, in the caller's order
     std::vector<void *> D;                // per problem: staged T'T' moments
     std::vector<double *> strips, TT, G, E;
+    std::vector<uint8_t *> nfull;         // FP32 problems: per pair, the points at which T' is whole
     std::vector<nla::BatchGroup> groups;
     unsigned long long *stats = nullptr;  // [8] summed over the batch
     nla::Shape shape;
@@ -80,8 +81,8 @@ void batch_enqueue(nl_batch *b, const nla::Shape &sh, cudaStream_t s)
     }
     for (size_t i = 0; i < b->sys.size(); ++i) {
         nl_system *S = b->sys[i];
-        nl_reduce_system_into(S, b->D[i], S->opts.precision == NL_FP32_COMP ? 1 : 0, b->strips[i], b->TT[i], b->G[i],
-                              b->E[i], s);
+        nl_reduce_system_into(S, b->D[i], S->opts.precision == NL_FP32_COMP ? 1 : 0, b->nfull[i], b->strips[i],
+                              b->TT[i], b->G[i], b->E[i], s);
     }
 }
 
@@ -140,6 +141,7 @@ extern "C" nl_status nl_batch_create(nl_pairs *const *pairs, const nl_assemble_o
             b->TT.push_back((double *)own(b->arena.get<double>(10 * m->n_outer)));
             b->G.push_back((double *)own(b->arena.get<double>(P->nnz)));
             b->E.push_back((double *)own(b->arena.get<double>(10 * m->nt)));
+            b->nfull.push_back(f32 ? (uint8_t *)own(b->arena.get<uint8_t>(P->npairs)) : nullptr);
         }
         // groups
         std::map<std::tuple<int, int, int, uint64_t>, std::vector<int>> gm;
@@ -166,7 +168,7 @@ extern "C" nl_status nl_batch_create(nl_pairs *const *pairs, const nl_assemble_o
             int64_t np_tot = 0, no_tot = 0;
             std::vector<nla::Prob> probs;
             for (int i : ids) {
-                nla::Prob pr = nla::make_prob(b->sys[i], b->D[i], b->strips[i], b->TT[i]);
+                nla::Prob pr = nla::make_prob(b->sys[i], b->D[i], b->strips[i], b->TT[i], b->nfull[i]);
                 pr.pair_base = np_tot;
                 pr.outer_base = no_tot;
                 probs.push_back(pr);

@@ -139,11 +139,13 @@ int nl_num_sms();
 
 // kernels of other translation units
 nl_status nl_pairs_build_impl(nl_mesh *mesh, double delta, nl_pairs **out);
-void nl_assemble_fp64(nl_system *sys, double *D, double *strips, double *TT, uint64_t *stats);
-void nl_assemble_fp32(nl_system *sys, float *D, double *strips, double *TT, uint64_t *stats);
-void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT);
-void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT,
-                           double *G, double *E, cudaStream_t s);
+void nl_assemble_fp64(nl_system *sys, double *D, double *strips, double *TT, uint8_t *nfull, uint64_t *stats);
+void nl_assemble_fp32(nl_system *sys, float *D, double *strips, double *TT, uint8_t *nfull, uint64_t *stats);
+// nfull (FP32 only, else NULL): per pair, the points at which T' is whole
+void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const uint8_t *nfull, const double *strips,
+                      const double *TT);
+void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const uint8_t *nfull, const double *strips,
+                           const double *TT, double *G, double *E, cudaStream_t s);
 nl_status nl_check_assemble_opts(const nl_assemble_opts *opts);
 nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts, const nl_device *dev = nullptr);
 nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_device *dev, nl_system **out);

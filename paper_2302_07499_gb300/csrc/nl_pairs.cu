@@ -382,7 +382,7 @@ __device__ bool pair_predicate(const PairArgs &A, const double3 xq[4], const flo
 // not matter: every element's list is sorted afterwards); the survivors go to
 // the outer element's bounded slot.
 template <int PASS>
-__global__ void __launch_bounds__(128) k_pairs(PairArgs A, const int64_t *bptr, int64_t *counts, int32_t *out)
+__global__ void __launch_bounds__(128, 4) k_pairs(PairArgs A, const int64_t *bptr, int64_t *counts, int32_t *out)
 {
     __shared__ int32_t wq[4][64];
     int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);

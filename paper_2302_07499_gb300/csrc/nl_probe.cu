@@ -36,7 +36,7 @@ extern "C" nl_status nl_probe_moments(const double *tets_xyz, const double *x, c
 {
     nl_clear_error();
     if (!tets_xyz || !x || !ids || !moments || n < 0) { nl_set_error("bad argument"); return NL_EINVAL; }
-    if (strategy < 0 || strategy > 2 || (precision != NL_FP64 && precision != NL_FP32_COMP)) {
+    if (strategy < 0 || strategy > 5 || (precision != NL_FP64 && precision != NL_FP32_COMP)) {
         nl_set_error("bad strategy or precision");
         return NL_EINVAL;
     }

@@ -356,6 +356,16 @@ static __device__ __noinline__ int strict_sample(const Strict *sx, StrictCap *ca
     return sdot(wy, wy) <= sx->d2 ? 1 : 0;
 }
 
+// FP64 barycenter test of the specification: the centroid
+// 0.25 ((v0 + v1) + (v2 + v3)) in the closed ball.
+static __device__ __noinline__ bool strict_bary(const Strict *sx)
+{
+    double v[4][3], x[3], w[3];
+    strict_load(sx, v, x);
+    for (int d = 0; d < 3; ++d) w[d] = ssub(smul(0.25, sadd(sadd(v[0][d], v[1][d]), sadd(v[2][d], v[3][d]))), x[d]);
+    return sdot(w, w) <= sx->d2;
+}
+
 static __device__ __noinline__ bool strict_meets(const Strict *sx)
 {
     double v[4][3], x[3];
@@ -400,6 +410,25 @@ __device__ __forceinline__ bool meets_ball(const P3<R> v[4], P3<R> x, R d2, cons
     bool run = dd <= d2;
     if (F32 && sx && absr(dd - d2) <= R(1e-4) * d2) run = strict_meets(sx);
     return run;
+}
+
+// The element-level approximate balls of Sec. 4.3 take T' whole or not at
+// all (STRAT 3 barycenter: the centroid in the closed ball; 4 overlap: T'
+// meets the closed ball; 5 inside: every vertex in the open ball).  inm is
+// the vertex classification; the FP32 path retakes close decisions in FP64.
+template <class R, int STRAT>
+__device__ __forceinline__ bool element_full(const P3<R> v[4], P3<R> x, R d2, int inm, const Strict *sx)
+{
+    constexpr bool F32 = sizeof(R) == 4;
+    if (STRAT == 5) return inm == 15;
+    if (STRAT == 4) return inm != 0 || meets_ball(v, x, d2, sx);
+    P3<R> w;
+    w.x = R(0.25) * ((v[0].x + v[1].x) + (v[2].x + v[3].x)) - x.x;
+    w.y = R(0.25) * ((v[0].y + v[1].y) + (v[2].y + v[3].y)) - x.y;
+    w.z = R(0.25) * ((v[0].z + v[1].z) + (v[2].z + v[3].z)) - x.z;
+    const R r2 = (w.x * w.x + w.y * w.y) + w.z * w.z;
+    if (F32 && sx && absr(r2 - d2) <= R(1e-5) * d2) return strict_bary(sx);
+    return r2 <= d2;
 }
 
 template <class R> __device__ __forceinline__ void closed_form_inside(Mom<R> &M, R volTp)
@@ -999,6 +1028,15 @@ __device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, 
                              uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st, const Strict *sx, R *cb)
 {
     int inm = classify(v, x, d2, sx);
+    if constexpr (STRAT >= 3) {
+        if (element_full<R, STRAT>(v, x, d2, inm, sx)) {
+            st.inside++;
+            closed_form_inside(M, volTp);
+        } else {
+            mom_zero(M);
+        }
+        return 0;
+    } else {
     if (inm == 15) {
         st.inside++;
         closed_form_inside(M, volTp);
@@ -1014,6 +1052,7 @@ __device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, 
     for (int k = 0; k < 4; ++k) M.m1[k] = o[1 + k];
     for (int k = 0; k < 10; ++k) M.m2[k] = o[5 + k];
     return 0;
+    }
 }
 
 }  // namespace nlq

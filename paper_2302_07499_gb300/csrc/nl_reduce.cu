@@ -54,8 +54,8 @@ template <class DT>
 __global__ void k_elem_blocks(const int64_t *__restrict__ tp_ptr, const int32_t *__restrict__ tp_pair,
                               const int32_t *__restrict__ pair_T, const double *__restrict__ tet_vol,
                               const uint8_t *__restrict__ in_omega, const int32_t *__restrict__ outer_of,
-                              const DT *__restrict__ D, const double *__restrict__ TT, double half_gamma, int64_t nt,
-                              double *E)
+                              const DT *__restrict__ D, const uint8_t *__restrict__ nfull, const double *__restrict__ TT,
+                              double half_gamma, int64_t nt, double *E)
 {
     int64_t el = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -64,12 +64,19 @@ __global__ void k_elem_blocks(const int64_t *__restrict__ tp_ptr, const int32_t 
     double acc[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+    // points at which T' = el is whole add |T'|(1 + delta_ab)/20 each (FP32
+    // path: kept out of the FP32 staging)
+    const double vol = tet_vol[el];
     for (int64_t j = tp_ptr[el] + lane; j < tp_ptr[el + 1]; j += 32) {
         int32_t p = tp_pair[j];
         double w = omega * (half_gamma * (tet_vol[pair_T[p]] * 0.25));
         const DT *d = D + 10 * (int64_t)p;
+        const double nf = nfull ? (double)nfull[p] : 0.0;
 #pragma unroll
-        for (int k = 0; k < 10; ++k) acc[k] += w * (double)d[k];
+        for (int k = 0; k < 10; ++k) {
+            const double cf = (k == 0 || k == 4 || k == 7 || k == 9) ? 0.1 : 0.05;
+            acc[k] += w * ((double)d[k] + nf * (vol * cf));
+        }
     }
 #pragma unroll
     for (int k = 0; k < 10; ++k)
@@ -166,8 +173,8 @@ unsigned wblocks(int64_t n) { return (unsigned)std::max<int64_t>(1, nl_cdiv<int6
 
 // The reduction into K, A, b with caller-given scratch G [nnz] and E [10 nt]
 // (stream-ordered, no synchronisation: capturable in a CUDA graph).
-void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT,
-                           double *G, double *E, cudaStream_t s)
+void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const uint8_t *nfull, const double *strips,
+                           const double *TT, double *G, double *E, cudaStream_t s)
 {
     nl_pairs *P = sys->pairs;
     nl_mesh *m = P->mesh;
@@ -176,12 +183,12 @@ void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const 
     NL_CHECK_LAUNCH();
     if (d_is_float)
         { k_elem_blocks<float><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->in_omega,
-                                                           m->outer_of, (const float *)D, TT, sys->opts.gamma / 2.0,
-                                                           m->nt, E); nl_count_launch(); }
+                                                           m->outer_of, (const float *)D, nfull, TT,
+                                                           sys->opts.gamma / 2.0, m->nt, E); nl_count_launch(); }
     else
         { k_elem_blocks<double><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol,
-                                                            m->in_omega, m->outer_of, (const double *)D, TT,
-                                                            sys->opts.gamma / 2.0, m->nt, E); nl_count_launch(); }
+                                                            m->in_omega, m->outer_of, (const double *)D, nullptr,
+                                                            TT, sys->opts.gamma / 2.0, m->nt, E); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     { k_final_K<<<wblocks(m->nv), 256, 0, s>>>(P->rowptr, P->perm, G, m->ne_ptr, m->ne_ent, P->elem_pos, E, m->nv,
                                             sys->K); nl_count_launch(); }
@@ -194,14 +201,15 @@ void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const 
     NL_CHECK_LAUNCH();
 }
 
-void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const double *strips, const double *TT)
+void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const uint8_t *nfull, const double *strips,
+                      const double *TT)
 {
     nl_pairs *P = sys->pairs;
     nl_mesh *m = P->mesh;
     Scratch sc(&sys->arena);
     double *G = sc.get<double>(P->nnz);
     double *E = sc.get<double>(10 * m->nt);
-    nl_reduce_system_into(sys, D, d_is_float, strips, TT, G, E, sys->arena.stream());
+    nl_reduce_system_into(sys, D, d_is_float, nfull, strips, TT, G, E, sys->arena.stream());
     // scratch is released (stream-ordered) when sc goes out of scope
     NL_CUDA(cudaStreamSynchronize(sys->arena.stream()));
 }

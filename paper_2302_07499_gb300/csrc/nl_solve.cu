@@ -15,6 +15,7 @@ namespace {
 struct CgState {
     double rr, pq, alpha, beta, tol2;
     int done, it;
+    unsigned int ticket;     // blocks of the current reduction that have written their partial
 };
 
 constexpr int RB = 256;   // threads per block in reductions
@@ -33,10 +34,34 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 }
 
 // q = A p (warp per row) and per-block partial of p.q
+// Sum of the nb block partials in a fixed order (lane l takes l, l+32, ...,
+// then a fixed butterfly); called by one full warp.
+__device__ __forceinline__ double warp_sum_parts(const double *part, int nb)
+{
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < nb; i += 32) s += __ldcg(part + i);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// The last block to finish a reduction (the others have written their
+// partials and passed a fence) sums the partials; returns true in that
+// block's first warp.
+__device__ __forceinline__ bool last_block(CgState *st)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    return last && threadIdx.x < 32;
+}
+
 template <class VT, class XT>
 __global__ void k_spmv_dot(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                            const VT *__restrict__ val, const XT *__restrict__ p, XT *q, int64_t n,
-                           double *part, const CgState *st)
+                           double *part, CgState *st)
 {
     __shared__ double sh[RB / 32];
     if (st && st->done) return;
@@ -54,19 +79,19 @@ __global__ void k_spmv_dot(const int64_t *__restrict__ rp, const int32_t *__rest
     }
     double t = block_sum(acc, sh);
     if (threadIdx.x == 0 && part) part[blockIdx.x] = t;
-}
-
-__global__ void k_alpha(const double *part, int nb, CgState *st)
-{
-    if (threadIdx.x != 0 || st->done) return;
-    double s = 0.0;
-    for (int i = 0; i < nb; ++i) s += part[i];
-    st->pq = s;
-    st->alpha = (s != 0.0) ? st->rr / s : 0.0;
+    // CG: the last block forms alpha = r.r / p.Ap
+    if (st && last_block(st)) {
+        const double pq = warp_sum_parts(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            st->pq = pq;
+            st->alpha = (pq != 0.0) ? st->rr / pq : 0.0;
+            st->ticket = 0;
+        }
+    }
 }
 
 template <class XT>
-__global__ void k_update_xr(XT *x, XT *r, const XT *p, const XT *q, int64_t n, double *part, const CgState *st)
+__global__ void k_update_xr(XT *x, XT *r, const XT *p, const XT *q, int64_t n, double *part, CgState *st)
 {
     __shared__ double sh[RB / 32];
     if (st->done) return;
@@ -80,17 +105,17 @@ __global__ void k_update_xr(XT *x, XT *r, const XT *p, const XT *q, int64_t n, d
     }
     double t = block_sum(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-__global__ void k_beta(const double *part, int nb, CgState *st)
-{
-    if (threadIdx.x != 0 || st->done) return;
-    double s = 0.0;
-    for (int i = 0; i < nb; ++i) s += part[i];
-    st->beta = (st->rr != 0.0) ? s / st->rr : 0.0;
-    st->rr = s;
-    st->it += 1;
-    if (s <= st->tol2 || !(s == s)) st->done = 1;
+    // the last block forms beta = r'.r' / r.r and tests convergence
+    if (last_block(st)) {
+        const double rr = warp_sum_parts(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            st->beta = (st->rr != 0.0) ? rr / st->rr : 0.0;
+            st->rr = rr;
+            st->it += 1;
+            if (rr <= st->tol2 || !(rr == rr)) st->done = 1;
+            st->ticket = 0;
+        }
+    }
 }
 
 template <class XT>
@@ -127,6 +152,7 @@ __global__ void k_start(const double *part, int nb, double rtol2, CgState *st)
     st->tol2 = rtol2 * s;
     st->done = (s == 0.0) ? 1 : 0;
     st->it = 0;
+    st->ticket = 0;
     st->alpha = st->beta = st->pq = 0.0;
 }
 
@@ -167,6 +193,15 @@ __global__ void k_scatter_u(const double *x, const int32_t *free_nodes, const do
     if (i < nf) u[free_nodes[i]] = x[i];
 }
 
+// Blocks of the CG kernels: a warp per row up to 16 blocks of 256 threads per
+// SM (the SpMV gathers are latency-bound; full occupancy keeps the most
+// loads in flight), at most 4096 (the partials of the no-allocation solve).
+int cg_blocks(int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>((int64_t)nl_num_sms() * 16, 4096),
+                                                       nl_cdiv<int64_t>(n * 32, RB)));
+}
+
 struct Cg {
     int nb = 0;
     double *part = nullptr;
@@ -190,9 +225,7 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b,
         int k = std::min(check_every, max_it - launched);
         for (int j = 0; j < k; ++j) {
             { k_spmv_dot<VT, XT><<<nb, RB, 0, s>>>(rp, ci, val, p, q, n, cg.part, cg.st); nl_count_launch(); }
-            { k_alpha<<<1, 32, 0, s>>>(cg.part, nb, cg.st); nl_count_launch(); }
             { k_update_xr<XT><<<nb, RB, 0, s>>>(x, r, p, q, n, cg.part, cg.st); nl_count_launch(); }
-            { k_beta<<<1, 32, 0, s>>>(cg.part, nb, cg.st); nl_count_launch(); }
             { k_update_p<XT><<<nb, RB, 0, s>>>(p, r, n, cg.st); nl_count_launch(); }
         }
         NL_CHECK_LAUNCH();
@@ -223,7 +256,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
         cudaStream_t s = S->arena.stream();
         Scratch sc(&S->arena);
         Cg cg;
-        cg.nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nl_num_sms() * 4, nl_cdiv<int64_t>(n * 32, RB)));
+        cg.nb = cg_blocks(n);
         cg.part = sc.get<double>(cg.nb);
         cg.st = sc.get<CgState>(1);
         double *x = sc.get<double>(n);
@@ -327,7 +360,7 @@ extern "C" nl_status nl_spmv_time(nl_system *S, int precision, int reps, double 
         float *xf = sc.get<float>(n), *yf = sc.get<float>(n);
         { k_fill_ones<<<(unsigned)nl_cdiv<int64_t>(n, 256), 256, 0, s>>>(xd, xf, n); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        const int nb = std::max(1, std::min<int>(nl_num_sms() * 8, (int)nl_cdiv<int64_t>(n * 32, RB)));
+        const int nb = cg_blocks(n);
         cudaEvent_t e0, e1;
         NL_CUDA(cudaEventCreate(&e0));
         NL_CUDA(cudaEventCreate(&e1));
@@ -376,6 +409,7 @@ constexpr int64_t kStaticMaxFree = 131072;        // unknowns (free nodes)
 constexpr int kStaticMaxBlocks = 4096;            // reduction partials
 constexpr size_t kStaticVecBytes = sizeof(double) * (size_t)kStaticMaxFree;
 constexpr size_t kStaticBytes = 5 * kStaticVecBytes + sizeof(double) * kStaticMaxBlocks + 256;
+static_assert(sizeof(CgState) <= 256, "the CG state slot of the static array");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -430,7 +464,7 @@ extern "C" nl_status nl_solve_static(nl_system *S, const nl_solve_opts *opts, do
         double *q = reinterpret_cast<double *>(base + 3 * kStaticVecBytes);
         double *rres = reinterpret_cast<double *>(base + 4 * kStaticVecBytes);
         Cg cg;
-        cg.nb = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nl_num_sms() * 4, nl_cdiv<int64_t>(n * 32, RB)));
+        cg.nb = cg_blocks(n);
         NL_REQUIRE(cg.nb <= kStaticMaxBlocks, "too many reduction blocks (%d)", cg.nb);
         cg.part = reinterpret_cast<double *>(base + 5 * kStaticVecBytes);
         cg.st = reinterpret_cast<CgState *>(base + 5 * kStaticVecBytes + sizeof(double) * kStaticMaxBlocks);

@@ -23,13 +23,15 @@ def nl():
 
 def _problems(nl):
     # (mesh, delta, options): mixed strategies, precisions, deltas and sizes;
-    # problems 2 and 3 share a group (FP32 fullcaps, 32 points, seed 1)
+    # problems 2 and 3 share a group (FP32 fullcaps, 32 points, seed 1); the
+    # last one is an element-level strategy
     spec = [((4, 1, 0.0, 0), dict(strategy=nl.NOCAPS, precision=nl.FP32_COMP)),
             ((5, 2, 0.2, 4), dict(strategy=nl.APPROXCAPS, precision=nl.FP32_COMP)),
             ((4, 2, 0.2, 5), dict(strategy=nl.FULLCAPS, mc_points=32, precision=nl.FP32_COMP)),
             ((6, 1, 0.0, 0), dict(strategy=nl.FULLCAPS, mc_points=32, precision=nl.FP32_COMP)),
             ((4, 2, 0.0, 0), dict(strategy=nl.NOCAPS, precision=nl.FP64)),
-            ((3, 3, 0.2, 6), dict(strategy=nl.FULLCAPS, mc_points=16, seed=7, precision=nl.FP64))]
+            ((3, 3, 0.2, 6), dict(strategy=nl.FULLCAPS, mc_points=16, seed=7, precision=nl.FP64)),
+            ((4, 2, 0.2, 8), dict(strategy=nl.BARYCENTER, precision=nl.FP32_COMP))]
     out = []
     for (inv_h, ratio, jit, seed), kw in spec:
         mesh, delta = I.cube_problem(inv_h, ratio, jitter_frac=jit, seed=seed)
@@ -58,7 +60,7 @@ def test_batch_equals_single_problem_assembly(nl, autotune, use_graph):
         solo.append(_arrays(nl.System(p, **kw), nl))
     batch = nl.Batch([(p, kw) for p, (_, _, kw) in zip(pairs, probs)], autotune=autotune, use_graph=use_graph)
     info = batch.info()
-    assert info["n_problems"] == len(probs) and info["n_groups"] == 5
+    assert info["n_problems"] == len(probs) and info["n_groups"] == 6
     assert info["graph"] == int(use_graph)
     assert info["n_tried"] == (6 if autotune else 0)
     for rep in range(2):
