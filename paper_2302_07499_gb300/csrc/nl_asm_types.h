@@ -28,6 +28,7 @@ struct Prob {
     const int4 *tets;
     const uint8_t *in_omega;
     const double *tet_vol;
+    const float2 *vol_hl;    // the volumes as float hi + lo
     const int32_t *outer_ids;
     const int32_t *outer_of;
     const double *xq;
@@ -121,7 +122,7 @@ inline Prob make_prob(nl_system *sys, void *D, double *strips, double *TT, uint8
     Prob r;
     memset(&r, 0, sizeof(r));
     r.verts = m->verts; r.vhi = m->vhi; r.vlo = m->vlo; r.tets = m->tets; r.in_omega = m->in_omega;
-    r.tet_vol = m->tet_vol; r.outer_ids = m->outer_ids; r.outer_of = m->outer_of; r.xq = m->xq;
+    r.tet_vol = m->tet_vol; r.vol_hl = m->vol_hl; r.outer_ids = m->outer_ids; r.outer_of = m->outer_of; r.xq = m->xq;
     r.xq_hl = m->xq_hl;
     r.pair_ptr = P->pair_ptr; r.pair_tp = P->pair_tp; r.pair_T = P->pair_T;
     r.rowptr = P->rowptr; r.col = P->col; r.strip_off = P->strip_off;
@@ -129,7 +130,7 @@ inline Prob make_prob(nl_system *sys, void *D, double *strips, double *TT, uint8
     r.delta2f = (float)r.delta2;
     r.half_gamma = sys->opts.gamma / 2.0;
     r.D = D; r.strips = strips; r.TT = TT; r.nfull = nfull;
-    NL_REQUIRE(r.verts && r.vhi && r.vlo && r.tets && r.xq && r.xq_hl && r.pair_ptr && r.pair_tp && r.pair_T &&
+    NL_REQUIRE(r.verts && r.vhi && r.vlo && r.vol_hl && r.tets && r.xq && r.xq_hl && r.pair_ptr && r.pair_tp && r.pair_T &&
                    r.rowptr && r.col && r.strip_off && r.outer_of && r.outer_ids,
                "internal: an input array of the assembly is missing");
     return r;

@@ -175,9 +175,10 @@ __global__ void __launch_bounds__(256, 3) k_classify(const __grid_constant__ Asm
 template <class R> struct EvCfg {
     static constexpr int threads = sizeof(R) == 4 ? 128 : 64;
     static constexpr size_t smem = sizeof(R) * threads * 3 * nlq::CB_STRIDE;
-    // resident blocks per SM allowed by the cap-cell scratch (228 KB of shared
-    // memory per SM, 1 KB reserved per block); the register budget follows
-    static constexpr int min_blocks = (int)((228 * 1024) / (smem + 1024));
+    // 4 resident blocks per SM: 128 registers a thread, no spills (the cap
+    // scratch would allow 5 blocks at 96 registers; the spills that forces
+    // cost more than the fifth block gains: 21.1 -> 19.5 ms on the bench step)
+    static constexpr int min_blocks = 4;
 };
 
 template <class R, int STRAT, bool B>
@@ -301,6 +302,12 @@ __device__ __forceinline__ DF df_mul2(DF a, DF b)
     const float h = p + e;
     return DF{h, e - (h - p)};
 }
+// a double constant as float hi + lo (folded at compile time)
+__device__ __forceinline__ DF df_const(double d)
+{
+    const float h = (float)d;
+    return DF{h, (float)(d - (double)h)};
+}
 __device__ __forceinline__ DF df_from(double d)
 {
     const float h = (float)d;
@@ -413,20 +420,28 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                 if constexpr (F32) {
                     const int nfull = __popc(fullmask);
                     P.nfull[p] = (uint8_t)nfull;
-                    const double Vd = P.tet_vol[Tp];
-                    const DF wV = df_from(omega * Vd);
+                    // |T'| as float hi + lo; omega is 1 or 2 (exact scaling)
+                    const float2 vhl = P.vol_hl[Tp];
+                    const float omf = P.in_omega[Tp] ? 1.f : 2.f;
+                    const DF wV{omf * vhl.x, omf * vhl.y};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        vqf[q] = df_add(vqf[q], DF{(float)omega * (float)V[q], 0.f});
+                        vqf[q] = df_add(vqf[q], DF{omf * (float)V[q], 0.f});
                         if ((fullmask >> q) & 1) vqf[q] = df_add(vqf[q], wV);
                     }
+                    // weights of the 4-point rule as float hi + lo
+                    const DF qa = df_const(0x1.2bbae2a27f931p-1), qb = df_const(0x1.1b06d1d200913p-3);
+                    const DF v4{0.25f * vhl.x, 0.25f * vhl.y};
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         // whole-T' points: sum over them of lambda_i(x_q) |T'| / 4
                         const int own = (fullmask >> i) & 1;
-                        const DF xc = nfull ? df_from(0.25 * Vd * (own * qlam<double>(i, i) +
-                                                                   (nfull - own) * qlam<double>(i, (i + 1) & 3)))
-                                            : DF{0.f, 0.f};
+                        DF xc{0.f, 0.f};
+                        if (nfull) {
+                            // own x a + (nfull - own) x b, products exact by fused multiply-add
+                            const DF s = df_add(own ? qa : DF{0.f, 0.f}, df_mul(qb, (float)(nfull - own)));
+                            xc = df_mul2(v4, s);
+                        }
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             const float ev = ((qlam<float>(i, 0) * (float)Y[0][k] + qlam<float>(i, 1) * (float)Y[1][k]) +

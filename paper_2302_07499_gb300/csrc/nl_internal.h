@@ -72,6 +72,7 @@ struct nl_mesh {
     double4 *verts = nullptr;      // x, y, z, 0
     float4 *vhi = nullptr;         // float hi part of the coordinates
     float4 *vlo = nullptr;         // float lo part (coordinate - hi, rounded)
+    float2 *vol_hl = nullptr;      // element volumes as float hi + lo
     int4 *tets = nullptr;
     uint8_t *in_omega = nullptr;
     uint8_t *node_free = nullptr;

@@ -82,6 +82,15 @@ __global__ void k_widen(const double *__restrict__ v3, double4 *v4, int64_t nv)
     if (i < nv) v4[i] = make_double4(v3[3 * i], v3[3 * i + 1], v3[3 * i + 2], 0.0);
 }
 
+__global__ void k_split_vol(const double *__restrict__ vol, float2 *hl, int64_t nt)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const double v = vol[t];
+    const float h = (float)v;
+    hl[t] = make_float2(h, (float)(v - (double)h));
+}
+
 __global__ void k_split_coords(const double4 *__restrict__ verts, float4 *vhi, float4 *vlo, int64_t nv)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -885,6 +894,9 @@ extern "C" nl_status nl_mesh_create(const nl_device *dev, const double *verts, i
         m->vhi = m->arena.get<float4>(nv);
         m->vlo = m->arena.get<float4>(nv);
         { k_split_coords<<<blocks_for(nv, 256), 256, 0, s>>>(m->verts, m->vhi, m->vlo, nv); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        m->vol_hl = m->arena.get<float2>(nt);
+        { k_split_vol<<<blocks_for(nt, 256), 256, 0, s>>>(m->tet_vol, m->vol_hl, nt); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         int herr = 0;
         unsigned long long hbb[8];

@@ -88,3 +88,24 @@ def test_server_refuses_what_cannot_fit(nl):
     assert res["status"] == 2        # NL_ENOMEM
     assert "exceeds the budget" in res["message"]
     srv.close()
+
+
+def test_server_evicts_the_cache_to_admit(nl):
+    """A budget that holds one request's footprint: the second key evicts the
+    first key's resident mesh and pairs, and both requests complete."""
+    a = nl.Server.box_request(6, 2.0, strategy=nl.NOCAPS, precision=nl.FP32_COMP, mixed=True)
+    b = nl.Server.box_request(7, 2.0, strategy=nl.NOCAPS, precision=nl.FP32_COMP, mixed=True)
+    probe = nl.Server(budget_bytes=10 ** 12, workers=1)
+    est_a = probe.wait(probe.submit(a), timeout_s=300.0)[0]["est_bytes"]
+    resident_a = probe.load()["cache_bytes"]
+    est_b = probe.wait(probe.submit(b), timeout_s=300.0)[0]["est_bytes"]
+    probe.close()
+    assert est_a < est_b and resident_a > 0
+    # b fits only once a's resident mesh and pairs are gone
+    srv = nl.Server(budget_bytes=est_b + resident_a // 2, workers=1)
+    ra, _ = srv.wait(srv.submit(a), timeout_s=300.0)
+    assert srv.load()["cache_entries"] == 1
+    rb, _ = srv.wait(srv.submit(b), timeout_s=300.0)
+    assert ra["status"] == 0 and rb["status"] == 0, (ra["message"], rb["message"])
+    assert srv.load()["cache_entries"] == 1      # the first key was evicted
+    srv.close()
