@@ -383,21 +383,42 @@ __device__ bool pair_predicate(const PairArgs &A, const double3 xq[4], const flo
     return false;
 }
 
+// Cheap part of the predicate: a vertex of T' surely within delta of an outer
+// point (FP32 distance below the sure-accept bound).  Branch-free.
+__device__ bool quick_accept(const PairArgs &A, const float3 xh[4], const float3 xl[4], int4 e)
+{
+    const int ids[4] = {e.x, e.y, e.z, e.w};
+    float vmin = 3.0e38f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 h = A.vhi[ids[k]], l = A.vlo[ids[k]];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float3 w = make_float3((h.x - xh[q].x) + (l.x - xl[q].x), (h.y - xh[q].y) + (l.y - xl[q].y),
+                                         (h.z - xh[q].z) + (l.z - xl[q].z));
+            vmin = fminf(vmin, dot3f(w, w));
+        }
+    }
+    return vmin < A.d2_lo;
+}
+
 // One warp per outer element: scan the stencil of grid cells and test each
 // candidate T'.  PASS 0 only bounds the number of candidates (centroid
 // filter).  PASS 1 applies the cheap filters to 32 candidates at a time,
 // queues the survivors per warp in shared memory, and runs the exact
-// predicate on full warps of queued candidates (the order of the output does
-// not matter: every element's list is sorted afterwards); the survivors go to
-// the outer element's bounded slot.
+// predicate on full warps of queued candidates: first the branch-free vertex
+// test, then, on full warps of the candidates it leaves undecided (a second
+// queue), the distance to T'.  The order of the output does not matter (every
+// element's list is sorted afterwards); the survivors go to the outer
+// element's bounded slot.
 template <int PASS>
 __global__ void __launch_bounds__(128, 4) k_pairs(PairArgs A, const int64_t *bptr, int64_t *counts, int32_t *out)
 {
-    __shared__ int32_t wq[4][64];
+    __shared__ int32_t wq[4][64], wq2[4][64];
     int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (warp >= A.n_outer) return;
-    int32_t *Q = wq[threadIdx.x >> 5];
+    int32_t *Q = wq[threadIdx.x >> 5], *Q2 = wq2[threadIdx.x >> 5];
     const unsigned lt = (1u << lane) - 1u;
     int32_t T = A.outer_ids[warp];
     const float4 cT = A.tet_cf[T];
@@ -415,21 +436,41 @@ __global__ void __launch_bounds__(128, 4) k_pairs(PairArgs A, const int64_t *bpt
     int cell = A.cell_of[T];
     int cx = cell % A.g.n[0], cy = (cell / A.g.n[0]) % A.g.n[1], cz = cell / (A.g.n[0] * A.g.n[1]);
     int64_t n = 0;
-    int nq = 0;     // queued candidates (warp-uniform, below 64)
+    int nq = 0, nq2 = 0;     // queued candidates (warp-uniform, below 64)
     int64_t base = (PASS == 1) ? bptr[warp] : 0;
-    // exact predicate on the last cnt queued candidates (cnt <= 32)
-    auto drain = [&](int cnt) {
+    // full predicate on the last cnt candidates of the second queue (cnt <= 32)
+    auto drain2 = [&](int cnt) {
         bool keep = false;
         int32_t Tp = -1;
         if (lane < cnt) {
-            Tp = Q[nq - cnt + lane];
+            Tp = Q2[nq2 - cnt + lane];
             keep = pair_predicate(A, xq, xh, xl, A.tets[Tp]);
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (keep) out[base + n + __popc(m & lt)] = Tp;
         n += __popc(m);
-        nq -= cnt;
+        nq2 -= cnt;
         __syncwarp();
+    };
+    // vertex test on the last cnt queued candidates (cnt <= 32): accepted ones
+    // go out, undecided ones to the second queue
+    auto drain = [&](int cnt) {
+        bool keep = false, undecided = false;
+        int32_t Tp = -1;
+        if (lane < cnt) {
+            Tp = Q[nq - cnt + lane];
+            keep = quick_accept(A, xh, xl, A.tets[Tp]);
+            undecided = !keep;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) out[base + n + __popc(m & lt)] = Tp;
+        n += __popc(m);
+        nq -= cnt;
+        const unsigned mu = __ballot_sync(0xffffffffu, undecided);
+        if (undecided) Q2[nq2 + __popc(mu & lt)] = Tp;
+        nq2 += __popc(mu);
+        __syncwarp();
+        if (nq2 >= 32) drain2(32);
     };
     for (int dz = -A.ks; dz <= A.ks; ++dz) {
         int z = cz + dz;
@@ -476,8 +517,10 @@ __global__ void __launch_bounds__(128, 4) k_pairs(PairArgs A, const int64_t *bpt
             }
         }
     }
-    if (PASS == 1)
+    if (PASS == 1) {
         while (nq > 0) drain(nq < 32 ? nq : 32);
+        while (nq2 > 0) drain2(nq2 < 32 ? nq2 : 32);
+    }
     if (lane == 0) counts[warp] = n;
 }
 
