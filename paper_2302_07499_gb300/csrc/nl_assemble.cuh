@@ -185,7 +185,7 @@ template <class R, int STRAT, bool B>
 __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_events(const __grid_constant__ AsmArgs A)
 {
     extern __shared__ __align__(16) unsigned char evsm[];
-    R *cb = reinterpret_cast<R *>(evsm) + 3 * nlq::CB_STRIDE * threadIdx.x;
+    R *cb = reinterpret_cast<R *>(evsm) + nlq::CB_STRIDE * threadIdx.x;   // cell j at cb + j * CB_STRIDE * threads
     nlq::Stats st{0, 0, 0, 0, 0};
     const int64_t nu = 4 * (A.p1 - A.p0);
     const int n0 = A.nev[0], n1 = A.nev[1], n2 = A.nev[2], n3 = A.nev[3];
@@ -210,7 +210,8 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
         R *out = reinterpret_cast<R *>(A.Mq) + 15 * (int64_t)e;
         const bool deferred = nlq::event_moments<R, STRAT>(v, x, sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2, inm,
                                                            A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q, out,
-                                                           st, (sizeof(R) == 4) ? &sx : nullptr, cb);
+                                                           st, (sizeof(R) == 4) ? &sx : nullptr, cb,
+                                                           nlq::CB_STRIDE * EvCfg<R>::threads);
         if (deferred) A.fix[atomicAdd(&A.nev[4], 1)] = e;
     }
     __shared__ unsigned long long sstat[4];
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmA
         const int inm = A.uinfo[u] & 15;
         double m15[15];
         nlq::event_moments<double, STRAT>(v, x, P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q,
-                                          m15, st, nullptr, nullptr);
+                                          m15, st, nullptr, nullptr, 0);
         float *out = reinterpret_cast<float *>(A.Mq) + 15 * (int64_t)e;
 #pragma unroll
         for (int k = 0; k < 15; ++k) out[k] = (float)m15[k];
@@ -764,7 +765,8 @@ __global__ void k_probe(const double *__restrict__ tv, const double4 *__restrict
     sx.d2 = delta2;
     __align__(16) R cb[3 * nlq::CB_STRIDE];   // 16-byte aligned: the sampler reads it with 16-byte loads
     const int d = nlq::point_moments<R, STRAT>(v, xx, (R)delta2, (R)vol, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
-                                               ids[3 * c + 2], M, st, sizeof(R) == 4 ? &sx : nullptr, cb);
+                                               ids[3 * c + 2], M, st, sizeof(R) == 4 ? &sx : nullptr, cb,
+                                               nlq::CB_STRIDE);
     defer[c] = d;
     if (d) return;
     out[15 * c] = (double)M.m0;
@@ -788,7 +790,7 @@ __global__ void k_probe_fp64(const double *__restrict__ tv, const double *__rest
     nlq::Stats st{0, 0, 0, 0, 0};
     double m15[15];
     nlq::event_moments<double, STRAT>(v, x, delta2, defer[c] - 1, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
-                                      ids[3 * c + 2], m15, st, nullptr, nullptr);
+                                      ids[3 * c + 2], m15, st, nullptr, nullptr, 0);
     for (int k = 0; k < 15; ++k) out[15 * c + k] = (double)(float)m15[k];
 }
 

@@ -565,35 +565,39 @@ __global__ void k_u64_to_i64(const unsigned long long *a, int64_t *b, int64_t n)
 }
 
 // ---------------------------------------------------------------------------
-// unique sorted gather with a shared-memory hash table (one block per group)
-constexpr int HCAP = 8192;      // hash slots
+// unique sorted gather with a shared-memory hash table (one block per group).
+// The counting pass uses HCAP slots (up to UCAP unique keys); the filling pass
+// knows the largest count and uses a table of twice that (rounded up to a
+// power of two), so that it holds more blocks per SM.
+constexpr int HCAP = 8192;      // hash slots of the counting pass
 constexpr int UCAP = 4096;      // unique entries per group
 constexpr int GB = 256;         // threads per block
 
-__device__ __forceinline__ void hash_insert(int32_t *tab, int *cnt, int *ovf, int32_t key)
+__device__ __forceinline__ void hash_insert(int32_t *tab, int hcap, int *cnt, int *ovf, int32_t key)
 {
-    unsigned h = ((unsigned)key * 2654435761u) & (HCAP - 1);
-    for (int probe = 0; probe < HCAP; ++probe) {
+    const unsigned mask = (unsigned)hcap - 1u;
+    unsigned h = ((unsigned)key * 2654435761u) & mask;
+    for (int probe = 0; probe < hcap; ++probe) {
         int32_t prev = atomicCAS(&tab[h], -1, key);
         if (prev == -1) { atomicAdd(cnt, 1); return; }
         if (prev == key) return;
-        h = (h + 1) & (HCAP - 1);
+        h = (h + 1) & mask;
     }
     atomicOr(ovf, 1);
 }
 
-__device__ void block_sort_write(int32_t *tab, int32_t *list, int *m, int32_t *dst)
+__device__ void block_sort_write(int32_t *tab, int hcap, int32_t *list, int ucap, int *m, int32_t *dst)
 {
     // compact the table, sort ascending, write out
-    for (int i = threadIdx.x; i < HCAP; i += blockDim.x) {
+    for (int i = threadIdx.x; i < hcap; i += blockDim.x) {
         int32_t k = tab[i];
         if (k != -1) {
             int p = atomicAdd(m, 1);
-            if (p < UCAP) list[p] = k;
+            if (p < ucap) list[p] = k;
         }
     }
     __syncthreads();
-    int n = min(*m, UCAP);
+    int n = min(*m, ucap);
     int p2 = 1;
     while (p2 < n) p2 <<= 1;
     for (int i = n + threadIdx.x; i < p2; i += blockDim.x) list[i] = 0x7fffffff;
@@ -632,24 +636,24 @@ __device__ __forceinline__ bool elem_active(const NNArgs &A, int64_t E)
 // node set of all elements coupled with E (its partners, the outer elements
 // that have E as a partner, and E itself)
 template <int PASS>
-__global__ void k_elem_nodes(NNArgs A, int64_t *cnt, const int64_t *ptr, int32_t *out, int *ovf)
+__global__ void k_elem_nodes(NNArgs A, int hcap, int ucap, int64_t *cnt, const int64_t *ptr, int32_t *out, int *ovf)
 {
     extern __shared__ int32_t sm[];
     int32_t *tab = sm;
-    int32_t *list = sm + HCAP;
+    int32_t *list = sm + hcap;
     __shared__ int n_u, m_u;
     int64_t E = blockIdx.x;
     if (!elem_active(A, E)) {
         if (PASS == 0 && threadIdx.x == 0) cnt[E] = 0;
         return;
     }
-    for (int i = threadIdx.x; i < HCAP; i += blockDim.x) tab[i] = -1;
+    for (int i = threadIdx.x; i < hcap; i += blockDim.x) tab[i] = -1;
     if (threadIdx.x == 0) { n_u = 0; m_u = 0; }
     __syncthreads();
     if (threadIdx.x < 4) {
         int4 e = A.tets[E];
         int ids[4] = {e.x, e.y, e.z, e.w};
-        hash_insert(tab, &n_u, ovf, ids[threadIdx.x]);
+        hash_insert(tab, hcap, &n_u, ovf, ids[threadIdx.x]);
     }
     int32_t o = A.outer_of[E];
     if (o >= 0) {
@@ -657,7 +661,7 @@ __global__ void k_elem_nodes(NNArgs A, int64_t *cnt, const int64_t *ptr, int32_t
         for (int64_t i = b * 4 + threadIdx.x; i < e * 4; i += blockDim.x) {
             int4 t = A.tets[A.pair_tp[i >> 2]];
             int k = (int)(i & 3);
-            hash_insert(tab, &n_u, ovf, k == 0 ? t.x : k == 1 ? t.y : k == 2 ? t.z : t.w);
+            hash_insert(tab, hcap, &n_u, ovf, k == 0 ? t.x : k == 1 ? t.y : k == 2 ? t.z : t.w);
         }
     }
     {
@@ -665,43 +669,56 @@ __global__ void k_elem_nodes(NNArgs A, int64_t *cnt, const int64_t *ptr, int32_t
         for (int64_t i = b * 4 + threadIdx.x; i < e * 4; i += blockDim.x) {
             int4 t = A.tets[A.pair_T[A.tp_pair[i >> 2]]];
             int k = (int)(i & 3);
-            hash_insert(tab, &n_u, ovf, k == 0 ? t.x : k == 1 ? t.y : k == 2 ? t.z : t.w);
+            hash_insert(tab, hcap, &n_u, ovf, k == 0 ? t.x : k == 1 ? t.y : k == 2 ? t.z : t.w);
         }
     }
     __syncthreads();
-    if (n_u > UCAP) { if (threadIdx.x == 0) atomicOr(ovf, 2); return; }
+    if (n_u > ucap) {
+        if (threadIdx.x == 0) {
+            atomicOr(ovf, 2);
+            if (PASS == 0) cnt[E] = 0;
+        }
+        return;
+    }
     if (PASS == 0) {
         if (threadIdx.x == 0) cnt[E] = n_u;
         return;
     }
-    block_sort_write(tab, list, &m_u, out + ptr[E]);
+    block_sort_write(tab, hcap, list, ucap, &m_u, out + ptr[E]);
 }
 
 // row of node r: union of the node sets of the active elements around r
 template <int PASS>
-__global__ void k_rows(NNArgs A, const int64_t *ne_ptr, const int32_t *ne_ent, const int64_t *nn_ptr,
-                       const int32_t *nn_ent, int64_t *cnt, const int64_t *ptr, int32_t *out, int *ovf)
+__global__ void k_rows(NNArgs A, int hcap, int ucap, const int64_t *ne_ptr, const int32_t *ne_ent,
+                       const int64_t *nn_ptr, const int32_t *nn_ent, int64_t *cnt, const int64_t *ptr, int32_t *out,
+                       int *ovf)
 {
     extern __shared__ int32_t sm[];
     int32_t *tab = sm;
-    int32_t *list = sm + HCAP;
+    int32_t *list = sm + hcap;
     __shared__ int n_u, m_u;
     int64_t r = blockIdx.x;
-    for (int i = threadIdx.x; i < HCAP; i += blockDim.x) tab[i] = -1;
+    for (int i = threadIdx.x; i < hcap; i += blockDim.x) tab[i] = -1;
     if (threadIdx.x == 0) { n_u = 0; m_u = 0; }
     __syncthreads();
     for (int64_t k = ne_ptr[r]; k < ne_ptr[r + 1]; ++k) {
         int64_t E = ne_ent[k] >> 2;
         for (int64_t i = nn_ptr[E] + threadIdx.x; i < nn_ptr[E + 1]; i += blockDim.x)
-            hash_insert(tab, &n_u, ovf, nn_ent[i]);
+            hash_insert(tab, hcap, &n_u, ovf, nn_ent[i]);
     }
     __syncthreads();
-    if (n_u > UCAP) { if (threadIdx.x == 0) atomicOr(ovf, 2); return; }
+    if (n_u > ucap) {
+        if (threadIdx.x == 0) {
+            atomicOr(ovf, 2);
+            if (PASS == 0) cnt[r] = 0;
+        }
+        return;
+    }
     if (PASS == 0) {
         if (threadIdx.x == 0) cnt[r] = n_u;
         return;
     }
-    block_sort_write(tab, list, &m_u, out + ptr[r]);
+    block_sort_write(tab, hcap, list, ucap, &m_u, out + ptr[r]);
 }
 
 __device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, int32_t key)
@@ -1119,31 +1136,55 @@ nl_status nl_pairs_build_impl(nl_mesh *m, double delta, nl_pairs **out)
         N.pair_T = P->pair_T; N.tp_ptr = P->tp_ptr; N.tp_pair = P->tp_pair; N.nt = nt;
         int *ovf = sc.get<int>(1);
         NL_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
-        size_t hsm = sizeof(int32_t) * (HCAP + UCAP);
+        const size_t hsm = sizeof(int32_t) * (HCAP + UCAP);   // the largest table + list (both passes)
         NL_CUDA(cudaFuncSetAttribute(k_elem_nodes<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
         NL_CUDA(cudaFuncSetAttribute(k_elem_nodes<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
         NL_CUDA(cudaFuncSetAttribute(k_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
         NL_CUDA(cudaFuncSetAttribute(k_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-        { k_elem_nodes<0><<<(unsigned)nt, GB, hsm, s>>>(N, cnt, nullptr, nullptr, ovf); nl_count_launch(); }
+        const size_t hsm0 = sizeof(int32_t) * HCAP;             // counting pass: no list
+        // the filling pass: a table of twice the largest count, a list of it
+        auto check_overflow = [&]() {
+            int hovf = 0;
+            NL_CUDA(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+            NL_CUDA(cudaStreamSynchronize(s));
+            NL_REQUIRE(hovf == 0, "sparsity pattern overflow (more than %d columns in a row); delta/h too large",
+                       UCAP);
+        };
+        auto fill_shape = [&](const int64_t *ptr, int64_t n, int &hcap, int &ucap) {
+            NL_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+            { k_max_seg<<<blocks_for(n, 256), 256, 0, s>>>(ptr, n, mx); nl_count_launch(); }
+            NL_CHECK_LAUNCH();
+            NL_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s));
+            NL_CUDA(cudaStreamSynchronize(s));
+            ucap = 32;
+            while (ucap < (int64_t)hmx && ucap < UCAP) ucap <<= 1;
+            hcap = std::min(HCAP, 2 * ucap);
+        };
+        int hcap1 = HCAP, ucap1 = UCAP;
+        { k_elem_nodes<0><<<(unsigned)nt, GB, hsm0, s>>>(N, HCAP, UCAP, cnt, nullptr, nullptr, ovf); nl_count_launch(); }
         NL_CHECK_LAUNCH();
+        check_overflow();
         int64_t *nn_ptr = sc.get<int64_t>(nt + 1);
         int64_t nn_total = nl_scan_counts(cnt, nn_ptr, nt, &P->arena, s);
         int32_t *nn_ent = sc.get<int32_t>(nn_total);
-        { k_elem_nodes<1><<<(unsigned)nt, GB, hsm, s>>>(N, nullptr, nn_ptr, nn_ent, ovf); nl_count_launch(); }
+        fill_shape(nn_ptr, nt, hcap1, ucap1);
+        { k_elem_nodes<1><<<(unsigned)nt, GB, sizeof(int32_t) * (hcap1 + ucap1), s>>>(N, hcap1, ucap1, nullptr, nn_ptr,
+                                                                                    nn_ent, ovf); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        { k_rows<0><<<(unsigned)nv, GB, hsm, s>>>(N, m->ne_ptr, m->ne_ent, nn_ptr, nn_ent, cnt, nullptr, nullptr, ovf); nl_count_launch(); }
+        { k_rows<0><<<(unsigned)nv, GB, hsm0, s>>>(N, HCAP, UCAP, m->ne_ptr, m->ne_ent, nn_ptr, nn_ent, cnt, nullptr,
+                                                   nullptr, ovf); nl_count_launch(); }
         NL_CHECK_LAUNCH();
+        check_overflow();
         P->rowptr = P->arena.get<int64_t>(nv + 1);
         P->nnz = nl_scan_counts(cnt, P->rowptr, nv, &P->arena, s);
         NL_REQUIRE(P->nnz < 0x7fffffffLL, "nnz %lld exceeds the int32 position index", (long long)P->nnz);
         P->col = P->arena.get<int32_t>(P->nnz);
-        { k_rows<1><<<(unsigned)nv, GB, hsm, s>>>(N, m->ne_ptr, m->ne_ent, nn_ptr, nn_ent, nullptr, P->rowptr, P->col,
-                                                 ovf); nl_count_launch(); }
+        fill_shape(P->rowptr, nv, hcap1, ucap1);
+        { k_rows<1><<<(unsigned)nv, GB, sizeof(int32_t) * (hcap1 + ucap1), s>>>(N, hcap1, ucap1, m->ne_ptr, m->ne_ent,
+                                                                            nn_ptr, nn_ent, nullptr, P->rowptr, P->col,
+                                                                            ovf); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        int hovf = 0;
-        NL_CUDA(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
-        NL_CUDA(cudaStreamSynchronize(s));
-        NL_REQUIRE(hovf == 0, "sparsity pattern overflow (more than %d columns in a row); delta/h too large", UCAP);
+        check_overflow();
 
         NL_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
         { k_row_len_max<<<blocks_for(nv, 256), 256, 0, s>>>(P->rowptr, nv, mx); nl_count_launch(); }

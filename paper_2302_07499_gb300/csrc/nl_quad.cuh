@@ -728,9 +728,13 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
 }
 
 // Per-thread scratch for the cap cells: per cell the 4 vertices (12 values)
-// and their barycentric rows with respect to T' (16 values).  The FP32
-// sampler reads it with 16-byte loads, so the scratch must be 16-byte aligned
-// (28 floats per cell keep every cell and every row on a 16-byte boundary).
+// and their barycentric rows with respect to T' (16 values).  Cell j of a
+// thread starts cs values after cell j - 1: the event kernel lays the cells
+// out cell-major across the block (cs = 28 x threads), so that the 16-byte
+// loads of a warp hit distinct banks whatever cell each lane samples.  The
+// FP32 sampler reads it with 16-byte loads, so the scratch must be 16-byte
+// aligned (28 floats per cell keep every cell and every row on a 16-byte
+// boundary).
 constexpr int CB_STRIDE = 28;
 static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16 == 0, "cap scratch alignment");
 
@@ -742,16 +746,16 @@ static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16
 //                    with nmc Philox samples (cell by cumulative volume,
 //                    uniform point from the spacings of three sorted
 //                    uniforms, acceptance |y-x|^2 <= delta^2).  Accepted
-//                    samples are accumulated as count, sum of z and sum of
-//                    z z^T with z = y - centroid(T'); the barycentric moments
-//                    follow from the affine map lambda'(y) = 1/4 + G z.
-//   cb: per-thread scratch of 36 values for the sampling cells.
+//                    samples add 1, lambda'(y) and lambda'(y) lambda'(y)^T,
+//                    lambda'(y) being the spacings' combination of the cell
+//                    vertices' barycentric rows (non-negative terms only).
+//   cb, cs: per-thread scratch for the sampling cells, cell j at cb + j cs.
 //   Returns true (and writes nothing) when the FP32 path defers the event to
 //   the FP64 pass: approxcaps with a vertex of T' within 1e-3 (relative) of
 //   the sphere, where the arc midpoints are ill-conditioned in FP32.
 template <class R, int STRAT>
 __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
-                              uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb)
+                              uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs)
 {
     Mom<R> M;
     constexpr bool F32 = sizeof(R) == 4;
@@ -915,7 +919,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
     for (int j = 0; j < ns; ++j) {
         P3<R> c0 = P(S[j][0]), c1 = P(S[j][1]), c2 = P(S[j][2]), c3 = P(S[j][3]);
         vol[j] = vol4(c0, c1, c2, c3);
-        R *o = cb + CB_STRIDE * j;
+        R *o = cb + cs * j;
         o[0] = c0.x; o[1] = c0.y; o[2] = c0.z; o[3] = c1.x; o[4] = c1.y; o[5] = c1.z;
         o[6] = c2.x; o[7] = c2.y; o[8] = c2.z; o[9] = c3.x; o[10] = c3.y; o[11] = c3.z;
         for (int kk = 0; kk < 4; ++kk) {
@@ -951,11 +955,10 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         R s2 = hi < mid0 ? mid0 : hi;
         R s1 = hi < mid0 ? hi : mid0;
         R be0 = s0, be1 = s1 - s0, be2 = s2 - s1, be3 = R(1) - s2;
-        const R *c = cb + CB_STRIDE * j;
+        const R *c = cb + cs * j;
         R cc[12];
         if constexpr (F32) {
-            // 16-byte loads: the per-thread stride of 336 bytes makes them
-            // conflict-free, where 4-byte loads would conflict 4 ways
+            // 16-byte loads, conflict-free in the cell-major layout
             const float4 *c4 = reinterpret_cast<const float4 *>(c);
             const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
             cc[0] = q0.x; cc[1] = q0.y; cc[2] = q0.z; cc[3] = q0.w; cc[4] = q1.x; cc[5] = q1.y;
@@ -975,7 +978,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
             if (unsure) {
                 int j64 = j;
                 inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64) != 0;
-                c = cb + CB_STRIDE * j64;
+                c = cb + cs * j64;
             }
         }
         // branch-free accumulation of the accepted sample
@@ -1025,7 +1028,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
 template <class R, int STRAT>
 // Returns the classification + 1 when the event is deferred to FP64, else 0.
 __device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, const uint32_t *rk, uint32_t idT,
-                             uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st, const Strict *sx, R *cb)
+                             uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st, const Strict *sx, R *cb, int cs)
 {
     int inm = classify(v, x, d2, sx);
     if constexpr (STRAT >= 3) {
@@ -1047,7 +1050,7 @@ __device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, 
         return 0;
     }
     R o[15];
-    if (event_moments<R, STRAT>(v, x, d2, inm, nmc, rk, idT, idTp, q, o, st, sx, cb)) return inm + 1;
+    if (event_moments<R, STRAT>(v, x, d2, inm, nmc, rk, idT, idTp, q, o, st, sx, cb, cs)) return inm + 1;
     M.m0 = o[0];
     for (int k = 0; k < 4; ++k) M.m1[k] = o[1 + k];
     for (int k = 0; k < 10; ++k) M.m2[k] = o[5 + k];

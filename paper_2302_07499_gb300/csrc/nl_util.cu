@@ -196,7 +196,9 @@ void nl_segmented_sort_i32(int32_t *keys, const int64_t *ptr, int64_t nseg, int6
                (long long)max_seg);
     int p2 = 1;
     while (p2 < max_seg) p2 <<= 1;
-    int threads = std::min(1024, std::max(32, p2 / 2));
+    // 128-thread blocks: most segments are far shorter than the longest, and
+    // small blocks keep more segments in flight per SM
+    int threads = std::min(128, std::max(32, p2 / 2));
     size_t smem = sizeof(int32_t) * (size_t)p2;
     // one process-wide limit for every size (concurrent callers never lower it)
     if (smem > 48 * 1024)
