@@ -147,20 +147,20 @@ __global__ void __launch_bounds__(256, 3) k_classify(const __grid_constant__ Asm
             }
         }
         // warp-aggregated slot allocation within the event's class (number of
-        // inside vertices), so that each warp of K2 runs one geometry case
+        // inside vertices), so that each warp of K2 runs one geometry case:
+        // the lanes of one class find each other, their first lane reserves
+        // the class's slots
         const int cls = __popc((unsigned)(info & 15));
         int32_t sl = -1;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const unsigned mm = __ballot_sync(0xffffffffu, ev && cls == c);
-            int basep = 0;
-            if (lane == 0 && mm) basep = atomicAdd(&A.nev[c], __popc(mm));
-            basep = __shfl_sync(0xffffffffu, basep, 0);
-            if (ev && cls == c) {
-                const int idx = basep + __popc(mm & ((1u << lane) - 1u));
-                sl = (int32_t)(c * nu + idx);
-                A.evu[c * nu + idx] = (int32_t)u;
-            }
+        const unsigned grp = __match_any_sync(0xffffffffu, ev ? cls : -1);
+        const int leader = __ffs(grp) - 1;
+        int basep = 0;
+        if (ev && lane == leader) basep = atomicAdd(&A.nev[cls], __popc(grp));
+        basep = __shfl_sync(0xffffffffu, basep, leader);
+        if (ev) {
+            const int idx = basep + __popc(grp & ((1u << lane) - 1u));
+            sl = (int32_t)(cls * nu + idx);
+            A.evu[cls * nu + idx] = (int32_t)u;
         }
         if (u < nu) {
             A.uinfo[u] = info;

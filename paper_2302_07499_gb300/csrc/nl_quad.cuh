@@ -406,6 +406,40 @@ template <class R>
 __device__ __forceinline__ bool meets_ball(const P3<R> v[4], P3<R> x, R d2, const Strict *sx)
 {
     constexpr bool F32 = sizeof(R) == 4;
+    if constexpr (F32) {
+        // branch-free decisions far from the sphere (relative margin 1e-4 on
+        // squared distances, far above the FP32 rounding): a bounding sphere
+        // of T' (centroid, farthest vertex) that misses the ball, or an edge
+        // of T' with a point inside the ball (any point of the segment gives
+        // an upper bound of the distance, so the clamped parameter need not
+        // be exact)
+        const P3<R> c = mk3<R>(R(0.25) * ((v[0].x + v[1].x) + (v[2].x + v[3].x)),
+                               R(0.25) * ((v[0].y + v[1].y) + (v[2].y + v[3].y)),
+                               R(0.25) * ((v[0].z + v[1].z) + (v[2].z + v[3].z)));
+        R rad2 = R(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const P3<R> w = sub(v[k], c);
+            const R r2 = dot(w, w);
+            rad2 = r2 > rad2 ? r2 : rad2;
+        }
+        const P3<R> wc = sub(c, x);
+        const R reach = sqrt(d2) + sqrt(rad2);
+        if (dot(wc, wc) > reach * reach * R(1.0001)) return false;
+        R emin = R(3.0e38);
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            const int i = e < 3 ? 0 : (e < 5 ? 1 : 2);
+            const int j = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+            const P3<R> ab = sub(v[j], v[i]), ap = sub(x, v[i]);
+            R t = __fdividef(dot(ap, ab), dot(ab, ab));
+            t = t < R(0) ? R(0) : (t > R(1) ? R(1) : t);
+            const P3<R> r = mk3<R>(ap.x - t * ab.x, ap.y - t * ab.y, ap.z - t * ab.z);
+            const R e2 = dot(r, r);
+            emin = e2 < emin ? e2 : emin;
+        }
+        if (emin < d2 * R(0.9999)) return true;
+    }
     R dd = d2_point_tet(x, v);
     bool run = dd <= d2;
     if (F32 && sx && absr(dd - d2) <= R(1e-4) * d2) run = strict_meets(sx);
