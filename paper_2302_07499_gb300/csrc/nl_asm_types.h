@@ -18,6 +18,10 @@ namespace nla {
 // Work is cut into chunks of outer elements so that the per-(pair, point)
 // records stay bounded in size.
 constexpr int64_t kUnitsPerChunk = int64_t(1) << 25;
+// values per event record of the moments (15 used; a multiple of 4 so that
+// records start on 16-byte boundaries and read as 16-byte vectors)
+constexpr int MQ_STRIDE = 16;
+static_assert(MQ_STRIDE % 4 == 0 && MQ_STRIDE >= 15, "moment records are read as 16-byte vectors");
 
 // One problem: its mesh, pairs and pattern (inputs), its outputs, and where
 // its outer elements and pairs start in the index space of a launch (0 for a
@@ -65,7 +69,7 @@ struct AsmArgs {
     int32_t *evu;            // [4][units] unit of each event, per class (m = 0..3)
     int *nev;                // [5] event count per class; nev[4] = deferred events
     int32_t *fix;            // [units] FP32 approxcaps events deferred to the FP64 pass
-    void *Mq;                // [events][15] moments (R)
+    void *Mq;                // [events][MQ_STRIDE] moments (R): 15 used, 16-byte aligned records
     unsigned long long *stats;  // [5]
 };
 

@@ -68,16 +68,6 @@ template <class R> __device__ __forceinline__ R qlam(int i, int q)
     return (i == q) ? R(0x1.2bbae2a27f931p-1) : R(0x1.1b06d1d200913p-3);
 }
 
-__device__ __forceinline__ int lower_bound_s(const int32_t *a, int n, int32_t key)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (a[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
 // T' vertex coordinates for the point x_q: global FP64 (R = double) or
 // relative to x_q as double-float differences (R = float), plus the FP64
 // context for the FP32 path's exact decisions.
@@ -174,7 +164,9 @@ __global__ void __launch_bounds__(256, 3) k_classify(const __grid_constant__ Asm
 // Monte Carlo loop over the cap (uniform trip count across the warp).
 template <class R> struct EvCfg {
     static constexpr int threads = sizeof(R) == 4 ? 128 : 64;
-    static constexpr size_t smem = sizeof(R) * threads * 3 * nlq::CB_STRIDE;
+    // the cap cells, then a 17-value record stage per thread (odd stride:
+    // conflict-free scalar accesses)
+    static constexpr size_t smem = sizeof(R) * threads * (3 * nlq::CB_STRIDE + 17);
     // 4 resident blocks per SM: 128 registers a thread, no spills (the cap
     // scratch would allow 5 blocks at 96 registers; the spills that forces
     // cost more than the fifth block gains: 21.1 -> 19.5 ms on the bench step)
@@ -207,12 +199,26 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
         nlq::Strict sx;
         load_point_geometry<R>(P, P.tets[Tp], o, q, v, x, sx);
         const int inm = A.uinfo[u] & 15;
-        R *out = reinterpret_cast<R *>(A.Mq) + 15 * (int64_t)e;
+        // the record is built in shared memory and written out once
+        R *out = reinterpret_cast<R *>(evsm) + 3 * nlq::CB_STRIDE * EvCfg<R>::threads + 17 * threadIdx.x;
         const bool deferred = nlq::event_moments<R, STRAT>(v, x, sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2, inm,
                                                            A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q, out,
                                                            st, (sizeof(R) == 4) ? &sx : nullptr, cb,
                                                            nlq::CB_STRIDE * EvCfg<R>::threads);
-        if (deferred) A.fix[atomicAdd(&A.nev[4], 1)] = e;
+        if (deferred) {
+            A.fix[atomicAdd(&A.nev[4], 1)] = e;
+        } else if constexpr (sizeof(R) == 4) {
+            float4 *g = reinterpret_cast<float4 *>(A.Mq) + (MQ_STRIDE / 4) * (int64_t)e;
+            g[0] = make_float4(out[0], out[1], out[2], out[3]);
+            g[1] = make_float4(out[4], out[5], out[6], out[7]);
+            g[2] = make_float4(out[8], out[9], out[10], out[11]);
+            g[3] = make_float4(out[12], out[13], out[14], 0.f);
+        } else {
+            double2 *g = reinterpret_cast<double2 *>(A.Mq) + (MQ_STRIDE / 2) * (int64_t)e;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) g[k] = make_double2(out[2 * k], out[2 * k + 1]);
+            g[7] = make_double2(out[14], 0.0);
+        }
     }
     __shared__ unsigned long long sstat[4];
     if (threadIdx.x < 4) sstat[threadIdx.x] = 0ULL;
@@ -260,7 +266,7 @@ __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmA
         double m15[15];
         nlq::event_moments<double, STRAT>(v, x, P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q,
                                           m15, st, nullptr, nullptr, 0);
-        float *out = reinterpret_cast<float *>(A.Mq) + 15 * (int64_t)e;
+        float *out = reinterpret_cast<float *>(A.Mq) + MQ_STRIDE * (int64_t)e;
 #pragma unroll
         for (int k = 0; k < 15; ++k) out[k] = (float)m15[k];
     }
@@ -400,7 +406,22 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         const int32_t sl = A.slot[u0 + q];
                         const int cls = (int)(sl / nu), idx = (int)(sl - (int64_t)cls * nu);
                         const int64_t ev = (int64_t)cpre[cls] + idx;
-                        const R *mq = reinterpret_cast<const R *>(A.Mq) + 15 * ev;
+                        R mq[MQ_STRIDE];
+                        if constexpr (F32) {
+                            const float4 *m4 = reinterpret_cast<const float4 *>(A.Mq) + (MQ_STRIDE / 4) * ev;
+#pragma unroll
+                            for (int k = 0; k < MQ_STRIDE / 4; ++k) {
+                                const float4 t4 = m4[k];
+                                mq[4 * k] = t4.x; mq[4 * k + 1] = t4.y; mq[4 * k + 2] = t4.z; mq[4 * k + 3] = t4.w;
+                            }
+                        } else {
+                            const double2 *m2 = reinterpret_cast<const double2 *>(A.Mq) + (MQ_STRIDE / 2) * ev;
+#pragma unroll
+                            for (int k = 0; k < MQ_STRIDE / 2; ++k) {
+                                const double2 t2 = m2[k];
+                                mq[2 * k] = t2.x; mq[2 * k + 1] = t2.y;
+                            }
+                        }
                         M.m0 = mq[0];
 #pragma unroll
                         for (int k = 0; k < 4; ++k) M.m1[k] = mq[1 + k];
@@ -462,11 +483,23 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                             Xs[tid * 16 + 4 * i + k] = (double)sum;
                         }
                 }
+                // positions of T''s nodes in the rows of T's nodes (present
+                // in every one of them): branch-free lower bounds, the four
+                // keys of a row in lockstep (the rows are the block's, so the
+                // warp does not diverge)
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i) {
+                    const int32_t *row = cols + i * mr;
+                    int b[4] = {0, 0, 0, 0};
+                    for (int n = lens[i]; n > 1;) {
+                        const int half = n >> 1;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        offs[tid * 16 + 4 * i + k] = lower_bound_s(cols + i * mr, lens[i], nodeP[k]);
+                        for (int k = 0; k < 4; ++k) b[k] = (row[b[k] + half] < nodeP[k]) ? b[k] + half : b[k];
+                        n -= half;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) offs[tid * 16 + 4 * i + k] = b[k] + (row[b[k]] < nodeP[k] ? 1 : 0);
+                }
                 if constexpr (F32) reinterpret_cast<DF *>(wsc)[tid] = df_from(-(omega * cT));
                 else wsc[tid] = -(omega * cT);
             }
@@ -576,7 +609,7 @@ void alloc_work(AsmArgs &A, Scratch &sc, int64_t max_units)
     A.evu = sc.get<int32_t>(4 * max_units);
     A.nev = sc.get<int>(5);
     A.fix = kDefer ? sc.get<int32_t>(max_units) : nullptr;
-    A.Mq = (void *)sc.get<R>(15 * max_units);
+    A.Mq = (void *)sc.get<R>(MQ_STRIDE * max_units);
 }
 
 // The three quadrature kernels over every chunk, stream-ordered, no host
