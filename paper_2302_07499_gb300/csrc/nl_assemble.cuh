@@ -332,6 +332,10 @@ __device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.
 // with c = (gamma/2)|T|/4 and omega = 2 for collar elements T'.  Strips are
 // accumulated by one warp per row in pair order (deterministic).
 constexpr int NT = 128;
+// per-pair stride of the 16 cross coefficients and their strip positions in
+// shared memory: odd, so that neither the per-pair writes nor the row-wise
+// reads of 8 pairs at a time pile up on a few banks
+constexpr int XS = 17;
 
 template <class R, bool B>
 __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs A)
@@ -340,10 +344,10 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
     const int mr = A.max_row;
     int32_t *cols = reinterpret_cast<int32_t *>(smem);                                        // [4][mr]
     double *strip = reinterpret_cast<double *>(smem + sizeof(int32_t) * 4 * ((mr + 1) & ~1));  // [4][mr]
-    // [NT][16] cross coefficients: R for FP64, double-float for FP32 (8 bytes either way)
+    // [NT][XS] cross coefficients: R for FP64, double-float for FP32 (8 bytes either way)
     double *Xs = strip + 4 * mr;
-    int32_t *offs = reinterpret_cast<int32_t *>(Xs + NT * 16);                                 // [NT][16]
-    double *wsc = reinterpret_cast<double *>(offs + NT * 16);                                  // [NT]
+    int32_t *offs = reinterpret_cast<int32_t *>(Xs + NT * XS);                                 // [NT][XS]
+    double *wsc = reinterpret_cast<double *>(offs + NT * XS);                                  // [NT]
     double *red = wsc + NT;                                                                    // [NT/32][4]
     __shared__ int lens[4];
     __shared__ unsigned long long sin_;
@@ -390,9 +394,14 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                 // FP32: points where T' is whole enter in double (their moments
                 // are closed forms of |T'|), the others from their FP32 records
                 int fullmask = 0;
+                // the pair's 4 units: 4 info bytes and 4 slots in one load each
+                // (u0 is a multiple of 4)
+                const uint32_t info4 = *reinterpret_cast<const uint32_t *>(A.uinfo + u0);
+                const int4 slot4 = *reinterpret_cast<const int4 *>(A.slot + u0);
+                const int32_t slots[4] = {slot4.x, slot4.y, slot4.z, slot4.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const uint8_t info = A.uinfo[u0 + q];
+                    const uint8_t info = (uint8_t)(info4 >> (8 * q));
                     Mom<R> M;
                     if ((info & 15) == 15) {
                         if constexpr (F32) {
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         }
                         inside++;
                     } else if (info & 0x10) {
-                        const int32_t sl = A.slot[u0 + q];
+                        const int32_t sl = slots[q];
                         const int cls = (int)(sl / nu), idx = (int)(sl - (int64_t)cls * nu);
                         const int64_t ev = (int64_t)cpre[cls] + idx;
                         R mq[MQ_STRIDE];
@@ -468,7 +477,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         for (int k = 0; k < 4; ++k) {
                             const float ev = ((qlam<float>(i, 0) * (float)Y[0][k] + qlam<float>(i, 1) * (float)Y[1][k]) +
                                               qlam<float>(i, 2) * (float)Y[2][k]) + qlam<float>(i, 3) * (float)Y[3][k];
-                            reinterpret_cast<DF *>(Xs)[tid * 16 + 4 * i + k] = df_add(xc, DF{ev, 0.f});
+                            reinterpret_cast<DF *>(Xs)[tid * XS + 4 * i + k] = df_add(xc, DF{ev, 0.f});
                         }
                     }
                 } else {
@@ -480,7 +489,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         for (int k = 0; k < 4; ++k) {
                             R sum = ((qlam<R>(i, 0) * Y[0][k] + qlam<R>(i, 1) * Y[1][k]) + qlam<R>(i, 2) * Y[2][k]) +
                                     qlam<R>(i, 3) * Y[3][k];
-                            Xs[tid * 16 + 4 * i + k] = (double)sum;
+                            Xs[tid * XS + 4 * i + k] = (double)sum;
                         }
                 }
                 // positions of T''s nodes in the rows of T's nodes (present
@@ -498,7 +507,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         n -= half;
                     }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) offs[tid * 16 + 4 * i + k] = b[k] + (row[b[k]] < nodeP[k] ? 1 : 0);
+                    for (int k = 0; k < 4; ++k) offs[tid * XS + 4 * i + k] = b[k] + (row[b[k]] < nodeP[k] ? 1 : 0);
                 }
                 if constexpr (F32) reinterpret_cast<DF *>(wsc)[tid] = df_from(-(omega * cT));
                 else wsc[tid] = -(omega * cT);
@@ -513,14 +522,14 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                 for (int g0 = 0; g0 < cnt; g0 += 8) {
                     const int t = g0 + (lane >> 2), k = lane & 3;
                     const bool act = t < cnt;
-                    const int c = act ? offs[t * 16 + 4 * i + k] : -1 - lane;
+                    const int c = act ? offs[t * XS + 4 * i + k] : -1 - lane;
                     const unsigned peers = __match_any_sync(0xffffffffu, c);
                     const int leader = __ffs(peers) - 1;
                     const int maxn = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
                     unsigned rest = (lane == leader) ? (peers & (peers - 1u)) : 0u;
                     if constexpr (F32) {
                         const DF v = act ? df_mul2(reinterpret_cast<const DF *>(wsc)[t],
-                                                   reinterpret_cast<const DF *>(Xs)[t * 16 + 4 * i + k])
+                                                   reinterpret_cast<const DF *>(Xs)[t * XS + 4 * i + k])
                                          : DF{0.f, 0.f};
                         DF sum = v;
                         for (int j = 1; j < maxn; ++j) {
@@ -532,7 +541,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         DF *sp = reinterpret_cast<DF *>(strip);
                         if (act && lane == leader) sp[i * mr + c] = df_add(sp[i * mr + c], sum);
                     } else {
-                        const double v = act ? wsc[t] * Xs[t * 16 + 4 * i + k] : 0.0;
+                        const double v = act ? wsc[t] * Xs[t * XS + 4 * i + k] : 0.0;
                         double sum = v;
                         for (int j = 1; j < maxn; ++j) {
                             const int src = rest ? __ffs(rest) - 1 : lane;
@@ -591,9 +600,9 @@ inline size_t combine_smem_bytes(int max_row, size_t real_size)
 {
     size_t b = sizeof(int32_t) * 4 * (size_t)((max_row + 1) & ~1);
     b += sizeof(double) * 4 * (size_t)max_row;
-    b += sizeof(double) * NT * 16;     // cross coefficients (double or double-float)
+    b += sizeof(double) * NT * XS;     // cross coefficients (double or double-float)
     (void)real_size;
-    b += sizeof(int32_t) * NT * 16;
+    b += sizeof(int32_t) * NT * XS;
     b += sizeof(double) * NT;
     b += sizeof(double) * (NT / 32) * 4;
     return b;

@@ -65,17 +65,23 @@ __global__ void k_elem_blocks(const int64_t *__restrict__ tp_ptr, const int32_t 
 #pragma unroll
     for (int k = 0; k < 10; ++k) acc[k] = 0.0;
     // points at which T' = el is whole add |T'|(1 + delta_ab)/20 each (FP32
-    // path: kept out of the FP32 staging)
+    // path: kept out of the FP32 staging); their weights are summed per lane
+    // (sw) and scaled once, so a pair costs 11 FP64 multiply-adds
     const double vol = tet_vol[el];
+    double sw = 0.0;
     for (int64_t j = tp_ptr[el] + lane; j < tp_ptr[el + 1]; j += 32) {
         int32_t p = tp_pair[j];
         double w = omega * (half_gamma * (tet_vol[pair_T[p]] * 0.25));
         const DT *d = D + 10 * (int64_t)p;
-        const double nf = nfull ? (double)nfull[p] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k] += w * (double)d[k];
+        if (nfull) sw += w * (double)nfull[p];
+    }
+    if (nfull) {
 #pragma unroll
         for (int k = 0; k < 10; ++k) {
             const double cf = (k == 0 || k == 4 || k == 7 || k == 9) ? 0.1 : 0.05;
-            acc[k] += w * ((double)d[k] + nf * (vol * cf));
+            acc[k] += sw * (vol * cf);
         }
     }
 #pragma unroll
