@@ -23,6 +23,7 @@
 #include "nl_asm_types.h"
 #include "nl_internal.h"
 #include "nl_quad.cuh"
+#include "nl_df.cuh"
 
 #include <string.h>
 
@@ -273,54 +274,6 @@ __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmA
     if (st.fallback) atomicAdd(&A.stats[4], (unsigned long long)st.fallback);
 }
 
-// ---------------------------------------------------------------------------
-// Double-float (hi + lo) arithmetic for the FP32 path's sums: error-free
-// transformations (Knuth's TwoSum, and the exact product by fused
-// multiply-add), so that strip sums keep about 44 bits without touching the
-// narrow FP64 pipe.
-struct DF {
-    float hi, lo;
-};
-__device__ __forceinline__ DF df_add(DF a, DF b)
-{
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    float e = (a.hi - (s - bb)) + (b.hi - bb);
-    e += a.lo + b.lo;
-    const float h = s + e;
-    return DF{h, e - (h - s)};
-}
-__device__ __forceinline__ DF df_mul(DF a, float x)
-{
-    const float p = a.hi * x;
-    float e = __fmaf_rn(a.hi, x, -p);
-    e = __fmaf_rn(a.lo, x, e);
-    const float h = p + e;
-    return DF{h, e - (h - p)};
-}
-// double-float times double-float (the products' low parts by fused
-// multiply-add; the lo x lo term is below the result's precision)
-__device__ __forceinline__ DF df_mul2(DF a, DF b)
-{
-    const float p = a.hi * b.hi;
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    const float h = p + e;
-    return DF{h, e - (h - p)};
-}
-// a double constant as float hi + lo (folded at compile time)
-__device__ __forceinline__ DF df_const(double d)
-{
-    const float h = (float)d;
-    return DF{h, (float)(d - (double)h)};
-}
-__device__ __forceinline__ DF df_from(double d)
-{
-    const float h = (float)d;
-    return DF{h, (float)(d - (double)h)};
-}
-__device__ __forceinline__ double df_to(DF a) { return (double)a.hi + (double)a.lo; }
 
 // ---------------------------------------------------------------------------
 // K3: one block per outer element T (persistent over the chunk's outer

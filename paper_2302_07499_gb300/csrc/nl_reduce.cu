@@ -11,6 +11,7 @@
 #include <algorithm>
 
 #include "nl_internal.h"
+#include "nl_df.cuh"
 
 namespace {
 
@@ -49,13 +50,13 @@ __global__ void k_strip_gather(const int64_t *__restrict__ rowptr, const int64_t
 
 // element blocks: warp per element; lanes take pairs lane, lane+32, ...;
 // fixed butterfly reduction.  Layout of the 10 values: (0,0) (0,1) (0,2)
-// (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3).
-template <class DT>
+// (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3).  FP64 path: D holds each pair's
+// full T'T' moments.
 __global__ void k_elem_blocks(const int64_t *__restrict__ tp_ptr, const int32_t *__restrict__ tp_pair,
                               const int32_t *__restrict__ pair_T, const double *__restrict__ tet_vol,
                               const uint8_t *__restrict__ in_omega, const int32_t *__restrict__ outer_of,
-                              const DT *__restrict__ D, const uint8_t *__restrict__ nfull, const double *__restrict__ TT,
-                              double half_gamma, int64_t nt, double *E)
+                              const double *__restrict__ D, const double *__restrict__ TT, double half_gamma, int64_t nt,
+                              double *E)
 {
     int64_t el = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -64,25 +65,12 @@ __global__ void k_elem_blocks(const int64_t *__restrict__ tp_ptr, const int32_t 
     double acc[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) acc[k] = 0.0;
-    // points at which T' = el is whole add |T'|(1 + delta_ab)/20 each (FP32
-    // path: kept out of the FP32 staging); their weights are summed per lane
-    // (sw) and scaled once, so a pair costs 11 FP64 multiply-adds
-    const double vol = tet_vol[el];
-    double sw = 0.0;
     for (int64_t j = tp_ptr[el] + lane; j < tp_ptr[el + 1]; j += 32) {
         int32_t p = tp_pair[j];
         double w = omega * (half_gamma * (tet_vol[pair_T[p]] * 0.25));
-        const DT *d = D + 10 * (int64_t)p;
+        const double *d = D + 10 * (int64_t)p;
 #pragma unroll
-        for (int k = 0; k < 10; ++k) acc[k] += w * (double)d[k];
-        if (nfull) sw += w * (double)nfull[p];
-    }
-    if (nfull) {
-#pragma unroll
-        for (int k = 0; k < 10; ++k) {
-            const double cf = (k == 0 || k == 4 || k == 7 || k == 9) ? 0.1 : 0.05;
-            acc[k] += sw * (vol * cf);
-        }
+        for (int k = 0; k < 10; ++k) acc[k] += w * d[k];
     }
 #pragma unroll
     for (int k = 0; k < 10; ++k)
@@ -92,6 +80,56 @@ __global__ void k_elem_blocks(const int64_t *__restrict__ tp_ptr, const int32_t 
 #pragma unroll
         for (int k = 1; k < 10; ++k)
             if (lane == k) v = acc[k];
+        int32_t o = outer_of[el];
+        if (o >= 0) v += TT[10 * (int64_t)o + lane];
+        E[10 * el + lane] = v;
+    }
+}
+
+// The same for the FP32 path, with double-float sums (FP32 pipes only): the
+// weight w = omega (gamma/2) |T| / 4 from |T| as float hi + lo, the 10
+// staged FP32 values of each pair, and the points at which T' = el is whole
+// (nfull per pair, kept out of the FP32 staging) as the sum of their weights
+// scaled once by |T'|(1 + delta_ab)/20.
+__global__ void k_elem_blocks_df(const int64_t *__restrict__ tp_ptr, const int32_t *__restrict__ tp_pair,
+                                 const int32_t *__restrict__ pair_T, const double *__restrict__ tet_vol,
+                                 const float2 *__restrict__ vol_hl, const uint8_t *__restrict__ in_omega,
+                                 const int32_t *__restrict__ outer_of, const float *__restrict__ D,
+                                 const uint8_t *__restrict__ nfull, const double *__restrict__ TT, double half_gamma,
+                                 int64_t nt, double *E)
+{
+    using nla::DF;
+    int64_t el = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (el >= nt) return;
+    const float omega = in_omega[el] ? 1.f : 2.f;
+    const DF hg4 = nla::df_from(half_gamma * 0.25);
+    DF acc[10], sw{0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = DF{0.f, 0.f};
+    for (int64_t j = tp_ptr[el] + lane; j < tp_ptr[el + 1]; j += 32) {
+        const int32_t p = tp_pair[j];
+        const float2 vh = vol_hl[pair_T[p]];
+        const DF w = nla::df_mul(nla::df_mul2(hg4, DF{vh.x, vh.y}), omega);
+        const float *d = D + 10 * (int64_t)p;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) acc[k] = nla::df_add(acc[k], nla::df_mul(w, d[k]));
+        if (nfull) sw = nla::df_add(sw, nla::df_mul(w, (float)nfull[p]));
+    }
+#pragma unroll
+    for (int k = 0; k < 10; ++k)
+        for (int off = 16; off > 0; off >>= 1)
+            acc[k] = nla::df_add(acc[k], DF{__shfl_xor_sync(0xffffffffu, acc[k].hi, off),
+                                            __shfl_xor_sync(0xffffffffu, acc[k].lo, off)});
+    for (int off = 16; off > 0; off >>= 1)
+        sw = nla::df_add(sw, DF{__shfl_xor_sync(0xffffffffu, sw.hi, off), __shfl_xor_sync(0xffffffffu, sw.lo, off)});
+    if (lane < 10) {
+        DF a = acc[0];
+#pragma unroll
+        for (int k = 1; k < 10; ++k)
+            if (lane == k) a = acc[k];
+        const double cf = (lane == 0 || lane == 4 || lane == 7 || lane == 9) ? 0.1 : 0.05;
+        double v = nla::df_to(a) + nla::df_to(sw) * (tet_vol[el] * cf);
         int32_t o = outer_of[el];
         if (o >= 0) v += TT[10 * (int64_t)o + lane];
         E[10 * el + lane] = v;
@@ -188,13 +226,13 @@ void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const 
                                                  m->nv, G); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     if (d_is_float)
-        { k_elem_blocks<float><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->in_omega,
-                                                           m->outer_of, (const float *)D, nfull, TT,
-                                                           sys->opts.gamma / 2.0, m->nt, E); nl_count_launch(); }
+        { k_elem_blocks_df<<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->vol_hl,
+                                                         m->in_omega, m->outer_of, (const float *)D, nfull, TT,
+                                                         sys->opts.gamma / 2.0, m->nt, E); nl_count_launch(); }
     else
-        { k_elem_blocks<double><<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol,
-                                                            m->in_omega, m->outer_of, (const double *)D, nullptr,
-                                                            TT, sys->opts.gamma / 2.0, m->nt, E); nl_count_launch(); }
+        { k_elem_blocks<<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->in_omega,
+                                                    m->outer_of, (const double *)D, TT, sys->opts.gamma / 2.0, m->nt,
+                                                    E); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     { k_final_K<<<wblocks(m->nv), 256, 0, s>>>(P->rowptr, P->perm, G, m->ne_ptr, m->ne_ent, P->elem_pos, E, m->nv,
                                             sys->K); nl_count_launch(); }
