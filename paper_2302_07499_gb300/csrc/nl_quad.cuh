@@ -954,8 +954,19 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         P3<R> c0 = P(S[j][0]), c1 = P(S[j][1]), c2 = P(S[j][2]), c3 = P(S[j][3]);
         vol[j] = vol4(c0, c1, c2, c3);
         R *o = cb + cs * j;
-        o[0] = c0.x; o[1] = c0.y; o[2] = c0.z; o[3] = c1.x; o[4] = c1.y; o[5] = c1.z;
-        o[6] = c2.x; o[7] = c2.y; o[8] = c2.z; o[9] = c3.x; o[10] = c3.y; o[11] = c3.z;
+        if constexpr (F32) {
+            // FP32: the last vertex and the edges from it (the point is
+            // c3 + sum_k beta_k (c_k - c3); FP32 decisions near the margins
+            // are retaken in FP64)
+            o[0] = c3.x; o[1] = c3.y; o[2] = c3.z;
+            o[3] = c0.x - c3.x; o[4] = c0.y - c3.y; o[5] = c0.z - c3.z;
+            o[6] = c1.x - c3.x; o[7] = c1.y - c3.y; o[8] = c1.z - c3.z;
+            o[9] = c2.x - c3.x; o[10] = c2.y - c3.y; o[11] = c2.z - c3.z;
+        } else {
+            // FP64: the vertices, for the specification's operation order
+            o[0] = c0.x; o[1] = c0.y; o[2] = c0.z; o[3] = c1.x; o[4] = c1.y; o[5] = c1.z;
+            o[6] = c2.x; o[7] = c2.y; o[8] = c2.z; o[9] = c3.x; o[10] = c3.y; o[11] = c3.z;
+        }
         for (int kk = 0; kk < 4; ++kk) {
             lam_row<R>(S[j][kk], pd, pt, o + 12 + 4 * kk);
             spack |= (unsigned long long)S[j][kk] << (3 * (4 * j + kk));
@@ -968,11 +979,20 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
     R cum0 = vol[0];
     R cum1 = (ns > 1) ? cum0 + vol[1] : BIG;
     if (ns == 1) cum0 = BIG;
-    // margins of the FP32 decisions
-    const R c0lo = cum0 - MARGIN * tot, c0hi = cum0 + MARGIN * tot;
-    const R c1lo = cum1 - MARGIN * tot, c1hi = cum1 + MARGIN * tot;
-    const R d2lo = d2 * (R(1) - MARGIN), d2hi = d2 * (R(1) + MARGIN);
-    R cnt = R(0), a1[4] = {R(0), R(0), R(0), R(0)}, a2[10];
+    // FP32: the cell choice compares the Philox word with the cumulative
+    // volumes scaled to 2^32 (thresholds t0, t1; never exceeded when there is
+    // one cell) and is retaken in FP64 within MARGIN 2^32 of a threshold
+    // (unsigned wrap-around: (u - tk + wk) < 2 wk); the ball test is retaken
+    // within MARGIN d2 of the sphere
+    auto thresh = [&](R cum) -> uint32_t {
+        const R g = (cum / tot) * R(4294967296.0);
+        return g >= R(4294967295.0) ? 0xFFFFFFFFu : (uint32_t)g;
+    };
+    const uint32_t t0 = F32 ? thresh(cum0) : 0u, t1 = F32 ? thresh(cum1) : 0u;
+    const uint32_t wk = (uint32_t)(MARGIN * R(4294967296.0));
+    const uint32_t w2 = 2u * wk;
+    const R dmar = MARGIN * d2;
+    R cnt = R(0), a2[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) a2[k] = R(0);
     uint32_t acc = 0;
@@ -980,8 +1000,15 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
     scap.ready = 0;
     for (int k = 0; k < nmc; ++k) {
         uint4 u = philox_rk(make_uint4(idT, idTp, q, (uint32_t)k), rk);
-        R r = unit_scale<R>(u.x) * tot;
-        int j = (r >= cum0 ? 1 : 0) + (r >= cum1 ? 1 : 0);
+        int j;
+        bool cell_unsure = false;
+        if constexpr (F32) {
+            j = (u.x > t0 ? 1 : 0) + (u.x > t1 ? 1 : 0);
+            cell_unsure = (u.x - t0 + wk) < w2 || (u.x - t1 + wk) < w2;
+        } else {
+            const R r = unit_scale<R>(u.x) * tot;
+            j = (r >= cum0 ? 1 : 0) + (r >= cum1 ? 1 : 0);
+        }
         R U0 = unif<R>(u.y), U1 = unif<R>(u.z), U2 = unif<R>(u.w);
         R lo = U0 < U1 ? U0 : U1, hi = U0 < U1 ? U1 : U0;
         R s0 = lo < U2 ? lo : U2;
@@ -1001,21 +1028,27 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
 #pragma unroll
             for (int kk = 0; kk < 12; ++kk) cc[kk] = c[kk];
         }
-        P3<R> y = mk3<R>(((be0 * cc[0] + be1 * cc[3]) + be2 * cc[6]) + be3 * cc[9],
-                         ((be0 * cc[1] + be1 * cc[4]) + be2 * cc[7]) + be3 * cc[10],
-                         ((be0 * cc[2] + be1 * cc[5]) + be2 * cc[8]) + be3 * cc[11]);
+        P3<R> y;
+        if constexpr (F32)
+            y = mk3<R>(((cc[0] + be0 * cc[3]) + be1 * cc[6]) + be2 * cc[9],
+                       ((cc[1] + be0 * cc[4]) + be1 * cc[7]) + be2 * cc[10],
+                       ((cc[2] + be0 * cc[5]) + be1 * cc[8]) + be2 * cc[11]);
+        else
+            y = mk3<R>(((be0 * cc[0] + be1 * cc[3]) + be2 * cc[6]) + be3 * cc[9],
+                       ((be0 * cc[1] + be1 * cc[4]) + be2 * cc[7]) + be3 * cc[10],
+                       ((be0 * cc[2] + be1 * cc[5]) + be2 * cc[8]) + be3 * cc[11]);
         P3<R> w = F32 ? y : sub(y, x);   // the FP32 path works relative to x
         R rr = (w.x * w.x + w.y * w.y) + w.z * w.z;
         bool inb = rr <= d2;
         if (F32 && sx) {
-            const bool unsure = (r > c0lo && r < c0hi) || (r > c1lo && r < c1hi) || (rr > d2lo && rr < d2hi);
-            if (unsure) {
+            if (cell_unsure || absr(rr - d2) < dmar) {
                 int j64 = j;
                 inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64) != 0;
                 c = cb + cs * j64;
             }
         }
-        // branch-free accumulation of the accepted sample
+        // branch-free accumulation of the accepted sample (the sums of
+        // lambda' are the row sums of lambda' lambda'^T: lambda' sums to 1)
         const R f = inb ? R(1) : R(0);
         R Lr[16];
         if constexpr (F32) {
@@ -1036,8 +1069,6 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
             lam[a] = f * (((be0 * L[a] + be1 * L[4 + a]) + be2 * L[8 + a]) + be3 * L[12 + a]);
         acc += inb ? 1u : 0u;
         cnt += f;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) a1[a] += lam[a];
         {
             int kk = 0;
 #pragma unroll
@@ -1050,8 +1081,11 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
     st.acc += acc;
     const R wgt = tot / R(nmc);
     out[0] += wgt * cnt;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) out[1 + a] += wgt * a1[a];
+    // packed upper triangle: (0,0) (0,1) (0,2) (0,3) (1,1) (1,2) (1,3) (2,2) (2,3) (3,3)
+    out[1] += wgt * (((a2[0] + a2[1]) + a2[2]) + a2[3]);
+    out[2] += wgt * (((a2[1] + a2[4]) + a2[5]) + a2[6]);
+    out[3] += wgt * (((a2[2] + a2[5]) + a2[7]) + a2[8]);
+    out[4] += wgt * (((a2[3] + a2[6]) + a2[8]) + a2[9]);
 #pragma unroll
     for (int k = 0; k < 10; ++k) out[5 + k] += wgt * a2[k];
     return false;
