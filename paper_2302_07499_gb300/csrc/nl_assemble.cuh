@@ -174,7 +174,13 @@ template <class R> struct EvCfg {
     static constexpr int min_blocks = 4;
 };
 
-template <class R, int STRAT, bool B>
+// FP32 nocaps and fullcaps: events whose m = 2 diagonal needs the FP64
+// retake are handed over by the main pass (RETAKE false) through the fix list
+// and redone by the RETAKE pass, whose warps then all take the FP64 branch
+// together.
+template <class R, int STRAT> constexpr bool kRetakePass = sizeof(R) == 4 && (STRAT == 0 || STRAT == 2);
+
+template <class R, int STRAT, bool B, bool RETAKE>
 __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_events(const __grid_constant__ AsmArgs A)
 {
     extern __shared__ __align__(16) unsigned char evsm[];
@@ -182,8 +188,9 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
     nlq::Stats st{0, 0, 0, 0, 0};
     const int64_t nu = 4 * (A.p1 - A.p0);
     const int n0 = A.nev[0], n1 = A.nev[1], n2 = A.nev[2], n3 = A.nev[3];
-    const int nev = n0 + n1 + n2 + n3;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nev; e += gridDim.x * blockDim.x) {
+    const int nev = RETAKE ? A.nev[4] : n0 + n1 + n2 + n3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nev; i += gridDim.x * blockDim.x) {
+        const int e = RETAKE ? A.fix[i] : i;
         // compact event index -> (class, index within the class)
         int c = 0, idx = e;
         if (idx >= n0) { idx -= n0; c = 1;
@@ -202,12 +209,12 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
         const int inm = A.uinfo[u] & 15;
         // the record is built in shared memory and written out once
         R *out = reinterpret_cast<R *>(evsm) + 3 * nlq::CB_STRIDE * EvCfg<R>::threads + 17 * threadIdx.x;
-        const bool deferred = nlq::event_moments<R, STRAT>(v, x, sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2, inm,
-                                                           A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q, out,
-                                                           st, (sizeof(R) == 4) ? &sx : nullptr, cb,
-                                                           nlq::CB_STRIDE * EvCfg<R>::threads);
+        constexpr bool diag_inline = RETAKE || !kRetakePass<R, STRAT>;
+        const bool deferred = nlq::event_moments<R, STRAT, diag_inline>(
+            v, x, sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp,
+            (uint32_t)q, out, st, (sizeof(R) == 4) ? &sx : nullptr, cb, nlq::CB_STRIDE * EvCfg<R>::threads);
         if (deferred) {
-            A.fix[atomicAdd(&A.nev[4], 1)] = e;
+            if constexpr (!RETAKE) A.fix[atomicAdd(&A.nev[4], 1)] = e;
         } else if constexpr (sizeof(R) == 4) {
             float4 *g = reinterpret_cast<float4 *>(A.Mq) + (MQ_STRIDE / 4) * (int64_t)e;
             g[0] = make_float4(out[0], out[1], out[2], out[3]);
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
     __shared__ unsigned long long sstat[4];
     if (threadIdx.x < 4) sstat[threadIdx.x] = 0ULL;
     __syncthreads();
-    if (st.cut) atomicAdd(&sstat[0], (unsigned long long)st.cut);
+    if (!RETAKE && st.cut) atomicAdd(&sstat[0], (unsigned long long)st.cut);   // the main pass counted them
     if (st.mc) atomicAdd(&sstat[1], (unsigned long long)st.mc);
     if (st.acc) atomicAdd(&sstat[2], (unsigned long long)st.acc);
     if (st.fallback) atomicAdd(&sstat[3], (unsigned long long)st.fallback);
@@ -570,7 +577,7 @@ void alloc_work(AsmArgs &A, Scratch &sc, int64_t max_units)
     A.slot = sc.get<int32_t>(max_units);
     A.evu = sc.get<int32_t>(4 * max_units);
     A.nev = sc.get<int>(5);
-    A.fix = kDefer ? sc.get<int32_t>(max_units) : nullptr;
+    A.fix = (kDefer || kRetakePass<R, STRAT>) ? sc.get<int32_t>(max_units) : nullptr;
     A.Mq = (void *)sc.get<R>(MQ_STRIDE * max_units);
 }
 
@@ -594,8 +601,12 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
     constexpr int ET = EvCfg<R>::threads;
     constexpr size_t ESM = EvCfg<R>::smem;
     if constexpr (STRAT <= 2) {
-        NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
-        NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, k_events<R, STRAT, B>, ET, ESM));
+        NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ESM));
+        if constexpr (kRetakePass<R, STRAT>)
+            NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT, B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ESM));
+        NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, k_events<R, STRAT, B, false>, ET, ESM));
     }
     ev_per_sm = ev_per_sm < 1 ? 1 : ev_per_sm;
     if (sh.events_blocks_per_sm > 0) ev_per_sm = std::min(ev_per_sm, sh.events_blocks_per_sm);
@@ -616,11 +627,17 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
         // kernel reads the actual count from device memory
         unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, ET), (int64_t)sms * ev_per_sm));
         if constexpr (STRAT <= 2) {
-            { k_events<R, STRAT, B><<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
+            { k_events<R, STRAT, B, false><<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
             NL_CHECK_LAUNCH();
         }
         if constexpr (kDefer) {
             { k_events_fp64<STRAT, B><<<(unsigned)(2 * sms), 64, 0, s>>>(A); nl_count_launch(); }
+            NL_CHECK_LAUNCH();
+        }
+        if constexpr (kRetakePass<R, STRAT>) {
+            // the handed-over events (a few per cent; the kernel reads their
+            // count from device memory)
+            { k_events<R, STRAT, B, true><<<(unsigned)sms, ET, ESM, s>>>(A); nl_count_launch(); }
             NL_CHECK_LAUNCH();
         }
         if (ev) NL_CUDA(cudaEventRecord(ev[4 * ci + 2], s));

@@ -784,10 +784,14 @@ static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16
 //                    lambda'(y) being the spacings' combination of the cell
 //                    vertices' barycentric rows (non-negative terms only).
 //   cb, cs: per-thread scratch for the sampling cells, cell j at cb + j cs.
-//   Returns true (and writes nothing) when the FP32 path defers the event to
-//   the FP64 pass: approxcaps with a vertex of T' within 1e-3 (relative) of
-//   the sphere, where the arc midpoints are ill-conditioned in FP32.
-template <class R, int STRAT>
+//   Returns true when the FP32 path defers the event (its output is then to
+//   be discarded): approxcaps with a vertex of T' within 1e-3 (relative) of
+//   the sphere, where the arc midpoints are ill-conditioned in FP32; and, when
+//   DIAG_INLINE is false, an m = 2 diagonal that the FP32 orientation cannot
+//   decide (its FP64 retake costs a warp far more than its share on this
+//   part's narrow FP64 pipe, so such events are redone together by a second
+//   pass with DIAG_INLINE true).
+template <class R, int STRAT, bool DIAG_INLINE = true>
 __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
                               uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs)
 {
@@ -848,6 +852,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
             const R dl = sqrt(d2);
             const R tol = R(1e-5) * L * L * (L > dl ? L : dl);
             if (absr(o1) <= tol || absr(o2) <= tol) {
+                if constexpr (!DIAG_INLINE) return true;
                 diag_c2d1 = strict_diag(sx, role[0], role[1], role[2], role[3]);
                 exact = true;
             }
