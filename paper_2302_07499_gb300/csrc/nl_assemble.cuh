@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
         constexpr bool diag_inline = RETAKE || !kRetakePass<R, STRAT>;
         const bool deferred = nlq::event_moments<R, STRAT, diag_inline>(
             v, x, sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp,
-            (uint32_t)q, out, st, (sizeof(R) == 4) ? &sx : nullptr, cb, nlq::CB_STRIDE * EvCfg<R>::threads);
+            (uint32_t)q, out, st, (sizeof(R) == 4) ? &sx : nullptr, cb, nlq::CB_STRIDE * EvCfg<R>::threads,
+            nlq::HullScratch<R>{reinterpret_cast<R *>(evsm) + threadIdx.x, EvCfg<R>::threads});
         if (deferred) {
             if constexpr (!RETAKE) A.fix[atomicAdd(&A.nev[4], 1)] = e;
         } else if constexpr (sizeof(R) == 4) {
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
 template <int STRAT, bool B>
 __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmArgs A)
 {
+    extern __shared__ __align__(16) unsigned char fsm[];   // hull scratch, threads interleaved
     nlq::Stats st{0, 0, 0, 0, 0};
     const int64_t nu = 4 * (A.p1 - A.p0);
     const int n0 = A.nev[0], n1 = A.nev[1], n2 = A.nev[2], nf = A.nev[4];
@@ -273,7 +275,8 @@ __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmA
         const int inm = A.uinfo[u] & 15;
         double m15[15];
         nlq::event_moments<double, STRAT>(v, x, P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q,
-                                          m15, st, nullptr, nullptr, 0);
+                                          m15, st, nullptr, nullptr, 0,
+                                          nlq::HullScratch<double>{reinterpret_cast<double *>(fsm) + threadIdx.x, 64});
         float *out = reinterpret_cast<float *>(A.Mq) + MQ_STRIDE * (int64_t)e;
 #pragma unroll
         for (int k = 0; k < 15; ++k) out[k] = (float)m15[k];
@@ -334,6 +337,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
             }
         }
         const double cT = P.half_gamma * (P.tet_vol[T] * 0.25);
+        const DF cTf = df_from(cT);
         double vq[4] = {0.0, 0.0, 0.0, 0.0};
         DF vqf[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         __syncthreads();
@@ -469,8 +473,14 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
 #pragma unroll
                     for (int k = 0; k < 4; ++k) offs[tid * XS + 4 * i + k] = b[k] + (row[b[k]] < nodeP[k] ? 1 : 0);
                 }
-                if constexpr (F32) reinterpret_cast<DF *>(wsc)[tid] = df_from(-(omega * cT));
-                else wsc[tid] = -(omega * cT);
+                // the weight -omega c_T: FP32 path in double-float (omega = 1
+                // or 2 scales exactly; no FP64 work per pair)
+                if constexpr (F32) {
+                    const float omf = P.in_omega[Tp] ? -1.f : -2.f;
+                    reinterpret_cast<DF *>(wsc)[tid] = DF{omf * cTf.hi, omf * cTf.lo};
+                } else {
+                    wsc[tid] = -(omega * cT);
+                }
             }
             __syncthreads();
             {
@@ -631,7 +641,8 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
             NL_CHECK_LAUNCH();
         }
         if constexpr (kDefer) {
-            { k_events_fp64<STRAT, B><<<(unsigned)(2 * sms), 64, 0, s>>>(A); nl_count_launch(); }
+            { k_events_fp64<STRAT, B><<<(unsigned)(2 * sms), 64, sizeof(double) * 64 * nlq::HULL_SCRATCH, s>>>(A);
+              nl_count_launch(); }
             NL_CHECK_LAUNCH();
         }
         if constexpr (kRetakePass<R, STRAT>) {
@@ -775,10 +786,13 @@ __global__ void k_probe(const double *__restrict__ tv, const double4 *__restrict
     sx.e = make_int4((int)(4 * c), (int)(4 * c + 1), (int)(4 * c + 2), (int)(4 * c + 3));
     sx.x = xs + 3 * c;
     sx.d2 = delta2;
-    __align__(16) R cb[3 * nlq::CB_STRIDE];   // 16-byte aligned: the sampler reads it with 16-byte loads
+    // 16-byte aligned: the sampler reads it with 16-byte loads; also the
+    // approxcaps hull's scratch (that strategy does not sample)
+    __align__(16) R cb[3 * nlq::CB_STRIDE];
+    static_assert(3 * nlq::CB_STRIDE >= nlq::HULL_SCRATCH, "hull scratch");
     const int d = nlq::point_moments<R, STRAT>(v, xx, (R)delta2, (R)vol, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
                                                ids[3 * c + 2], M, st, sizeof(R) == 4 ? &sx : nullptr, cb,
-                                               nlq::CB_STRIDE);
+                                               nlq::CB_STRIDE, nlq::HullScratch<R>{cb, 1});
     defer[c] = d;
     if (d) return;
     out[15 * c] = (double)M.m0;
@@ -800,9 +814,9 @@ __global__ void k_probe_fp64(const double *__restrict__ tv, const double *__rest
     for (int k = 0; k < 4; ++k) v[k] = nlq::mk3<double>(t[3 * k], t[3 * k + 1], t[3 * k + 2]);
     P3<double> x = nlq::mk3<double>(xs[3 * c], xs[3 * c + 1], xs[3 * c + 2]);
     nlq::Stats st{0, 0, 0, 0, 0};
-    double m15[15];
+    double m15[15], hb[nlq::HULL_SCRATCH];
     nlq::event_moments<double, STRAT>(v, x, delta2, defer[c] - 1, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
-                                      ids[3 * c + 2], m15, st, nullptr, nullptr, 0);
+                                      ids[3 * c + 2], m15, st, nullptr, nullptr, 0, nlq::HullScratch<double>{hb, 1});
     for (int k = 0; k < 15; ++k) out[15 * c + k] = (double)(float)m15[k];
 }
 

@@ -574,33 +574,48 @@ template <class R> __device__ __forceinline__ int orient_sign(P3<R> a, P3<R> b, 
 
 constexpr int HULL_MAXP = 12;
 constexpr int HULL_MAXF = 24;
+constexpr int HULL_MAXH = 16;
+// The hull's point table lives in a per-thread scratch (it is indexed at run
+// time): value i of the thread at p[i s].  Points k < HULL_MAXP: coordinates
+// at 3k..3k+2, barycentric row with respect to T' at 36 + 4k..36 + 4k + 3
+// (84 values; the event kernel interleaves the threads of a block, s = block
+// size, so that any index is conflict-free).
+constexpr int HULL_SCRATCH = 3 * HULL_MAXP + 4 * HULL_MAXP;
+template <class R> struct HullScratch {
+    R *p;
+    int s;
+    __device__ __forceinline__ R &operator()(int i) const { return p[i * s]; }
+};
 
 template <class R>
 __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, const int role[4], const P3<R> pp[4],
-                                    const R pt[4], const PDesc pd[4], bool diag_c2d1, Mom<R> &M, const Strict *sx)
+                                    const R pt[4], const PDesc pd[4], bool diag_c2d1, Mom<R> &M, const Strict *sx,
+                                    const HullScratch<R> &hs)
 {
     constexpr bool F32 = sizeof(R) == 4;
-    P3<R> X[HULL_MAXP];
-    R Lr[HULL_MAXP][4];
+    auto X = [&](int k) -> P3<R> { return mk3<R>(hs(3 * k), hs(3 * k + 1), hs(3 * k + 2)); };
+    auto setX = [&](int k, P3<R> q) { hs(3 * k) = q.x; hs(3 * k + 1) = q.y; hs(3 * k + 2) = q.z; };
+    auto Lr = [&](int k, int a) -> R & { return hs(3 * HULL_MAXP + 4 * k + a); };
     int n = 0;
     // table: T' vertices 0..3, edge points 4..7, arc midpoints 8..
     for (int k = 0; k < 4; ++k) {
-        X[k] = v[k];
-        for (int a = 0; a < 4; ++a) Lr[k][a] = (a == k) ? R(1) : R(0);
+        setX(k, v[k]);
+        for (int a = 0; a < 4; ++a) Lr(k, a) = (a == k) ? R(1) : R(0);
     }
     const int np = m * (4 - m);
     for (int k = 0; k < np; ++k) {
-        X[4 + k] = pp[k];
+        setX(4 + k, pp[k]);
         for (int a = 0; a < 4; ++a)
-            Lr[4 + k][a] = (a == pd[k].i) ? (R(1) - pt[k]) : ((a == pd[k].o) ? pt[k] : R(0));
+            Lr(4 + k, a) = (a == pd[k].i) ? (R(1) - pt[k]) : ((a == pd[k].o) ? pt[k] : R(0));
     }
     n = 4 + 4;
-    // scale for tolerances
-    // initial faces of hull(I u P) (point indices), oriented outward below
-    uint8_t F[HULL_MAXF][3];
+    // faces of the hull, packed point indices i | j << 8 | k << 16 (outward
+    // orientation), initially those of hull(I u P)
+    uint32_t F[HULL_MAXF];
     int nf = 0;
     const int a = role[0];
-    auto add = [&](int i, int j, int k) { F[nf][0] = (uint8_t)i; F[nf][1] = (uint8_t)j; F[nf][2] = (uint8_t)k; nf++; };
+    auto pack = [](int i, int j, int k) -> uint32_t { return (uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)k << 16); };
+    auto add = [&](int i, int j, int k) { F[nf++] = pack(i, j, k); };
     if (m == 1) {
         add(a, 4, 5); add(a, 5, 6); add(a, 6, 4); add(4, 6, 5);
     } else if (m == 2) {
@@ -622,10 +637,11 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
         for (int k = 0; k < np; ++k) { ci.x += pp[k].x; ci.y += pp[k].y; ci.z += pp[k].z; cnt++; }
         R inv = R(1) / R(cnt);
         ci = mk3<R>(ci.x * inv, ci.y * inv, ci.z * inv);
-        for (int f = 0; f < nf; ++f)
-            if (orient_sign(X[F[f][0]], X[F[f][1]], X[F[f][2]], ci) > 0) {
-                uint8_t t = F[f][1]; F[f][1] = F[f][2]; F[f][2] = t;
-            }
+        for (int f = 0; f < nf; ++f) {
+            const uint32_t g = F[f];
+            const int i0 = g & 0xff, i1 = (g >> 8) & 0xff, i2 = g >> 16;
+            if (orient_sign(X(i0), X(i1), X(i2), ci) > 0) F[f] = pack(i0, i2, i1);
+        }
     }
     // arc midpoints
     int inrank[4], outrank[4];
@@ -659,8 +675,8 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
         P3<R> xc = sub(x, cf);
         R r2 = d2 - dot(xc, xc);
         if (!(r2 > R(0))) continue;
-        P3<R> mid = mk3<R>(R(0.5) * (X[pA].x + X[pB].x), R(0.5) * (X[pA].y + X[pB].y), R(0.5) * (X[pA].z + X[pB].z));
-        P3<R> ch = sub(X[pB], X[pA]);
+        P3<R> mid = mk3<R>(R(0.5) * (X(pA).x + X(pB).x), R(0.5) * (X(pA).y + X(pB).y), R(0.5) * (X(pA).z + X(pB).z));
+        P3<R> ch = sub(X(pB), X(pA));
         R cc = dot(ch, ch);
         P3<R> mu;
         R l0, ls, lt;
@@ -696,57 +712,67 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
         }
         if (!keep) continue;
         if (n >= HULL_MAXP) return false;
-        X[n] = mu;
-        for (int aa = 0; aa < 4; ++aa) Lr[n][aa] = R(0);
-        Lr[n][fv[0]] = l0; Lr[n][fv[1]] = ls; Lr[n][fv[2]] = lt;
-        // insert: faces that see mu
-        bool vis[HULL_MAXF];
-        int nvis = 0;
+        setX(n, mu);
+        for (int aa = 0; aa < 4; ++aa) Lr(n, aa) = R(0);
+        Lr(n, fv[0]) = l0; Lr(n, fv[1]) = ls; Lr(n, fv[2]) = lt;
+        // insert: faces that see mu (bit mask)
+        uint32_t vis = 0u;
         for (int f = 0; f < nf; ++f) {
-            const int i0 = F[f][0], i1 = F[f][1], i2 = F[f][2];
+            const uint32_t g = F[f];
+            const int i0 = g & 0xff, i1 = (g >> 8) & 0xff, i2 = g >> 16;
             // faces in the plane of T''s face o (zero o-th barycentric coordinate
             // at all three points, exact by construction) hold mu in their plane
-            if (Lr[i0][o] == R(0) && Lr[i1][o] == R(0) && Lr[i2][o] == R(0)) { vis[f] = false; continue; }
-            vis[f] = orient_sign(X[i0], X[i1], X[i2], mu) > 0;
-            nvis += vis[f] ? 1 : 0;
+            if (Lr(i0, o) == R(0) && Lr(i1, o) == R(0) && Lr(i2, o) == R(0)) continue;
+            if (orient_sign(X(i0), X(i1), X(i2), mu) > 0) vis |= 1u << f;
         }
-        if (nvis == 0) continue;              // inside (or on) the hull already
-        // horizon: edges of visible faces whose neighbour across is not visible
-        uint8_t hz[HULL_MAXF * 3][2];
+        if (vis == 0u) continue;              // inside (or on) the hull already
+        // horizon: edges of visible faces whose reverse edge belongs to no
+        // other visible face
+        uint32_t hz[HULL_MAXH];
         int nh = 0;
-        for (int f = 0; f < nf; ++f) {
-            if (!vis[f]) continue;
+        for (uint32_t vm = vis; vm; vm &= vm - 1u) {
+            const uint32_t g = F[__ffs(vm) - 1];
+            const int gi[3] = {(int)(g & 0xff), (int)((g >> 8) & 0xff), (int)(g >> 16)};
             for (int e = 0; e < 3; ++e) {
-                int i0 = F[f][e], i1 = F[f][(e + 1) % 3];
-                bool other_vis = false, found = false;
-                for (int g2 = 0; g2 < nf && !found; ++g2) {
-                    if (g2 == f) continue;
-                    for (int e2i = 0; e2i < 3; ++e2i)
-                        if (F[g2][e2i] == i1 && F[g2][(e2i + 1) % 3] == i0) { found = true; other_vis = vis[g2]; break; }
+                const int i0 = gi[e], i1 = gi[(e + 1) % 3];
+                bool shared = false;
+                for (uint32_t wm = vis; wm && !shared; wm &= wm - 1u) {
+                    const uint32_t h = F[__ffs(wm) - 1];
+                    const int hi[3] = {(int)(h & 0xff), (int)((h >> 8) & 0xff), (int)(h >> 16)};
+                    shared = (hi[0] == i1 && hi[1] == i0) || (hi[1] == i1 && hi[2] == i0) || (hi[2] == i1 && hi[0] == i0);
                 }
-                if (!found) return false;       // not a closed surface
-                if (!other_vis) { hz[nh][0] = (uint8_t)i0; hz[nh][1] = (uint8_t)i1; nh++; }
+                if (!shared) {
+                    if (nh >= HULL_MAXH) return false;
+                    hz[nh++] = (uint32_t)i0 | ((uint32_t)i1 << 8);
+                }
             }
         }
+        // (near-coplanar faces can pinch the visible region at a vertex; the
+        // cone over every horizon edge still closes the surface)
+        if (nh < 3) return false;
+        const int nvis = __popc(vis);
         if (nf - nvis + nh > HULL_MAXF) return false;
         int w2 = 0;
         for (int f = 0; f < nf; ++f)
-            if (!vis[f]) { F[w2][0] = F[f][0]; F[w2][1] = F[f][1]; F[w2][2] = F[f][2]; w2++; }
+            if (!((vis >> f) & 1u)) F[w2++] = F[f];
         nf = w2;
-        for (int h = 0; h < nh; ++h) { F[nf][0] = hz[h][0]; F[nf][1] = hz[h][1]; F[nf][2] = (uint8_t)n; nf++; }
+        for (int h = 0; h < nh; ++h) F[nf++] = hz[h] | ((uint32_t)n << 16);
         n++;
     }
     // cone from the mean of the hull's points
-    bool inh[HULL_MAXP];
-    for (int k = 0; k < HULL_MAXP; ++k) inh[k] = false;
-    for (int f = 0; f < nf; ++f) { inh[F[f][0]] = true; inh[F[f][1]] = true; inh[F[f][2]] = true; }
+    uint32_t inh = 0u;
+    for (int f = 0; f < nf; ++f) {
+        const uint32_t g = F[f];
+        inh |= (1u << (g & 0xff)) | (1u << ((g >> 8) & 0xff)) | (1u << (g >> 16));
+    }
     P3<R> c = mk3<R>(R(0), R(0), R(0));
     R Lc[4] = {R(0), R(0), R(0), R(0)};
     int cnt = 0;
     for (int k = 0; k < n; ++k)
-        if (inh[k]) {
-            c.x += X[k].x; c.y += X[k].y; c.z += X[k].z;
-            for (int aa = 0; aa < 4; ++aa) Lc[aa] += Lr[k][aa];
+        if ((inh >> k) & 1u) {
+            const P3<R> q = X(k);
+            c.x += q.x; c.y += q.y; c.z += q.z;
+            for (int aa = 0; aa < 4; ++aa) Lc[aa] += Lr(k, aa);
             cnt++;
         }
     if (cnt < 4) return false;
@@ -754,9 +780,12 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
     c = mk3<R>(c.x * inv, c.y * inv, c.z * inv);
     for (int aa = 0; aa < 4; ++aa) Lc[aa] *= inv;
     for (int f = 0; f < nf; ++f) {
-        const int i0 = F[f][0], i1 = F[f][1], i2 = F[f][2];
-        R vol = vol4(c, X[i0], X[i1], X[i2]);
-        add_cell(M, vol, Lc, Lr[i0], Lr[i1], Lr[i2]);
+        const uint32_t g = F[f];
+        const int i0 = g & 0xff, i1 = (g >> 8) & 0xff, i2 = g >> 16;
+        R vol = vol4(c, X(i0), X(i1), X(i2));
+        R L0[4], L1[4], L2[4];
+        for (int aa = 0; aa < 4; ++aa) { L0[aa] = Lr(i0, aa); L1[aa] = Lr(i1, aa); L2[aa] = Lr(i2, aa); }
+        add_cell(M, vol, Lc, L0, L1, L2);
     }
     return true;
 }
@@ -784,6 +813,7 @@ static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16
 //                    lambda'(y) being the spacings' combination of the cell
 //                    vertices' barycentric rows (non-negative terms only).
 //   cb, cs: per-thread scratch for the sampling cells, cell j at cb + j cs.
+//   hs: per-thread scratch of the approxcaps hull (HULL_SCRATCH values).
 //   Returns true when the FP32 path defers the event (its output is then to
 //   be discarded): approxcaps with a vertex of T' within 1e-3 (relative) of
 //   the sphere, where the arc midpoints are ill-conditioned in FP32; and, when
@@ -793,7 +823,8 @@ static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16
 //   pass with DIAG_INLINE true).
 template <class R, int STRAT, bool DIAG_INLINE = true>
 __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
-                              uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs)
+                              uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs,
+                              const HullScratch<R> &hs)
 {
     Mom<R> M;
     constexpr bool F32 = sizeof(R) == 4;
@@ -875,7 +906,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
             }
         }
         if (near) return true;
-        done_hull = approx_hull_moments<R>(v, x, d2, m, role, pp, pt, pd, diag_c2d1, H, sx);
+        done_hull = approx_hull_moments<R>(v, x, d2, m, role, pp, pt, pd, diag_c2d1, H, sx, hs);
         if (done_hull) M = H;
         else st.fallback++;
     }
@@ -1101,7 +1132,8 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
 template <class R, int STRAT>
 // Returns the classification + 1 when the event is deferred to FP64, else 0.
 __device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, const uint32_t *rk, uint32_t idT,
-                             uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st, const Strict *sx, R *cb, int cs)
+                             uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st, const Strict *sx, R *cb, int cs,
+                             const HullScratch<R> &hs)
 {
     int inm = classify(v, x, d2, sx);
     if constexpr (STRAT >= 3) {
@@ -1123,7 +1155,7 @@ __device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, 
         return 0;
     }
     R o[15];
-    if (event_moments<R, STRAT>(v, x, d2, inm, nmc, rk, idT, idTp, q, o, st, sx, cb, cs)) return inm + 1;
+    if (event_moments<R, STRAT>(v, x, d2, inm, nmc, rk, idT, idTp, q, o, st, sx, cb, cs, hs)) return inm + 1;
     M.m0 = o[0];
     for (int k = 0; k < 4; ++k) M.m1[k] = o[1 + k];
     for (int k = 0; k < 10; ++k) M.m2[k] = o[5 + k];
