@@ -647,8 +647,9 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
         }
         if constexpr (kRetakePass<R, STRAT>) {
             // the handed-over events (a few per cent; the kernel reads their
-            // count from device memory)
-            { k_events<R, STRAT, B, true><<<(unsigned)sms, ET, ESM, s>>>(A); nl_count_launch(); }
+            // count from device memory); full occupancy, as their FP64 work is
+            // latency-bound
+            { k_events<R, STRAT, B, true><<<(unsigned)(sms * ev_per_sm), ET, ESM, s>>>(A); nl_count_launch(); }
             NL_CHECK_LAUNCH();
         }
         if (ev) NL_CUDA(cudaEventRecord(ev[4 * ci + 2], s));

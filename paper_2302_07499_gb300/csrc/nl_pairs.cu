@@ -51,29 +51,47 @@ __global__ void k_mesh_prep(const double4 *__restrict__ verts, const int4 *__res
                             double4 *tet_cr, double *tet_vol, int *err, unsigned long long *bb)
 {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
-    int4 e = tets[t];
-    if (e.x < 0 || e.y < 0 || e.z < 0 || e.w < 0 || e.x >= nv || e.y >= nv || e.z >= nv || e.w >= nv) {
-        atomicOr(err, 1);
-        tet_cr[t] = make_double4(0, 0, 0, 0);
-        tet_vol[t] = 0.0;
-        return;
+    // bounding values as order-preserving integers; neutral for lanes past the
+    // end or with a bad element
+    unsigned long long enc[7] = {0ULL, ~0ULL, ~0ULL, ~0ULL, 0ULL, 0ULL, 0ULL};
+    if (t < nt) {
+        int4 e = tets[t];
+        if (e.x < 0 || e.y < 0 || e.z < 0 || e.w < 0 || e.x >= nv || e.y >= nv || e.z >= nv || e.w >= nv) {
+            atomicOr(err, 1);
+            tet_cr[t] = make_double4(0, 0, 0, 0);
+            tet_vol[t] = 0.0;
+        } else {
+            double3 v0 = ld3(verts[e.x]), v1 = ld3(verts[e.y]), v2 = ld3(verts[e.z]), v3 = ld3(verts[e.w]);
+            double d = det3(sub3(v1, v0), sub3(v2, v0), sub3(v3, v0));
+            if (!(d > 0.0)) atomicOr(err, 2);
+            tet_vol[t] = fabs(d) / 6.0;
+            double3 c = make_double3(0.25 * ((v0.x + v1.x) + (v2.x + v3.x)), 0.25 * ((v0.y + v1.y) + (v2.y + v3.y)),
+                                     0.25 * ((v0.z + v1.z) + (v2.z + v3.z)));
+            // the largest distance to a vertex: one square root of the
+            // largest square (sqrt is monotone and correctly rounded)
+            double r2 = dot3(sub3(v0, c), sub3(v0, c));
+            r2 = fmax(r2, dot3(sub3(v1, c), sub3(v1, c)));
+            r2 = fmax(r2, dot3(sub3(v2, c), sub3(v2, c)));
+            r2 = fmax(r2, dot3(sub3(v3, c), sub3(v3, c)));
+            const double r = sqrt(r2);
+            tet_cr[t] = make_double4(c.x, c.y, c.z, r);
+            enc[0] = ord_enc(r);
+            enc[1] = ord_enc(c.x); enc[2] = ord_enc(c.y); enc[3] = ord_enc(c.z);
+            enc[4] = enc[1]; enc[5] = enc[2]; enc[6] = enc[3];
+        }
     }
-    double3 v0 = ld3(verts[e.x]), v1 = ld3(verts[e.y]), v2 = ld3(verts[e.z]), v3 = ld3(verts[e.w]);
-    double d = det3(sub3(v1, v0), sub3(v2, v0), sub3(v3, v0));
-    if (!(d > 0.0)) atomicOr(err, 2);
-    tet_vol[t] = fabs(d) / 6.0;
-    double3 c = make_double3(0.25 * ((v0.x + v1.x) + (v2.x + v3.x)), 0.25 * ((v0.y + v1.y) + (v2.y + v3.y)),
-                             0.25 * ((v0.z + v1.z) + (v2.z + v3.z)));
-    double r = 0.0;
-    r = fmax(r, sqrt(dot3(sub3(v0, c), sub3(v0, c))));
-    r = fmax(r, sqrt(dot3(sub3(v1, c), sub3(v1, c))));
-    r = fmax(r, sqrt(dot3(sub3(v2, c), sub3(v2, c))));
-    r = fmax(r, sqrt(dot3(sub3(v3, c), sub3(v3, c))));
-    tet_cr[t] = make_double4(c.x, c.y, c.z, r);
-    atomicMax(&bb[0], ord_enc(r));
-    atomicMin(&bb[1], ord_enc(c.x)); atomicMin(&bb[2], ord_enc(c.y)); atomicMin(&bb[3], ord_enc(c.z));
-    atomicMax(&bb[4], ord_enc(c.x)); atomicMax(&bb[5], ord_enc(c.y)); atomicMax(&bb[6], ord_enc(c.z));
+    // warp reduction first: one atomic per warp and value
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, enc[k], o);
+            enc[k] = (k >= 1 && k <= 3) ? (w < enc[k] ? w : enc[k]) : (w > enc[k] ? w : enc[k]);
+        }
+    if ((threadIdx.x & 31) == 0) {
+        if (enc[0]) atomicMax(&bb[0], enc[0]);
+        if (enc[1] != ~0ULL) { atomicMin(&bb[1], enc[1]); atomicMin(&bb[2], enc[2]); atomicMin(&bb[3], enc[3]); }
+        if (enc[4]) { atomicMax(&bb[4], enc[4]); atomicMax(&bb[5], enc[5]); atomicMax(&bb[6], enc[6]); }
+    }
 }
 
 __global__ void k_widen(const double *__restrict__ v3, double4 *v4, int64_t nv)

@@ -90,8 +90,11 @@ __global__ void k_spmv_dot(const int64_t *__restrict__ rp, const int32_t *__rest
     }
 }
 
-template <class XT>
-__global__ void k_update_xr(XT *x, XT *r, const XT *p, const XT *q, int64_t n, double *part, CgState *st)
+// With FUSE_P (small systems) the last block also updates p = r + beta p for
+// every row (reading r and p through L2: other blocks wrote r), which saves
+// the separate p launch of the iteration.
+template <class XT, bool FUSE_P>
+__global__ void k_update_xr(XT *x, XT *r, XT *p, const XT *q, int64_t n, double *part, CgState *st)
 {
     __shared__ double sh[RB / 32];
     if (st->done) return;
@@ -106,14 +109,45 @@ __global__ void k_update_xr(XT *x, XT *r, const XT *p, const XT *q, int64_t n, d
     double t = block_sum(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
     // the last block forms beta = r'.r' / r.r and tests convergence
-    if (last_block(st)) {
-        const double rr = warp_sum_parts(part, gridDim.x);
-        if (threadIdx.x == 0) {
-            st->beta = (st->rr != 0.0) ? rr / st->rr : 0.0;
-            st->rr = rr;
-            st->it += 1;
-            if (rr <= st->tol2 || !(rr == rr)) st->done = 1;
-            st->ticket = 0;
+    if constexpr (!FUSE_P) {
+        if (last_block(st)) {
+            const double rr = warp_sum_parts(part, gridDim.x);
+            if (threadIdx.x == 0) {
+                st->beta = (st->rr != 0.0) ? rr / st->rr : 0.0;
+                st->rr = rr;
+                st->it += 1;
+                if (rr <= st->tol2 || !(rr == rr)) st->done = 1;
+                st->ticket = 0;
+            }
+        }
+    } else {
+        __shared__ bool last;
+        __shared__ double beta_s;
+        __shared__ int done_s;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+        __syncthreads();
+        if (last) {                        // block-uniform
+            if (threadIdx.x < 32) {
+                const double rr = warp_sum_parts(part, gridDim.x);
+                if (threadIdx.x == 0) {
+                    const double beta = (st->rr != 0.0) ? rr / st->rr : 0.0;
+                    const int done = (rr <= st->tol2 || !(rr == rr)) ? 1 : 0;
+                    st->beta = beta;
+                    st->rr = rr;
+                    st->it += 1;
+                    if (done) st->done = 1;
+                    st->ticket = 0;
+                    beta_s = beta;
+                    done_s = done;
+                }
+            }
+            __syncthreads();
+            if (!done_s) {
+                const XT b = (XT)beta_s;
+                for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = __ldcg(r + i) + b * __ldcg(p + i);
+            }
         }
     }
 }
@@ -202,6 +236,9 @@ int cg_blocks(int64_t n)
                                                        nl_cdiv<int64_t>(n * 32, RB)));
 }
 
+// systems up to this many rows update p in the last block of the x/r update
+constexpr int64_t kFuseRows = 65536;
+
 struct Cg {
     int nb = 0;
     double *part = nullptr;
@@ -225,8 +262,12 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b,
         int k = std::min(check_every, max_it - launched);
         for (int j = 0; j < k; ++j) {
             { k_spmv_dot<VT, XT><<<nb, RB, 0, s>>>(rp, ci, val, p, q, n, cg.part, cg.st); nl_count_launch(); }
-            { k_update_xr<XT><<<nb, RB, 0, s>>>(x, r, p, q, n, cg.part, cg.st); nl_count_launch(); }
-            { k_update_p<XT><<<nb, RB, 0, s>>>(p, r, n, cg.st); nl_count_launch(); }
+            if (n <= kFuseRows) {
+                { k_update_xr<XT, true><<<nb, RB, 0, s>>>(x, r, p, q, n, cg.part, cg.st); nl_count_launch(); }
+            } else {
+                { k_update_xr<XT, false><<<nb, RB, 0, s>>>(x, r, p, q, n, cg.part, cg.st); nl_count_launch(); }
+                { k_update_p<XT><<<nb, RB, 0, s>>>(p, r, n, cg.st); nl_count_launch(); }
+            }
         }
         NL_CHECK_LAUNCH();
         launched += k;
