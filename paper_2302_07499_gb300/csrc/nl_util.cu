@@ -187,11 +187,84 @@ __global__ void k_seg_bitonic(int32_t *keys, const int64_t *ptr, int pow2)
     (void)pow2;
 }
 
+// Segments of up to 1024 keys: one warp per segment, K keys per lane in
+// registers (key i = 32 r + lane in register r), the same bitonic network:
+// partners 32 or more apart are in the same lane (register exchange), closer
+// ones in another lane (shuffle).  No block barrier.
+template <int K>
+__device__ __forceinline__ void warp_bitonic(int32_t *keys, int64_t b, int n, int lane)
+{
+    int32_t v[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int i = 32 * r + lane;
+        v[r] = i < n ? keys[b + i] : 0x7fffffff;
+    }
+    constexpr int P = 32 * K;
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int rj = j >> 5;
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    if ((r & rj) == 0) {
+                        const bool up = ((32 * r + lane) & k) == 0;
+                        const int32_t a = v[r], c = v[r | rj];
+                        const int32_t lo = a < c ? a : c, hi = a < c ? c : a;
+                        v[r] = up ? lo : hi;
+                        v[r | rj] = up ? hi : lo;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    const int i = 32 * r + lane;
+                    const int32_t w = __shfl_xor_sync(0xffffffffu, v[r], j);
+                    const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+                    v[r] = keep_min ? (v[r] < w ? v[r] : w) : (v[r] < w ? w : v[r]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const int i = 32 * r + lane;
+        if (i < n) keys[b + i] = v[r];
+    }
+}
+
+__global__ void k_seg_warp(int32_t *keys, const int64_t *ptr, int64_t nseg)
+{
+    const int64_t sg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sg >= nseg) return;                 // warp-uniform
+    const int64_t b = ptr[sg];
+    const int n = (int)(ptr[sg + 1] - b);
+    if (n <= 1) return;
+    if (n <= 32) warp_bitonic<1>(keys, b, n, lane);
+    else if (n <= 64) warp_bitonic<2>(keys, b, n, lane);
+    else if (n <= 128) warp_bitonic<4>(keys, b, n, lane);
+    else if (n <= 256) warp_bitonic<8>(keys, b, n, lane);
+    else if (n <= 512) warp_bitonic<16>(keys, b, n, lane);
+    else warp_bitonic<32>(keys, b, n, lane);
+}
+
 void nl_segmented_sort_i32(int32_t *keys, const int64_t *ptr, int64_t nseg, int64_t max_seg,
                            DevArena *arena, cudaStream_t s)
 {
     (void)arena;
     if (nseg <= 0 || max_seg <= 1) return;
+    if (max_seg <= 1024) {
+        const int64_t blocks = (nseg + 7) / 8;     // 8 warps (segments) per block
+        for (int64_t b0 = 0; b0 < blocks; b0 += 2147483647LL) {
+            const int64_t nb = std::min<int64_t>(blocks - b0, 2147483647LL);
+            { k_seg_warp<<<(unsigned)nb, 256, 0, s>>>(keys, ptr + 8 * b0, nseg - 8 * b0); nl_count_launch(); }
+            NL_CHECK_LAUNCH();
+        }
+        return;
+    }
     NL_REQUIRE(max_seg <= 32768, "a segment of %lld entries exceeds the 32768 supported by the sort",
                (long long)max_seg);
     int p2 = 1;
