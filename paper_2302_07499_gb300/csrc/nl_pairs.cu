@@ -345,6 +345,7 @@ struct PairArgs {
     int ks;                 // stencil radius in cells
     double delta, d2;
     float d2_lo, d2_hi;     // FP32 sure-accept / sure-reject bounds on d^2
+    float qa_lo;            // sure-accept bound for distances from the hi parts alone (< 0: unused)
     float deltaf;
     int64_t n_outer;
 };
@@ -403,21 +404,23 @@ __device__ bool pair_predicate(const PairArgs &A, const double3 xq[4], const flo
 
 // Cheap part of the predicate: a vertex of T' surely within delta of an outer
 // point (FP32 distance below the sure-accept bound).  Branch-free.
-__device__ bool quick_accept(const PairArgs &A, const float3 xh[4], const float3 xl[4], int4 e)
+// The hi parts of the coordinates alone: their error (the lo parts, at most
+// 2^-24 of the coordinates' magnitude, plus the rounding of the difference) is
+// folded into qa_lo, set on the host from the mesh's extent.
+__device__ bool quick_accept(const PairArgs &A, const float3 xh[4], int4 e)
 {
     const int ids[4] = {e.x, e.y, e.z, e.w};
     float vmin = 3.0e38f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float4 h = A.vhi[ids[k]], l = A.vlo[ids[k]];
+        const float4 h = A.vhi[ids[k]];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float3 w = make_float3((h.x - xh[q].x) + (l.x - xl[q].x), (h.y - xh[q].y) + (l.y - xl[q].y),
-                                         (h.z - xh[q].z) + (l.z - xl[q].z));
+            const float3 w = make_float3(h.x - xh[q].x, h.y - xh[q].y, h.z - xh[q].z);
             vmin = fminf(vmin, dot3f(w, w));
         }
     }
-    return vmin < A.d2_lo;
+    return vmin < A.qa_lo;
 }
 
 // One warp per outer element: scan the stencil of grid cells and test each
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(128, 4) k_pairs(PairArgs A, const int64_t *bpt
         int32_t Tp = -1;
         if (lane < cnt) {
             Tp = Q[nq - cnt + lane];
-            keep = quick_accept(A, xh, xl, A.tets[Tp]);
+            keep = quick_accept(A, xh, A.tets[Tp]);
             undecided = !keep;
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -1105,6 +1108,18 @@ nl_status nl_pairs_build_impl(nl_mesh *m, double delta, nl_pairs **out)
         A.outer_ids = m->outer_ids; A.xq = m->xq; A.cell_of = cell_of; A.cell_ptr = cell_ptr; A.cell_ent = cell_ent;
         A.g = g; A.ks = ks; A.delta = delta; A.d2 = delta * delta;
         A.d2_lo = (float)(A.d2 * (1.0 - 1e-4)); A.d2_hi = (float)(A.d2 * (1.0 + 1e-4));
+        {
+            // |coordinates| <= M: each component of a hi-part difference errs
+            // by at most 3 M 2^-24, the vector by e = 3 sqrt(3) M 2^-24; a
+            // squared FP32 distance below (delta - 2e)^2 (less a relative
+            // 1e-6 for its own rounding) is then surely within delta
+            double M = 0.0;
+            for (int d = 0; d < 3; ++d)
+                M = std::max(M, std::max(fabs(m->bbmin[d] - m->rmax), fabs(m->bbmax[d] + m->rmax)));
+            const double e = 3.0 * sqrt(3.0) * M * 0x1p-24;
+            const double r = delta - 2.0 * e;
+            A.qa_lo = r > 0.0 ? (float)std::min(A.d2 * (1.0 - 1e-4), r * r * (1.0 - 1e-6)) : -1.0f;
+        }
         A.deltaf = (float)delta;
         A.n_outer = no;
         unsigned pblocks = blocks_for(no * 32, 128);

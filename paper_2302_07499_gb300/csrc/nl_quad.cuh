@@ -15,6 +15,7 @@
 //             of the method's arithmetic specification.
 // R = float:  coordinates are relative to the outer point (x = 0).
 #pragma once
+#include <type_traits>
 
 #include <stdint.h>
 
@@ -822,7 +823,7 @@ static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16
 //   part's narrow FP64 pipe, so such events are redone together by a second
 //   pass with DIAG_INLINE true).
 template <class R, int STRAT, bool DIAG_INLINE = true>
-__device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
+__device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
                               uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs,
                               const HullScratch<R> &hs)
 {
@@ -953,62 +954,198 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
     for (int k = 0; k < 4; ++k) out[1 + k] = M.m1[k];
 #pragma unroll
     for (int k = 0; k < 10; ++k) out[5 + k] = M.m2[k];
-    if (STRAT != 2 || nmc <= 0) return false;
+    (void)nmc; (void)rk; (void)idT; (void)idTp; (void)q; (void)cb; (void)cs;
+    return false;
+}
 
-    // cap cells S = T' \ hull(I u P) in the specification's order
-    int S[3][4];
-    int ns;
-    if (m == 0) {
-        S[0][0] = 0; S[0][1] = 1; S[0][2] = 2; S[0][3] = 3;
-        ns = 1;
-    } else if (m == 1) {
-        const int b = role[1], c = role[2], d = role[3];
-        S[0][0] = b; S[0][1] = NLQ_P(0); S[0][2] = NLQ_P(1); S[0][3] = NLQ_P(2);
-        S[1][0] = b; S[1][1] = c; S[1][2] = d; S[1][3] = NLQ_P(2);
-        S[2][0] = b; S[2][1] = c; S[2][2] = NLQ_P(2); S[2][3] = NLQ_P(1);
-        ns = 3;
-    } else if (m == 2) {
-        const int c = role[2], d = role[3];
-        S[0][0] = c; S[0][1] = d; S[0][2] = NLQ_P(1); S[0][3] = NLQ_P(3);
-        if (!diag_c2d1) {
-            S[1][0] = c; S[1][1] = NLQ_P(0); S[1][2] = NLQ_P(2); S[1][3] = NLQ_P(3);
-            S[2][0] = c; S[2][1] = NLQ_P(0); S[2][2] = NLQ_P(3); S[2][3] = NLQ_P(1);
-        } else {
-            S[1][0] = c; S[1][1] = NLQ_P(0); S[1][2] = NLQ_P(2); S[1][3] = NLQ_P(1);
-            S[2][0] = c; S[2][1] = NLQ_P(2); S[2][2] = NLQ_P(3); S[2][3] = NLQ_P(1);
-        }
-        ns = 3;
+// The same for nocaps and fullcaps, with the number of inside vertices as a
+// compile-time constant (the warps of the event kernel hold one class), so
+// that the edge points, the cells and the roles are indexed statically and
+// stay in registers; barycentric rows stay in T''s own vertex order (the
+// roles only select).  The arithmetic, and so the result, is that of
+// event_moments_generic; approxcaps goes there.
+template <class R, int STRAT, bool DIAG_INLINE = true>
+__device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
+                              uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs,
+                              const HullScratch<R> &hs)
+{
+    if constexpr (STRAT == 1) {
+        return event_moments_generic<R, STRAT, DIAG_INLINE>(v, x, d2, inm, nmc, rk, idT, idTp, q, out, st, sx, cb,
+                                                             cs, hs);
     } else {
-        const int d = role[3];
-        S[0][0] = d; S[0][1] = NLQ_P(0); S[0][2] = NLQ_P(1); S[0][3] = NLQ_P(2);
-        ns = 1;
-    }
+    Mom<R> M;
+    constexpr bool F32 = sizeof(R) == 4;
+    // FP32 decision margins (relative): the FP32 sample point differs from the
+    // FP64 one by a few 1e-7 of the cell size, far inside these margins
+    const R MARGIN = R(4e-6);
+    mom_zero(M);
+    const int m = __popc(inm);
+    if (m > 0) st.cut++;
+    // the sampler's cap cells (fullcaps): count, volumes, packed point
+    // indices (T' vertex 0..3 or edge point 4 + k) and edge points
+    int ns = 0, np = 0;
     unsigned long long spack = 0ULL;
     uint32_t pdpack = 0u;
     R vol[3] = {R(0), R(0), R(0)};
-    for (int j = 0; j < ns; ++j) {
-        P3<R> c0 = P(S[j][0]), c1 = P(S[j][1]), c2 = P(S[j][2]), c3 = P(S[j][3]);
-        vol[j] = vol4(c0, c1, c2, c3);
-        R *o = cb + cs * j;
-        if constexpr (F32) {
-            // FP32: the last vertex and the edges from it (the point is
-            // c3 + sum_k beta_k (c_k - c3); FP32 decisions near the margins
-            // are retaken in FP64)
-            o[0] = c3.x; o[1] = c3.y; o[2] = c3.z;
-            o[3] = c0.x - c3.x; o[4] = c0.y - c3.y; o[5] = c0.z - c3.z;
-            o[6] = c1.x - c3.x; o[7] = c1.y - c3.y; o[8] = c1.z - c3.z;
-            o[9] = c2.x - c3.x; o[10] = c2.y - c3.y; o[11] = c2.z - c3.z;
-        } else {
-            // FP64: the vertices, for the specification's operation order
-            o[0] = c0.x; o[1] = c0.y; o[2] = c0.z; o[3] = c1.x; o[4] = c1.y; o[5] = c1.z;
-            o[6] = c2.x; o[7] = c2.y; o[8] = c2.z; o[9] = c3.x; o[10] = c3.y; o[11] = c3.z;
+    bool defer = false;
+    auto geom = [&](auto mconst) {
+        constexpr int Mi = decltype(mconst)::value;
+        constexpr int NO = 4 - Mi;
+        constexpr int NP = Mi * NO;
+        // roles: the inside vertices in increasing local index, then the
+        // outside ones
+        int role[4];
+        {
+            unsigned ins = (unsigned)inm & 15u, outs = (~(unsigned)inm) & 15u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k < Mi) { role[k] = __ffs(ins) - 1; ins &= ins - 1u; }
+                else { role[k] = __ffs(outs) - 1; outs &= outs - 1u; }
+            }
         }
-        for (int kk = 0; kk < 4; ++kk) {
-            lam_row<R>(S[j][kk], pd, pt, o + 12 + 4 * kk);
-            spack |= (unsigned long long)S[j][kk] << (3 * (4 * j + kk));
+        P3<R> vr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            vr[k] = role[k] == 0 ? v[0] : (role[k] == 1 ? v[1] : (role[k] == 2 ? v[2] : v[3]));
+        // edge/sphere points, edge (inside role a, outside role b) at a NO + b - Mi
+        P3<R> pp[NP > 0 ? NP : 1];
+        R pt[NP > 0 ? NP : 1];
+#pragma unroll
+        for (int a = 0; a < Mi; ++a)
+#pragma unroll
+            for (int b = Mi; b < 4; ++b) {
+                const int n = a * NO + (b - Mi);
+                const P3<R> w = sub(vr[a], x);
+                const P3<R> e = sub(vr[b], vr[a]);
+                const R A = (e.x * e.x + e.y * e.y) + e.z * e.z;
+                const R B = (e.x * w.x + e.y * w.y) + e.z * w.z;
+                const R C = ((w.x * w.x + w.y * w.y) + w.z * w.z) - d2;
+                const R sq = sqrt(B * B - A * C);
+                const R t = (B >= R(0)) ? (-C) / (B + sq) : (sq - B) / A;
+                pp[n] = mk3<R>(vr[a].x + t * e.x, vr[a].y + t * e.y, vr[a].z + t * e.z);
+                pt[n] = t;
+            }
+        // table point p: p < 4 the vertex of role p, else edge point p - 4
+        auto Pt = [&](int p) -> P3<R> { return p < 4 ? vr[p] : pp[p >= 4 ? p - 4 : 0]; };
+        auto Lrow = [&](int p, R *L) {
+            if (p < 4) {
+                const int r = role[p];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) L[a] = (a == r) ? R(1) : R(0);
+            } else {
+                const int n = p - 4;
+                const int i = role[n / NO], o = role[Mi + n % NO];
+                const R t = pt[n >= 0 && n < NP ? n : 0];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) L[a] = (a == i) ? (R(1) - t) : ((a == o) ? t : R(0));
+            }
+        };
+        auto orig = [&](int p) -> unsigned long long { return (unsigned long long)(p < 4 ? role[p] : p); };
+        bool diag_c2d1 = false;
+        if constexpr (Mi == 2) {
+            const P3<R> c1 = pp[0], d1 = pp[1], c2 = pp[2], dd2 = pp[3];
+            const R o1 = orient(c1, c2, dd2, d1), o2 = orient(c1, c2, dd2, vr[0]);
+            bool exact = false;
+            if (F32 && sx) {
+                // The FP32 points and determinants err by less than about
+                // (3 delta/L + 6) 2^-24 L^3 (coordinates of size delta relative to
+                // x, quad of size L); decisions within 1e-5 L^2 max(L, delta) of
+                // zero, nine times that bound or more, are retaken in FP64.
+                const P3<R> e1 = sub(vr[2], vr[0]), e2 = sub(vr[3], vr[1]);
+                const R L1 = (absr(e1.x) + absr(e1.y)) + absr(e1.z), L2 = (absr(e2.x) + absr(e2.y)) + absr(e2.z);
+                const R L = L1 > L2 ? L1 : L2;
+                const R dl = sqrt(d2);
+                const R tol = R(1e-5) * L * L * (L > dl ? L : dl);
+                if (absr(o1) <= tol || absr(o2) <= tol) {
+                    if constexpr (!DIAG_INLINE) {
+                        defer = true;
+                        return;
+                    } else {
+                        diag_c2d1 = strict_diag(sx, role[0], role[1], role[2], role[3]);
+                        exact = true;
+                    }
+                }
+            }
+            if (!exact) diag_c2d1 = (o1 > R(0) && o2 < R(0)) || (o1 < R(0) && o2 > R(0));
         }
+        // deterministic cells: hull(I u P), coned from the first inside vertex
+        auto cell = [&](int p0, int p1, int p2, int p3) {
+            R L0[4], L1[4], L2[4], L3[4];
+            Lrow(p0, L0); Lrow(p1, L1); Lrow(p2, L2); Lrow(p3, L3);
+            const R vc = vol4(Pt(p0), Pt(p1), Pt(p2), Pt(p3));
+            add_cell(M, vc, L0, L1, L2, L3);
+        };
+        if constexpr (Mi == 1) {
+            cell(0, 4, 5, 6);
+        } else if constexpr (Mi == 2) {
+            cell(0, 1, 6, 7);
+            if (!diag_c2d1) { cell(0, 4, 6, 7); cell(0, 4, 7, 5); }
+            else { cell(0, 4, 6, 5); cell(0, 6, 7, 5); }
+        } else if constexpr (Mi == 3) {
+            cell(0, 4, 5, 6); cell(0, 1, 2, 6); cell(0, 1, 6, 5);
+        }
+        if constexpr (STRAT == 2) {
+            if (nmc > 0) {
+                // cap cells S = T' \ hull(I u P) in the specification's order
+                auto capcell = [&](int j, int p0, int p1, int p2, int p3) {
+                    const P3<R> c0 = Pt(p0), c1 = Pt(p1), c2 = Pt(p2), c3 = Pt(p3);
+                    vol[j] = vol4(c0, c1, c2, c3);
+                    R *o = cb + cs * j;
+                    if constexpr (F32) {
+                        // FP32: the last vertex and the edges from it (the point
+                        // is c3 + sum_k beta_k (c_k - c3); FP32 decisions near the
+                        // margins are retaken in FP64)
+                        o[0] = c3.x; o[1] = c3.y; o[2] = c3.z;
+                        o[3] = c0.x - c3.x; o[4] = c0.y - c3.y; o[5] = c0.z - c3.z;
+                        o[6] = c1.x - c3.x; o[7] = c1.y - c3.y; o[8] = c1.z - c3.z;
+                        o[9] = c2.x - c3.x; o[10] = c2.y - c3.y; o[11] = c2.z - c3.z;
+                    } else {
+                        // FP64: the vertices, for the specification's operation order
+                        o[0] = c0.x; o[1] = c0.y; o[2] = c0.z; o[3] = c1.x; o[4] = c1.y; o[5] = c1.z;
+                        o[6] = c2.x; o[7] = c2.y; o[8] = c2.z; o[9] = c3.x; o[10] = c3.y; o[11] = c3.z;
+                    }
+                    Lrow(p0, o + 12); Lrow(p1, o + 16); Lrow(p2, o + 20); Lrow(p3, o + 24);
+                    spack |= (orig(p0) << (3 * (4 * j))) | (orig(p1) << (3 * (4 * j + 1))) |
+                             (orig(p2) << (3 * (4 * j + 2))) | (orig(p3) << (3 * (4 * j + 3)));
+                };
+                if constexpr (Mi == 0) {
+                    capcell(0, 0, 1, 2, 3);
+                    ns = 1;
+                } else if constexpr (Mi == 1) {
+                    capcell(0, 1, 4, 5, 6); capcell(1, 1, 2, 3, 6); capcell(2, 1, 2, 6, 5);
+                    ns = 3;
+                } else if constexpr (Mi == 2) {
+                    capcell(0, 2, 3, 5, 7);
+                    if (!diag_c2d1) { capcell(1, 2, 4, 6, 7); capcell(2, 2, 4, 7, 5); }
+                    else { capcell(1, 2, 4, 6, 5); capcell(2, 2, 6, 7, 5); }
+                    ns = 3;
+                } else {
+                    capcell(0, 3, 4, 5, 6);
+                    ns = 1;
+                }
+#pragma unroll
+                for (int n = 0; n < NP; ++n)
+                    pdpack |= (uint32_t)(role[n / NO] | (role[Mi + n % NO] << 2)) << (4 * n);
+                np = NP;
+            }
+        }
+    };
+    switch (m) {
+    case 0: geom(std::integral_constant<int, 0>{}); break;
+    case 1: geom(std::integral_constant<int, 1>{}); break;
+    case 2: geom(std::integral_constant<int, 2>{}); break;
+    default: geom(std::integral_constant<int, 3>{}); break;
     }
-    for (int n = 0; n < np; ++n) pdpack |= (uint32_t)(pd[n].i | (pd[n].o << 2)) << (4 * n);
+    if (defer) return true;
+
+    // the deterministic part goes out first (its registers are free during sampling)
+    out[0] = M.m0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[1 + k] = M.m1[k];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) out[5 + k] = M.m2[k];
+    if (STRAT != 2 || nmc <= 0) return false;
+
     R tot = R(0);
     for (int j = 0; j < ns; ++j) tot += vol[j];
     const R BIG = R(3.0e38);
@@ -1125,6 +1262,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
 #pragma unroll
     for (int k = 0; k < 10; ++k) out[5 + k] += wgt * a2[k];
     return false;
+    }
 }
 
 // Moments for one (T', x) including classification: used by the diagnostic
