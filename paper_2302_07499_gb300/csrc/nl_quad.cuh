@@ -1171,6 +1171,79 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
     uint32_t acc = 0;
     StrictCap scap;
     scap.ready = 0;
+    if (F32 && ns == 1) {
+        // FP32, one cap cell (m = 0 or 3; warp-uniform, the warps hold one
+        // class): no cell choice, and the accepted samples' spacings are
+        // summed as sum beta beta^T (non-negative terms), mapped to the
+        // moments of lambda' = sum_k beta_k L_k once at the end (the sums of
+        // lambda' are its row sums, as below)
+        R sbb[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) sbb[k] = R(0);
+        for (int k = 0; k < nmc; ++k) {
+            const uint4 u = philox_rk(make_uint4(idT, idTp, q, (uint32_t)k), rk);
+            R U0 = unif<R>(u.y), U1 = unif<R>(u.z), U2 = unif<R>(u.w);
+            R lo = U0 < U1 ? U0 : U1, hi = U0 < U1 ? U1 : U0;
+            R s0 = lo < U2 ? lo : U2;
+            R mid0 = lo < U2 ? U2 : lo;
+            R s2 = hi < mid0 ? mid0 : hi;
+            R s1 = hi < mid0 ? hi : mid0;
+            R be[4] = {s0, s1 - s0, s2 - s1, R(1) - s2};
+            R cc[12];
+            if constexpr (F32) {
+                const float4 *c4 = reinterpret_cast<const float4 *>(cb);
+                const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
+                cc[0] = q0.x; cc[1] = q0.y; cc[2] = q0.z; cc[3] = q0.w; cc[4] = q1.x; cc[5] = q1.y;
+                cc[6] = q1.z; cc[7] = q1.w; cc[8] = q2.x; cc[9] = q2.y; cc[10] = q2.z; cc[11] = q2.w;
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < 12; ++kk) cc[kk] = cb[kk];
+            }
+            const P3<R> w = mk3<R>(((cc[0] + be[0] * cc[3]) + be[1] * cc[6]) + be[2] * cc[9],
+                                   ((cc[1] + be[0] * cc[4]) + be[1] * cc[7]) + be[2] * cc[10],
+                                   ((cc[2] + be[0] * cc[5]) + be[1] * cc[8]) + be[2] * cc[11]);
+            const R rr = (w.x * w.x + w.y * w.y) + w.z * w.z;
+            bool inb = rr <= d2;
+            if (sx && absr(rr - d2) < dmar) {
+                int j64 = 0;
+                inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64) != 0;
+            }
+            const R f = inb ? R(1) : R(0);
+            acc += inb ? 1u : 0u;
+            cnt += f;
+            R fb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) fb[a] = f * be[a];
+            int kk = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = a; b < 4; ++b) sbb[kk++] += fb[a] * be[b];
+        }
+        // the cell's rows L_k (lambda' at its vertices):
+        // sum lambda' lambda'^T = sum_kl sbb_kl L_k L_l^T
+        R L[16];
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) L[kk] = cb[12 + kk];
+        auto bb = [&](int k, int l) -> R {
+            const int a = k < l ? k : l, b = k < l ? l : k;
+            return sbb[(a == 0) ? b : (a == 1) ? 3 + b : (a == 2) ? 5 + b : 9];
+        };
+        R t[4][4];    // t[k][a] = sum_l sbb_kl L_l[a]
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                t[k][a] = ((bb(k, 0) * L[a] + bb(k, 1) * L[4 + a]) + bb(k, 2) * L[8 + a]) + bb(k, 3) * L[12 + a];
+        int kk = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int b = a; b < 4; ++b) {
+                a2[kk++] = ((L[a] * t[0][b] + L[4 + a] * t[1][b]) + L[8 + a] * t[2][b]) + L[12 + a] * t[3][b];
+            }
+        }
+    } else
     for (int k = 0; k < nmc; ++k) {
         uint4 u = philox_rk(make_uint4(idT, idTp, q, (uint32_t)k), rk);
         int j;
