@@ -803,29 +803,21 @@ constexpr int CB_STRIDE = 28;
 static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16 == 0, "cap scratch alignment");
 
 // Moments of the approximate ball inside T' for a point x whose
-// classification inm has 1..3 vertices inside, or 0 vertices for a fullcaps
-// cap that meets the ball.
-//   nocaps/fullcaps: exact moments of the cells of hull(I u P);
-//   fullcaps:        plus the Monte Carlo estimate over S = T' \ hull(I u P)
-//                    with nmc Philox samples (cell by cumulative volume,
-//                    uniform point from the spacings of three sorted
-//                    uniforms, acceptance |y-x|^2 <= delta^2).  Accepted
-//                    samples add 1, lambda'(y) and lambda'(y) lambda'(y)^T,
-//                    lambda'(y) being the spacings' combination of the cell
-//                    vertices' barycentric rows (non-negative terms only).
-//   cb, cs: per-thread scratch for the sampling cells, cell j at cb + j cs.
+// classification inm has 1..3 vertices inside, with run-time roles: the
+// approxcaps path (the hull of Sec. 3.3 over I, P and the arc midpoints, or
+// the nocaps cells of hull(I u P) when a hull cannot be completed).  The
+// nocaps and fullcaps events go through event_moments below, which
+// specialises the same geometry on the number of inside vertices.
 //   hs: per-thread scratch of the approxcaps hull (HULL_SCRATCH values).
 //   Returns true when the FP32 path defers the event (its output is then to
-//   be discarded): approxcaps with a vertex of T' within 1e-3 (relative) of
-//   the sphere, where the arc midpoints are ill-conditioned in FP32; and, when
+//   be discarded): a vertex of T' within 1e-3 (relative) of the sphere, where
+//   the arc midpoints are ill-conditioned in FP32 (redone in FP64); and, when
 //   DIAG_INLINE is false, an m = 2 diagonal that the FP32 orientation cannot
-//   decide (its FP64 retake costs a warp far more than its share on this
-//   part's narrow FP64 pipe, so such events are redone together by a second
-//   pass with DIAG_INLINE true).
+//   decide.
 template <class R, int STRAT, bool DIAG_INLINE = true>
-__device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
-                              uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs,
-                              const HullScratch<R> &hs)
+__device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk,
+                                      uint32_t idT, uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx,
+                                      R *cb, int cs, const HullScratch<R> &hs)
 {
     Mom<R> M;
     constexpr bool F32 = sizeof(R) == 4;
@@ -958,12 +950,24 @@ __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, 
     return false;
 }
 
-// The same for nocaps and fullcaps, with the number of inside vertices as a
-// compile-time constant (the warps of the event kernel hold one class), so
-// that the edge points, the cells and the roles are indexed statically and
-// stay in registers; barycentric rows stay in T''s own vertex order (the
-// roles only select).  The arithmetic, and so the result, is that of
-// event_moments_generic; approxcaps goes there.
+// Moments of the approximate ball inside T' for a point x whose
+// classification inm has 1..3 vertices inside, or 0 vertices for a fullcaps
+// cap that meets the ball:
+//   nocaps/fullcaps: exact moments of the cells of hull(I u P);
+//   fullcaps:        plus the Monte Carlo estimate over S = T' \ hull(I u P)
+//                    with nmc Philox samples (cell by cumulative volume,
+//                    uniform point from the spacings of three sorted
+//                    uniforms, acceptance |y-x|^2 <= delta^2).  Accepted
+//                    samples add 1, lambda'(y) and lambda'(y) lambda'(y)^T,
+//                    lambda'(y) being the spacings' combination of the cell
+//                    vertices' barycentric rows (non-negative terms only).
+// The number of inside vertices is a compile-time constant here (the warps
+// of the event kernel hold one class), so that the roles, the edge points and
+// the cell tables are indexed statically and stay in registers; barycentric
+// rows stay in T''s own vertex order (the roles only select).  Approxcaps
+// goes to event_moments_generic.
+//   cb, cs: per-thread scratch for the sampling cells, cell j at cb + j cs.
+//   Returns true when the event is deferred (see event_moments_generic).
 template <class R, int STRAT, bool DIAG_INLINE = true>
 __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
                               uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs,
