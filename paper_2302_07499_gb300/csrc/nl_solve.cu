@@ -16,6 +16,9 @@ struct CgState {
     double rr, pq, alpha, beta, tol2;
     int done, it;
     unsigned int ticket;     // blocks of the current reduction that have written their partial
+    unsigned int bar_count;  // grid barrier of the single-launch CG: arrivals,
+    unsigned int bar_gen;    // generation,
+    int bar_err;             // set when a wait gave up (bounded spin)
 };
 
 constexpr int RB = 256;   // threads per block in reductions
@@ -188,6 +191,122 @@ __global__ void k_start(const double *part, int nb, double rtol2, CgState *st)
     st->it = 0;
     st->ticket = 0;
     st->alpha = st->beta = st->pq = 0.0;
+    st->bar_count = 0;
+    st->bar_gen = 0;
+    st->bar_err = 0;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks resident).  The last
+// block to arrive resets the count and advances the generation; the others
+// wait for the new generation, at most about a second (then the error flag
+// is set and every block leaves: the host falls back to the multi-launch CG).
+__device__ bool grid_barrier(CgState *st)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = &st->bar_gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&st->bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            st->bar_count = 0u;
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            unsigned int spins = 0;
+            while (*gen == g) {
+                if (++spins > (1u << 25)) {
+                    atomicExch(&st->bar_err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        ok = *(volatile int *)&st->bar_err == 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Sum of the nb block partials in the fixed order of warp_sum_parts, formed by
+// every block (the same value in all of them) and broadcast to its threads.
+__device__ __forceinline__ double grid_sum(const double *part, int nb, double *bc)
+{
+    if (threadIdx.x < 32) {
+        const double s = warp_sum_parts(part, nb);
+        if (threadIdx.x == 0) *bc = s;
+    }
+    __syncthreads();
+    const double v = *bc;
+    __syncthreads();
+    return v;
+}
+
+// The whole CG loop in one cooperative launch (small systems, where the
+// launches of the multi-kernel loop dominate): per iteration q = A p with the
+// partials of p.q, barrier, alpha, the x/r update with the partials of r.r,
+// barrier, beta and the convergence test (the same in every block: the sums
+// are formed in the same order), the p update, barrier.  Values another block
+// wrote are read through L2.
+template <class VT, class XT>
+__global__ void __launch_bounds__(RB) k_cg_persist(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                   const VT *__restrict__ val, XT *x, XT *r, XT *p, XT *q, int64_t n,
+                                                   double *part, double *part2, CgState *st, int max_it)
+{
+    __shared__ double sh[RB / 32];
+    __shared__ double bc;
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    double rr = st->rr;
+    const double tol2 = st->tol2;
+    int it = 0, done = 0;
+    while (it < max_it) {
+        double acc = 0.0;
+        for (int64_t row = gt >> 5; row < n; row += warps) {
+            VT sum = VT(0);
+            for (int64_t e = rp[row] + lane; e < rp[row + 1]; e += 32) sum += val[e] * (VT)__ldcg(p + ci[e]);
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) {
+                q[row] = (XT)sum;
+                acc += (double)__ldcg(p + row) * (double)sum;
+            }
+        }
+        double t = block_sum(acc, sh);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+        if (!grid_barrier(st)) break;
+        const double pq = grid_sum(part, gridDim.x, &bc);
+        const XT a = (XT)((pq != 0.0) ? rr / pq : 0.0);
+        acc = 0.0;
+        for (int64_t i = gt; i < n; i += gs) {
+            x[i] += a * p[i];
+            const XT ri = r[i] - a * __ldcg(q + i);
+            r[i] = ri;
+            acc += (double)ri * (double)ri;
+        }
+        t = block_sum(acc, sh);
+        if (threadIdx.x == 0) part2[blockIdx.x] = t;
+        if (!grid_barrier(st)) break;
+        const double rn = grid_sum(part2, gridDim.x, &bc);
+        const double beta = (rr != 0.0) ? rn / rr : 0.0;
+        rr = rn;
+        ++it;
+        if (rn <= tol2 || !(rn == rn)) {
+            done = 1;
+            break;
+        }
+        const XT b = (XT)beta;
+        for (int64_t i = gt; i < n; i += gs) p[i] = r[i] + b * p[i];
+        if (!grid_barrier(st)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->rr = rr;
+        st->it = it;
+        st->done = done;
+    }
 }
 
 // r = b - A x (FP64), partial |r|^2
@@ -242,8 +361,24 @@ constexpr int64_t kFuseRows = 65536;
 struct Cg {
     int nb = 0;
     double *part = nullptr;
+    double *part2 = nullptr;   // second partials of the single-launch CG (null: not used)
     CgState *st = nullptr;
 };
+
+// Blocks of the single-launch CG: all resident at once (a cooperative launch
+// fails rather than oversubscribe), at most the partials' size.
+template <class VT, class XT>
+int persist_blocks(int nb)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_persist<VT, XT>, RB, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    // at most one block per SM: the iterations of these small systems are
+    // latency-bound, and fewer blocks make the barriers cheaper
+    return std::min(std::min(nb, occ * nl_num_sms()), nl_num_sms());
+}
 
 // Run CG from x = 0 on A x = b*scale; returns iterations; converged flag in *conv.
 template <class VT, class XT>
@@ -258,6 +393,30 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b,
     CgState h{};
     int launched = 0;
     *conv = false;
+    if (cg.part2 && n <= kFuseRows) {
+        const int nbp = persist_blocks<VT, XT>(nb);
+        if (nbp > 0) {
+            void *args[] = {(void *)&rp, (void *)&ci, (void *)&val, (void *)&x, (void *)&r, (void *)&p, (void *)&q,
+                            (void *)&n, (void *)&cg.part, (void *)&cg.part2, (void *)&cg.st, (void *)&max_it};
+            const cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_cg_persist<VT, XT>,
+                                                               dim3((unsigned)nbp), dim3(RB), args, 0, s);
+            if (le != cudaSuccess) (void)cudaGetLastError();     // not launched: the multi-launch loop below
+            else nl_count_launch();
+            NL_CUDA(cudaMemcpyAsync(&h, cg.st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+            NL_CUDA(cudaStreamSynchronize(s));
+            if (le == cudaSuccess && h.bar_err == 0) {
+                *conv = h.done && (h.rr == h.rr);
+                return h.it;
+            }
+            if (le == cudaSuccess) {
+                // a barrier wait gave up: redo the solve with separate launches
+                { k_init<XT><<<nb, RB, 0, s>>>(b, x, r, p, n, scale, cg.part); nl_count_launch(); }
+                NL_CHECK_LAUNCH();
+                { k_start<<<1, 32, 0, s>>>(cg.part, nb, rtol * rtol, cg.st); nl_count_launch(); }
+                NL_CHECK_LAUNCH();
+            }
+        }
+    }
     while (launched < max_it) {
         int k = std::min(check_every, max_it - launched);
         for (int j = 0; j < k; ++j) {
@@ -299,6 +458,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
         Cg cg;
         cg.nb = cg_blocks(n);
         cg.part = sc.get<double>(cg.nb);
+        cg.part2 = sc.get<double>(cg.nb);
         cg.st = sc.get<CgState>(1);
         double *x = sc.get<double>(n);
         double *rres = sc.get<double>(n);
