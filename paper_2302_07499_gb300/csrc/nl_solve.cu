@@ -357,6 +357,9 @@ int cg_blocks(int64_t n)
 
 // systems up to this many rows update p in the last block of the x/r update
 constexpr int64_t kFuseRows = 65536;
+// and up to this many run the whole loop in one cooperative launch (larger
+// ones are bandwidth-bound and want more resident blocks than one per SM)
+constexpr int64_t kPersistRows = 16384;
 
 struct Cg {
     int nb = 0;
@@ -393,7 +396,7 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b,
     CgState h{};
     int launched = 0;
     *conv = false;
-    if (cg.part2 && n <= kFuseRows) {
+    if (cg.part2 && n <= kPersistRows) {
         const int nbp = persist_blocks<VT, XT>(nb);
         if (nbp > 0) {
             void *args[] = {(void *)&rp, (void *)&ci, (void *)&val, (void *)&x, (void *)&r, (void *)&p, (void *)&q,
