@@ -65,11 +65,10 @@ struct AsmArgs {
     uint32_t rk[20];         // Philox round keys
     // per-chunk work arrays
     uint8_t *uinfo;          // [4*(p1-p0)] vertex-inside mask | 0x10 event | 0x20 zero
-    int32_t *slot;           // [4*(p1-p0)] class*units + index within the class, or -1
     int32_t *evu;            // [4][units] unit of each event, per class (m = 0..3)
     int *nev;                // [5] event count per class; nev[4] = deferred events
     int32_t *fix;            // [units] FP32 approxcaps events deferred to the FP64 pass
-    void *Mq;                // [events][MQ_STRIDE] moments (R): 15 used, 16-byte aligned records
+    void *Mq;                // [units][MQ_STRIDE] moments (R) of the events, by unit: 15 used, 16-byte aligned records
     unsigned long long *stats;  // [5]
 };
 

@@ -142,7 +142,6 @@ __global__ void __launch_bounds__(256, 3) k_classify(const __grid_constant__ Asm
         // the lanes of one class find each other, their first lane reserves
         // the class's slots
         const int cls = __popc((unsigned)(info & 15));
-        int32_t sl = -1;
         const unsigned grp = __match_any_sync(0xffffffffu, ev ? cls : -1);
         const int leader = __ffs(grp) - 1;
         int basep = 0;
@@ -150,13 +149,9 @@ __global__ void __launch_bounds__(256, 3) k_classify(const __grid_constant__ Asm
         basep = __shfl_sync(0xffffffffu, basep, leader);
         if (ev) {
             const int idx = basep + __popc(grp & ((1u << lane) - 1u));
-            sl = (int32_t)(cls * nu + idx);
             A.evu[cls * nu + idx] = (int32_t)u;
         }
-        if (u < nu) {
-            A.uinfo[u] = info;
-            A.slot[u] = sl;
-        }
+        if (u < nu) A.uinfo[u] = info;
     }
 }
 
@@ -217,13 +212,13 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
         if (deferred) {
             if constexpr (!RETAKE) A.fix[atomicAdd(&A.nev[4], 1)] = e;
         } else if constexpr (sizeof(R) == 4) {
-            float4 *g = reinterpret_cast<float4 *>(A.Mq) + (MQ_STRIDE / 4) * (int64_t)e;
+            float4 *g = reinterpret_cast<float4 *>(A.Mq) + (MQ_STRIDE / 4) * (int64_t)u;
             g[0] = make_float4(out[0], out[1], out[2], out[3]);
             g[1] = make_float4(out[4], out[5], out[6], out[7]);
             g[2] = make_float4(out[8], out[9], out[10], out[11]);
             g[3] = make_float4(out[12], out[13], out[14], 0.f);
         } else {
-            double2 *g = reinterpret_cast<double2 *>(A.Mq) + (MQ_STRIDE / 2) * (int64_t)e;
+            double2 *g = reinterpret_cast<double2 *>(A.Mq) + (MQ_STRIDE / 2) * (int64_t)u;
 #pragma unroll
             for (int k = 0; k < 7; ++k) g[k] = make_double2(out[2 * k], out[2 * k + 1]);
             g[7] = make_double2(out[14], 0.0);
@@ -277,7 +272,7 @@ __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmA
         nlq::event_moments<double, STRAT>(v, x, P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q,
                                           m15, st, nullptr, nullptr, 0,
                                           nlq::HullScratch<double>{reinterpret_cast<double *>(fsm) + threadIdx.x, 64});
-        float *out = reinterpret_cast<float *>(A.Mq) + MQ_STRIDE * (int64_t)e;
+        float *out = reinterpret_cast<float *>(A.Mq) + MQ_STRIDE * (int64_t)u;
 #pragma unroll
         for (int k = 0; k < 15; ++k) out[k] = (float)m15[k];
     }
@@ -318,8 +313,6 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
     static_assert(sizeof(DF) == sizeof(double), "strip and weight slots hold a double or a double-float");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long inside = 0;
-    const int64_t nu = 4 * (A.p1 - A.p0);
-    const int cpre[4] = {0, A.nev[0], A.nev[0] + A.nev[1], A.nev[0] + A.nev[1] + A.nev[2]};
 
     for (int64_t og = A.o0 + blockIdx.x; og < A.o1; og += gridDim.x) {
         int64_t o;
@@ -358,11 +351,9 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                 // FP32: points where T' is whole enter in double (their moments
                 // are closed forms of |T'|), the others from their FP32 records
                 int fullmask = 0;
-                // the pair's 4 units: 4 info bytes and 4 slots in one load each
-                // (u0 is a multiple of 4)
+                // the pair's 4 units: 4 info bytes in one load (u0 is a multiple
+                // of 4)
                 const uint32_t info4 = *reinterpret_cast<const uint32_t *>(A.uinfo + u0);
-                const int4 slot4 = *reinterpret_cast<const int4 *>(A.slot + u0);
-                const int32_t slots[4] = {slot4.x, slot4.y, slot4.z, slot4.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const uint8_t info = (uint8_t)(info4 >> (8 * q));
@@ -376,9 +367,9 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         }
                         inside++;
                     } else if (info & 0x10) {
-                        const int32_t sl = slots[q];
-                        const int cls = (int)(sl / nu), idx = (int)(sl - (int64_t)cls * nu);
-                        const int64_t ev = (int64_t)cpre[cls] + idx;
+                        // the unit's record (records are stored by unit: the
+                        // pair's four are contiguous)
+                        const int64_t ev = u0 + q;
                         R mq[MQ_STRIDE];
                         if constexpr (F32) {
                             const float4 *m4 = reinterpret_cast<const float4 *>(A.Mq) + (MQ_STRIDE / 4) * ev;
@@ -584,7 +575,6 @@ void alloc_work(AsmArgs &A, Scratch &sc, int64_t max_units)
 {
     constexpr bool kDefer = sizeof(R) == 4 && STRAT == 1;
     A.uinfo = sc.get<uint8_t>(max_units);
-    A.slot = sc.get<int32_t>(max_units);
     A.evu = sc.get<int32_t>(4 * max_units);
     A.nev = sc.get<int>(5);
     A.fix = (kDefer || kRetakePass<R, STRAT>) ? sc.get<int32_t>(max_units) : nullptr;

@@ -124,7 +124,7 @@ int64_t estimate_bytes(const nl_request &r)
     const double nt = 6.0 * (double)r.cells * r.cells * r.cells;
     const double sz = r.assemble.precision == NL_FP32_COMP ? 4.0 : 8.0;
     const double units = std::min(4.0 * pairs, (double)(int64_t(1) << 25));
-    const double b = pairs * (12.0 + 10.0 * sz + 24.0) + units * (25.0 + 16.0 * sz) + nt * 400.0;
+    const double b = pairs * (12.0 + 10.0 * sz + 24.0) + units * (21.0 + 16.0 * sz) + nt * 400.0;
     return (int64_t)b;
 }
 
