@@ -1,0 +1,82 @@
+"""Host logic of the bench that feeds its roofline object: the committed DRAM
+traffic record is used only while the quadrature kernel sources are the ones
+it was captured on, and the peak falls back when the measured file lacks it."""
+import json
+import os
+import shutil
+
+import pytest
+
+import bench
+
+SOURCES = ("nl_quad.cuh", "nl_assemble.cuh", "nl_assemble32.cu")
+
+
+@pytest.fixture()
+def fake_root(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2302_07499_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in SOURCES:
+        shutil.copy(os.path.join(bench.ROOT, "paper_2302_07499_gb300", "csrc", f), csrc / f)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    return tmp_path
+
+
+def _write_record(root, sha, value=1.5e9):
+    rec = {"source_sha": sha, "dram_bytes_per_step": value}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+
+
+def test_traffic_record_used_while_sources_match(fake_root):
+    _write_record(fake_root, bench._kernel_source_sha())
+    assert bench._traffic_record() == 1.5e9
+
+
+def test_traffic_record_dropped_once_a_source_changes(fake_root):
+    _write_record(fake_root, bench._kernel_source_sha())
+    for f in SOURCES:
+        p = fake_root / "paper_2302_07499_gb300" / "csrc" / f
+        orig = p.read_bytes()
+        p.write_bytes(orig + b"\n")
+        assert bench._traffic_record() is None, f
+        p.write_bytes(orig)
+    assert bench._traffic_record() == 1.5e9
+
+
+def test_traffic_record_missing_or_malformed(fake_root):
+    assert bench._traffic_record() is None
+    (fake_root / "profiles" / "traffic.json").write_text("{not json")
+    assert bench._traffic_record() is None
+
+
+def test_committed_traffic_record_is_consistent():
+    """The committed record scales the captured launch's bytes by the sample
+    ratio it states, so its per-step figure follows from its own fields."""
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
+    cap = rec["dram_read_bytes_captured"] + rec["dram_write_bytes_captured"]
+    want = cap * rec["mc_samples_per_step"] / rec["mc_samples_captured"]
+    assert abs(rec["dram_bytes_per_step"] - want) <= 1e-9 * want
+    assert len(rec["source_sha"]) == 16
+
+
+def test_measured_peak_and_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._measured_peak("hbm_gbs", 6800.0) == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7000.5}))
+    assert bench._measured_peak("hbm_gbs", 6800.0) == (7000.5, "measured")
+    assert bench._measured_peak("bf16_tflops", 1900.0) == (1900.0, "fallback")
+
+
+def test_quadrature_ops_counts_each_unit_once():
+    """Each counted unit adds its own per-unit operation figure: pairs carry
+    four outer points each, and the cut-point work adds linearly."""
+    zero = dict(pairs=0, cut_points=0, mc_samples=0, mc_accepted=0)
+    assert bench._quadrature_ops(zero) == 0
+    for key, per in (("cut_points", bench.OPS_PER_CUT), ("mc_samples", bench.OPS_PER_SAMPLE),
+                     ("mc_accepted", bench.OPS_PER_ACCEPTED), ("pairs", 4 * bench.OPS_PER_PAIR_POINT)):
+        st = dict(zero, **{key: 1000})
+        assert bench._quadrature_ops(st) == 1000 * per, key
+    st = dict(pairs=3, cut_points=5, mc_samples=7, mc_accepted=2)
+    parts = sum(bench._quadrature_ops(dict(zero, **{k: v})) for k, v in st.items())
+    assert bench._quadrature_ops(st) == parts
