@@ -308,7 +308,8 @@ nl_status nl_batch_create(nl_pairs *const *pairs, const nl_assemble_opts *opts, 
  * synchronises the stream before returning.  Errors: NL_EINVAL, NL_ECUDA. */
 nl_status nl_batch_run(nl_batch *batch);
 
-/* The system of problem i (the caller's order), owned by the batch. */
+/* The system of problem i (the caller's order), owned by the batch.
+ * Errors: NL_EINVAL (NULL argument, i out of range). */
 nl_status nl_batch_system(nl_batch *batch, int i, nl_system **out);
 
 typedef struct {
@@ -323,6 +324,7 @@ typedef struct {
     double tried_ms[16];
     uint64_t pairs, cut_points, inside_points, mc_samples, mc_accepted, hull_fallbacks;   /* last run, summed */
 } nl_batch_info;
+/* Errors: NL_EINVAL (NULL argument). */
 nl_status nl_batch_get_info(const nl_batch *batch, nl_batch_info *info);
 void nl_batch_destroy(nl_batch *batch);
 
@@ -372,18 +374,29 @@ typedef struct {
     int queued, running, cache_entries;
     int64_t cache_bytes, running_bytes;
 } nl_server_load;
+/* Errors: NL_EINVAL (NULL argument; workers outside 1..16, budget <= 0 or
+ * queue capacity < 1), NL_ECUDA (no device, stream creation).  *out is NULL
+ * on error. */
 nl_status nl_server_create(const nl_server_opts *opts, nl_server **out);
-/* Queue a request (copied); the ticket names it until nl_server_release. */
+/* Queue a request (copied); the ticket names it until nl_server_release.
+ * Errors: NL_EINVAL (NULL argument, cells < 1, delta not positive and
+ * finite, hi <= lo, g_nodal set), NL_EBUSY (queue_capacity requests
+ * pending).  Device errors of the request itself arrive in its result. */
 nl_status nl_server_submit(nl_server *server, const nl_request *req, uint64_t *ticket);
-/* The request's state and result so far (never blocks). */
+/* The request's state and result so far (never blocks).  Errors: NL_EINVAL
+ * (NULL argument, unknown ticket). */
 nl_status nl_server_poll(nl_server *server, uint64_t ticket, nl_result *res);
 /* Wait until the request is done (timeout_s <= 0: no limit; NL_ETIMEOUT
  * otherwise), then copy its result and, when u_out is not NULL, its nodal
- * solution (n_vert doubles, host memory of n_u >= n_vert entries). */
+ * solution (n_vert doubles, host memory of n_u >= n_vert entries).
+ * Errors: NL_EINVAL (NULL server, unknown ticket, n_u too small),
+ * NL_ETIMEOUT.  The request's own status is res->status. */
 nl_status nl_server_wait(nl_server *server, uint64_t ticket, double timeout_s, nl_result *res, double *u_out,
                          int64_t n_u);
-/* Forget a finished request (NL_EBUSY while it is queued or running). */
+/* Forget a finished request (NL_EBUSY while it is queued or running;
+ * NL_EINVAL for an unknown ticket). */
 nl_status nl_server_release(nl_server *server, uint64_t ticket);
+/* Errors: NL_EINVAL (NULL argument). */
 nl_status nl_server_get_load(nl_server *server, nl_server_load *out);
 /* Stops the workers after their current requests; queued ones are dropped. */
 void nl_server_destroy(nl_server *server);

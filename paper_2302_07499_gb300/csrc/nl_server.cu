@@ -340,13 +340,13 @@ extern "C" nl_status nl_server_create(const nl_server_opts *opts, nl_server **ou
         NL_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
         for (int i = 0; i < opts->workers; ++i) {
             Worker *w = new Worker();
+            S->workers.push_back(w);    // owned by the server before anything can fail
             w->srv = S;
             NL_CUDA(cudaStreamCreateWithFlags(&w->s, cudaStreamNonBlocking));
             w->dev.alloc = worker_alloc;
             w->dev.free = worker_free;
             w->dev.ctx = w;
             w->dev.stream = w->s;
-            S->workers.push_back(w);
         }
         for (Worker *w : S->workers) w->th = std::thread(worker_main, w);
     } catch (NlError &e) {
