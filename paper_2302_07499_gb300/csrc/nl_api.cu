@@ -87,8 +87,7 @@ nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_dev
         uint8_t *nfull = f32 ? sc.get<uint8_t>(P->npairs) : nullptr;
         uint64_t *st = sc.get<uint64_t>(8);
         NL_CUDA(cudaMemsetAsync(st, 0, sizeof(uint64_t) * 8, s));
-        cudaEvent_t ev[3];
-        for (int i = 0; i < 3; ++i) NL_CUDA(cudaEventCreate(&ev[i]));
+        ScopedEvent ev[3];
         NL_CUDA(cudaEventRecord(ev[0], s));
         if (f32) nl_assemble_fp32(S, (float *)D, strips, TT, nfull, st);
         else nl_assemble_fp64(S, (double *)D, strips, TT, nullptr, st);
@@ -99,7 +98,6 @@ nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_dev
         float ms0 = 0.f, ms1 = 0.f;
         NL_CUDA(cudaEventElapsedTime(&ms0, ev[0], ev[1]));
         NL_CUDA(cudaEventElapsedTime(&ms1, ev[1], ev[2]));
-        for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
         S->stats.quadrature_ms = ms0;
         S->stats.reduce_ms = ms1;
         uint64_t hs[8];

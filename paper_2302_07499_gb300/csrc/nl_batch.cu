@@ -89,17 +89,13 @@ void batch_enqueue(nl_batch *b, const nla::Shape &sh, cudaStream_t s)
 // One timed run of the batch with the given shape (ms).
 double batch_time(nl_batch *b, const nla::Shape &sh, cudaStream_t s)
 {
-    cudaEvent_t e0, e1;
-    NL_CUDA(cudaEventCreate(&e0));
-    NL_CUDA(cudaEventCreate(&e1));
+    ScopedEvent e0, e1;
     NL_CUDA(cudaEventRecord(e0, s));
     batch_enqueue(b, sh, s);
     NL_CUDA(cudaEventRecord(e1, s));
     NL_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
     NL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return ms;
 }
 
@@ -291,9 +287,7 @@ extern "C" nl_status nl_batch_run(nl_batch *b)
         // work queued by the caller before this call comes first
         NL_CUDA(cudaEventRecord(b->join, s));
         NL_CUDA(cudaStreamWaitEvent(bs, b->join, 0));
-        cudaEvent_t e0, e1;
-        NL_CUDA(cudaEventCreate(&e0));
-        NL_CUDA(cudaEventCreate(&e1));
+        ScopedEvent e0, e1;
         NL_CUDA(cudaEventRecord(e0, bs));
         if (b->exec) {
             NL_CUDA(cudaGraphLaunch(b->exec, bs));
@@ -305,13 +299,8 @@ extern "C" nl_status nl_batch_run(nl_batch *b)
         NL_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
         NL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         b->last_ms = ms;
-        unsigned long long hs[8];
-        NL_CUDA(cudaMemcpy(hs, b->stats, sizeof(hs), cudaMemcpyDeviceToHost));
         for (nl_system *S : b->sys) S->stats.quadrature_ms = ms;
-        (void)hs;
     } catch (NlError &e) {
         return e.st;
     }

@@ -40,6 +40,20 @@ struct NlError {
         }                                                                              \
     } while (0)
 
+// A timing event destroyed with its scope, so a call that throws between
+// creating and reading it does not leak it.
+struct ScopedEvent {
+    cudaEvent_t e = nullptr;
+    ScopedEvent() { NL_CUDA(cudaEventCreate(&e)); }
+    ~ScopedEvent()
+    {
+        if (e) cudaEventDestroy(e);
+    }
+    ScopedEvent(const ScopedEvent &) = delete;
+    ScopedEvent &operator=(const ScopedEvent &) = delete;
+    operator cudaEvent_t() const { return e; }
+};
+
 // Device allocations owned by a handle; released in reverse order.
 struct DevArena {
     nl_device dev{};

@@ -565,9 +565,7 @@ extern "C" nl_status nl_spmv_time(nl_system *S, int precision, int reps, double 
         { k_fill_ones<<<(unsigned)nl_cdiv<int64_t>(n, 256), 256, 0, s>>>(xd, xf, n); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         const int nb = cg_blocks(n);
-        cudaEvent_t e0, e1;
-        NL_CUDA(cudaEventCreate(&e0));
-        NL_CUDA(cudaEventCreate(&e1));
+        ScopedEvent e0, e1;
         for (int w = 0; w < 2; ++w) {
             NL_CUDA(cudaEventRecord(e0, s));
             for (int k = 0; k < (w ? reps : 1); ++k) {
@@ -582,8 +580,6 @@ extern "C" nl_status nl_spmv_time(nl_system *S, int precision, int reps, double 
         NL_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
         NL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         *ms_per_spmv = ms / reps;
         const double vb = precision == NL_FP64 ? 8.0 : 4.0;
         if (bytes_per_spmv) *bytes_per_spmv = (double)nnz * (vb + 4.0) + (double)(n + 1) * 8.0 + 2.0 * n * vb;
