@@ -201,6 +201,84 @@ def test_nocaps_cells_volume_closed_forms():
     assert seen == {0, 1, 2, 3, 4}
 
 
+
+def _arc_midpoint_in_face(fv, p1, p2, x, delta):
+    """The midpoint of the sphere's circle arc between p1 and p2 in the plane
+    of the face fv[0..2] that lies inside the face, or None: the two arc
+    midpoints are c +- r u (c the circle's centre, u the in-plane unit normal
+    of the chord); the one in the triangle is kept."""
+    n = np.cross(fv[1] - fv[0], fv[2] - fv[0])
+    c = x - ((x - fv[0]) @ n) / (n @ n) * n
+    r2 = delta ** 2 - (x - c) @ (x - c)
+    if r2 <= 0:
+        return None
+    u = np.cross(n, p2 - p1)
+    u /= np.linalg.norm(u)
+    E = np.stack([fv[1] - fv[0], fv[2] - fv[0]], axis=1)
+    kept = []
+    for cand in (c + math.sqrt(r2) * u, c - math.sqrt(r2) * u):
+        st = np.linalg.lstsq(E, cand - fv[0], rcond=None)[0]
+        if st.min() >= -1e-12 and st.sum() <= 1 + 1e-12:
+            kept.append(cand)
+    assert len(kept) <= 1
+    return kept[0] if kept else None
+
+
+def test_approxcaps_moments_of_independently_built_hull():
+    """Sec. 3.3: the approximate ball in T' is the convex hull of the inside
+    vertices, the edge/sphere points and, on each face cut between two edge
+    points, the midpoint of the sphere's arc in that face.  The points are
+    built here from numpy's roots and circle geometry, the hull is split into
+    tetrahedra by Qhull, and the moments (lambda' linear, so the degree-2
+    rule is exact on each tetrahedron) must equal the oracle's."""
+    from scipy.spatial import ConvexHull, Delaunay
+    rng = np.random.default_rng(21)
+    counts = {1: 0, 2: 0, 3: 0}
+    mids = 0
+    lam_q = np.full((4, 4), QB)
+    np.fill_diagonal(lam_q, QA)
+    while min(counts.values()) < 40:
+        v = rand_tet(rng)
+        x = v[rng.integers(4)] + rng.normal(size=3) * 0.4
+        delta = float(rng.uniform(0.4, 1.4))
+        inside = np.sum((v - x) ** 2, axis=1) < delta ** 2
+        m = int(inside.sum())
+        if m not in counts:
+            continue
+        ins, out = np.nonzero(inside)[0], np.nonzero(~inside)[0]
+        P = {}
+        for i in ins:
+            for o in out:
+                P[(i, o)] = v[i] + _sphere_t(v[i], v[o], x, delta) * (v[o] - v[i])
+        pts = [v[i] for i in ins] + list(P.values())
+        for f_out in range(4):
+            face = [k for k in range(4) if k != f_out]
+            ep = [P[(i, o)] if (i, o) in P else P[(o, i)] for a, i in enumerate(face) for o in face[a + 1:]
+                  if inside[i] != inside[o]]
+            if len(ep) == 2:
+                mu = _arc_midpoint_in_face(v[face], ep[0], ep[1], x, delta)
+                if mu is not None:
+                    pts.append(mu)
+                    mids += 1
+        pts = np.array(pts)
+        counts[m] += 1
+        M, _, _ = O.region_moments(v, x, delta, O.APPROXCAPS)
+        assert M[0] == pytest.approx(ConvexHull(pts).volume, rel=1e-9)
+        # moments of lambda' over the hull, tetrahedron by tetrahedron
+        T = np.linalg.inv(np.vstack([v.T, np.ones(4)]))      # lambda'(y) = T @ (y, 1)
+        want = np.zeros(15)
+        for simp in Delaunay(pts).simplices:
+            w = pts[simp]
+            vol = abs(np.linalg.det(w[1:] - w[0])) / 6
+            for q in range(4):
+                y = lam_q[q] @ w
+                lam = T @ np.append(y, 1.0)
+                want[0] += vol / 4
+                want[1:5] += vol / 4 * lam
+                want[5:] += vol / 4 * np.array([lam[a] * lam[b] for a in range(4) for b in range(a, 4)])
+        assert np.allclose(M, want, rtol=1e-8, atol=1e-12 * abs(O.tet_volume(v)))
+    assert mids > 40
+
 def test_moments_closed_form_and_partition_of_unity():
     rng = np.random.default_rng(5)
     v = rand_tet(rng)
