@@ -279,6 +279,39 @@ def test_approxcaps_moments_of_independently_built_hull():
         assert np.allclose(M, want, rtol=1e-8, atol=1e-12 * abs(O.tet_volume(v)))
     assert mids > 40
 
+
+def test_fullcaps_moments_per_element_match_plain_sampling():
+    """Sec. 4.3.2: fullcaps is unbiased for the moments of B_delta(x) cap T'.
+    For single elements with 1, 2 and 3 inside vertices, its mean over seeds
+    must agree (5 sigma) with plain uniform sampling of the whole T' (numpy's
+    generator, Dirichlet barycentrics, indicator of the ball), moment by
+    moment."""
+    rng = np.random.default_rng(31)
+    gen = np.random.default_rng(32)
+    done = {1: 0, 2: 0, 3: 0}
+    while min(done.values()) < 2:
+        v = rand_tet(rng)
+        x = v[rng.integers(4)] + rng.normal(size=3) * 0.3
+        delta = float(rng.uniform(0.5, 1.2))
+        m = int(np.sum(np.sum((v - x) ** 2, axis=1) < delta ** 2))
+        if m not in done or done[m] >= 2:
+            continue
+        done[m] += 1
+        runs = np.array([O.region_moments(v, x, delta, O.FULLCAPS, nmc=4096, seed=s, idT=1, idTp=2, q=3)[0]
+                         for s in range(8)])
+        mean_o, se_o = runs.mean(axis=0), runs.std(axis=0, ddof=1) / math.sqrt(len(runs))
+        V = abs(O.tet_volume(v))
+        n = 4_000_000
+        lam = gen.dirichlet(np.ones(4), size=n)
+        f = np.sum((lam @ v - x) ** 2, axis=1) <= delta ** 2
+        cols = [f.astype(float)] + [f * lam[:, a] for a in range(4)] + \
+               [f * lam[:, a] * lam[:, b] for a in range(4) for b in range(a, 4)]
+        est = np.array([V * c.mean() for c in cols])
+        se = np.array([V * c.std() / math.sqrt(n) for c in cols])
+        band = 5 * np.sqrt(se ** 2 + se_o ** 2) + 1e-12 * V
+        assert np.all(np.abs(mean_o - est) <= band), (m, mean_o - est, band)
+
+
 def test_moments_closed_form_and_partition_of_unity():
     rng = np.random.default_rng(5)
     v = rand_tet(rng)
