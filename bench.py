@@ -629,7 +629,9 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 20, so that the clock sampler sees the timed region; "
+                         "5 for batch256_seed3, whose steps take seconds)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube24_d0125_fullcaps64", choices=sorted(WORKLOADS) + ["batch256_seed3", "serve_stream_seed5"])
@@ -642,6 +644,8 @@ def main():
     ap.add_argument("--batch-pairs", type=float, default=6e8,
                     help="element-pair budget of one sub-batch (workload batch256_seed3)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 5 if args.workload == "batch256_seed3" else 20
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
