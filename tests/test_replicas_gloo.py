@@ -45,3 +45,22 @@ def test_two_replicas_report_the_slowest_rank():
     for rank, t, thr in res:
         assert t == 15.0                       # the slower rank's 15 ms
         assert thr == pytest.approx(2 * 1000 / 0.015)
+
+
+def test_reference_arm_prints_once_under_torchrun():
+    """With two ranks the reference arm (the oracle on the host cores) runs on
+    rank 0 alone, which prints the one JSON line; rank 1 exits 0 without work."""
+    import json
+    import subprocess
+    env = dict(os.environ, NL_REF_OUTER="8", OMP_NUM_THREADS="2")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 1
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
