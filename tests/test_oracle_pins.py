@@ -526,6 +526,30 @@ def test_pairs_grid_equals_brute_force():
         assert np.all(np.isin(a[0], pTp[pT == pTp]))
 
 
+
+def test_pairs_degenerate_ends():
+    """Alg. 2 at its two ends.  A quadrature point of T is nearer to T's own
+    boundary than to any other element, so a delta below the smallest
+    point-to-face distance leaves exactly the pairs (T, T); a delta above the
+    domain's diameter pairs every outer element with every element."""
+    m = I.kuhn_box(-0.25, 1.25, 6, jitter_frac=0.2, seed=13)
+    outer = np.nonzero(m.tet_in_omega)[0]
+    dmin = np.inf
+    for t in outer:
+        v = m.verts[m.tets[t]]
+        for k in range(4):
+            f = v[[i for i in range(4) if i != k]]
+            n = np.cross(f[1] - f[0], f[2] - f[0])
+            n /= np.linalg.norm(n)
+            dmin = min(dmin, np.abs((O.quad_points(v) - f[0]) @ n).min())
+    diam = np.linalg.norm(m.verts.max(axis=0) - m.verts.min(axis=0))
+    for use_grid in (True, False):
+        o, ptr, tp = O.pairs(m, 0.5 * dmin, use_grid=use_grid)
+        assert np.array_equal(o, outer) and np.all(np.diff(ptr) == 1) and np.array_equal(tp, outer)
+        o, ptr, tp = O.pairs(m, 1.01 * diam, use_grid=use_grid)
+        assert np.all(np.diff(ptr) == m.nt)
+        assert np.array_equal(tp.reshape(len(outer), m.nt), np.tile(np.arange(m.nt), (len(outer), 1)))
+
 # ---------------------------------------------------------------- assembly and solve
 @pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS, O.BARYCENTER, O.OVERLAP, O.INSIDE])
 def test_stiffness_symmetric_zero_row_sums_psd(strat):
