@@ -4,6 +4,7 @@ it was captured on, and the peak falls back when the measured file lacks it."""
 import json
 import os
 import shutil
+import time
 
 import pytest
 
@@ -80,3 +81,34 @@ def test_quadrature_ops_counts_each_unit_once():
     st = dict(pairs=3, cut_points=5, mc_samples=7, mc_accepted=2)
     parts = sum(bench._quadrature_ops(dict(zero, **{k: v})) for k, v in st.items())
     assert bench._quadrature_ops(st) == parts
+
+
+def _fake_smi(dirpath, rows):
+    script = dirpath / "nvidia-smi"
+    body = "\n".join("echo '%s'; sleep 0.02" % r for r in rows)
+    script.write_text("#!/bin/sh\n%s\nexec sleep 30\n" % body)
+    script.chmod(0o755)
+
+
+def test_clock_sampler_parses_rows_and_reasons(tmp_path, monkeypatch):
+    rows = ["0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2055, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage"]
+    _fake_smi(tmp_path, rows)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    time.sleep(0.5)
+    c = s.stop()
+    assert c["samples"] == 3                    # malformed rows are skipped
+    assert c["sm_mhz"] == 2055.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
