@@ -551,6 +551,34 @@ def test_pairs_degenerate_ends():
         assert np.array_equal(tp.reshape(len(outer), m.nt), np.tile(np.arange(m.nt), (len(outer), 1)))
 
 # ---------------------------------------------------------------- assembly and solve
+@pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS])
+def test_folded_system_equals_unfolded_form_when_balls_cover_the_mesh(strat):
+    """Sec. 2.2 and Alg. 5 with the collar weight 2 and psi = gamma/2.  With
+    delta above the mesh's diameter every ball holds the whole mesh, so every
+    strategy is exact.  The unfolded form over all element pairs of the mesh,
+    (gamma/2) sum_{T,T'} int_T int_T' (phi_i(x)-phi_i(y)) (phi_j(x)-phi_j(y)),
+    then equals gamma (|mesh| M_ij - a_i a_j) on the free nodes: M is the P1
+    mass matrix, a_i = int phi_i, the free nodes' basis functions vanish on
+    the collar, and the 4-point rule is exact for phi_i phi_j.  The folded
+    assembly (outer elements in Omega only) must give the same matrix A."""
+    mesh, _ = I.cube_problem(3, 1, jitter_frac=0.2, seed=17)
+    delta = 1.01 * np.linalg.norm(mesh.verts.max(axis=0) - mesh.verts.min(axis=0))
+    gamma = 0.7
+    K = O.assemble_K(mesh, delta, gamma, strat, nmc=8, seed=3)
+    A, _, free = O.system(mesh, K, np.zeros(mesh.nv), np.zeros(mesh.nv))
+    assert len(free) == 8
+    M = np.zeros((mesh.nv, mesh.nv))
+    vol_all = 0.0
+    for t in mesh.tets:
+        v = mesh.verts[t]
+        vol = abs(np.linalg.det(v[1:] - v[0])) / 6
+        vol_all += vol
+        M[np.ix_(t, t)] += vol / 20 * (np.ones((4, 4)) + np.eye(4))
+    a = M.sum(axis=1)               # int phi_i, as the phi_j sum to one
+    want = gamma * (vol_all * M - np.outer(a, a))[np.ix_(free, free)]
+    assert np.allclose(A.toarray(), want, rtol=1e-11, atol=1e-13 * np.abs(want).max())
+
+
 @pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS, O.BARYCENTER, O.OVERLAP, O.INSIDE])
 def test_stiffness_symmetric_zero_row_sums_psd(strat):
     # delta = h leaves no element wholly inside a ball; the element-level
