@@ -560,12 +560,15 @@ def test_folded_system_equals_unfolded_form_when_balls_cover_the_mesh(strat):
     then equals gamma (|mesh| M_ij - a_i a_j) on the free nodes: M is the P1
     mass matrix, a_i = int phi_i, the free nodes' basis functions vanish on
     the collar, and the 4-point rule is exact for phi_i phi_j.  The folded
-    assembly (outer elements in Omega only) must give the same matrix A."""
+    assembly (outer elements in Omega only) must give the same matrix A, and
+    the right-hand side F - K[free, collar] g with the same K."""
     mesh, _ = I.cube_problem(3, 1, jitter_frac=0.2, seed=17)
     delta = 1.01 * np.linalg.norm(mesh.verts.max(axis=0) - mesh.verts.min(axis=0))
     gamma = 0.7
     K = O.assemble_K(mesh, delta, gamma, strat, nmc=8, seed=3)
-    A, _, free = O.system(mesh, K, np.zeros(mesh.nv), np.zeros(mesh.nv))
+    F = O.load_vector(mesh, -6.0)
+    g = I.quadratic_g(mesh.verts)
+    A, b, free = O.system(mesh, K, F, g)
     assert len(free) == 8
     M = np.zeros((mesh.nv, mesh.nv))
     vol_all = 0.0
@@ -575,8 +578,13 @@ def test_folded_system_equals_unfolded_form_when_balls_cover_the_mesh(strat):
         vol_all += vol
         M[np.ix_(t, t)] += vol / 20 * (np.ones((4, 4)) + np.eye(4))
     a = M.sum(axis=1)               # int phi_i, as the phi_j sum to one
-    want = gamma * (vol_all * M - np.outer(a, a))[np.ix_(free, free)]
+    Kc = gamma * (vol_all * M - np.outer(a, a))
+    want = Kc[np.ix_(free, free)]
     assert np.allclose(A.toarray(), want, rtol=1e-11, atol=1e-13 * np.abs(want).max())
+    # the volume constraint moves the collar values to the right-hand side
+    con = np.nonzero(mesh.node_free == 0)[0]
+    b_want = F[free] - Kc[np.ix_(free, con)] @ g[con]
+    assert np.allclose(b, b_want, rtol=1e-11, atol=1e-13 * np.abs(b_want).max())
 
 
 @pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS, O.BARYCENTER, O.OVERLAP, O.INSIDE])
