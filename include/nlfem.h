@@ -418,6 +418,23 @@ nl_status nl_probe_moments(const double *tets_xyz, const double *x, const uint32
                            double delta, int strategy, int mc_points, uint64_t seed, int precision,
                            double *moments);
 
+/* nl_probe_mc_samples — the fullcaps Monte Carlo samples of n single cases
+ * (T' vertices tets_xyz[c][4][3], outer point x[c][3], Philox counter words
+ * ids[c] = (T, T', q)), drawn by the same device code as nl_assemble's
+ * fullcaps events (Sec. 4.3.2, Alg. 4): per case n_samples[c] = mc_points,
+ * or 0 when T' has no cap for x (all vertices inside, or T' not meeting the
+ * closed ball); per sample k (arrays [n][mc_points], row-major):
+ * cell[c][k] the cap cell the sample fell in (-1 past n_samples[c]),
+ * accepted[c][k] = 1 when |y - x|^2 <= delta^2, y[c][k][3] the point.
+ * NL_FP64: the points of the arithmetic specification (global coordinates,
+ * no fused multiply-add).  NL_FP32_COMP: the FP32 path's decisions and its
+ * FP32 point relative to x, returned as x + that offset.  At most 2^20 cases.
+ * Errors: NL_EINVAL (NULL pointer, mc_points outside 1..4096, precision),
+ * NL_ECUDA. */
+nl_status nl_probe_mc_samples(const double *tets_xyz, const double *x, const uint32_t *ids, int64_t n, double delta,
+                              int mc_points, uint64_t seed, int precision, int32_t *n_samples, int32_t *cell,
+                              uint8_t *accepted, double *y);
+
 /* nl_probe_philox — Philox4x32-10 (Salmon et al., SC'11) of n counters
  * ctr[n][4] under the key (key & 0xffffffff, key >> 32): the generator that
  * draws the fullcaps Monte Carlo points.  out[n][4].  Errors: NL_EINVAL,
@@ -431,6 +448,22 @@ nl_status nl_probe_philox(const uint32_t *ctr, uint64_t key, int64_t n, uint32_t
  * the algorithmic traffic nnz (value + column index) + rowptr + x + y.
  * Errors: NL_EINVAL, NL_ECUDA. */
 nl_status nl_spmv_time(nl_system *sys, int precision, int reps, double *ms_per_spmv, double *bytes_per_spmv);
+
+/* nl_probe_alu_rates — measured ALU throughput of the current device, the
+ * denominators of the quadrature kernels' ALU roofline (no part of the
+ * paper's method).  Each entry is operations per second of one
+ * register-only microbenchmark (independent chains, 8 blocks of 256 threads
+ * per SM, best of 3 runs timed with CUDA events on the default stream):
+ *   [0] FP32 fused multiply-add   [1] FP64 fused multiply-add
+ *   [2] 32-bit mad.lo             [3] 32-bit mul.hi
+ *   [4] 3-input xor, counted as 2 operations
+ *   [5] Philox4x32-10 draws, 80 operations each
+ *   [6] the fullcaps sample of Sec. 4.3.2 (a Philox draw, the cell choice,
+ *       three uniforms, their sort, the spacings, the point and the ball
+ *       test), 121 operations each, with its cell in registers.
+ * n must be at least 7.  Takes a few tens of milliseconds; synchronises the
+ * device.  Errors: NL_EINVAL, NL_ECUDA. */
+nl_status nl_probe_alu_rates(double *ops_per_s, int n);
 
 /* Thread-local message of the last failing call (empty string if none). */
 const char *nl_last_error(void);

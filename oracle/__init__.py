@@ -72,6 +72,9 @@ def lib():
                                             C.c_uint32, C.c_uint32, C.c_uint32, dp, dp]
             L.or_pair_block.argtypes = [dp, dp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
                                         C.c_uint64, C.c_uint32, C.c_uint32, dp]
+            L.or_cap_samples.argtypes = [dp, dp, C.c_double, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32,
+                                         C.c_uint32, dp, i32p, u8p]
+            L.or_cap_samples.restype = C.c_int
             L.or_assemble_blocks.argtypes = [dp, i32p, u8p, C.c_double, C.c_double, C.c_int, C.c_int,
                                              C.c_uint64, i32p, i32p, C.c_int64, dp, C.c_int]
             L.or_assemble_blocks.restype = C.c_int64
@@ -155,6 +158,20 @@ def region_moments(vTp, x, delta, strategy, nmc=0, seed=1, idT=0, idTp=0, q=0):
     acc = lib().or_region_moments(_p(v, C.c_double), _p(xx, C.c_double), float(delta), int(strategy), int(nmc),
                                   int(seed), int(idT), int(idTp), int(q), _p(M, C.c_double), _p(mv, C.c_double))
     return M, float(mv[0]), int(acc)
+
+
+def cap_samples(vTp, x, delta, nmc, seed=1, idT=0, idTp=0, q=0):
+    """The fullcaps Monte Carlo samples of one (T', x) case, as the assembly
+    draws them: (y [n,3], cell [n], accepted [n]) with n = nmc, or n = 0 when
+    T' has no cap for x."""
+    v = _f64(vTp).reshape(12)
+    xx = _f64(x).reshape(3)
+    y = np.zeros((max(nmc, 1), 3))
+    cell = np.zeros(max(nmc, 1), dtype=np.int32)
+    acc = np.zeros(max(nmc, 1), dtype=np.uint8)
+    n = lib().or_cap_samples(_p(v, C.c_double), _p(xx, C.c_double), float(delta), int(nmc), int(seed), int(idT),
+                             int(idTp), int(q), _p(y, C.c_double), _p(cell, C.c_int32), _p(acc, C.c_uint8))
+    return y[:n], cell[:n], acc[:n].astype(bool)
 
 
 def pair_block(vT, vTp, delta, gamma, tp_in_collar, strategy, nmc=0, seed=1, idT=0, idTp=0):

@@ -845,6 +845,41 @@ void or_mc_point(const double *Sflat, int ns, const uint32_t u[4], double y[3], 
     if (which) *which = j;
 }
 
+/* The Monte Carlo samples of the cap S = T' minus hull(I u P) around x
+ * (Sec. 4.3.2, Alg. 4).  The cap exists only when T' meets the closed ball:
+ * some vertex inside, or, with none inside, the distance from x to T' at
+ * most delta.  Then nmc samples are drawn with key = seed and counter
+ * (idT, idTp, q, k); each is handed to fn with its cap cell and whether
+ * |y - x|^2 <= delta^2, together with the weight |S|/nmc.  Returns the number
+ * of samples drawn (0 when there is no cap).                                */
+typedef void (*sample_fn)(void *ctx, int k, const double y[3], int cell, int accepted, double wgt);
+
+static int cap_samples(const double v[4][3], const double vTp[12], const double x[3], double delta,
+                       const classify_t *c, int nmc, uint64_t seed, uint32_t idT, uint32_t idTp, uint32_t q,
+                       sample_fn fn, void *ctx)
+{
+    if (c->m == 4 || nmc <= 0) return 0;
+    if (c->m == 0 && !(or_dist2_point_tet(x, vTp) <= delta * delta)) return 0;
+    double S[3][4][3];
+    int ns = cap_cells(v, c, S);
+    double tot = 0.0;
+    for (int j = 0; j < ns; ++j) tot += tet_volume(S[j][0], S[j][1], S[j][2], S[j][3]);
+    double wgt = tot / (double)nmc;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double d2 = delta * delta;
+    for (int k = 0; k < nmc; ++k) {
+        uint32_t ctr[4] = {idT, idTp, q, (uint32_t)k}, u[4];
+        or_philox4x32_10(ctr, key, u);
+        double y[3];
+        int which = 0;
+        or_mc_point(&S[0][0][0], ns, u, y, &which);
+        double w[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
+        double r2 = (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2];
+        fn(ctx, k, y, which, r2 <= d2, wgt);
+    }
+    return nmc;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Moments of the approximate ball inside T' around x: M[0] = |R|,
  * M[1+a] = int_R lambda'_a, M[5..14] = int_R lambda'_a lambda'_b (a<=b,
@@ -862,6 +897,24 @@ static void add_point(double M[15], const double v[4][3], const double y[3], dou
     int k = 5;
     for (int a = 0; a < 4; ++a)
         for (int b = a; b < 4; ++b) M[k++] += w * lam[a] * lam[b];
+}
+
+/* accepted samples add 1, lambda'(y) and lambda'(y) lambda'(y)^T times |S|/N */
+struct moments_ctx {
+    double *M;
+    const double (*v)[3];
+    int acc;
+    double *mc_vol;
+};
+
+static void moments_sample(void *p, int k, const double y[3], int cell, int accepted, double wgt)
+{
+    struct moments_ctx *ctx = (struct moments_ctx *)p;
+    (void)k; (void)cell;
+    if (!accepted) return;
+    add_point(ctx->M, ctx->v, y, wgt);
+    ctx->acc++;
+    if (ctx->mc_vol) *ctx->mc_vol += wgt;
 }
 
 int or_region_moments(const double vTp[12], const double x[3], double delta, int strategy,
@@ -882,33 +935,10 @@ int or_region_moments(const double vTp[12], const double x[3], double delta, int
         or_quad_points(flat, yq);
         for (int k = 0; k < 4; ++k) add_point(M, v, yq + 3 * k, vol / 4.0);
     }
-    int acc = 0;
-    if (strategy == OR_FULLCAPS && c.m < 4 && nmc > 0) {
-        /* the cap exists only if T' meets the ball (Alg. 4) */
-        if (c.m > 0 || or_dist2_point_tet(x, vTp) <= delta * delta) {
-            double S[3][4][3];
-            int ns = cap_cells(v, &c, S);
-            double tot = 0.0;
-            for (int j = 0; j < ns; ++j) tot += tet_volume(S[j][0], S[j][1], S[j][2], S[j][3]);
-            double wgt = tot / (double)nmc;
-            uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-            double d2 = delta * delta;
-            for (int k = 0; k < nmc; ++k) {
-                uint32_t ctr[4] = {idT, idTp, q, (uint32_t)k}, u[4];
-                or_philox4x32_10(ctr, key, u);
-                double y[3];
-                or_mc_point(&S[0][0][0], ns, u, y, NULL);
-                double w[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
-                double r2 = (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2];
-                if (r2 <= d2) {
-                    add_point(M, v, y, wgt);
-                    acc++;
-                    if (mc_vol) *mc_vol += wgt;
-                }
-            }
-        }
-    }
-    return acc;
+    struct moments_ctx mc = {M, v, 0, mc_vol};
+    if (strategy == OR_FULLCAPS)
+        cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, q, moments_sample, &mc);
+    return mc.acc;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -923,6 +953,24 @@ static void add_block(double blk[64], const double lx[4], const double v[4][3], 
     for (int a = 0; a < 4; ++a) { d[a] = -lx[a]; d[4 + a] = lam[a]; }
     for (int i = 0; i < 8; ++i)
         for (int j = 0; j < 8; ++j) blk[8 * i + j] += w * d[i] * d[j];
+}
+
+/* accepted samples add omega (gamma/2) w_q (|S|/N) d d^T */
+struct block_ctx {
+    double *blk;
+    const double *lx;
+    const double (*v)[3];
+    double coef;
+    int acc;
+};
+
+static void block_sample(void *p, int k, const double y[3], int cell, int accepted, double wgt)
+{
+    struct block_ctx *ctx = (struct block_ctx *)p;
+    (void)k; (void)cell;
+    if (!accepted) return;
+    add_block(ctx->blk, ctx->lx, ctx->v, y, ctx->coef * wgt);
+    ctx->acc++;
 }
 
 int or_pair_block(const double vT[12], const double vTp[12], double delta, double gamma,
@@ -953,28 +1001,43 @@ int or_pair_block(const double vT[12], const double vTp[12], double delta, doubl
             or_quad_points(flat, yq);
             for (int k = 0; k < 4; ++k) add_block(blk, lx, v, yq + 3 * k, coef * (vol / 4.0));
         }
-        if (strategy == OR_FULLCAPS && c.m < 4 && nmc > 0) {
-            if (c.m > 0 || or_dist2_point_tet(x, vTp) <= delta * delta) {
-                double S[3][4][3];
-                int ns = cap_cells(v, &c, S);
-                double tot = 0.0;
-                for (int j = 0; j < ns; ++j) tot += tet_volume(S[j][0], S[j][1], S[j][2], S[j][3]);
-                double wgt = tot / (double)nmc;
-                uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-                double d2 = delta * delta;
-                for (int k = 0; k < nmc; ++k) {
-                    uint32_t ctr[4] = {idT, idTp, (uint32_t)q, (uint32_t)k}, u[4];
-                    or_philox4x32_10(ctr, key, u);
-                    double y[3];
-                    or_mc_point(&S[0][0][0], ns, u, y, NULL);
-                    double w[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
-                    double r2 = (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2];
-                    if (r2 <= d2) { add_block(blk, lx, v, y, coef * wgt); acc++; }
-                }
-            }
+        if (strategy == OR_FULLCAPS) {
+            struct block_ctx bc = {blk, lx, v, coef, 0};
+            cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, (uint32_t)q, block_sample, &bc);
+            acc += bc.acc;
         }
     }
     return acc;
+}
+
+/* The Monte Carlo samples of one (T', x) case as the assembly draws them:
+ * y[3k..3k+2] the point, cell[k] its cap cell, accepted[k] = 1 when
+ * |y - x|^2 <= delta^2 (arrays of nmc entries).  Returns the number of
+ * samples drawn (0 when T' has no cap for x: all four vertices inside, or
+ * T' not meeting the closed ball).                                          */
+struct record_ctx {
+    double *y;
+    int32_t *cell;
+    uint8_t *acc;
+};
+
+static void record_sample(void *p, int k, const double y[3], int cell, int accepted, double wgt)
+{
+    struct record_ctx *ctx = (struct record_ctx *)p;
+    (void)wgt;
+    ctx->y[3 * k] = y[0]; ctx->y[3 * k + 1] = y[1]; ctx->y[3 * k + 2] = y[2];
+    ctx->cell[k] = cell;
+    ctx->acc[k] = (uint8_t)accepted;
+}
+
+int or_cap_samples(const double vTp[12], const double x[3], double delta, int nmc, uint64_t seed,
+                   uint32_t idT, uint32_t idTp, uint32_t q, double *y, int32_t *cell, uint8_t *accepted)
+{
+    const double (*v)[3] = (const double (*)[3])vTp;
+    classify_t c;
+    classify(v, x, delta, &c);
+    struct record_ctx rc = {y, cell, accepted};
+    return cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, q, record_sample, &rc);
 }
 
 /* Blocks for a list of pairs (one 8x8 block per pair, rows/cols = the four

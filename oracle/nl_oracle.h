@@ -25,6 +25,8 @@ void or_mc_point(const double *S, int ns, const uint32_t u[4], double y[3], int 
 int or_region_moments(const double vTp[12], const double x[3], double delta, int strategy,
                       int nmc, uint64_t seed, uint32_t idT, uint32_t idTp, uint32_t q,
                       double M[15], double *mc_vol);
+int or_cap_samples(const double vTp[12], const double x[3], double delta, int nmc, uint64_t seed,
+                   uint32_t idT, uint32_t idTp, uint32_t q, double *y, int32_t *cell, uint8_t *accepted);
 int or_pair_block(const double vT[12], const double vTp[12], double delta, double gamma,
                   int tp_in_collar, int strategy, int nmc, uint64_t seed,
                   uint32_t idT, uint32_t idTp, double blk[64]);

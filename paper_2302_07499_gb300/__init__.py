@@ -10,4 +10,5 @@ package is the Python binding.
 """
 from ._binding import (APPROXCAPS, BARYCENTER, INSIDE, OVERLAP, DEVICE, FP32_COMP, FP64, FULLCAPS, HOST, MAT_A, MAT_K, NOCAPS, Device,  # noqa
                        Mesh, NlError, Pairs, System, lib, probe_moments, probe_philox, EXPORTED, LIB_PATH,
-                       kernel_launches, Batch, Server, mesh_box)
+                       kernel_launches, Batch, Server, mesh_box, probe_mc_samples,
+                       probe_alu_rates)

@@ -115,7 +115,8 @@ EXPORTED = ["nl_mesh_create", "nl_mesh_destroy", "nl_pairs_build", "nl_pairs_des
             "nl_system_stats", "nl_solve", "nl_probe_moments", "nl_probe_philox", "nl_last_error", "nl_version", "nl_kernel_launches",
             "nl_solve_static", "nl_batch_create", "nl_batch_run", "nl_batch_system", "nl_batch_get_info",
             "nl_batch_destroy", "nl_mesh_create_box", "nl_server_create", "nl_server_submit", "nl_server_poll",
-            "nl_server_wait", "nl_server_release", "nl_server_get_load", "nl_server_destroy", "nl_spmv_time"]
+            "nl_server_wait", "nl_server_release", "nl_server_get_load", "nl_server_destroy", "nl_spmv_time",
+            "nl_probe_mc_samples", "nl_probe_alu_rates"]
 
 _lib = None
 
@@ -146,6 +147,8 @@ def lib():
     L.nl_solve.argtypes = [vp, C.POINTER(nl_solve_opts), vp, C.c_int, C.POINTER(nl_solve_info)]
     L.nl_probe_moments.argtypes = [vp, vp, vp, i64, dp, C.c_int, C.c_int, C.c_uint64, C.c_int, vp]
     L.nl_probe_philox.argtypes = [vp, C.c_uint64, i64, vp]
+    L.nl_probe_alu_rates.argtypes = [vp, C.c_int]
+    L.nl_probe_mc_samples.argtypes = [vp, vp, vp, i64, dp, C.c_int, C.c_uint64, C.c_int, vp, vp, vp, vp]
     L.nl_last_error.restype = C.c_char_p
     L.nl_version.restype = C.c_char_p
     L.nl_kernel_launches.restype = C.c_uint64
@@ -566,6 +569,34 @@ def probe_moments(tets_xyz, x, ids, delta, strategy, mc_points=0, seed=1, precis
     _check(lib().nl_probe_moments(_ptr(tv), _ptr(xs), _ptr(ii), n, float(delta), int(strategy), int(mc_points),
                                   int(seed), int(precision), _ptr(out)))
     return out
+
+
+def probe_mc_samples(tets_xyz, x, ids, delta, mc_points, seed=1, precision=FP64):
+    """(n_samples [n], cell [n, mc], accepted [n, mc], y [n, mc, 3]) of the
+    fullcaps Monte Carlo samples of single cases (nl_probe_mc_samples)."""
+    tv = np.ascontiguousarray(tets_xyz, dtype=np.float64).reshape(-1, 12)
+    xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    ii = np.ascontiguousarray(ids, dtype=np.uint32).reshape(-1, 3)
+    n = tv.shape[0]
+    ns = np.zeros(n, dtype=np.int32)
+    cell = np.zeros((n, mc_points), dtype=np.int32)
+    acc = np.zeros((n, mc_points), dtype=np.uint8)
+    y = np.zeros((n, mc_points, 3))
+    _check(lib().nl_probe_mc_samples(_ptr(tv), _ptr(xs), _ptr(ii), n, float(delta), int(mc_points), int(seed),
+                                     int(precision), _ptr(ns), _ptr(cell), _ptr(acc), _ptr(y)))
+    return ns, cell, acc.astype(bool), y
+
+
+ALU_RATE_NAMES = ("ffma_fp32", "dfma_fp64", "mad_lo_u32", "mul_hi_u32", "xor3_as_2", "philox_ops",
+                  "fullcaps_sample_ops")
+
+
+def probe_alu_rates():
+    """Measured operations per second of the ALU microbenchmarks of
+    nl_probe_alu_rates, by name."""
+    out = np.zeros(len(ALU_RATE_NAMES))
+    _check(lib().nl_probe_alu_rates(_ptr(out), out.size))
+    return dict(zip(ALU_RATE_NAMES, out.tolist()))
 
 
 def probe_philox(ctr, key):

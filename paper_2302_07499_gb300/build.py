@@ -17,7 +17,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 # the method follow a fixed operation order there
 NO_FMA = {"nl_pairs.cu", "nl_assemble64.cu"}
 SOURCES = ["nl_util.cu", "nl_pairs.cu", "nl_assemble64.cu", "nl_assemble32.cu", "nl_reduce.cu",
-           "nl_api.cu", "nl_solve.cu", "nl_probe.cu", "nl_batch.cu", "nl_server.cu"]
+           "nl_api.cu", "nl_solve.cu", "nl_probe.cu", "nl_batch.cu", "nl_server.cu", "nl_peaks.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
           "-I", CSRC]

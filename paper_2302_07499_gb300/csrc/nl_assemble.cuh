@@ -741,10 +741,11 @@ struct RoundKeys {
     uint32_t k[20];
 };
 
-template <class R, int STRAT>
+template <class R, int STRAT, bool REC = false>
 __global__ void k_probe(const double *__restrict__ tv, const double4 *__restrict__ tv4, const double *__restrict__ xs,
                         const uint32_t *__restrict__ ids, int64_t n, double delta2, int nmc,
-                        const __grid_constant__ RoundKeys rk, double *out, int *defer)
+                        const __grid_constant__ RoundKeys rk, double *out, int *defer, double *rec = nullptr,
+                        int *nrec = nullptr)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
@@ -781,9 +782,11 @@ __global__ void k_probe(const double *__restrict__ tv, const double4 *__restrict
     // approxcaps hull's scratch (that strategy does not sample)
     __align__(16) R cb[3 * nlq::CB_STRIDE];
     static_assert(3 * nlq::CB_STRIDE >= nlq::HULL_SCRATCH, "hull scratch");
-    const int d = nlq::point_moments<R, STRAT>(v, xx, (R)delta2, (R)vol, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
-                                               ids[3 * c + 2], M, st, sizeof(R) == 4 ? &sx : nullptr, cb,
-                                               nlq::CB_STRIDE, nlq::HullScratch<R>{cb, 1});
+    const int d = nlq::point_moments<R, STRAT, REC>(v, xx, (R)delta2, (R)vol, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
+                                                    ids[3 * c + 2], M, st, sizeof(R) == 4 ? &sx : nullptr, cb,
+                                                    nlq::CB_STRIDE, nlq::HullScratch<R>{cb, 1},
+                                                    REC ? rec + (int64_t)5 * nmc * c : nullptr,
+                                                    REC ? nrec + c : nullptr);
     defer[c] = d;
     if (d) return;
     out[15 * c] = (double)M.m0;
@@ -809,6 +812,21 @@ __global__ void k_probe_fp64(const double *__restrict__ tv, const double *__rest
     nlq::event_moments<double, STRAT>(v, x, delta2, defer[c] - 1, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
                                       ids[3 * c + 2], m15, st, nullptr, nullptr, 0, nlq::HullScratch<double>{hb, 1});
     for (int k = 0; k < 15; ++k) out[15 * c + k] = (double)(float)m15[k];
+}
+
+// The fullcaps Monte Carlo samples of each case (REC instantiation of the
+// probe kernel): rec[c][k][5] = (cap cell, accepted, y), nrec[c] = samples
+// drawn (0 without a cap or for a deferred case).
+template <class R>
+void launch_probe_samples(const double *tv, const double4 *tv4, const double *xs, const uint32_t *ids, int64_t n,
+                          double delta2, int nmc, uint64_t seed, double *out, int *defer, double *rec, int *nrec)
+{
+    RoundKeys key;
+    philox_round_keys(seed, key.k);
+    unsigned blocks = (unsigned)((n + 127) / 128);
+    k_probe<R, 2, true><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, nmc, key, out, defer, rec, nrec);
+    nl_count_launch();
+    NL_CHECK_LAUNCH();
 }
 
 template <class R>

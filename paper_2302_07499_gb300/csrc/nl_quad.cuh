@@ -967,11 +967,14 @@ __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, 
 // rows stay in T''s own vertex order (the roles only select).  Approxcaps
 // goes to event_moments_generic.
 //   cb, cs: per-thread scratch for the sampling cells, cell j at cb + j cs.
+//   REC, rec: with REC (the diagnostic probe only), sample k is recorded at
+//   rec[5k..5k+4] = (cap cell, accepted, y) with y global (FP64) or relative
+//   to x (FP32).
 //   Returns true when the event is deferred (see event_moments_generic).
-template <class R, int STRAT, bool DIAG_INLINE = true>
+template <class R, int STRAT, bool DIAG_INLINE = true, bool REC = false>
 __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
                               uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs,
-                              const HullScratch<R> &hs)
+                              const HullScratch<R> &hs, double *rec = nullptr)
 {
     if constexpr (STRAT == 1) {
         return event_moments_generic<R, STRAT, DIAG_INLINE>(v, x, d2, inm, nmc, rk, idT, idTp, q, out, st, sx, cb,
@@ -1212,6 +1215,10 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
                 int j64 = 0;
                 inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64) != 0;
             }
+            if constexpr (REC) {
+                rec[5 * k] = 0.0; rec[5 * k + 1] = inb ? 1.0 : 0.0;
+                rec[5 * k + 2] = (double)w.x; rec[5 * k + 3] = (double)w.y; rec[5 * k + 4] = (double)w.z;
+            }
             const R f = inb ? R(1) : R(0);
             acc += inb ? 1u : 0u;
             cnt += f;
@@ -1295,7 +1302,12 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
                 int j64 = j;
                 inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64) != 0;
                 c = cb + cs * j64;
+                if constexpr (REC) j = j64;
             }
+        }
+        if constexpr (REC) {
+            rec[5 * k] = (double)j; rec[5 * k + 1] = inb ? 1.0 : 0.0;
+            rec[5 * k + 2] = (double)y.x; rec[5 * k + 3] = (double)y.y; rec[5 * k + 4] = (double)y.z;
         }
         // branch-free accumulation of the accepted sample (the sums of
         // lambda' are the row sums of lambda' lambda'^T: lambda' sums to 1)
@@ -1344,12 +1356,15 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
 
 // Moments for one (T', x) including classification: used by the diagnostic
 // probe; the assembly splits the two steps across kernels.
-template <class R, int STRAT>
+template <class R, int STRAT, bool REC = false>
 // Returns the classification + 1 when the event is deferred to FP64, else 0.
+// With REC the Monte Carlo samples go to rec (see event_moments) and *nrec
+// receives their number (0 when there is no cap).
 __device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, const uint32_t *rk, uint32_t idT,
                              uint32_t idTp, uint32_t q, Mom<R> &M, Stats &st, const Strict *sx, R *cb, int cs,
-                             const HullScratch<R> &hs)
+                             const HullScratch<R> &hs, double *rec = nullptr, int *nrec = nullptr)
 {
+    if constexpr (REC) *nrec = 0;
     int inm = classify(v, x, d2, sx);
     if constexpr (STRAT >= 3) {
         if (element_full<R, STRAT>(v, x, d2, inm, sx)) {
@@ -1370,7 +1385,10 @@ __device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, 
         return 0;
     }
     R o[15];
-    if (event_moments<R, STRAT>(v, x, d2, inm, nmc, rk, idT, idTp, q, o, st, sx, cb, cs, hs)) return inm + 1;
+    const uint32_t mc0 = st.mc;
+    if (event_moments<R, STRAT, true, REC>(v, x, d2, inm, nmc, rk, idT, idTp, q, o, st, sx, cb, cs, hs, rec))
+        return inm + 1;
+    if constexpr (REC) *nrec = (int)(st.mc - mc0);
     M.m0 = o[0];
     for (int k = 0; k < 4; ++k) M.m1[k] = o[1 + k];
     for (int k = 0; k < 10; ++k) M.m2[k] = o[5 + k];

@@ -112,3 +112,47 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     s = bench.ClockSampler(0)
     s.start()
     assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_entry_errors_metric():
+    """The bench's per-entry error: relative to the entry, with the floors
+    for near-zero entries (1e-3 of the diagonals' geometric mean, 1e-7 of the
+    largest diagonal)."""
+    import numpy as np
+    rp = np.array([0, 2, 4])
+    ci = np.array([0, 1, 0, 1])
+    ref = np.array([4.0, 1e-9, 1e-9, 1.0])
+    got = ref * np.array([1 + 1e-6, 1.0, 1.0, 1.0]) + np.array([0.0, 2e-6, 0.0, 0.0])
+    e = bench.entry_errors((rp, ci, got), (rp, ci, ref))
+    assert abs(e[0] - 1e-6) < 1e-15
+    assert abs(e[1] - 2e-6 / (1e-3 * 2.0)) < 1e-12          # floor: 1e-3 sqrt(4 * 1)
+    assert e[2] == 0.0 and e[3] == 0.0
+
+
+def test_l2_error_of_the_interpolant_of_the_quadratic():
+    """For u = |x|^2 the P1 interpolant's error on an element is
+    sum_{i<j} lambda_i lambda_j |v_i - v_j|^2; its square integrates exactly
+    from the monomial integrals of the barycentrics, which the bench's
+    degree-5 rule must reproduce."""
+    import math
+    import numpy as np
+    import nl_inputs as I
+    mesh = I.kuhn_box(-0.25, 1.25, 6, jitter_frac=0.2, seed=5)
+    u = (mesh.verts ** 2).sum(axis=1)
+    got = bench.l2_error_quadratic(mesh, u)
+
+    def mono(alpha, vol):
+        return vol * 6.0 * math.prod(math.factorial(a) for a in alpha) / math.factorial(sum(alpha) + 3)
+    pairs = [(i, j) for i in range(4) for j in range(i + 1, 4)]
+    want = 0.0
+    for t in np.nonzero(mesh.tet_in_omega)[0]:
+        v = mesh.verts[mesh.tets[t]]
+        vol = abs(np.linalg.det(v[1:] - v[0])) / 6
+        c = {p: float(np.sum((v[p[0]] - v[p[1]]) ** 2)) for p in pairs}
+        for p in pairs:
+            for r in pairs:
+                alpha = [0, 0, 0, 0]
+                for k in p + r:
+                    alpha[k] += 1
+                want += c[p] * c[r] * mono(alpha, vol)
+    assert abs(got - math.sqrt(want)) <= 1e-12 * math.sqrt(want)

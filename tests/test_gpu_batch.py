@@ -76,3 +76,44 @@ def test_batch_equals_single_problem_assembly(nl, autotune, use_graph):
     u, inf = batch.system(0).solve(rtol=1e-10)
     assert inf["status"] == 0
     batch.close()
+
+
+def test_batched_problems_match_the_oracle(nl):
+    """Batched systems against the CPU oracle directly (not only against the
+    single-problem path): K and A per entry, b against the oracle's system,
+    for an FP64 fullcaps, an FP64 approxcaps and an FP32-comp fullcaps problem
+    of one batch."""
+    import oracle as O
+    from _helpers import FLOOR_FP64, entry_rel_err
+    dev = nl.Device()
+    spec = [((4, 2, 0.2, 5), dict(strategy=nl.FULLCAPS, mc_points=32, seed=3, precision=nl.FP64)),
+            ((3, 3, 0.2, 6), dict(strategy=nl.APPROXCAPS, precision=nl.FP64)),
+            ((5, 1, 0.2, 7), dict(strategy=nl.FULLCAPS, mc_points=16, seed=1, precision=nl.FP32_COMP))]
+    meshes, items = [], []
+    for (inv_h, ratio, jit, seed), kw in spec:
+        mesh, delta = I.cube_problem(inv_h, ratio, jitter_frac=jit, seed=seed)
+        kw = dict(kw, gamma=I.gamma_const(delta), f_const=-6.0, g=I.quadratic_g(mesh.verts))
+        m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+        meshes.append((mesh, delta, kw, m))
+        items.append((nl.Pairs(m, delta), kw))
+    batch = nl.Batch(items, autotune=False, use_graph=True)
+    batch.run()
+    for i, (mesh, delta, kw, _) in enumerate(meshes):
+        s = batch.system(i)
+        fp64 = kw["precision"] == nl.FP64
+        tol, floor = (1e-12, FLOOR_FP64) if fp64 else (1e-5, 1e-7)
+        Kref = O.assemble_K(mesh, delta, kw["gamma"], kw["strategy"], nmc=kw.get("mc_points", 0),
+                            seed=kw.get("seed", 1))
+        assert entry_rel_err(s.scipy(nl.MAT_K), Kref, floor) <= tol, i
+        A, b, free = O.system(mesh, Kref, O.load_vector(mesh, -6.0), kw["g"])
+        assert entry_rel_err(s.scipy(nl.MAT_A), A, floor) <= tol, i
+        bg, fn = s.rhs()
+        assert np.array_equal(fn.cpu().numpy(), free)
+        # b_i = F_i - sum_j K_ij g_j over the collar nodes: with entries within
+        # tol, b_i is within tol of the sum of the terms' magnitudes
+        con = np.nonzero(mesh.node_free == 0)[0]
+        F = O.load_vector(mesh, -6.0)
+        mag = np.abs(F[free]) + abs(Kref.tocsr()[free][:, con]) @ np.abs(kw["g"][con])
+        assert np.all(np.abs(bg.cpu().numpy() - b) <= tol * mag + 1e-15 * np.abs(b).max()), i
+    assert batch.info()["hull_fallbacks"] == 0
+    batch.close()

@@ -1,15 +1,17 @@
 """Parity at the benchmark's full sizes and in its launch configuration
-(FP32-comp, fullcaps, the whole pair list in the bench's chunking): sampled
-outputs that the oracle computes one by one, and properties that hold at any
-size.
+(fullcaps FP32-comp at configs 2 and 3, fullcaps FP64 and approxcaps FP32-comp
+at config 2; the whole pair list in the bench's chunking): sampled outputs
+that the oracle computes one by one, and properties that hold at any size.
 
   * pair lists of sampled outer elements: bit-exact against the oracle's
     grid search for those elements;
   * sampled rows of K: the oracle sums the 8x8 blocks of every pair that
-    touches the row's node; entries within the FP32-comp bar (1e-5, per-entry
-    metric with the floors of the small-size tests);
-  * the whole K: exactly symmetric; row sums zero to 1e-6 of the row's
-    absolute sum (the moments of one (pair, point) are FP32).
+    touches the row's node; entries within the bar of the precision (FP64
+    1e-12, FP32-comp 1e-5; per-entry metric with the floors of the small-size
+    tests);
+  * the whole K: exactly symmetric; row sums zero to 1e-13 (FP64) or 1e-6
+    (FP32-comp: the moments of one (pair, point) are FP32) of the row's
+    absolute sum.
 """
 import numpy as np
 import pytest
@@ -59,12 +61,13 @@ def _oracle_row(mesh, delta, gamma, strategy, nmc, seed, node):
     return row
 
 
-def _check_case(nl, mesh, delta, strategy, nmc, n_outer_sample, rows, tol):
+def _check_case(nl, mesh, delta, strategy, nmc, n_outer_sample, rows, tol, precision=None, floor=1e-7):
     dev = nl.Device()
     gamma = I.gamma_const(delta)
     m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
     p = nl.Pairs(m, delta)
-    s = nl.System(p, strategy=strategy, mc_points=nmc, seed=1, precision=nl.FP32_COMP, gamma=gamma, f_const=-6.0,
+    prec = nl.FP32_COMP if precision is None else precision
+    s = nl.System(p, strategy=strategy, mc_points=nmc, seed=1, precision=prec, gamma=gamma, f_const=-6.0,
                   g=I.quadratic_g(mesh.verts))
     assert s.stats()["hull_fallbacks"] == 0
     # sampled pair lists
@@ -79,7 +82,7 @@ def _check_case(nl, mesh, delta, strategy, nmc, n_outer_sample, rows, tol):
     assert abs(K - K.T).max() == 0.0
     rs = np.abs(np.asarray(K.sum(axis=1)).ravel())
     ras = np.asarray(abs(K).sum(axis=1)).ravel()
-    assert np.all(rs <= 1e-6 * ras)
+    assert np.all(rs <= (1e-13 if prec == nl.FP64 else 1e-6) * ras)
     # sampled rows against the oracle
     diag = K.diagonal()
     for node in rows:
@@ -90,7 +93,7 @@ def _check_case(nl, mesh, delta, strategy, nmc, n_outer_sample, rows, tol):
         scale = np.abs(diag).max()
         for c, v in got.items():
             rv = ref.get(c, 0.0)
-            den = max(abs(rv), 1e-3 * np.sqrt(abs(diag[node] * diag[c])), 1e-7 * scale)
+            den = max(abs(rv), 1e-3 * np.sqrt(abs(diag[node] * diag[c])), floor * scale)
             assert abs(v - rv) <= tol * den, (node, c, v, rv)
 
 
@@ -107,3 +110,21 @@ def test_fullsize_jitter38_fullcaps128_fp32(nl):
     m1 = 39
     rows = [19 + m1 * (19 + m1 * 19), 4 + m1 * (20 + m1 * 17)]
     _check_case(nl, mesh, delta, nl.FULLCAPS, 128, 100, rows, 1e-5)
+
+
+def _cube24_rows():
+    m1 = 25
+    return [12 + m1 * (12 + m1 * 12), 5 + m1 * (12 + m1 * 12), 3 + m1 * (3 + m1 * 10)]
+
+
+def test_fullsize_cube24_fullcaps64_fp64(nl):
+    """The FP64 form of the bench workload's assembly: every decision and
+    every sample point of the specification, entries within 1e-12."""
+    from _helpers import FLOOR_FP64
+    mesh, delta = I.config_mesh("cube24_d0125")
+    _check_case(nl, mesh, delta, nl.FULLCAPS, 64, 100, _cube24_rows(), 1e-12, precision=nl.FP64, floor=FLOOR_FP64)
+
+
+def test_fullsize_cube24_approxcaps_fp32(nl):
+    mesh, delta = I.config_mesh("cube24_d0125")
+    _check_case(nl, mesh, delta, nl.APPROXCAPS, 0, 100, _cube24_rows(), 1e-5)
