@@ -6,7 +6,10 @@ precompute, element-pair search and sparsity pattern, quadrature +
 deterministic reduction into K, A and b, and the CG solve.  The metric is
 element pairs per second of that step (plus p50/p99 step latency), for the
 FP32-compensated form, with the plain FP64 form of the same step reported
-beside it.
+beside it.  The default workload is the unstructured-like mesh: the Kuhn grid
+of the unit cube plus a 3h collar at h = 1/32 with interior vertices jittered
+by up to 0.2h (329,232 elements), delta = 3h, fullcaps with 128 Monte Carlo
+points.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -60,6 +63,76 @@ OPS_PER_ACCEPTED = 31
 OPS_PER_CUT = 300
 OPS_PER_PAIR_POINT = 28
 ALU_LANES_PER_SM = 128
+DEFAULT_WORKLOAD = "jitter38_d3h_fullcaps128"
+
+
+def entry_errors(K, Kref):
+    """Per-entry relative errors of K against Kref (same pattern), with the
+    floor of the parity tests for near-zero entries:
+    |a - r| / max(|r_ij|, 1e-3 sqrt(|r_ii r_jj|), 1e-7 max_k |r_kk|)."""
+    rp, ci, v = K
+    rp0, ci0, v0 = Kref
+    assert np.array_equal(rp, rp0) and np.array_equal(ci, ci0)
+    n = rp.size - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    d = np.zeros(n)
+    dm = ci0 == rows
+    d[rows[dm]] = np.abs(v0[dm])
+    den = np.maximum(np.maximum(np.abs(v0), 1e-3 * np.sqrt(d[rows] * d[ci0])), 1e-7 * d.max())
+    return np.abs(v - v0) / np.where(den > 0, den, 1.0)
+
+
+def _gm_rule_degree5():
+    """Grundmann-Moeller rule of degree 5 on the tetrahedron (Grundmann &
+    Moeller, SIAM J. Numer. Anal. 15 (1978)): barycentric points, weights
+    summing to one."""
+    from math import factorial
+    s, n = 2, 3
+    d = 2 * s + 1
+    pts, wts = [], []
+
+    def comps(total, parts):
+        if parts == 1:
+            yield (total,)
+            return
+        for i in range(total + 1):
+            for rest in comps(total - i, parts - 1):
+                yield (i,) + rest
+    for i in range(s + 1):
+        w = (-1) ** i * 2.0 ** (-2 * s) * (d + n - 2 * i) ** d / (factorial(i) * factorial(d + n - i))
+        for beta in comps(s - i, n + 1):
+            pts.append([(2 * b + 1) / (d + n - 2 * i) for b in beta])
+            wts.append(w * factorial(n))
+    return np.array(pts), np.array(wts)
+
+
+def l2_error_quadratic(mesh, u_nodal):
+    """||u_h - u||_{L2(Omega)} for the manufactured u = |x|^2, u_h the P1
+    interpolant of the nodal solution (degree-5 rule per element of Omega)."""
+    bary, w = _gm_rule_degree5()
+    sel = np.nonzero(mesh.tet_in_omega)[0]
+    v = mesh.verts[mesh.tets[sel]]
+    e = v[:, 1:] - v[:, :1]
+    vol = np.abs(np.einsum("ij,ij->i", e[:, 0], np.cross(e[:, 1], e[:, 2]))) / 6.0
+    x = np.einsum("qk,nkd->nqd", bary, v)
+    uh = np.einsum("qk,nk->nq", bary, u_nodal[mesh.tets[sel]])
+    ue = (x * x).sum(axis=2)
+    return float(np.sqrt(np.sum(vol[:, None] * w[None, :] * (uh - ue) ** 2)))
+
+
+def alu_peak(nl, sm_max_mhz, sms):
+    """The k_events roofline's denominator: the measured rate of the
+    fullcaps sample's own operation mix (register-only microbenchmark at full
+    occupancy, nl_probe_alu_rates), with the per-class rates beside it."""
+    rates = nl.probe_alu_rates()
+    derived = sms * ALU_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
+    return rates["fullcaps_sample_ops"] / 1e12, {
+        "source": "measured: nl_probe_alu_rates, the fullcaps sample's operation mix (a Philox4x32-10 draw, the "
+                  "cell choice, three uniforms, their sort, the spacings, the point and the ball test; 121 ops) "
+                  "in registers at 64 warps per SM, best of 3",
+        "rates_tops": {k: v / 1e12 for k, v in rates.items()},
+        "derived_issue_peak_tops": derived,
+        "derived_note": "%d SMs x %d lanes x 1 op/clk x %.0f MHz" % (sms, ALU_LANES_PER_SM, sm_max_mhz)}
 
 
 def _measured_peak(key, fallback):
@@ -210,7 +283,7 @@ def run_ours(args, ws, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(precision, mixed, record=None):
+    def step(precision, mixed, keep=False):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         ev[0].record(stream)
         m = nl.Mesh(d_verts, d_tets, d_om, d_free, dev)
@@ -227,6 +300,9 @@ def run_ours(args, ws, rank, local):
         out = {"total_ms": t[3], "mesh_ms": t[0], "pairs_ms": t[1] - t[0], "assemble_ms": t[2] - t[1],
                "solve_ms": t[3] - t[2], "npairs": p.info["n_pairs"], "stats": s.stats(), "cg": info,
                "nnz_a": p.info["nnz_a"], "n_free": p.info["n_free"], "nnz": p.info["nnz"]}
+        if keep:      # outside every timed region: the matrix and the solution for the accuracy report
+            out["K"] = s.csr_numpy(nl.MAT_K)
+            out["u"] = d_u.cpu().numpy().copy()
         s.close(); p.close(); m.close()
         return out
 
@@ -258,16 +334,25 @@ def run_ours(args, ws, rank, local):
     npairs = steps[0]["npairs"]
     value = replica_throughput(ws, npairs, t_max)
 
-    # FP64 form of the same step (fewer steps: the FP64 pipe is narrow on this part)
+    # the FP32-comp step once more, untimed, for its matrix and solution
+    kept32 = step(nl.FP32_COMP, True, keep=True)
+
+    # FP64 form of the same step (fewer steps: the FP64 pipe is narrow on this
+    # part).  Its kernels are warmed up on the small cube6 problem.
     fp64 = None
+    accuracy = None
     if args.fp64_steps > 0:
-        for _ in range(1):
-            flush_l2()
-            step(nl.FP64, False)
+        wm, wd = I.config_mesh("cube6_d025")
+        wmesh = nl.Mesh(wm.verts, wm.tets, wm.tet_in_omega, wm.node_free, dev)
+        wp = nl.Pairs(wmesh, wd)
+        ws_ = nl.System(wp, strategy=strategy, mc_points=nmc, seed=seed, precision=nl.FP64, gamma=I.gamma_const(wd),
+                        f_const=-6.0, g=I.quadratic_g(wm.verts))
+        ws_.solve(rtol=rtol)
+        ws_.close(); wp.close(); wmesh.close()
         r64 = []
-        for _ in range(args.fp64_steps):
+        for k in range(args.fp64_steps):
             flush_l2()
-            r64.append(step(nl.FP64, False))
+            r64.append(step(nl.FP64, False, keep=(k == args.fp64_steps - 1)))
         m64 = float(np.mean([r["total_ms"] for r in r64]))
         fp64 = {"value": npairs / (m64 / 1e3), "unit": UNIT, "ms_per_step": m64,
                 "assemble_ms": float(np.mean([r["assemble_ms"] for r in r64])),
@@ -275,6 +360,24 @@ def run_ours(args, ws, rank, local):
                 "cg_iterations": r64[0]["cg"]["iterations"], "steps": args.fp64_steps,
                 "p50_ms": float(np.percentile([r["total_ms"] for r in r64], 50)),
                 "p99_ms": float(np.percentile([r["total_ms"] for r in r64], 99))}
+        # accuracy of the FP32-comp form against the FP64 form of the same run
+        # (the FP64 path matches the CPU oracle to 1e-12 per entry in the
+        # parity tests), and of both solutions against the manufactured u
+        err = entry_errors(kept32["K"], r64[-1]["K"])
+        l2_32 = l2_error_quadratic(mesh, kept32["u"])
+        l2_64 = l2_error_quadratic(mesh, r64[-1]["u"])
+        accuracy = {"entry_rel_err_fp32comp_vs_fp64": {"max": float(err.max()),
+                                                       "p99_9": float(np.percentile(err, 99.9)),
+                                                       "entries": int(err.size), "bar": 1e-5},
+                    "l2_error_vs_exact_u": {"fp32comp_mixed_cg": l2_32, "fp64_cg": l2_64,
+                                            "ratio": l2_32 / l2_64 if l2_64 > 0 else None, "bar_ratio": 1.01},
+                    "cg": {"fp32comp_mixed": {"iterations": kept32["cg"]["iterations"],
+                                              "refinements": kept32["cg"]["refinements"],
+                                              "rel_residual": kept32["cg"]["rel_residual"]},
+                           "fp64": {"iterations": r64[-1]["cg"]["iterations"],
+                                    "rel_residual": r64[-1]["cg"]["rel_residual"]}},
+                    "metric": "per entry |a - r| / max(|r_ij|, 1e-3 sqrt(|r_ii r_jj|), 1e-7 max |r_kk|) over all "
+                              "entries of K; L2 over Omega with the degree-5 Grundmann-Moeller rule"}
 
     # end to end through the C-ABI with host buffers (H2D of the inputs and D2H
     # of the solution inside the timed region)
@@ -325,13 +428,13 @@ def run_ours(args, ws, rank, local):
     ops = _event_ops(st)
     props = torch.cuda.get_device_properties(local)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = props.multi_processor_count * ALU_LANES_PER_SM * sm_max * 1e6 / 1e12
+    peak, peak_info = alu_peak(nl, sm_max, props.multi_processor_count)
     achieved = ops / (ems / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_events<float,%s>" % STRAT_NAME[strategy],
                 "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": _traffic_record(),
-                "peak_source": "derived: %d SMs x %d lanes x 1 op/clk x %.0f MHz (no measured ALU peak)"
-                % (props.multi_processor_count, ALU_LANES_PER_SM, sm_max),
+                "peak_source": peak_info["source"], "peak_detail": peak_info,
+                "frac_of_derived_issue_peak": achieved / peak_info["derived_issue_peak_tops"],
                 "algorithmic_ops_per_step": ops, "kernel_ms_per_step": ems, "share_of_step": ems / ms_mean,
                 "quadrature": {"kernels": "k_classify + k_events + k_combine", "ms": qms,
                                "algorithmic_ops": _quadrature_ops(st),
@@ -339,6 +442,8 @@ def run_ours(args, ws, rank, local):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds)
+        one = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds / 2, threads=1)
+        cpu["one_core"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
 
     phases = {k: float(np.mean([s_[k] for s_ in steps])) for k in ("mesh_ms", "pairs_ms", "assemble_ms", "solve_ms")}
     phases["quadrature_ms"] = qms
@@ -350,8 +455,9 @@ def run_ours(args, ws, rank, local):
         "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": args.workload,
-                   "mesh": "%s: Kuhn grid, %d tets, %d vertices, delta=%g, gamma=15/(2 pi delta^5)"
-                   % (cfg, mesh.nt, mesh.nv, delta),
+                   "mesh": "%s: Kuhn grid%s, %d tets, %d vertices, delta=%g, gamma=15/(2 pi delta^5)"
+                   % (cfg, ", interior vertices jittered by up to 0.2h (seed 7)" if cfg.startswith("jitter") else "",
+                      mesh.nt, mesh.nv, delta),
                    "strategy": STRAT_NAME[strategy], "mc_points": nmc, "seed": seed,
                    "precision": "FP32 per-(pair,point) arithmetic, FP64 accumulation and entries",
                    "solve": "mixed CG (FP32 inner, FP64 residual/updates) to rel. residual %g" % rtol,
@@ -363,6 +469,7 @@ def run_ours(args, ws, rank, local):
         "cg": {"iterations": steps[-1]["cg"]["iterations"], "refinements": steps[-1]["cg"]["refinements"],
                "rel_residual": steps[-1]["cg"]["rel_residual"]},
         "fp64": fp64,
+        "accuracy": accuracy,
         "roofline": roofline,
         "spmv": spmv,
         "cpu_baseline": cpu,
@@ -378,13 +485,13 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
-def cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=15.0):
-    """The oracle as it stands, on the host cores, over a bounded contiguous
-    sample of outer elements of the same workload (pair search + per-pair
-    blocks + accumulation into K)."""
+def cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=15.0, threads=0):
+    """The oracle as it stands, on the host cores (all of them, or `threads`),
+    over a bounded contiguous sample of outer elements of the same workload
+    (pair search + per-pair blocks + accumulation into K)."""
     import oracle as O
     outer_all = np.nonzero(mesh.tet_in_omega)[0].astype(np.int32)
-    cores = O.num_threads()
+    cores = threads or O.num_threads()
 
     def run(outer):
         t0 = time.perf_counter()
@@ -394,7 +501,7 @@ def cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=15.0):
         O.blocks_to_matrix(mesh, pT, pTp, blocks)
         return len(pT), time.perf_counter() - t0
 
-    n0 = min(len(outer_all), 64)
+    n0 = min(len(outer_all), 64 if cores > 1 else 8)
     np0, t0 = run(outer_all[:n0])
     n1 = int(min(len(outer_all), max(n0, n0 * budget_s / max(t0, 1e-3))))
     npairs, t = run(outer_all[:n1])
@@ -634,8 +741,9 @@ def main():
                          "5 for batch256_seed3, whose steps take seconds)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cube24_d0125_fullcaps64", choices=sorted(WORKLOADS) + ["batch256_seed3", "serve_stream_seed5"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch256_seed3", "serve_stream_seed5"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 form (each takes ~17 s on "
+                    "the default workload)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=300, help="workload serve_stream_seed5: requests replayed")
