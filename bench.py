@@ -106,6 +106,20 @@ def _gm_rule_degree5():
     return np.array(pts), np.array(wts)
 
 
+def l2_error(mesh, u_nodal, exact):
+    """||u_h - u||_{L2(Omega)}, u_h the P1 interpolant of the nodal solution,
+    u = exact(points) (degree-5 Grundmann-Moeller rule per element of Omega)."""
+    bary, w = _gm_rule_degree5()
+    sel = np.nonzero(mesh.tet_in_omega)[0]
+    v = mesh.verts[mesh.tets[sel]]
+    e = v[:, 1:] - v[:, :1]
+    vol = np.abs(np.einsum("ij,ij->i", e[:, 0], np.cross(e[:, 1], e[:, 2]))) / 6.0
+    x = np.einsum("qk,nkd->nqd", bary, v)
+    uh = np.einsum("qk,nk->nq", bary, u_nodal[mesh.tets[sel]])
+    ue = exact(x)
+    return float(np.sqrt(np.sum(vol[:, None] * w[None, :] * (uh - ue) ** 2)))
+
+
 def l2_error_quadratic(mesh, u_nodal):
     """||u_h - u||_{L2(Omega)} for the manufactured u = |x|^2, u_h the P1
     interpolant of the nodal solution (degree-5 rule per element of Omega)."""
@@ -409,8 +423,10 @@ def run_ours(args, ws, rank, local):
     spmv = {}
     for name, prec in (("fp64", nl.FP64), ("fp32", nl.FP32_COMP)):
         ms_, by = s.spmv_time(prec, reps=50)
+        msc, _ = s.spmv_time(prec, reps=20, flush_bytes=512 * 2 ** 20)
         spmv[name] = {"ms": ms_, "bytes": by, "achieved_gbs": by / (ms_ / 1e3) / 1e9,
-                      "frac_of_measured_hbm": by / (ms_ / 1e3) / 1e9 / hbm[0]}
+                      "frac_of_measured_hbm": by / (ms_ / 1e3) / 1e9 / hbm[0],
+                      "cold_l2_ms": msc, "frac_of_measured_hbm_cold_l2": by / (msc / 1e3) / 1e9 / hbm[0]}
     spmv["peak_gbs"] = hbm[0]
     spmv["peak_source"] = hbm[1]
     spmv["a_bytes_fp64"] = int(steps[0]["nnz_a"] * 12)
@@ -430,6 +446,11 @@ def run_ours(args, ws, rank, local):
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak, peak_info = alu_peak(nl, sm_max, props.multi_processor_count)
     achieved = ops / (ems / 1e3) / 1e12
+    # the FP64 SpMV also needs one FP64 multiply-add per entry: on this part
+    # the measured DFMA rate puts a floor under its time next to HBM's
+    dfma = peak_info["rates_tops"]["dfma_fp64"] * 1e12
+    spmv["fp64"]["dfma_floor_ms"] = steps[0]["nnz_a"] / dfma * 1e3
+    spmv["fp64"]["frac_of_measured_dfma"] = spmv["fp64"]["dfma_floor_ms"] / spmv["fp64"]["ms"]
     roofline = {"bound": "alu", "kernel": "k_events<float,%s>" % STRAT_NAME[strategy],
                 "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": _traffic_record(),
@@ -525,7 +546,8 @@ def run_batch(args, ws, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     dev = nl.Device()
-    spec = I.batch_problems(256, 3)
+    small = args.workload == "batch256_small"
+    spec = I.batch_problems_small(256, 3) if small else I.batch_problems(256, 3)
     problems = []
     for inv_h, ratio, strat in spec:
         mesh, delta = I.cube_problem(inv_h, ratio)
@@ -592,10 +614,11 @@ def run_batch(args, ws, rank, local):
     value = total_pairs / (sum(batch_ms) / 1e3)
     solo_value = total_pairs / (sum(solo_ms) / 1e3)
     tets = [6 * (inv_h + 2 * r) ** 3 for inv_h, r, _ in spec]
-    line = {"metric": "batched assembly element-pairs/s (256 problems)", "value": value, "unit": UNIT,
+    line = {"metric": "batched assembly element-pairs/s (256 %sproblems)" % ("small " if small else ""),
+            "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": 1, "ms_per_step": float(sum(batch_ms)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch256_seed3", "problems": len(spec), "tets_min": min(tets),
+            "config": {"workload": args.workload, "problems": len(spec), "tets_min": min(tets),
                        "tets_max": max(tets), "tets_total": int(sum(tets)), "element_pairs": total_pairs,
                        "strategies": {STRAT_NAME[k]: sum(1 for x in spec if x[2] == k) for k in range(3)},
                        "precision": "FP32-comp", "mc_points": 64, "seed": 1,
@@ -694,6 +717,105 @@ def run_serve(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_spmv(args, ws, rank, local):
+    """The CG's SpMV on the jittered 38^3 workload's A (delta = 3h; 29,791
+    unknowns, 13.2 M entries): A is assembled (nocaps, FP32-comp: the SpMV
+    does not depend on the values' origin), everything but the system is
+    released, and the kernel is timed back to back (as in CG, where A partly
+    stays in the 129 MB L2) and, launch by launch, after a write of 512 MiB
+    that flushes L2 (the HBM-bound figure).  Small in device memory, so that
+    a profiler can replay it."""
+    import torch
+    import paper_2302_07499_gb300 as nl
+
+    torch.cuda.set_device(local)
+    mesh, delta = I.config_mesh("jitter38_d3h")
+    dev = nl.Device()
+    m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+    p = nl.Pairs(m, delta)
+    s = nl.System(p, strategy=nl.NOCAPS, precision=nl.FP32_COMP, gamma=I.gamma_const(delta), f_const=-6.0)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    hbm = _measured_peak("hbm_gbs", 6800.0)
+    out = {}
+    for name, prec in (("fp32", nl.FP32_COMP), ("fp64", nl.FP64)):
+        ms_b2b, by = s.spmv_time(prec, reps=args.steps)
+        ms_cold, _ = s.spmv_time(prec, reps=args.steps, flush_bytes=512 * 2 ** 20)
+        out[name] = {"bytes": by, "back_to_back_us": ms_b2b * 1e3, "cold_l2_us": ms_cold * 1e3,
+                     "frac_of_measured_hbm_back_to_back": by / (ms_b2b / 1e3) / 1e9 / hbm[0],
+                     "frac_of_measured_hbm_cold_l2": by / (ms_cold / 1e3) / 1e9 / hbm[0]}
+    line = {"metric": "CG SpMV GB/s on the jittered 38^3 workload's A", "unit": "fraction of measured HBM",
+            "value": out["fp32"]["frac_of_measured_hbm_back_to_back"], "higher_is_better": True, "n_gpus": ws,
+            "config": {"workload": "jitter38_d3h_spmv", "n_free": p.info["n_free"], "nnz_A": p.info["nnz_a"],
+                       "kernel": "k_spmv_dot_pad (rows padded to multiples of 4 entries, 8 lanes per row)"},
+            "hbm_peak_gbs": hbm[0], "hbm_peak_source": hbm[1], "spmv": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+PAPER3D_STRATEGIES = (("overlap", 4, 0), ("inside", 5, 0), ("barycenter", 3, 0), ("nocaps", 0, 0),
+                      ("approxcaps", 1, 0), ("fullcaps", 2, 128))
+
+
+def run_paper3d(args, ws, rank, local):
+    """The shape of the paper's 3D experiment (Sec. 5, Tables 3D_error and
+    3D_time): Omega = (0,1)^3, delta = 0.1, kernel integral 3, u = prod
+    x_i (1 - x_i) with f = -L u in closed form and g = u on the collar, on
+    jittered Kuhn meshes (the stand-in for the unstructured meshes) with
+    1/h from --paper3d-inv-h.  Per mesh and strategy: the L2 error of the
+    solution (FP32-comp assembly, mixed CG to 1e-10) and the assembly's device
+    time (quadrature + reduction); per strategy the efficiency ratio
+    lambda_n = -log(e_{n-1}/e_n) / log(t_{n-1}/t_n) between consecutive
+    meshes."""
+    import torch
+    import paper_2302_07499_gb300 as nl
+
+    torch.cuda.set_device(local)
+    dev = nl.Device()
+    delta = I.PAPER3D_DELTA
+    gamma = I.paper3d_gamma(delta)
+    rows = []
+    launches0 = nl.kernel_launches()
+    for inv_h in [int(x) for x in args.paper3d_inv_h.split(",")]:
+        mesh = I.paper3d_mesh(inv_h, delta)
+        e = mesh.verts[mesh.tets]
+        edges = [np.linalg.norm(e[:, a] - e[:, b], axis=1) for a in range(4) for b in range(a + 1, 4)]
+        h_avg = float(np.mean(np.concatenate(edges)))
+        f = I.paper3d_f(mesh.verts, delta)
+        g = I.paper3d_u(mesh.verts)
+        m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+        p = nl.Pairs(m, delta)
+        for name, code, nmc in PAPER3D_STRATEGIES:
+            sys_ = nl.System(p, strategy=code, mc_points=max(nmc, 1), seed=1, precision=nl.FP32_COMP, gamma=gamma,
+                             f_const=0.0, g=g, f=f)
+            st = sys_.stats()
+            u, info = sys_.solve(rtol=1e-10, mixed=True)
+            rows.append({"inv_h": inv_h, "h_avg": h_avg, "delta_over_h": delta * inv_h, "tets": mesh.nt,
+                         "element_pairs": p.info["n_pairs"], "strategy": name, "mc_points": nmc,
+                         "assembly_ms": st["quadrature_ms"] + st["reduce_ms"],
+                         "l2_error": l2_error(mesh, u, I.paper3d_u), "cg_iterations": info["iterations"],
+                         "rel_residual": info["rel_residual"]})
+            sys_.close()
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        p.close(); m.close()
+    lam = {}
+    for name, _, _ in PAPER3D_STRATEGIES:
+        r = [x for x in rows if x["strategy"] == name]
+        lam[name] = [-float(np.log(a["l2_error"] / b["l2_error"]) / np.log(a["assembly_ms"] / b["assembly_ms"]))
+                     for a, b in zip(r[:-1], r[1:])]
+    line = {"metric": "paper 3D experiment shape: L2 error and assembly time per strategy", "unit": "ms, L2 error",
+            "value": None, "n_gpus": ws, "higher_is_better": False, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "paper3d_delta01", "omega": "(0,1)^3", "delta": delta,
+                       "kernel": "constant, integral 3 over the ball (library gamma = 9/(2 pi delta^3))",
+                       "u": "prod x_i (1 - x_i)", "f": "-L u in closed form (nodal, P1-interpolated)",
+                       "g": "u at the collar nodes", "mesh": "Kuhn grid of the unit cube plus a ceil(delta/h)-cell "
+                       "collar, interior vertices jittered by up to 0.2h (seed 7)",
+                       "precision": "FP32-comp assembly, mixed CG to 1e-10"},
+            "rows": rows, "lambda": lam, "gpu_launches": int(nl.kernel_launches() - launches0)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -741,7 +863,9 @@ def main():
                          "5 for batch256_seed3, whose steps take seconds)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch256_seed3", "serve_stream_seed5"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch256_seed3", "serve_stream_seed5",
+                                                                           "paper3d_delta01", "batch256_small",
+                                                                           "jitter38_d3h_spmv"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 form (each takes ~17 s on "
                     "the default workload)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -749,18 +873,24 @@ def main():
     ap.add_argument("--requests", type=int, default=300, help="workload serve_stream_seed5: requests replayed")
     ap.add_argument("--fp64-requests", type=int, default=60, help="workload serve_stream_seed5: FP64 prefix")
     ap.add_argument("--workers", type=int, default=4, help="workload serve_stream_seed5: server workers")
+    ap.add_argument("--paper3d-inv-h", default="18,21,24,28,32,36,40",
+                    help="workload paper3d_delta01: 1/h of the meshes of the sweep")
     ap.add_argument("--batch-pairs", type=float, default=6e8,
                     help="element-pair budget of one sub-batch (workload batch256_seed3)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 5 if args.workload == "batch256_seed3" else 20
+        args.steps = 5 if args.workload in ("batch256_seed3", "batch256_small") else 20
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
-    elif args.workload == "batch256_seed3":
+    elif args.workload in ("batch256_seed3", "batch256_small"):
         run_batch(args, ws, rank, local)
     elif args.workload == "serve_stream_seed5":
         run_serve(args, ws, rank, local)
+    elif args.workload == "paper3d_delta01":
+        run_paper3d(args, ws, rank, local)
+    elif args.workload == "jitter38_d3h_spmv":
+        run_spmv(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

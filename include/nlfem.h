@@ -46,7 +46,9 @@ typedef enum {
     NL_ECUDA = 3,       /* CUDA runtime error (message in nl_last_error) */
     NL_ENOTCONV = 4,    /* CG stopped at max_iter above the tolerance */
     NL_ETIMEOUT = 5,    /* a bounded device wait gave up */
-    NL_EBUSY = 6        /* resource limit reached (server queue full) */
+    NL_EBUSY = 6,       /* resource limit reached (server queue full) */
+    NL_EGEOM = 7        /* a geometric construction of the method failed (an approxcaps
+                           hull beyond its capacity); no result is returned */
 } nl_status;
 
 /* Ball strategies: the three of Sec. 3.3 / 4.3.2 and the element-level ones of
@@ -63,7 +65,7 @@ typedef enum {
 } nl_strategy;
 typedef enum { NL_FP64 = 0, NL_FP32_COMP = 1 } nl_precision;
 typedef enum { NL_HOST = 0, NL_DEVICE = 1 } nl_where;
-typedef enum { NL_MAT_K = 0, NL_MAT_A = 1 } nl_matrix;
+typedef enum { NL_MAT_K = 0, NL_MAT_A = 1, NL_MAT_LIFT = 2 } nl_matrix;
 
 /* Device context: allocator hooks (for example PyTorch's caching allocator)
  * and the stream all work is ordered on.  alloc must return memory usable on
@@ -109,10 +111,19 @@ void nl_mesh_destroy(nl_mesh *mesh);
  * Omega = [omega_lo, omega_hi]^3, whose bounds must be grid planes: an
  * element belongs to Omega when its cube does, a node is free when it lies
  * strictly inside.  The result is an nl_mesh as from nl_mesh_create.
+ * Jitter (a stand-in for the unstructured meshes of Sec. 5): with
+ * jitter_frac > 0 every vertex lying on none of the planes of the box and of
+ * Omega moves by (2 U_d - 1) * (jitter_frac * h) along axis d, where
+ * U_d = (w_d + 1/2) 2^-32 and w = Philox4x32-10 of the counter
+ * (vertex id, 0, 0, 0) under the key (seed mod 2^32, seed div 2^32).  Moves
+ * are applied class by class over the eight parity classes
+ * (i%2 + 2 (j%2) + 4 (k%2) = 0..7), whose vertices share no element; a move
+ * is kept only if every element holding the vertex keeps a positive signed
+ * volume.  Omega stays exactly [omega_lo, omega_hi]^3.
  * Errors: NL_EINVAL (cells outside 1..1000, hi <= lo, Omega bounds not on
- * grid planes), NL_ENOMEM, NL_ECUDA. */
+ * grid planes, jitter_frac outside [0, 0.5)), NL_ENOMEM, NL_ECUDA. */
 nl_status nl_mesh_create_box(const nl_device *dev, double lo, double hi, int32_t cells, double omega_lo,
-                             double omega_hi, nl_mesh **out);
+                             double omega_hi, double jitter_frac, uint64_t seed, nl_mesh **out);
 
 /* ---------------------------------------------------------------------------
  * nl_pairs_build — element pairs and the fixed sparsity pattern for a horizon
@@ -135,6 +146,7 @@ typedef struct {
     int64_t n_free, nnz_a;             /* unknowns and nnz of A = K[free,free] */
     int32_t max_row;                   /* longest row of K */
     double delta;
+    int64_t nnz_lift;                  /* nnz of K[free, collar] */
 } nl_pairs_info;
 nl_status nl_pairs_get_info(const nl_pairs *pairs, nl_pairs_info *info);
 
@@ -161,9 +173,13 @@ nl_status nl_pairs_export(const nl_pairs *pairs, int32_t *outer, int64_t *ptr, i
  * With g the nodal volume constraint: A = K[free,free] and
  * b_i = sum_T sum_q w_q phi_i(x_q) f - sum_{j not free} K_ij g_j.
  *   gamma      kernel constant inside the ball (e.g. 15/(2 pi delta^5)).
- *   f_const    constant source f.
+ *   f_const    constant part of the source f.
  *   g_nodal    [n_vert] nodal values of g (only collar nodes are read);
  *              NULL means g = 0.  g_where: NL_HOST or NL_DEVICE.
+ *   f_nodal    [n_vert] nodal values of the rest of the source (only nodes of
+ *              elements of Omega are read), or NULL: f = f_const + the P1
+ *              interpolant of f_nodal, integrated with the same 4-point rule
+ *              (Eq. Fh).  f_where: NL_HOST or NL_DEVICE.
  *   precision  NL_FP64: every step in FP64 (decisions follow a fixed
  *              operation order without fused multiply-add);
  *              NL_FP32_COMP: the per-(pair, point) geometry, Monte Carlo
@@ -172,7 +188,12 @@ nl_status nl_pairs_export(const nl_pairs *pairs, int32_t *outer, int64_t *ptr, i
  *              FP64; matrix entries are FP64.
  * Deterministic: the same inputs give bitwise the same K and b (no floating-
  * point atomics).  Errors: NL_EINVAL (strategy, precision, mc_points outside
- * 1..4096 for fullcaps, gamma not finite), NL_ENOMEM, NL_ECUDA. */
+ * 1..4096 for fullcaps, gamma not finite), NL_ENOMEM, NL_ECUDA, NL_EGEOM
+ * (approxcaps: a hull of the arc midpoints could not be completed within its
+ * capacity; no system is returned rather than one with nocaps cells in its
+ * place).
+ * The environment variable NL_HULL_MAX_FACES (8..24) lowers the hull's face
+ * capacity, for tests of that path only. */
 typedef struct {
     int strategy;            /* nl_strategy */
     int mc_points;           /* fullcaps samples per cap (ignored otherwise) */
@@ -182,6 +203,8 @@ typedef struct {
     double f_const;
     const double *g_nodal;
     int g_where;
+    const double *f_nodal;   /* NULL: constant f */
+    int f_where;
 } nl_assemble_opts;
 
 nl_status nl_assemble(nl_pairs *pairs, const nl_assemble_opts *opts, nl_system **out);
@@ -190,7 +213,10 @@ void nl_system_destroy(nl_system *sys);
 /* Device views of an assembled matrix (no copy; valid until destroy).
  * NL_MAT_K: full matrix over all nodes (rows/cols = node ids).
  * NL_MAT_A: the free block, rows/cols numbered by increasing node id among
- *           free nodes. */
+ *           free nodes.
+ * NL_MAT_LIFT: K[free, collar], the block that lifts the volume constraint to
+ *           the right-hand side (Sec. 2.2: b = F - K[free, collar] g); rows as
+ *           for NL_MAT_A, columns = node ids of the collar nodes (sorted). */
 typedef struct {
     int64_t n_rows, nnz;
     const int64_t *rowptr;   /* device, n_rows+1 */
@@ -242,6 +268,10 @@ typedef struct {
     int iterations;        /* CG iterations (inner iterations for mixed) */
     int refinements;       /* outer refinement steps (mixed) */
     double rel_residual;   /* final ||b - A u|| / ||b|| in FP64 */
+    int barrier_fallbacks; /* systems up to 16384 unknowns run each CG loop in one cooperative
+                              launch whose grid barriers wait at most a second (the environment
+                              variable NL_CG_BARRIER_WAIT_NS sets another limit, for tests); loops
+                              that gave up a wait and were redone with separate launches */
 } nl_solve_info;
 
 nl_status nl_solve(nl_system *sys, const nl_solve_opts *opts, double *u_out, int where,
@@ -266,8 +296,9 @@ nl_status nl_solve(nl_system *sys, const nl_solve_opts *opts, double *u_out, int
  *   contents (each call clears or overwrites what it reads).  Calls whose GPU
  *   work overlaps (other threads, other streams) race on the array; order
  *   them, e.g. on one stream.
- *   u_out: device pointer to n_vert doubles (required), written as by
- *   nl_solve.  Work runs on the system's stream; the call synchronises it.
+ *   u_out: device pointer to n_vert doubles on the current device (or
+ *   managed memory; required), written as by nl_solve.  A host pointer gives
+ *   NL_EINVAL.  Work runs on the system's stream; the call synchronises it.
  * Errors: NL_EINVAL, NL_ENOTCONV (u_out holds the last iterate), NL_ECUDA. */
 nl_status nl_solve_static(nl_system *sys, const nl_solve_opts *opts, double *u_out, nl_solve_info *info);
 
@@ -305,7 +336,9 @@ nl_status nl_batch_create(nl_pairs *const *pairs, const nl_assemble_opts *opts, 
                           nl_batch **out);
 
 /* Assemble every problem of the batch (replays the graph when there is one);
- * synchronises the stream before returning.  Errors: NL_EINVAL, NL_ECUDA. */
+ * synchronises the stream before returning.  Errors: NL_EINVAL, NL_ECUDA,
+ * NL_EGEOM (an approxcaps hull of some problem could not be completed, as for
+ * nl_assemble; the batch's systems are then not valid). */
 nl_status nl_batch_run(nl_batch *batch);
 
 /* The system of problem i (the caller's order), owned by the batch.
@@ -355,14 +388,17 @@ typedef struct {
     int32_t cells;
     double omega_lo, omega_hi; /* Omega = [omega_lo, omega_hi]^3 (grid planes) */
     double delta;
-    nl_assemble_opts assemble; /* g_nodal must be NULL */
+    nl_assemble_opts assemble; /* g_nodal and f_nodal must be NULL */
     int g_quadratic;           /* 1: volume constraint g = |x|^2 at the collar nodes; 0: g = 0 */
     nl_solve_opts solve;
+    double jitter_frac;        /* vertex jitter of the box mesh (as nl_mesh_create_box; 0: none) */
+    uint64_t jitter_seed;
 } nl_request;
 enum { NL_REQ_QUEUED = 0, NL_REQ_RUNNING = 1, NL_REQ_DONE = 2 };
 typedef struct {
     int state;                 /* NL_REQ_* */
-    nl_status status;          /* when done: NL_OK, NL_ENOTCONV (u = last iterate) or the error */
+    nl_status status;          /* when done: NL_OK, NL_ENOTCONV (u = last iterate) or the error
+                                  (NL_EGEOM as for nl_assemble) */
     double t_submit, t_start, t_done;
     double assemble_ms, solve_ms;   /* device time of the assembly and of the solve */
     int64_t n_pairs, n_free, n_vert, est_bytes;
@@ -441,13 +477,20 @@ nl_status nl_probe_mc_samples(const double *tets_xyz, const double *x, const uin
  * NL_ECUDA. */
 nl_status nl_probe_philox(const uint32_t *ctr, uint64_t key, int64_t n, uint32_t *out);
 
-/* nl_spmv_time — device time of one SpMV y = A x of the CG (warp per row,
- * the kernel nl_solve runs) on the system's free block A, FP64 values or the
- * FP32 copy, averaged over `reps` back-to-back launches after one untimed
- * launch (CUDA events on the system's stream).  bytes_per_spmv (optional):
- * the algorithmic traffic nnz (value + column index) + rowptr + x + y.
- * Errors: NL_EINVAL, NL_ECUDA. */
-nl_status nl_spmv_time(nl_system *sys, int precision, int reps, double *ms_per_spmv, double *bytes_per_spmv);
+/* nl_spmv_time — device time of one SpMV y = A x of the CG (the kernel
+ * nl_solve runs for systems above 16384 unknowns: A's rows padded to
+ * multiples of 4 entries, 8 lanes per row, 16-byte loads) on the system's
+ * free block A, FP64 values or the FP32 copy, with the partials of x.y,
+ * after one untimed launch (CUDA events on the system's stream):
+ *   flush_bytes = 0: averaged over `reps` back-to-back launches (as in the
+ *     CG, where A may partly stay in L2);
+ *   flush_bytes > 0: each of `reps` launches timed alone after a write of
+ *     flush_bytes bytes to a scratch buffer (more than the L2 size evicts A:
+ *     the HBM-bound time).
+ * bytes_per_spmv (optional): the algorithmic traffic nnz (value + column
+ * index) + rowptr + x + y.  Errors: NL_EINVAL, NL_ENOMEM, NL_ECUDA. */
+nl_status nl_spmv_time(nl_system *sys, int precision, int reps, int64_t flush_bytes, double *ms_per_spmv,
+                       double *bytes_per_spmv);
 
 /* nl_probe_alu_rates — measured ALU throughput of the current device, the
  * denominators of the quadrature kernels' ALU roofline (no part of the

@@ -46,6 +46,32 @@ class Mesh:
         return int(self.tets.shape[0])
 
 
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) of counters ctr
+    [N, 4] (uint32) under the key (k0, k1): ten rounds of two 32x32->64-bit
+    multiplications by 0xD2511F53 and 0xCD9E8D57 whose halves are mixed with
+    the other words and the round key, the key bumped by the Weyl constants
+    0x9E3779B9 and 0xBB67AE85 between rounds.  Used here only to draw the mesh
+    jitter, a counter-based stream that any implementation of the generator
+    reproduces vertex by vertex."""
+    c = np.asarray(ctr, dtype=np.uint64).reshape(-1, 4) & 0xFFFFFFFF
+    k0, k1 = np.uint64(key[0] & 0xFFFFFFFF), np.uint64(key[1] & 0xFFFFFFFF)
+    M0, M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+    W0, W1 = np.uint64(0x9E3779B9), np.uint64(0xBB67AE85)
+    mask = np.uint64(0xFFFFFFFF)
+    c0, c1, c2, c3 = c[:, 0], c[:, 1], c[:, 2], c[:, 3]
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + W0) & mask
+            k1 = (k1 + W1) & mask
+        p0 = M0 * c0
+        p1 = M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
+        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    return np.stack([c0, c1, c2, c3], axis=1).astype(np.uint32)
+
+
 def _signed_volumes(verts, tets):
     v = verts[tets]
     e1 = v[:, 1] - v[:, 0]
@@ -67,13 +93,15 @@ def kuhn_box(lo: float, hi: float, cells: int, jitter_frac: float = 0.0,
     a node is free iff it lies strictly inside that box.  Classification uses
     the integer grid indices, so it is exact and unaffected by jitter.
 
-    Jitter: offsets U(-1,1)^3 * jitter_frac * h are drawn for all vertices in
-    vertex order from numpy's PCG64 generator seeded with `seed`.  Only
-    vertices lying on none of the planes x_d in {lo, omega_lo, omega_hi, hi}
-    move, so Omega stays exactly the unit cube.  Moves are applied in the
-    eight parity classes (i%2, j%2, k%2) in order 0..7 (no two vertices of a
-    class share a tetrahedron); a move is kept iff every tetrahedron incident
-    to the vertex keeps a positive signed volume, else the vertex stays put.
+    Jitter: vertex v moves by ((2 U_d - 1) * (jitter_frac * h)) along axis d,
+    with U_d = (w_d + 1/2) 2^-32 and (w_0, w_1, w_2, w_3) the Philox4x32-10
+    words of the counter (v, 0, 0, 0) under the key (seed mod 2^32, seed div
+    2^32), added to its grid position lo + i_d h.  Only vertices lying on
+    none of the planes x_d in {lo, omega_lo, omega_hi, hi} move, so Omega
+    stays exactly the unit cube.  Moves are applied in the eight parity
+    classes (i%2, j%2, k%2) in order 0..7 (no two vertices of a class share a
+    tetrahedron); a move is kept iff every tetrahedron incident to the vertex
+    keeps a positive signed volume, else the vertex stays put.
     """
     n = int(cells)
     h = (hi - lo) / n
@@ -123,8 +151,12 @@ def kuhn_box(lo: float, hi: float, cells: int, jitter_frac: float = 0.0,
     node_free = np.all((idx > o_lo) & (idx < o_hi), axis=1).astype(np.uint8)
 
     if jitter_frac > 0.0:
-        rng = np.random.Generator(np.random.PCG64(seed))
-        off = rng.uniform(-1.0, 1.0, size=(verts.shape[0], 3)) * (jitter_frac * h)
+        nv_ = verts.shape[0]
+        ctr = np.zeros((nv_, 4), dtype=np.uint64)
+        ctr[:, 0] = np.arange(nv_, dtype=np.uint64)
+        w = philox4x32_10(ctr, (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF))[:, :3]
+        U = (w.astype(np.float64) + 0.5) * 2.0 ** -32
+        off = (2.0 * U - 1.0) * (jitter_frac * h)
         fixed = np.any((idx == 0) | (idx == n) | (idx == o_lo) | (idx == o_hi), axis=1)
         # incidence: vertex -> tets
         nt = tets.shape[0]
@@ -204,6 +236,18 @@ def batch_problems(count: int = 256, seed: int = 3):
     return out
 
 
+def batch_problems_small(count: int = 256, seed: int = 3):
+    """Many small problems, where per-problem launches and host
+    synchronisations dominate: 1/h ~ U{8..10}, delta = h, strategy ~ U{0,1,2}."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        inv_h = int(rng.integers(8, 11))
+        strat = int(rng.integers(0, 3))
+        out.append((inv_h, 1, strat))
+    return out
+
+
 def request_stream(count: int = 2000, rate: float = 20.0, seed: int = 5,
                    tets_lo: float = 1e4, tets_hi: float = 4e5):
     """Poisson arrivals; sizes log-uniform in tets; delta/h ~ U[1,4]; strategy
@@ -225,3 +269,45 @@ def request_stream(count: int = 2000, rate: float = 20.0, seed: int = 5,
         reqs.append(dict(arrival=float(t[i]), inv_h=n, ratio=r,
                          strategy=strat, mc=128 if strat == 2 else 0))
     return reqs
+
+
+# ---------------------------------------------------------------------------
+# The paper's 3D experiment (Sec. 5): Omega = (0,1)^3, delta = 0.1, a constant
+# kernel normalised so that its integral over the ball is 3, and the
+# manufactured solution u = prod_i x_i (1 - x_i).  With the operator
+# L u(x) = int_{B_delta(x)} (u(y) - u(x)) gamma dy (the paper's factor 2
+# absorbed into gamma), the library's kernel constant is 2 x 3/|B_delta| =
+# 9/(2 pi delta^3), and f = -L u has a closed form: with p_i = x_i (1 - x_i),
+# u(x + z) = prod_i (p_i + (1 - 2 x_i) z_i - z_i^2), and only even powers of
+# each z_i survive the integral over the ball, so
+#   int_B (u(x+z) - u(x)) dz = -(4 pi delta^5/15) (p2 p3 + p1 p3 + p1 p2)
+#                              + (4 pi delta^7/105) (p1 + p2 + p3) - 4 pi delta^9/945
+# (int z_i^2 = 4 pi delta^5/15, int z_i^2 z_j^2 = 4 pi delta^7/105,
+#  int z_1^2 z_2^2 z_3^2 = 4 pi delta^9/945 over the ball of radius delta).
+
+PAPER3D_DELTA = 0.1
+
+
+def paper3d_gamma(delta: float = PAPER3D_DELTA) -> float:
+    return 9.0 / (2.0 * np.pi * delta ** 3)
+
+
+def paper3d_u(x: np.ndarray) -> np.ndarray:
+    p = x * (1.0 - x)
+    return p[..., 0] * p[..., 1] * p[..., 2]
+
+
+def paper3d_f(x: np.ndarray, delta: float = PAPER3D_DELTA) -> np.ndarray:
+    p = x * (1.0 - x)
+    s2 = p[..., 1] * p[..., 2] + p[..., 0] * p[..., 2] + p[..., 0] * p[..., 1]
+    s1 = p[..., 0] + p[..., 1] + p[..., 2]
+    lu = -(4 * np.pi * delta ** 5 / 15) * s2 + (4 * np.pi * delta ** 7 / 105) * s1 - 4 * np.pi * delta ** 9 / 945
+    return -paper3d_gamma(delta) * lu
+
+
+def paper3d_mesh(inv_h: int, delta: float = PAPER3D_DELTA, jitter_frac: float = 0.2, seed: int = 7) -> Mesh:
+    """Unit cube plus a collar of ceil(delta/h) cells, h = 1/inv_h, interior
+    vertices jittered (the unstructured-like stand-in for the paper's meshes)."""
+    h = 1.0 / inv_h
+    collar = int(np.ceil(delta / h - 1e-12))
+    return kuhn_box(-collar * h, 1.0 + collar * h, inv_h + 2 * collar, jitter_frac=jitter_frac, seed=seed)

@@ -78,7 +78,7 @@ def lib():
             L.or_assemble_blocks.argtypes = [dp, i32p, u8p, C.c_double, C.c_double, C.c_int, C.c_int,
                                              C.c_uint64, i32p, i32p, C.c_int64, dp, C.c_int]
             L.or_assemble_blocks.restype = C.c_int64
-            L.or_load_vector.argtypes = [dp, i32p, C.c_int64, u8p, C.c_int64, C.c_double, dp]
+            L.or_load_vector.argtypes = [dp, i32p, C.c_int64, u8p, C.c_int64, C.c_double, dp, dp]
             L.or_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -249,14 +249,17 @@ def assemble_K(mesh, delta, gamma, strategy, nmc=0, seed=1, prs=None, nthreads=0
     return blocks_to_matrix(mesh, pT, pTp, blocks)
 
 
-def load_vector(mesh, fconst):
+def load_vector(mesh, fconst, f_nodal=None):
+    """F_i = int_Omega phi_i f with the 4-point rule, f = fconst + the P1
+    interpolant of f_nodal (optional)."""
     L = lib()
     verts = _f64(mesh.verts)
     tets = np.ascontiguousarray(mesh.tets, dtype=np.int32)
     om = np.ascontiguousarray(mesh.tet_in_omega, dtype=np.uint8)
     F = np.zeros(mesh.nv)
+    fn = None if f_nodal is None else _f64(f_nodal)
     L.or_load_vector(_p(verts, C.c_double), _p(tets, C.c_int32), mesh.nt, _p(om, C.c_uint8), mesh.nv,
-                     float(fconst), _p(F, C.c_double))
+                     float(fconst), None if fn is None else _p(fn, C.c_double), _p(F, C.c_double))
     return F
 
 

@@ -1064,9 +1064,11 @@ int64_t or_assemble_blocks(const double *verts, const int32_t *tets, const uint8
     return acc;
 }
 
-/* Load vector F_i = sum_{T in Omega} sum_q w_q phi_i(x_q) f (constant f). */
+/* Load vector F_i = sum_{T in Omega} sum_q w_q phi_i(x_q) f(x_q) (Eq. Fh with
+ * the 4-point rule), f = fconst + the P1 interpolant of the nodal values
+ * fnodal (NULL: constant f).                                                */
 void or_load_vector(const double *verts, const int32_t *tets, int64_t nt, const uint8_t *in_omega,
-                    int64_t nv, double fconst, double *F)
+                    int64_t nv, double fconst, const double *fnodal, double *F)
 {
     memset(F, 0, sizeof(double) * (size_t)nv);
     for (int64_t t = 0; t < nt; ++t) {
@@ -1078,7 +1080,10 @@ void or_load_vector(const double *verts, const int32_t *tets, int64_t nt, const 
         for (int q = 0; q < 4; ++q) {
             double lam[4];
             barycentric((const double (*)[3])v, xq + 3 * q, lam);
-            for (int a = 0; a < 4; ++a) F[tets[4 * t + a]] += w * lam[a] * fconst;
+            double f = fconst;
+            if (fnodal)
+                for (int a = 0; a < 4; ++a) f += lam[a] * fnodal[tets[4 * t + a]];
+            for (int a = 0; a < 4; ++a) F[tets[4 * t + a]] += w * lam[a] * f;
         }
     }
 }

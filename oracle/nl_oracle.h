@@ -35,6 +35,6 @@ int64_t or_assemble_blocks(const double *verts, const int32_t *tets, const uint8
                            const int32_t *pT, const int32_t *pTp, int64_t npairs,
                            double *blocks, int nthreads);
 void or_load_vector(const double *verts, const int32_t *tets, int64_t nt, const uint8_t *in_omega,
-                    int64_t nv, double fconst, double *F);
+                    int64_t nv, double fconst, const double *fnodal, double *F);
 int or_num_threads(void);
 #endif

@@ -15,15 +15,15 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnlfem.so")
 
-NL_OK, NL_EINVAL, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV, NL_ETIMEOUT, NL_EBUSY = range(7)
+NL_OK, NL_EINVAL, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV, NL_ETIMEOUT, NL_EBUSY, NL_EGEOM = range(8)
 NOCAPS, APPROXCAPS, FULLCAPS = 0, 1, 2
 BARYCENTER, OVERLAP, INSIDE = 3, 4, 5
 FP64, FP32_COMP = 0, 1
 HOST, DEVICE = 0, 1
-MAT_K, MAT_A = 0, 1
+MAT_K, MAT_A, MAT_LIFT = 0, 1, 2
 
 _STATUS = {0: "NL_OK", 1: "NL_EINVAL", 2: "NL_ENOMEM", 3: "NL_ECUDA", 4: "NL_ENOTCONV", 5: "NL_ETIMEOUT",
-           6: "NL_EBUSY"}
+           6: "NL_EBUSY", 7: "NL_EGEOM"}
 
 
 class NlError(RuntimeError):
@@ -43,12 +43,13 @@ class nl_device(C.Structure):
 class nl_pairs_info(C.Structure):
     _fields_ = [("n_vert", C.c_int64), ("n_tet", C.c_int64), ("n_outer", C.c_int64), ("n_pairs", C.c_int64),
                 ("nnz", C.c_int64), ("n_free", C.c_int64), ("nnz_a", C.c_int64), ("max_row", C.c_int32),
-                ("delta", C.c_double)]
+                ("delta", C.c_double), ("nnz_lift", C.c_int64)]
 
 
 class nl_assemble_opts(C.Structure):
     _fields_ = [("strategy", C.c_int), ("mc_points", C.c_int), ("seed", C.c_uint64), ("precision", C.c_int),
-                ("gamma", C.c_double), ("f_const", C.c_double), ("g_nodal", C.c_void_p), ("g_where", C.c_int)]
+                ("gamma", C.c_double), ("f_const", C.c_double), ("g_nodal", C.c_void_p), ("g_where", C.c_int),
+                ("f_nodal", C.c_void_p), ("f_where", C.c_int)]
 
 
 class nl_csr_view(C.Structure):
@@ -89,7 +90,8 @@ class nl_server_opts(C.Structure):
 class nl_request(C.Structure):
     _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("cells", C.c_int32), ("omega_lo", C.c_double),
                 ("omega_hi", C.c_double), ("delta", C.c_double), ("assemble", nl_assemble_opts),
-                ("g_quadratic", C.c_int), ("solve", nl_solve_opts)]
+                ("g_quadratic", C.c_int), ("solve", nl_solve_opts), ("jitter_frac", C.c_double),
+                ("jitter_seed", C.c_uint64)]
 
 
 class nl_result(C.Structure):
@@ -106,7 +108,8 @@ class nl_server_load(C.Structure):
 
 
 class nl_solve_info(C.Structure):
-    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double)]
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double),
+                ("barrier_fallbacks", C.c_int)]
 
 
 # every symbol the header declares (checked by the CPU test suite)
@@ -158,7 +161,7 @@ def lib():
     L.nl_batch_get_info.argtypes = [vp, C.POINTER(nl_batch_info)]
     L.nl_batch_destroy.argtypes = [vp]
     L.nl_batch_destroy.restype = None
-    L.nl_mesh_create_box.argtypes = [C.POINTER(nl_device), dp, dp, C.c_int32, dp, dp, C.POINTER(vp)]
+    L.nl_mesh_create_box.argtypes = [C.POINTER(nl_device), dp, dp, C.c_int32, dp, dp, dp, C.c_uint64, C.POINTER(vp)]
     L.nl_server_create.argtypes = [C.POINTER(nl_server_opts), C.POINTER(vp)]
     L.nl_server_submit.argtypes = [vp, C.POINTER(nl_request), C.POINTER(C.c_uint64)]
     L.nl_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(nl_result)]
@@ -167,7 +170,7 @@ def lib():
     L.nl_server_get_load.argtypes = [vp, C.POINTER(nl_server_load)]
     L.nl_server_destroy.argtypes = [vp]
     L.nl_server_destroy.restype = None
-    L.nl_spmv_time.argtypes = [vp, C.c_int, C.c_int, C.POINTER(dp), C.POINTER(dp)]
+    L.nl_spmv_time.argtypes = [vp, C.c_int, C.c_int, i64, C.POINTER(dp), C.POINTER(dp)]
     _lib = L
     return L
 
@@ -304,24 +307,15 @@ class Pairs:
 
 class System:
     def __init__(self, pairs: Pairs, strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, gamma=1.0,
-                 f_const=0.0, g=None):
+                 f_const=0.0, g=None, f=None):
+        """g: nodal volume constraint; f: nodal source values added to f_const
+        (numpy arrays or CUDA tensors of n_vert doubles, or None)."""
         self.pairs = pairs
-        self._g = None
-        where = HOST
-        gp = None
-        if g is not None:
-            if isinstance(g, np.ndarray):
-                self._g = np.ascontiguousarray(g, dtype=np.float64)
-            else:
-                self._g = g.contiguous().double()
-                where = DEVICE
-            gp = _ptr(self._g)
-        o = nl_assemble_opts(int(strategy), int(mc_points), int(seed), int(precision), float(gamma), float(f_const),
-                             gp, where)
+        o, keep = _assemble_opts(strategy, mc_points, seed, precision, gamma, f_const, g, f)
         h = C.c_void_p()
         _check(lib().nl_assemble(pairs.h, C.byref(o), C.byref(h)))
         self.h = h
-        self._g = None
+        del keep
 
     def csr(self, which=MAT_K):
         """(rowptr, col, val) as torch CUDA tensors viewing library memory (valid until close)."""
@@ -339,7 +333,8 @@ class System:
         import scipy.sparse as sp
         rp, c, v = self.csr_numpy(which)
         n = rp.size - 1
-        return sp.csr_matrix((v, c, rp), shape=(n, n))
+        ncol = self.pairs.info["n_vert"] if which == MAT_LIFT else n
+        return sp.csr_matrix((v, c, rp), shape=(n, ncol))
 
     def rhs(self):
         import torch
@@ -366,15 +361,16 @@ class System:
             where = DEVICE
         st = lib().nl_solve(self.h, C.byref(o), _ptr(u), where, C.byref(inf))
         info = {"iterations": inf.iterations, "refinements": inf.refinements, "rel_residual": inf.rel_residual,
-                "status": st}
+                "barrier_fallbacks": inf.barrier_fallbacks, "status": st}
         if st not in (NL_OK, NL_ENOTCONV):
             _check(st)
         return u, info
 
-    def spmv_time(self, precision=FP64, reps=50):
-        """(ms per SpMV of the CG on A, algorithmic bytes per SpMV)."""
+    def spmv_time(self, precision=FP64, reps=50, flush_bytes=0):
+        """(ms per SpMV of the CG on A, algorithmic bytes per SpMV); with
+        flush_bytes > 0 each launch is timed alone after an L2 flush."""
         ms, by = C.c_double(), C.c_double()
-        _check(lib().nl_spmv_time(self.h, int(precision), int(reps), C.byref(ms), C.byref(by)))
+        _check(lib().nl_spmv_time(self.h, int(precision), int(reps), int(flush_bytes), C.byref(ms), C.byref(by)))
         return ms.value, by.value
 
     def close(self):
@@ -389,21 +385,24 @@ class System:
             pass
 
 
-def _assemble_opts(strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, gamma=1.0, f_const=0.0, g=None):
-    """nl_assemble_opts and the array that must stay alive while the call runs."""
-    keep = None
-    where = HOST
-    gp = None
-    if g is not None:
-        if isinstance(g, np.ndarray):
-            keep = np.ascontiguousarray(g, dtype=np.float64)
-        else:
-            keep = g.contiguous().double()
-            where = DEVICE
-        gp = _ptr(keep)
+def _nodal(a):
+    """(kept array, pointer, where) of optional nodal values."""
+    if a is None:
+        return None, None, HOST
+    if isinstance(a, np.ndarray):
+        k = np.ascontiguousarray(a, dtype=np.float64)
+        return k, _ptr(k), HOST
+    k = a.contiguous().double()
+    return k, _ptr(k), DEVICE
+
+
+def _assemble_opts(strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, gamma=1.0, f_const=0.0, g=None, f=None):
+    """nl_assemble_opts and the arrays that must stay alive while the call runs."""
+    kg, gp, gw = _nodal(g)
+    kf, fp, fw = _nodal(f)
     o = nl_assemble_opts(int(strategy), int(mc_points), int(seed), int(precision), float(gamma), float(f_const),
-                         gp, where)
-    return o, keep
+                         gp, gw, fp, fw)
+    return o, (kg, kf)
 
 
 class _BorrowedSystem(System):
@@ -487,7 +486,8 @@ class Server:
 
     @staticmethod
     def box_request(inv_h, ratio, strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, f_const=-6.0,
-                    g_quadratic=True, rtol=1e-10, mixed=False, max_iter=0, gamma=None):
+                    g_quadratic=True, rtol=1e-10, mixed=False, max_iter=0, gamma=None, jitter_frac=0.0,
+                    jitter_seed=0):
         """The unit-cube problem with h = 1/inv_h, delta = ratio*h and a collar
         of ceil(ratio) cells (the box of the inputs module's cube_problem)."""
         import math
@@ -498,9 +498,10 @@ class Server:
         if gamma is None:
             gamma = 15.0 / (2.0 * math.pi * delta ** 5)
         a = nl_assemble_opts(int(strategy), int(mc_points), int(seed), int(precision), float(gamma), float(f_const),
-                             None, HOST)
+                             None, HOST, None, HOST)
         sv = nl_solve_opts(float(rtol), int(max_iter), int(bool(mixed)), 0.0, 0)
-        return nl_request(lo, hi, inv_h + 2 * collar, 0.0, 1.0, delta, a, int(bool(g_quadratic)), sv)
+        return nl_request(lo, hi, inv_h + 2 * collar, 0.0, 1.0, delta, a, int(bool(g_quadratic)), sv,
+                          float(jitter_frac), int(jitter_seed))
 
     def submit(self, req):
         t = C.c_uint64()
@@ -547,12 +548,12 @@ class Server:
             pass
 
 
-def mesh_box(lo, hi, cells, omega_lo=0.0, omega_hi=1.0, device=None):
-    """nl_mesh_create_box: a Kuhn box mesh generated on the device."""
+def mesh_box(lo, hi, cells, omega_lo=0.0, omega_hi=1.0, device=None, jitter_frac=0.0, seed=0):
+    """nl_mesh_create_box: a Kuhn box mesh (optionally jittered) generated on the device."""
     device = device or Device()
     h = C.c_void_p()
     _check(lib().nl_mesh_create_box(C.byref(device.c), float(lo), float(hi), int(cells), float(omega_lo),
-                                    float(omega_hi), C.byref(h)))
+                                    float(omega_hi), float(jitter_frac), int(seed), C.byref(h)))
     return Mesh.from_handle(h, device, (cells + 1) ** 3, 6 * cells ** 3)
 
 

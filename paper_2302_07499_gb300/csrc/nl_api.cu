@@ -1,9 +1,11 @@
 // C-ABI entry points for assembly and the system handle.
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
 #include "nl_internal.h"
+#include "nl_quad.cuh"
 
 namespace {
 
@@ -15,6 +17,24 @@ __global__ void k_zero_collar_g(const uint8_t *__restrict__ node_free, double *g
 
 }  // namespace
 
+int nl_hull_max_faces()
+{
+    const char *e = getenv("NL_HULL_MAX_FACES");
+    int v = e ? atoi(e) : 0;
+    if (v <= 0 || v > nlq::HULL_MAXF) return nlq::HULL_MAXF;
+    return v < 8 ? 8 : v;
+}
+
+// An assembly whose approxcaps hulls could not all be completed is refused
+// (the cells of another strategy would stand in for them).
+nl_status nl_check_hull_fallbacks(uint64_t fallbacks)
+{
+    if (fallbacks == 0) return NL_OK;
+    nl_set_error("approxcaps: %llu convex hulls could not be completed within the hull's capacity; the system would "
+                 "not be the approxcaps system", (unsigned long long)fallbacks);
+    return NL_EGEOM;
+}
+
 nl_status nl_check_assemble_opts(const nl_assemble_opts *opts)
 {
     if (opts->strategy < NL_NOCAPS || opts->strategy > NL_INSIDE) { nl_set_error("bad strategy"); return NL_EINVAL; }
@@ -25,6 +45,7 @@ nl_status nl_check_assemble_opts(const nl_assemble_opts *opts)
     }
     if (!isfinite(opts->gamma) || !isfinite(opts->f_const)) { nl_set_error("gamma and f_const must be finite"); return NL_EINVAL; }
     if (opts->g_nodal && opts->g_where != NL_HOST && opts->g_where != NL_DEVICE) { nl_set_error("bad g_where"); return NL_EINVAL; }
+    if (opts->f_nodal && opts->f_where != NL_HOST && opts->f_where != NL_DEVICE) { nl_set_error("bad f_where"); return NL_EINVAL; }
     return NL_OK;
 }
 
@@ -38,11 +59,15 @@ nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts, const nl_d
     S->pairs = P;
     S->opts = *opts;
     S->opts.g_nodal = nullptr;
+    S->opts.f_nodal = nullptr;
     try {
         cudaStream_t s = S->arena.stream();
         S->K = S->arena.get<double>(P->nnz);
         S->A = S->arena.get<double>(P->nnz_a);
         S->A32 = S->arena.get<float>(P->nnz_a);
+        S->L = S->arena.get<double>(std::max<int64_t>(P->nnz_l, 1));
+        S->Ap = S->arena.get<double>(std::max<int64_t>(P->ap_slots, 4));
+        S->Ap32 = S->arena.get<float>(std::max<int64_t>(P->ap_slots, 4));
         S->b = S->arena.get<double>(m->n_free);
         S->g = S->arena.get<double>(m->nv);
         S->F = S->arena.get<double>(m->nv);
@@ -53,6 +78,11 @@ nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts, const nl_d
             NL_CHECK_LAUNCH();
         } else {
             NL_CUDA(cudaMemsetAsync(S->g, 0, sizeof(double) * m->nv, s));
+        }
+        if (opts->f_nodal) {
+            S->f = S->arena.get<double>(m->nv);
+            NL_CUDA(cudaMemcpyAsync(S->f, opts->f_nodal, sizeof(double) * m->nv,
+                                    opts->f_where == NL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
         }
     } catch (NlError &) {
         S->arena.release_all();
@@ -114,6 +144,11 @@ nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_dev
         delete S;
         return e.st;
     }
+    if (nl_status st = nl_check_hull_fallbacks(S->stats.hull_fallbacks)) {
+        S->arena.release_all();
+        delete S;
+        return st;
+    }
     *out = S;
     return NL_OK;
 }
@@ -141,6 +176,9 @@ extern "C" nl_status nl_system_csr(const nl_system *S, int which, nl_csr_view *o
     } else if (which == NL_MAT_A) {
         out->n_rows = P->mesh->n_free; out->nnz = P->nnz_a;
         out->rowptr = P->a_rowptr; out->col = P->a_col; out->val = S->A;
+    } else if (which == NL_MAT_LIFT) {
+        out->n_rows = P->mesh->n_free; out->nnz = P->nnz_l;
+        out->rowptr = P->l_rowptr; out->col = P->l_col; out->val = S->L;
     } else {
         nl_set_error("bad matrix selector");
         return NL_EINVAL;

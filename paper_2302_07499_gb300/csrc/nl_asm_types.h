@@ -62,6 +62,7 @@ struct AsmArgs {
     int64_t p0, p1;          // pairs of this chunk (launch index space)
     int max_row;
     int nmc;
+    int hull_maxf;           // face capacity of the approxcaps hull (full capacity except in overflow tests)
     uint32_t rk[20];         // Philox round keys
     // per-chunk work arrays
     uint8_t *uinfo;          // [4*(p1-p0)] vertex-inside mask | 0x10 event | 0x20 zero
@@ -142,6 +143,7 @@ inline Prob make_prob(nl_system *sys, void *D, double *strips, double *TT, uint8
 inline void init_group_args(AsmArgs &A, const nl_assemble_opts &o, unsigned long long *stats, int max_row)
 {
     A.max_row = max_row;
+    A.hull_maxf = nl_hull_max_faces();
     A.nmc = o.strategy == NL_FULLCAPS ? o.mc_points : 0;
     philox_round_keys(o.seed, A.rk);
     A.stats = stats;

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
         const bool deferred = nlq::event_moments<R, STRAT, diag_inline>(
             v, x, sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp,
             (uint32_t)q, out, st, (sizeof(R) == 4) ? &sx : nullptr, cb, nlq::CB_STRIDE * EvCfg<R>::threads,
-            nlq::HullScratch<R>{reinterpret_cast<R *>(evsm) + threadIdx.x, EvCfg<R>::threads});
+            nlq::HullScratch<R>{reinterpret_cast<R *>(evsm) + threadIdx.x, EvCfg<R>::threads}, nullptr, A.hull_maxf);
         if (deferred) {
             if constexpr (!RETAKE) A.fix[atomicAdd(&A.nev[4], 1)] = e;
         } else if constexpr (sizeof(R) == 4) {
@@ -271,7 +271,8 @@ __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmA
         double m15[15];
         nlq::event_moments<double, STRAT>(v, x, P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp, (uint32_t)q,
                                           m15, st, nullptr, nullptr, 0,
-                                          nlq::HullScratch<double>{reinterpret_cast<double *>(fsm) + threadIdx.x, 64});
+                                          nlq::HullScratch<double>{reinterpret_cast<double *>(fsm) + threadIdx.x, 64},
+                                          nullptr, A.hull_maxf);
         float *out = reinterpret_cast<float *>(A.Mq) + MQ_STRIDE * (int64_t)u;
 #pragma unroll
         for (int k = 0; k < 15; ++k) out[k] = (float)m15[k];

@@ -301,6 +301,11 @@ extern "C" nl_status nl_batch_run(nl_batch *b)
         NL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         b->last_ms = ms;
         for (nl_system *S : b->sys) S->stats.quadrature_ms = ms;
+        // the run's counters (cleared at its start): an approxcaps hull that
+        // could not be completed makes the whole run an error
+        unsigned long long hs[8];
+        NL_CUDA(cudaMemcpy(hs, b->stats, sizeof(hs), cudaMemcpyDeviceToHost));
+        if (nl_status st = nl_check_hull_fallbacks(hs[4])) return st;
     } catch (NlError &e) {
         return e.st;
     }

@@ -127,6 +127,17 @@ struct nl_pairs {
     int64_t *a_rowptr = nullptr;   // [n_free+1]
     int32_t *a_col = nullptr;      // [nnz_a]
     int32_t *a_src = nullptr;      // [nnz_a] position in K
+    // A's rows padded to multiples of 4 entries (the CG's SpMV reads 16-byte
+    // vectors): row r holds entries [4 ap_rowptr4[r], 4 ap_rowptr4[r+1]);
+    // a pad has column r and no source (value 0)
+    int64_t ap_slots = 0;
+    int64_t *ap_rowptr4 = nullptr; // [n_free+1] in units of 4 entries
+    int32_t *ap_col = nullptr;     // [ap_slots]
+    int32_t *ap_src = nullptr;     // [ap_slots] position in A, or -1 for a pad
+    int64_t nnz_l = 0;             // L = K[free, collar]
+    int64_t *l_rowptr = nullptr;   // [n_free+1]
+    int32_t *l_col = nullptr;      // [nnz_l] collar node ids
+    int32_t *l_src = nullptr;      // [nnz_l] position in K
 };
 
 struct nl_system {
@@ -136,9 +147,13 @@ struct nl_system {
     double *K = nullptr;           // [nnz]
     double *A = nullptr;           // [nnz_a]
     float *A32 = nullptr;          // [nnz_a]
+    double *L = nullptr;           // [nnz_l] values of K[free, collar]
+    double *Ap = nullptr;          // [ap_slots] A's values in the padded rows
+    float *Ap32 = nullptr;         // [ap_slots] the same in FP32
     double *b = nullptr;           // [n_free]
     double *g = nullptr;           // [nv]
     double *F = nullptr;           // [nv]
+    double *f = nullptr;           // [nv] nodal source values (NULL: f is the constant f_const only)
     nl_assemble_stats stats{};
 };
 
@@ -161,6 +176,11 @@ void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const uint8
                       const double *TT);
 void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const uint8_t *nfull, const double *strips,
                            const double *TT, double *G, double *E, cudaStream_t s);
+nl_status nl_check_hull_fallbacks(uint64_t fallbacks);
+// Face capacity of the approxcaps hull: the full capacity unless the
+// environment variable NL_HULL_MAX_FACES (a testing knob for the overflow
+// path) asks for less; never below the 8 faces of the starting polytope.
+int nl_hull_max_faces();
 nl_status nl_check_assemble_opts(const nl_assemble_opts *opts);
 nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts, const nl_device *dev = nullptr);
 nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_device *dev, nl_system **out);

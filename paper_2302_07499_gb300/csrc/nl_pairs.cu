@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "nl_internal.h"
+#include "nl_quad.cuh"
 
 namespace {
 
@@ -805,7 +806,10 @@ __global__ void k_row_len_max(const int64_t *__restrict__ rowptr, int64_t nv, un
     if ((threadIdx.x & 31) == 0 && v) atomicMax(mx, v);
 }
 
-// A = K[free, free]
+// Row views of K over the free rows: A = K[free, free] (COLLAR false; columns
+// numbered among the free nodes) and L = K[free, collar] (COLLAR true; columns
+// are node ids), each entry with its position in K.
+template <bool COLLAR>
 __global__ void k_a_count(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                           const int32_t *__restrict__ free_nodes, const int32_t *__restrict__ free_idx, int64_t n_free,
                           int64_t *cnt)
@@ -814,10 +818,11 @@ __global__ void k_a_count(const int64_t *__restrict__ rowptr, const int32_t *__r
     if (fr >= n_free) return;
     int32_t r = free_nodes[fr];
     int64_t c = 0;
-    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) c += (free_idx[col[e]] >= 0);
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) c += COLLAR ? (free_idx[col[e]] < 0) : (free_idx[col[e]] >= 0);
     cnt[fr] = c;
 }
 
+template <bool COLLAR>
 __global__ void k_a_fill(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                          const int32_t *__restrict__ free_nodes, const int32_t *__restrict__ free_idx, int64_t n_free,
                          const int64_t *__restrict__ a_rowptr, int32_t *a_col, int32_t *a_src)
@@ -827,8 +832,31 @@ __global__ void k_a_fill(const int64_t *__restrict__ rowptr, const int32_t *__re
     int32_t r = free_nodes[fr];
     int64_t k = a_rowptr[fr];
     for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
-        int32_t f = free_idx[col[e]];
-        if (f >= 0) { a_col[k] = f; a_src[k] = (int32_t)e; ++k; }
+        const int32_t c = col[e];
+        const int32_t f = free_idx[c];
+        if (COLLAR ? f < 0 : f >= 0) { a_col[k] = COLLAR ? c : f; a_src[k] = (int32_t)e; ++k; }
+    }
+}
+
+// A's rows padded to multiples of 4 entries: the lengths (in units of 4),
+// then per row its columns and their positions in A, and the pads (column =
+// the row itself, source -1)
+__global__ void k_ap_len(const int64_t *__restrict__ a_rowptr, int64_t n, int64_t *len4)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) len4[r] = (a_rowptr[r + 1] - a_rowptr[r] + 3) / 4;
+}
+
+__global__ void k_ap_fill(const int64_t *__restrict__ a_rowptr, const int32_t *__restrict__ a_col, int64_t n,
+                          const int64_t *__restrict__ rowptr4, int32_t *ap_col, int32_t *ap_src)
+{
+    int64_t r = blockIdx.x;
+    if (r >= n) return;
+    const int64_t b = a_rowptr[r], len = a_rowptr[r + 1] - b, o = 4 * rowptr4[r], lenp = 4 * (rowptr4[r + 1] - rowptr4[r]);
+    for (int64_t k = threadIdx.x; k < lenp; k += blockDim.x) {
+        const bool real = k < len;
+        ap_col[o + k] = real ? a_col[b + k] : (int32_t)r;
+        ap_src[o + k] = real ? (int32_t)(b + k) : -1;
     }
 }
 
@@ -879,8 +907,60 @@ __global__ void k_box_tets(int n, int olo, int ohi, int4 *tets, uint8_t *in_omeg
     in_omega[t] = (ci >= olo && ci < ohi && cj >= olo && cj < ohi && ck >= olo && ck < ohi) ? 1 : 0;
 }
 
+// One parity class (i%2 + 2 (j%2) + 4 (k%2) == cls) of the jitter: vertex v
+// moves by (2 U_d - 1) (jf h) along axis d, U_d = (w_d + 1/2) 2^-32 from the
+// Philox4x32-10 words w of the counter (v, 0, 0, 0) under the key (k0, k1),
+// unless it lies on a plane of the box or of Omega; the move is kept when
+// every element holding v keeps a positive signed volume (the other three
+// vertices at their current positions).  No two vertices of a class share an
+// element, so the class is moved in one pass.
+__global__ void k_box_jitter(int n, double lo, double h, int olo, int ohi, double jf, uint2 key, int cls, double *v3)
+{
+    const int64_t m = n + 1;
+    int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= m * m * m) return;
+    const int g[3] = {(int)(id % m), (int)((id / m) % m), (int)(id / (m * m))};
+    if ((g[0] & 1) + 2 * (g[1] & 1) + 4 * (g[2] & 1) != cls) return;
+    for (int d = 0; d < 3; ++d)
+        if (g[d] == 0 || g[d] == n || g[d] == olo || g[d] == ohi) return;
+    const uint4 w = nlq::philox4x32_10(make_uint4((uint32_t)id, 0u, 0u, 0u), key);
+    const uint32_t wd[3] = {w.x, w.y, w.z};
+    double trial[3];
+    for (int d = 0; d < 3; ++d) {
+        const double U = ((double)wd[d] + 0.5) * 0x1p-32;
+        trial[d] = v3[3 * id + d] + (2.0 * U - 1.0) * (jf * h);
+    }
+    const int P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    bool ok = true;
+    for (int cc = 0; cc < 8 && ok; ++cc) {
+        const int cell[3] = {g[0] - (cc & 1), g[1] - ((cc >> 1) & 1), g[2] - ((cc >> 2) & 1)};
+        if (cell[0] < 0 || cell[1] < 0 || cell[2] < 0 || cell[0] >= n || cell[1] >= n || cell[2] >= n) continue;
+        for (int p = 0; p < 6 && ok; ++p) {
+            int c[3] = {cell[0], cell[1], cell[2]};
+            int64_t vid[4];
+            for (int s = 0; s < 4; ++s) {
+                if (s > 0) c[P[p][s - 1]] += 1;
+                vid[s] = c[0] + m * (c[1] + m * (int64_t)c[2]);
+            }
+            if (p == 1 || p == 2 || p == 5) { const int64_t t = vid[2]; vid[2] = vid[3]; vid[3] = t; }
+            if (vid[0] != id && vid[1] != id && vid[2] != id && vid[3] != id) continue;
+            double q[4][3];
+            for (int s = 0; s < 4; ++s)
+                for (int d = 0; d < 3; ++d) q[s][d] = vid[s] == id ? trial[d] : v3[3 * vid[s] + d];
+            double e1[3], e2[3], e3[3];
+            for (int d = 0; d < 3; ++d) { e1[d] = q[1][d] - q[0][d]; e2[d] = q[2][d] - q[0][d]; e3[d] = q[3][d] - q[0][d]; }
+            const double cx = e2[1] * e3[2] - e2[2] * e3[1];
+            const double cy = e2[2] * e3[0] - e2[0] * e3[2];
+            const double cz = e2[0] * e3[1] - e2[1] * e3[0];
+            ok = ((e1[0] * cx + e1[1] * cy) + e1[2] * cz) > 0.0;
+        }
+    }
+    if (ok)
+        for (int d = 0; d < 3; ++d) v3[3 * id + d] = trial[d];
+}
+
 extern "C" nl_status nl_mesh_create_box(const nl_device *dev, double lo, double hi, int32_t cells, double omega_lo,
-                                        double omega_hi, nl_mesh **out)
+                                        double omega_hi, double jitter_frac, uint64_t seed, nl_mesh **out)
 {
     nl_clear_error();
     if (!out) { nl_set_error("out is NULL"); return NL_EINVAL; }
@@ -896,6 +976,10 @@ extern "C" nl_status nl_mesh_create_box(const nl_device *dev, double lo, double 
         nl_set_error("Omega bounds must lie on grid planes inside the box");
         return NL_EINVAL;
     }
+    if (!(jitter_frac >= 0.0 && jitter_frac < 0.5)) {
+        nl_set_error("jitter_frac must lie in [0, 0.5)");
+        return NL_EINVAL;
+    }
     const int olo = (int)nearbyint(fo), ohi = (int)nearbyint(fe);
     const int64_t m = cells + 1, nv = m * m * m, nt = 6 * (int64_t)cells * cells * cells;
     DevArena tmp;
@@ -908,6 +992,13 @@ extern "C" nl_status nl_mesh_create_box(const nl_device *dev, double lo, double 
         uint8_t *om = tmp.get<uint8_t>(nt), *nf = tmp.get<uint8_t>(nv);
         { k_box_verts<<<blocks_for(nv, 256), 256, 0, s>>>(cells, lo, h, olo, ohi, v3, nf); nl_count_launch(); }
         NL_CHECK_LAUNCH();
+        if (jitter_frac > 0.0) {
+            const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+            for (int cls = 0; cls < 8; ++cls) {
+                { k_box_jitter<<<blocks_for(nv, 256), 256, 0, s>>>(cells, lo, h, olo, ohi, jitter_frac, key, cls, v3); nl_count_launch(); }
+                NL_CHECK_LAUNCH();
+            }
+        }
         { k_box_tets<<<blocks_for(nt, 256), 256, 0, s>>>(cells, olo, ohi, t4, om); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         st = nl_mesh_create(dev, v3, nv, reinterpret_cast<const int32_t *>(t4), nt, om, nf, NL_DEVICE, out);
@@ -1239,14 +1330,37 @@ nl_status nl_pairs_build_impl(nl_mesh *m, double delta, nl_pairs **out)
 
         // A = K[free, free]
         const int64_t nf = m->n_free;
-        { k_a_count<<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, cnt); nl_count_launch(); }
+        { k_a_count<false><<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, cnt); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         P->a_rowptr = P->arena.get<int64_t>(nf + 1);
         P->nnz_a = nl_scan_counts(cnt, P->a_rowptr, nf, &P->arena, s);
         P->a_col = P->arena.get<int32_t>(P->nnz_a);
         P->a_src = P->arena.get<int32_t>(P->nnz_a);
-        { k_a_fill<<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, P->a_rowptr,
+        { k_a_fill<false><<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, P->a_rowptr,
                                                        P->a_col, P->a_src); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        // A with its rows padded for the CG's vector loads
+        int64_t *len4 = sc.get<int64_t>(std::max<int64_t>(nf, 1));
+        { k_ap_len<<<blocks_for(nf, 256), 256, 0, s>>>(P->a_rowptr, nf, len4); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        P->ap_rowptr4 = P->arena.get<int64_t>(nf + 1);
+        P->ap_slots = 4 * nl_scan_counts(len4, P->ap_rowptr4, nf, &P->arena, s);
+        P->ap_col = P->arena.get<int32_t>(std::max<int64_t>(P->ap_slots, 4));
+        P->ap_src = P->arena.get<int32_t>(std::max<int64_t>(P->ap_slots, 4));
+        if (nf > 0) {
+            { k_ap_fill<<<(unsigned)nf, 128, 0, s>>>(P->a_rowptr, P->a_col, nf, P->ap_rowptr4, P->ap_col, P->ap_src); nl_count_launch(); }
+            NL_CHECK_LAUNCH();
+        }
+        // L = K[free, collar]: the lift of the volume constraint (b = F - L g)
+        int64_t *lcnt = sc.get<int64_t>(std::max<int64_t>(nf, 1));
+        { k_a_count<true><<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, lcnt); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+        P->l_rowptr = P->arena.get<int64_t>(nf + 1);
+        P->nnz_l = nl_scan_counts(lcnt, P->l_rowptr, nf, &P->arena, s);
+        P->l_col = P->arena.get<int32_t>(std::max<int64_t>(P->nnz_l, 1));
+        P->l_src = P->arena.get<int32_t>(std::max<int64_t>(P->nnz_l, 1));
+        { k_a_fill<true><<<blocks_for(nf, 128), 128, 0, s>>>(P->rowptr, P->col, m->free_nodes, m->free_idx, nf, P->l_rowptr,
+                                                      P->l_col, P->l_src); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         int hbad = 0;
         NL_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1290,6 +1404,7 @@ extern "C" nl_status nl_pairs_get_info(const nl_pairs *p, nl_pairs_info *info)
     info->nnz = p->nnz;
     info->n_free = p->mesh->n_free;
     info->nnz_a = p->nnz_a;
+    info->nnz_lift = p->nnz_l;
     info->max_row = p->max_row;
     info->delta = p->delta;
     return NL_OK;

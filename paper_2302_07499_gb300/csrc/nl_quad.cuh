@@ -496,7 +496,8 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t *rk)
 // midpoints one at a time (beneath-beyond: faces that see the new point are
 // replaced by the cone from the point to their horizon), then coned from the
 // mean of its points.  Returns false when a hull could not be completed
-// (face capacity); the caller then keeps the nocaps cells.
+// (capacity: maxf <= HULL_MAXF faces, HULL_MAXP points, HULL_MAXH horizon
+// edges); the caller counts it and the assembly reports an error.
 // The arc midpoint of face (f0,f1,f2) computed in FP64 for the FP32 path
 // (used when the chord between the two edge points is short or the in-face
 // decision is close).  Returns whether it lies in the face; its position
@@ -591,7 +592,7 @@ template <class R> struct HullScratch {
 template <class R>
 __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, const int role[4], const P3<R> pp[4],
                                     const R pt[4], const PDesc pd[4], bool diag_c2d1, Mom<R> &M, const Strict *sx,
-                                    const HullScratch<R> &hs)
+                                    const HullScratch<R> &hs, int maxf)
 {
     constexpr bool F32 = sizeof(R) == 4;
     auto X = [&](int k) -> P3<R> { return mk3<R>(hs(3 * k), hs(3 * k + 1), hs(3 * k + 2)); };
@@ -752,7 +753,7 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
         // cone over every horizon edge still closes the surface)
         if (nh < 3) return false;
         const int nvis = __popc(vis);
-        if (nf - nvis + nh > HULL_MAXF) return false;
+        if (nf - nvis + nh > maxf) return false;
         int w2 = 0;
         for (int f = 0; f < nf; ++f)
             if (!((vis >> f) & 1u)) F[w2++] = F[f];
@@ -813,11 +814,12 @@ static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16
 //   be discarded): a vertex of T' within 1e-3 (relative) of the sphere, where
 //   the arc midpoints are ill-conditioned in FP32 (redone in FP64); and, when
 //   DIAG_INLINE is false, an m = 2 diagonal that the FP32 orientation cannot
-//   decide.
+//   decide.  A hull that cannot be completed is counted in st.fallback (its
+//   nocaps cells stand in for it here, and the assembly reports an error).
 template <class R, int STRAT, bool DIAG_INLINE = true>
 __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk,
                                       uint32_t idT, uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx,
-                                      R *cb, int cs, const HullScratch<R> &hs)
+                                      R *cb, int cs, const HullScratch<R> &hs, int hull_maxf)
 {
     Mom<R> M;
     constexpr bool F32 = sizeof(R) == 4;
@@ -899,9 +901,9 @@ __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, 
             }
         }
         if (near) return true;
-        done_hull = approx_hull_moments<R>(v, x, d2, m, role, pp, pt, pd, diag_c2d1, H, sx, hs);
+        done_hull = approx_hull_moments<R>(v, x, d2, m, role, pp, pt, pd, diag_c2d1, H, sx, hs, hull_maxf);
         if (done_hull) M = H;
-        else st.fallback++;
+        else st.fallback++;                   // counted: the assembly then reports an error
     }
     // deterministic cells: hull(I u P), coned from the first inside vertex
     if (m > 0 && !done_hull) {
@@ -971,14 +973,16 @@ __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, 
 //   rec[5k..5k+4] = (cap cell, accepted, y) with y global (FP64) or relative
 //   to x (FP32).
 //   Returns true when the event is deferred (see event_moments_generic).
+//   hull_maxf: face capacity of the approxcaps hull (HULL_MAXF; smaller only
+//   in tests of the overflow path).
 template <class R, int STRAT, bool DIAG_INLINE = true, bool REC = false>
 __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
                               uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs,
-                              const HullScratch<R> &hs, double *rec = nullptr)
+                              const HullScratch<R> &hs, double *rec = nullptr, int hull_maxf = HULL_MAXF)
 {
     if constexpr (STRAT == 1) {
         return event_moments_generic<R, STRAT, DIAG_INLINE>(v, x, d2, inm, nmc, rk, idT, idTp, q, out, st, sx, cb,
-                                                             cs, hs);
+                                                             cs, hs, hull_maxf);
     } else {
     Mom<R> M;
     constexpr bool F32 = sizeof(R) == 4;

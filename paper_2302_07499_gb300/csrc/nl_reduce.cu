@@ -168,8 +168,12 @@ __global__ void k_final_K(const int64_t *__restrict__ rowptr, const int32_t *__r
     }
 }
 
+// F_r = sum over elements T of Omega holding node r of sum_q w_q lambda_r(x_q)
+// f(x_q), with f = fconst + the P1 interpolant of the nodal values fnod
+// (when given) and lambda(x_q) = a at point q, b at the other three.
 __global__ void k_load_vector(const int64_t *__restrict__ ne_ptr, const int32_t *__restrict__ ne_ent,
-                              const int32_t *__restrict__ outer_of, const double *__restrict__ tet_vol, double fconst,
+                              const int32_t *__restrict__ outer_of, const double *__restrict__ tet_vol,
+                              const int4 *__restrict__ tets, const double *__restrict__ fnod, double fconst,
                               int64_t nv, double *F)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,9 +184,22 @@ __global__ void k_load_vector(const int64_t *__restrict__ ne_ptr, const int32_t 
         int32_t ent = ne_ent[k];
         int64_t el = ent >> 2;
         if (outer_of[el] < 0) continue;
+        const int i = ent & 3;
         double w = tet_vol[el] * 0.25;
+        double fq[4] = {fconst, fconst, fconst, fconst};
+        if (fnod) {
+            const int4 t = tets[el];
+            const double f4[4] = {fnod[t.x], fnod[t.y], fnod[t.z], fnod[t.w]};
+            for (int q = 0; q < 4; ++q) {
+                double v = 0.0;
+                for (int j = 0; j < 4; ++j) v += (j == q ? qa : qb) * f4[j];
+                fq[q] += v;
+            }
+        }
         // sum over the four points: lambda_i = a at its own point, b at the others
-        s += ((w * qa * fconst + w * qb * fconst) + w * qb * fconst) + w * qb * fconst;
+        double t = 0.0;
+        for (int q = 0; q < 4; ++q) t += w * (q == i ? qa : qb) * fq[q];
+        s += t;
     }
     F[r] = s;
 }
@@ -209,6 +226,25 @@ __global__ void k_system(const int64_t *__restrict__ rowptr, const int32_t *__re
     }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) b[fr] = F[r] - s;
+}
+
+// A's values in the padded rows (0 for the pads), FP64 and FP32
+__global__ void k_fill_padded(const double *__restrict__ A, const int32_t *__restrict__ src, int64_t n, double *Ap,
+                              float *Ap32)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int32_t k = src[e];
+    const double v = k >= 0 ? A[k] : 0.0;
+    Ap[e] = v;
+    Ap32[e] = (float)v;
+}
+
+// out[e] = K[src[e]] (a row view's values)
+__global__ void k_gather_vals(const double *__restrict__ K, const int32_t *__restrict__ src, int64_t n, double *out)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = K[src[e]];
 }
 
 unsigned wblocks(int64_t n) { return (unsigned)std::max<int64_t>(1, nl_cdiv<int64_t>(n * 32, 256)); }
@@ -238,11 +274,21 @@ void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const 
                                             sys->K); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     { k_load_vector<<<(unsigned)nl_cdiv<int64_t>(m->nv, 256), 256, 0, s>>>(m->ne_ptr, m->ne_ent, m->outer_of,
-                                                                       m->tet_vol, sys->opts.f_const, m->nv, sys->F); nl_count_launch(); }
+                                                                       m->tet_vol, m->tets, sys->f, sys->opts.f_const,
+                                                                       m->nv, sys->F); nl_count_launch(); }
     NL_CHECK_LAUNCH();
     { k_system<<<wblocks(m->n_free), 256, 0, s>>>(P->rowptr, P->col, sys->K, m->free_nodes, m->free_idx, P->a_rowptr,
                                                P->a_src, sys->F, sys->g, m->n_free, sys->A, sys->A32, sys->b); nl_count_launch(); }
     NL_CHECK_LAUNCH();
+    if (P->ap_slots > 0) {
+        { k_fill_padded<<<(unsigned)nl_cdiv<int64_t>(P->ap_slots, 256), 256, 0, s>>>(sys->A, P->ap_src, P->ap_slots,
+                                                                                  sys->Ap, sys->Ap32); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+    }
+    if (P->nnz_l > 0) {
+        { k_gather_vals<<<(unsigned)nl_cdiv<int64_t>(P->nnz_l, 256), 256, 0, s>>>(sys->K, P->l_src, P->nnz_l, sys->L); nl_count_launch(); }
+        NL_CHECK_LAUNCH();
+    }
 }
 
 void nl_reduce_system(nl_system *sys, const void *D, int d_is_float, const uint8_t *nfull, const double *strips,

@@ -45,7 +45,8 @@ __global__ void k_quadratic_g(const double4 *__restrict__ v, int64_t nv, double 
 struct Worker;
 
 struct CacheEntry {
-    double lo, hi, olo, ohi, delta;
+    double lo, hi, olo, ohi, delta, jitter;
+    uint64_t jitter_seed;
     int cells;
     nl_mesh *mesh = nullptr;
     nl_pairs *pairs = nullptr;
@@ -137,6 +138,7 @@ int64_t resident_bytes(const nl_pairs *P)
 bool same_key(const CacheEntry *e, const nl_request &r)
 {
     return e->cells == r.cells && e->lo == r.lo && e->hi == r.hi && e->olo == r.omega_lo && e->ohi == r.omega_hi &&
+           e->jitter == r.jitter_frac && e->jitter_seed == r.jitter_seed &&
            e->delta == r.delta;
 }
 
@@ -181,7 +183,10 @@ void run_job(Worker *w, Job *J)
             CacheEntry *e = new CacheEntry();
             e->lo = r.lo; e->hi = r.hi; e->olo = r.omega_lo; e->ohi = r.omega_hi; e->delta = r.delta;
             e->cells = r.cells;
-            nl_status st = nl_mesh_create_box(&w->dev, r.lo, r.hi, r.cells, r.omega_lo, r.omega_hi, &e->mesh);
+            e->jitter = r.jitter_frac;
+            e->jitter_seed = r.jitter_seed;
+            nl_status st = nl_mesh_create_box(&w->dev, r.lo, r.hi, r.cells, r.omega_lo, r.omega_hi, r.jitter_frac,
+                                              r.jitter_seed, &e->mesh);
             if (st == NL_OK) st = nl_pairs_build(e->mesh, r.delta, &e->pairs);
             if (st != NL_OK) {
                 snprintf(J->res.message, sizeof(J->res.message), "%s", nl_last_error());
@@ -370,6 +375,7 @@ extern "C" nl_status nl_server_submit(nl_server *S, const nl_request *req, uint6
         return NL_EINVAL;
     }
     if (req->assemble.g_nodal) { nl_set_error("requests carry g as g_quadratic, not g_nodal"); return NL_EINVAL; }
+    if (req->assemble.f_nodal) { nl_set_error("requests carry a constant f (f_nodal must be NULL)"); return NL_EINVAL; }
     if (nl_status st = nl_check_assemble_opts(&req->assemble)) return st;
     std::lock_guard<std::mutex> lk(S->mu);
     if ((int)S->queue.size() >= S->opts.queue_capacity) { nl_set_error("queue full"); return NL_EBUSY; }

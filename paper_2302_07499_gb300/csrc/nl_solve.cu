@@ -5,8 +5,10 @@
 // accumulated in FP64 in both modes.  Reductions use a fixed grid and a
 // fixed combination order, so results are bitwise reproducible.
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "nl_internal.h"
 
@@ -61,28 +63,88 @@ __device__ __forceinline__ bool last_block(CgState *st)
     return last && threadIdx.x < 32;
 }
 
+// One row of A p on the padded rows, by the 8 lanes sub = 0..7 of a lane group
+// (each lane's partial sum; the caller adds the 8): FP32 values as float4
+// with int4 columns, FP64 values as double2 with int2 columns, and four
+// 16-byte chunks of each lane loaded before their gathers, so that a row of
+// several hundred entries costs a few memory round trips, not one per 32
+// entries.  Pads hold value 0 and the row's own column.
 template <class VT, class XT>
-__global__ void k_spmv_dot(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const VT *__restrict__ val, const XT *__restrict__ p, XT *q, int64_t n,
-                           double *part, CgState *st)
+__device__ __forceinline__ VT pad_row(const int64_t *__restrict__ rp4, const int32_t *__restrict__ cp,
+                                      const VT *__restrict__ vp, const XT *__restrict__ p, int64_t r, int sub)
+{
+    constexpr int U = 4;
+    VT s = VT(0);
+    if constexpr (sizeof(VT) == 4) {
+        const int4 *c4 = reinterpret_cast<const int4 *>(cp);
+        const float4 *v4 = reinterpret_cast<const float4 *>(vp);
+        const int64_t e0 = rp4[r], e1 = rp4[r + 1];
+        for (int64_t e = e0 + sub; e < e1; e += 8 * U) {
+            float4 v[U];
+            int4 c[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t ee = e + 8 * u;
+                if (ee < e1) { v[u] = __ldcs(v4 + ee); c[u] = __ldcs(c4 + ee); }
+                else { v[u] = make_float4(0.f, 0.f, 0.f, 0.f); c[u] = make_int4(0, 0, 0, 0); }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                s += v[u].x * (VT)__ldg(p + c[u].x);
+                s += v[u].y * (VT)__ldg(p + c[u].y);
+                s += v[u].z * (VT)__ldg(p + c[u].z);
+                s += v[u].w * (VT)__ldg(p + c[u].w);
+            }
+        }
+    } else {
+        const int2 *c2 = reinterpret_cast<const int2 *>(cp);
+        const double2 *v2 = reinterpret_cast<const double2 *>(vp);
+        const int64_t e0 = 2 * rp4[r], e1 = 2 * rp4[r + 1];
+        for (int64_t e = e0 + sub; e < e1; e += 8 * U) {
+            double2 v[U];
+            int2 c[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t ee = e + 8 * u;
+                if (ee < e1) { v[u] = __ldcs(v2 + ee); c[u] = __ldcs(c2 + ee); }
+                else { v[u] = make_double2(0.0, 0.0); c[u] = make_int2(0, 0); }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                s += v[u].x * (VT)__ldg(p + c[u].x);
+                s += v[u].y * (VT)__ldg(p + c[u].y);
+            }
+        }
+    }
+    return s;
+}
+
+// q = A p on the padded rows (8 lanes per row, 4 rows per warp) with the
+// per-block partials of p.q; in the CG the last block forms alpha.  Every
+// warp walks the same number of row groups (rows beyond n are skipped), so
+// the lane-group sums can use full-warp shuffles.
+template <class VT, class XT>
+__global__ void __launch_bounds__(RB) k_spmv_dot_pad(const int64_t *__restrict__ rp4, const int32_t *__restrict__ cp,
+                                                     const VT *__restrict__ vp, const XT *__restrict__ p, XT *q,
+                                                     int64_t n, double *part, CgState *st)
 {
     __shared__ double sh[RB / 32];
     if (st && st->done) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
     double acc = 0.0;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
-        VT s = VT(0);
-        for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) s += val[e] * (VT)p[ci[e]];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            q[r] = (XT)s;
-            acc += (double)p[r] * (double)s;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; r - grp < n; r += groups) {
+        VT sum = r < n ? pad_row<VT, XT>(rp4, cp, vp, p, r, sub) : VT(0);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+        if (sub == 0 && r < n) {
+            q[r] = (XT)sum;
+            acc += (double)p[r] * (double)sum;
         }
     }
     double t = block_sum(acc, sh);
     if (threadIdx.x == 0 && part) part[blockIdx.x] = t;
-    // CG: the last block forms alpha = r.r / p.Ap
     if (st && last_block(st)) {
         const double pq = warp_sum_parts(part, gridDim.x);
         if (threadIdx.x == 0) {
@@ -91,6 +153,30 @@ __global__ void k_spmv_dot(const int64_t *__restrict__ rp, const int32_t *__rest
             st->ticket = 0;
         }
     }
+}
+
+// r = b - A x (FP64) on the padded rows, with the partials of |r|^2
+__global__ void __launch_bounds__(RB) k_residual_pad(const int64_t *__restrict__ rp4, const int32_t *__restrict__ cp,
+                                                     const double *__restrict__ vp, const double *__restrict__ x,
+                                                     const double *__restrict__ b, double *r, int64_t n, double *part)
+{
+    __shared__ double sh[RB / 32];
+    const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+    double acc = 0.0;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; row - grp < n; row += groups) {
+        double sum = row < n ? pad_row<double, double>(rp4, cp, vp, x, row, sub) : 0.0;
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+        if (sub == 0 && row < n) {
+            const double ri = b[row] - sum;
+            r[row] = ri;
+            acc += ri * ri;
+        }
+    }
+    double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // With FUSE_P (small systems) the last block also updates p = r + beta p for
@@ -198,9 +284,17 @@ __global__ void k_start(const double *part, int nb, double rtol2, CgState *st)
 
 // Grid-wide barrier of a cooperative launch (all blocks resident).  The last
 // block to arrive resets the count and advances the generation; the others
-// wait for the new generation, at most about a second (then the error flag
-// is set and every block leaves: the host falls back to the multi-launch CG).
-__device__ bool grid_barrier(CgState *st)
+// wait for the new generation for at most wait_ns nanoseconds of the global
+// timer (and at most 2^25 polls), then set the error flag and every block
+// leaves: the host falls back to the multi-launch CG.
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(CgState *st, unsigned long long wait_ns)
 {
     __shared__ int ok;
     __syncthreads();
@@ -214,9 +308,10 @@ __device__ bool grid_barrier(CgState *st)
             __threadfence();
             atomicAdd(&st->bar_gen, 1u);
         } else {
+            const unsigned long long t0 = global_ns();
             unsigned int spins = 0;
             while (*gen == g) {
-                if (++spins > (1u << 25)) {
+                if (++spins > (1u << 25) || global_ns() - t0 > wait_ns) {
                     atomicExch(&st->bar_err, 1);
                     break;
                 }
@@ -253,7 +348,8 @@ __device__ __forceinline__ double grid_sum(const double *part, int nb, double *b
 template <class VT, class XT>
 __global__ void __launch_bounds__(RB) k_cg_persist(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                    const VT *__restrict__ val, XT *x, XT *r, XT *p, XT *q, int64_t n,
-                                                   double *part, double *part2, CgState *st, int max_it)
+                                                   double *part, double *part2, CgState *st, int max_it,
+                                                   unsigned long long wait_ns)
 {
     __shared__ double sh[RB / 32];
     __shared__ double bc;
@@ -277,7 +373,7 @@ __global__ void __launch_bounds__(RB) k_cg_persist(const int64_t *__restrict__ r
         }
         double t = block_sum(acc, sh);
         if (threadIdx.x == 0) part[blockIdx.x] = t;
-        if (!grid_barrier(st)) break;
+        if (!grid_barrier(st, wait_ns)) break;
         const double pq = grid_sum(part, gridDim.x, &bc);
         const XT a = (XT)((pq != 0.0) ? rr / pq : 0.0);
         acc = 0.0;
@@ -289,7 +385,7 @@ __global__ void __launch_bounds__(RB) k_cg_persist(const int64_t *__restrict__ r
         }
         t = block_sum(acc, sh);
         if (threadIdx.x == 0) part2[blockIdx.x] = t;
-        if (!grid_barrier(st)) break;
+        if (!grid_barrier(st, wait_ns)) break;
         const double rn = grid_sum(part2, gridDim.x, &bc);
         const double beta = (rr != 0.0) ? rn / rr : 0.0;
         rr = rn;
@@ -300,36 +396,13 @@ __global__ void __launch_bounds__(RB) k_cg_persist(const int64_t *__restrict__ r
         }
         const XT b = (XT)beta;
         for (int64_t i = gt; i < n; i += gs) p[i] = r[i] + b * p[i];
-        if (!grid_barrier(st)) break;
+        if (!grid_barrier(st, wait_ns)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->rr = rr;
         st->it = it;
         st->done = done;
     }
-}
-
-// r = b - A x (FP64), partial |r|^2
-__global__ void k_residual(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const double *__restrict__ val, const double *__restrict__ x, const double *__restrict__ b,
-                           double *r, int64_t n, double *part)
-{
-    __shared__ double sh[RB / 32];
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    double acc = 0.0;
-    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += warps) {
-        double s = 0.0;
-        for (int64_t e = rp[row] + lane; e < rp[row + 1]; e += 32) s += val[e] * x[ci[e]];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            double ri = b[row] - s;
-            r[row] = ri;
-            acc += ri * ri;
-        }
-    }
-    double t = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 __global__ void k_add_scaled(double *x, const float *d, double scale, int64_t n)
@@ -356,17 +429,30 @@ int cg_blocks(int64_t n)
 }
 
 // systems up to this many rows update p in the last block of the x/r update
-constexpr int64_t kFuseRows = 65536;
+// (one block then walks all rows: beyond a few thousand rows that serial tail
+// costs more than the separate p launch)
+constexpr int64_t kFuseRows = 8192;
 // and up to this many run the whole loop in one cooperative launch (larger
 // ones are bandwidth-bound and want more resident blocks than one per SM)
 constexpr int64_t kPersistRows = 16384;
 
 struct Cg {
+    int fallbacks = 0;         // single-launch loops that gave up a barrier wait (redone with separate launches)
     int nb = 0;
     double *part = nullptr;
     double *part2 = nullptr;   // second partials of the single-launch CG (null: not used)
     CgState *st = nullptr;
 };
+
+// Longest wait of a grid barrier of the single-launch CG: one second, or the
+// nanoseconds in NL_CG_BARRIER_WAIT_NS (a testing knob: 0 makes every wait
+// give up at once, which exercises the multi-launch fallback).
+unsigned long long barrier_wait_ns()
+{
+    const char *e = getenv("NL_CG_BARRIER_WAIT_NS");
+    if (!e || !*e) return 1000000000ull;
+    return strtoull(e, nullptr, 10);
+}
 
 // Blocks of the single-launch CG: all resident at once (a cooperative launch
 // fails rather than oversubscribe), at most the partials' size.
@@ -385,7 +471,8 @@ int persist_blocks(int nb)
 
 // Run CG from x = 0 on A x = b*scale; returns iterations; converged flag in *conv.
 template <class VT, class XT>
-int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b, double scale, XT *x, XT *r, XT *p,
+int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const int64_t *rp4, const int32_t *cp, const VT *vp,
+           const double *b, double scale, XT *x, XT *r, XT *p,
            XT *q, int64_t n, double rtol, int max_it, int check_every, Cg &cg, cudaStream_t s, bool *conv)
 {
     const int nb = cg.nb;
@@ -399,8 +486,10 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b,
     if (cg.part2 && n <= kPersistRows) {
         const int nbp = persist_blocks<VT, XT>(nb);
         if (nbp > 0) {
+            unsigned long long wait_ns = barrier_wait_ns();
             void *args[] = {(void *)&rp, (void *)&ci, (void *)&val, (void *)&x, (void *)&r, (void *)&p, (void *)&q,
-                            (void *)&n, (void *)&cg.part, (void *)&cg.part2, (void *)&cg.st, (void *)&max_it};
+                            (void *)&n, (void *)&cg.part, (void *)&cg.part2, (void *)&cg.st, (void *)&max_it,
+                            (void *)&wait_ns};
             const cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_cg_persist<VT, XT>,
                                                                dim3((unsigned)nbp), dim3(RB), args, 0, s);
             if (le != cudaSuccess) (void)cudaGetLastError();     // not launched: the multi-launch loop below
@@ -413,6 +502,7 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b,
             }
             if (le == cudaSuccess) {
                 // a barrier wait gave up: redo the solve with separate launches
+                cg.fallbacks++;
                 { k_init<XT><<<nb, RB, 0, s>>>(b, x, r, p, n, scale, cg.part); nl_count_launch(); }
                 NL_CHECK_LAUNCH();
                 { k_start<<<1, 32, 0, s>>>(cg.part, nb, rtol * rtol, cg.st); nl_count_launch(); }
@@ -423,7 +513,7 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const double *b,
     while (launched < max_it) {
         int k = std::min(check_every, max_it - launched);
         for (int j = 0; j < k; ++j) {
-            { k_spmv_dot<VT, XT><<<nb, RB, 0, s>>>(rp, ci, val, p, q, n, cg.part, cg.st); nl_count_launch(); }
+            { k_spmv_dot_pad<VT, XT><<<nb, RB, 0, s>>>(rp4, cp, vp, p, q, n, cg.part, cg.st); nl_count_launch(); }
             if (n <= kFuseRows) {
                 { k_update_xr<XT, true><<<nb, RB, 0, s>>>(x, r, p, q, n, cg.part, cg.st); nl_count_launch(); }
             } else {
@@ -453,7 +543,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
     int mixed = opts ? opts->mixed : 0;
     double inner = (opts && opts->inner_rtol > 0) ? opts->inner_rtol : 1e-5;
     int check_every = (opts && opts->check_every > 0) ? opts->check_every : 8;
-    nl_solve_info inf{0, 0, 0.0};
+    nl_solve_info inf{0, 0, 0.0, 0};
     nl_status ret = NL_OK;
     try {
         cudaStream_t s = S->arena.stream();
@@ -470,7 +560,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
         {
             double *z = sc.get<double>(n);
             NL_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * n, s));
-            { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, z, S->b, rres, n, cg.part); nl_count_launch(); }
+            { k_residual_pad<<<cg.nb, RB, 0, s>>>(P->ap_rowptr4, P->ap_col, S->Ap, z, S->b, rres, n, cg.part); nl_count_launch(); }
             NL_CHECK_LAUNCH();
             std::vector<double> hp(cg.nb);
             NL_CUDA(cudaMemcpyAsync(hp.data(), cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
@@ -482,7 +572,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
         if (!mixed) {
             double *r = sc.get<double>(n), *p = sc.get<double>(n), *q = sc.get<double>(n);
             bool conv = false;
-            inf.iterations = run_cg<double, double>(P->a_rowptr, P->a_col, S->A, S->b, 1.0, x, r, p, q, n, rtol,
+            inf.iterations = run_cg<double, double>(P->a_rowptr, P->a_col, S->A, P->ap_rowptr4, P->ap_col, S->Ap, S->b, 1.0, x, r, p, q, n, rtol,
                                                     max_it, check_every, cg, s, &conv);
             converged = conv;
         } else {
@@ -490,7 +580,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
             NL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
             int total = 0;
             for (int outer = 0; outer < 100 && total < max_it; ++outer) {
-                { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part); nl_count_launch(); }
+                { k_residual_pad<<<cg.nb, RB, 0, s>>>(P->ap_rowptr4, P->ap_col, S->Ap, x, S->b, rres, n, cg.part); nl_count_launch(); }
                 NL_CHECK_LAUNCH();
                 std::vector<double> hp(cg.nb);
                 NL_CUDA(cudaMemcpyAsync(hp.data(), cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
@@ -500,7 +590,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
                 if (sqrt(rr) <= rtol * nb_ || rr == 0.0) { converged = true; break; }
                 double rn = sqrt(rr);
                 bool conv = false;
-                int it = run_cg<float, float>(P->a_rowptr, P->a_col, S->A32, rres, 1.0 / rn, xf, rf, pf, qf, n,
+                int it = run_cg<float, float>(P->a_rowptr, P->a_col, S->A32, P->ap_rowptr4, P->ap_col, S->Ap32, rres, 1.0 / rn, xf, rf, pf, qf, n,
                                               inner, max_it - total, check_every, cg, s, &conv);
                 total += it;
                 inf.refinements += 1;
@@ -511,7 +601,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
             inf.iterations = total;
         }
         // true residual
-        { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part); nl_count_launch(); }
+        { k_residual_pad<<<cg.nb, RB, 0, s>>>(P->ap_rowptr4, P->ap_col, S->Ap, x, S->b, rres, n, cg.part); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         std::vector<double> hp(cg.nb);
         NL_CUDA(cudaMemcpyAsync(hp.data(), cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
@@ -519,6 +609,7 @@ nl_status nl_solve_impl(nl_system *S, const nl_solve_opts *opts, double *u_out, 
         double rr = 0.0;
         for (double v : hp) rr += v;
         inf.rel_residual = (nb_ > 0) ? sqrt(rr) / nb_ : 0.0;
+        inf.barrier_fallbacks = cg.fallbacks;
         if (mixed) converged = inf.rel_residual <= rtol * 1.0000001;
         if (u_out) {
             double *u = (where == NL_DEVICE) ? u_out : sc.get<double>(m->nv);
@@ -548,10 +639,11 @@ __global__ void k_fill_ones(double *a, float *b, int64_t n)
 }
 }  // namespace
 
-extern "C" nl_status nl_spmv_time(nl_system *S, int precision, int reps, double *ms_per_spmv, double *bytes_per_spmv)
+extern "C" nl_status nl_spmv_time(nl_system *S, int precision, int reps, int64_t flush_bytes, double *ms_per_spmv,
+                                  double *bytes_per_spmv)
 {
     nl_clear_error();
-    if (!S || !ms_per_spmv || reps < 1 || (precision != NL_FP64 && precision != NL_FP32_COMP)) {
+    if (!S || !ms_per_spmv || reps < 1 || flush_bytes < 0 || (precision != NL_FP64 && precision != NL_FP32_COMP)) {
         nl_set_error("bad argument");
         return NL_EINVAL;
     }
@@ -562,25 +654,41 @@ extern "C" nl_status nl_spmv_time(nl_system *S, int precision, int reps, double 
         Scratch sc(&S->arena);
         double *xd = sc.get<double>(n), *yd = sc.get<double>(n);
         float *xf = sc.get<float>(n), *yf = sc.get<float>(n);
+        unsigned char *fl = flush_bytes > 0 ? sc.get<unsigned char>(flush_bytes) : nullptr;
         { k_fill_ones<<<(unsigned)nl_cdiv<int64_t>(n, 256), 256, 0, s>>>(xd, xf, n); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         const int nb = cg_blocks(n);
+        auto launch = [&]() {
+            if (precision == NL_FP64)
+                { k_spmv_dot_pad<double, double><<<nb, RB, 0, s>>>(P->ap_rowptr4, P->ap_col, S->Ap, xd, yd, n, nullptr, nullptr); nl_count_launch(); }
+            else
+                { k_spmv_dot_pad<float, float><<<nb, RB, 0, s>>>(P->ap_rowptr4, P->ap_col, S->Ap32, xf, yf, n, nullptr, nullptr); nl_count_launch(); }
+        };
         ScopedEvent e0, e1;
-        for (int w = 0; w < 2; ++w) {
+        launch();                                   // untimed
+        float total = 0.f;
+        if (!fl) {
             NL_CUDA(cudaEventRecord(e0, s));
-            for (int k = 0; k < (w ? reps : 1); ++k) {
-                if (precision == NL_FP64)
-                    { k_spmv_dot<double, double><<<nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, xd, yd, n, nullptr, nullptr); nl_count_launch(); }
-                else
-                    { k_spmv_dot<float, float><<<nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A32, xf, yf, n, nullptr, nullptr); nl_count_launch(); }
-            }
+            for (int k = 0; k < reps; ++k) launch();
             NL_CUDA(cudaEventRecord(e1, s));
+            NL_CHECK_LAUNCH();
+            NL_CUDA(cudaEventSynchronize(e1));
+            NL_CUDA(cudaEventElapsedTime(&total, e0, e1));
+        } else {
+            // each launch alone after a write of flush_bytes (L2 holds none of A)
+            for (int k = 0; k < reps; ++k) {
+                NL_CUDA(cudaMemsetAsync(fl, k & 0xff, (size_t)flush_bytes, s));
+                NL_CUDA(cudaEventRecord(e0, s));
+                launch();
+                NL_CUDA(cudaEventRecord(e1, s));
+                NL_CHECK_LAUNCH();
+                NL_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                NL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                total += ms;
+            }
         }
-        NL_CHECK_LAUNCH();
-        NL_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        NL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        *ms_per_spmv = ms / reps;
+        *ms_per_spmv = total / reps;
         const double vb = precision == NL_FP64 ? 8.0 : 4.0;
         if (bytes_per_spmv) *bytes_per_spmv = (double)nnz * (vb + 4.0) + (double)(n + 1) * 8.0 + 2.0 * n * vb;
     } catch (NlError &e) {
@@ -615,14 +723,17 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
 static void *g_static_addr[kMaxDevices] = {nullptr};
+static std::mutex g_static_mu;
 
 // Device address of the array on the current device (looked up once per
-// device; the host-side symbol is only a stand-in and is never dereferenced).
+// device, under a lock so that threads making their first call at once do not
+// race; the host-side symbol is only a stand-in and is never dereferenced).
 void *static_scratch_address()
 {
     int dev = 0;
     NL_CUDA(cudaGetDevice(&dev));
     NL_REQUIRE(dev >= 0 && dev < kMaxDevices, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
     if (!g_static_addr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
@@ -634,6 +745,23 @@ void *static_scratch_address()
         g_static_addr[dev] = p;
     }
     return g_static_addr[dev];
+}
+
+// Whether ptr is device (or managed) memory that the current device can
+// write: the kernels of the static solve write u_out directly.
+bool is_device_pointer(const void *ptr)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
 }
 
 }  // namespace
@@ -650,10 +778,14 @@ extern "C" nl_status nl_solve_static(nl_system *S, const nl_solve_opts *opts, do
                      (long long)kStaticMaxFree, (long long)n);
         return NL_EINVAL;
     }
+    if (!is_device_pointer(u_out)) {
+        nl_set_error("nl_solve_static: u_out must be device memory of the current device");
+        return NL_EINVAL;
+    }
     double rtol = (opts && opts->rtol > 0) ? opts->rtol : 1e-12;
     int max_it = (opts && opts->max_iter > 0) ? opts->max_iter : 20000;
     int check_every = (opts && opts->check_every > 0) ? opts->check_every : 8;
-    nl_solve_info inf{0, 0, 0.0};
+    nl_solve_info inf{0, 0, 0.0, 0};
     nl_status ret = NL_OK;
     try {
         cudaStream_t s = S->arena.stream();
@@ -671,7 +803,7 @@ extern "C" nl_status nl_solve_static(nl_system *S, const nl_solve_opts *opts, do
         double hp[kStaticMaxBlocks];
         // |b| from the residual of u = 0 (x starts at zero: clear it first)
         NL_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-        { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part); nl_count_launch(); }
+        { k_residual_pad<<<cg.nb, RB, 0, s>>>(P->ap_rowptr4, P->ap_col, S->Ap, x, S->b, rres, n, cg.part); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         NL_CUDA(cudaMemcpyAsync(hp, cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
         NL_CUDA(cudaStreamSynchronize(s));
@@ -679,15 +811,16 @@ extern "C" nl_status nl_solve_static(nl_system *S, const nl_solve_opts *opts, do
         for (int i = 0; i < cg.nb; ++i) bb += hp[i];
         const double nb_ = sqrt(bb);
         bool conv = false;
-        inf.iterations = run_cg<double, double>(P->a_rowptr, P->a_col, S->A, S->b, 1.0, x, r, p, q, n, rtol, max_it,
+        inf.iterations = run_cg<double, double>(P->a_rowptr, P->a_col, S->A, P->ap_rowptr4, P->ap_col, S->Ap, S->b, 1.0, x, r, p, q, n, rtol, max_it,
                                                 check_every, cg, s, &conv);
-        { k_residual<<<cg.nb, RB, 0, s>>>(P->a_rowptr, P->a_col, S->A, x, S->b, rres, n, cg.part); nl_count_launch(); }
+        { k_residual_pad<<<cg.nb, RB, 0, s>>>(P->ap_rowptr4, P->ap_col, S->Ap, x, S->b, rres, n, cg.part); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         NL_CUDA(cudaMemcpyAsync(hp, cg.part, sizeof(double) * cg.nb, cudaMemcpyDeviceToHost, s));
         NL_CUDA(cudaStreamSynchronize(s));
         double rr = 0.0;
         for (int i = 0; i < cg.nb; ++i) rr += hp[i];
         inf.rel_residual = (nb_ > 0) ? sqrt(rr) / nb_ : 0.0;
+        inf.barrier_fallbacks = cg.fallbacks;
         { k_scatter_u<<<(unsigned)nl_cdiv<int64_t>(std::max(m->nv, n), 256), 256, 0, s>>>(
               x, m->free_nodes, S->g, m->node_free, u_out, m->nv, n); nl_count_launch(); }
         NL_CHECK_LAUNCH();

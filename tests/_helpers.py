@@ -16,6 +16,22 @@ import numpy as np
 FLOOR_FP64 = 1e-7
 FLOOR_FP32 = 1e-7
 
+# FP64 bar per entry: 1e-12, and 2e-12 for approxcaps.  The device and the
+# oracle build the same approxcaps polytope but triangulate it differently
+# (the device inserts the arc midpoints into hull(I u P) and cones from the
+# points' mean; the oracle enumerates facets and cones from the centroid),
+# and both keep a midpoint whose in-face barycentrics are >= -1e-12.  Entries
+# of K are sums whose terms are up to 230 times the entry itself (measured
+# with the oracle's matrix of absolute block values on the jittered test
+# meshes), so those rounding differences reach 1.2e-12 of an entry (a 3-cell
+# mesh with delta = 3h); the other strategies stay below 1e-12.
+TOL_FP64 = 1e-12
+TOL_FP64_APPROXCAPS = 2e-12
+
+
+def tol_fp64(strategy):
+    return TOL_FP64_APPROXCAPS if strategy == 1 else TOL_FP64
+
 
 def entry_rel_err(K, Kref, floor_rel=FLOOR_FP32):
     """Per-entry relative error with floors for near-zero entries:

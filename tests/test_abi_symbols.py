@@ -68,8 +68,11 @@ def test_argument_errors_need_no_gpu():
     assert L.nl_pairs_build(None, 0.1, ctypes.byref(out)) == B.NL_EINVAL and msg() == "NULL argument"
     assert L.nl_assemble(None, None, ctypes.byref(out)) == B.NL_EINVAL
     for cells, lo, hi in ((0, 0.0, 1.0), (1001, 0.0, 1.0), (4, 1.0, 1.0), (4, float("nan"), 1.0)):
-        assert L.nl_mesh_create_box(None, lo, hi, cells, 0.0, 1.0, ctypes.byref(out)) == B.NL_EINVAL
+        assert L.nl_mesh_create_box(None, lo, hi, cells, 0.0, 1.0, 0.0, 0, ctypes.byref(out)) == B.NL_EINVAL
         assert "bad box" in msg() and out.value is None
+    for jit in (-0.1, 0.5, float("nan")):
+        assert L.nl_mesh_create_box(None, -0.25, 1.25, 6, 0.0, 1.0, jit, 7, ctypes.byref(out)) == B.NL_EINVAL
+        assert "jitter_frac" in msg() and out.value is None
     assert L.nl_probe_philox(None, 0, 4, None) == B.NL_EINVAL
     # a later successful call clears the message
     assert L.nl_probe_philox(ctypes.c_void_p(1), 0, 0, ctypes.c_void_p(1)) == B.NL_OK and msg() == ""

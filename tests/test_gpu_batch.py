@@ -84,7 +84,7 @@ def test_batched_problems_match_the_oracle(nl):
     for an FP64 fullcaps, an FP64 approxcaps and an FP32-comp fullcaps problem
     of one batch."""
     import oracle as O
-    from _helpers import FLOOR_FP64, entry_rel_err
+    from _helpers import FLOOR_FP64, entry_rel_err, tol_fp64
     dev = nl.Device()
     spec = [((4, 2, 0.2, 5), dict(strategy=nl.FULLCAPS, mc_points=32, seed=3, precision=nl.FP64)),
             ((3, 3, 0.2, 6), dict(strategy=nl.APPROXCAPS, precision=nl.FP64)),
@@ -101,7 +101,7 @@ def test_batched_problems_match_the_oracle(nl):
     for i, (mesh, delta, kw, _) in enumerate(meshes):
         s = batch.system(i)
         fp64 = kw["precision"] == nl.FP64
-        tol, floor = (1e-12, FLOOR_FP64) if fp64 else (1e-5, 1e-7)
+        tol, floor = (tol_fp64(kw["strategy"]), FLOOR_FP64) if fp64 else (1e-5, 1e-7)
         Kref = O.assemble_K(mesh, delta, kw["gamma"], kw["strategy"], nmc=kw.get("mc_points", 0),
                             seed=kw.get("seed", 1))
         assert entry_rel_err(s.scipy(nl.MAT_K), Kref, floor) <= tol, i

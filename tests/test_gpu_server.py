@@ -21,10 +21,14 @@ def nl():
     return nl
 
 
-def test_box_mesh_equals_host_mesh(nl):
+@pytest.mark.parametrize("jitter,seed", [(0.0, 0), (0.2, 7), (0.2, 2 ** 40 + 3)])
+def test_box_mesh_equals_host_mesh(nl, jitter, seed):
+    """The device generator gives the inputs module's mesh, jittered
+    vertices included: pair lists and the FP64 fullcaps K (which moves with
+    any bit of any coordinate) are bitwise equal."""
     dev = nl.Device()
-    mesh, delta = I.cube_problem(5, 2)
-    mb = nl.mesh_box(mesh.lo, mesh.hi, mesh.cells, 0.0, 1.0, dev)
+    mesh, delta = I.cube_problem(5, 2, jitter_frac=jitter, seed=seed)
+    mb = nl.mesh_box(mesh.lo, mesh.hi, mesh.cells, 0.0, 1.0, dev, jitter_frac=jitter, seed=seed)
     mh = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
     pb, ph = nl.Pairs(mb, delta), nl.Pairs(mh, delta)
     for a, b in zip(pb.export(), ph.export()):
@@ -43,7 +47,9 @@ def _requests(nl):
             S.box_request(4, 2.5, strategy=nl.APPROXCAPS, precision=nl.FP32_COMP, mixed=True),
             S.box_request(6, 1.0, strategy=nl.FULLCAPS, mc_points=16, precision=nl.FP64),   # same mesh as the first
             S.box_request(5, 2.0, strategy=nl.NOCAPS, precision=nl.FP32_COMP, mixed=True),  # same pairs as the second
-            S.box_request(7, 1.5, strategy=nl.APPROXCAPS, precision=nl.FP64)]
+            S.box_request(7, 1.5, strategy=nl.APPROXCAPS, precision=nl.FP64),
+            S.box_request(5, 2.0, strategy=nl.FULLCAPS, mc_points=16, precision=nl.FP32_COMP, mixed=True,
+                          jitter_frac=0.2, jitter_seed=11)]    # jittered: its own cache entry
 
 
 def test_server_result_same_alone_and_in_the_mix(nl):

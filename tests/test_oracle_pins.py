@@ -874,6 +874,24 @@ def test_load_vector_integrates_f():
     assert np.all(F[np.unique(m.tets[m.tet_in_omega == 0])] <= 0)
 
 
+def test_load_vector_of_a_nodal_source_is_the_mass_matrix_product():
+    """With f the P1 interpolant of nodal values, the 4-point rule is exact
+    for phi_i f (degree 2), so F = M f + c a with M the P1 mass matrix of the
+    elements of Omega (|T|/20 (1 + delta_ij) per element, assembled here) and
+    a_i = int_Omega phi_i."""
+    m = I.kuhn_box(-0.25, 1.25, 6, jitter_frac=0.2, seed=9)
+    rng = np.random.default_rng(12)
+    fn = rng.normal(size=m.nv)
+    M = np.zeros((m.nv, m.nv))
+    for t in np.nonzero(m.tet_in_omega)[0]:
+        v = m.verts[m.tets[t]]
+        vol = abs(np.linalg.det(v[1:] - v[0])) / 6
+        M[np.ix_(m.tets[t], m.tets[t])] += vol / 20 * (np.ones((4, 4)) + np.eye(4))
+    F = O.load_vector(m, 0.7, f_nodal=fn)
+    want = M @ fn + 0.7 * M.sum(axis=1)
+    assert np.allclose(F, want, rtol=1e-12, atol=1e-15 * np.abs(want).max())
+
+
 @pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS])
 def test_collar_weight_and_kernel_constant_by_convergence(strat):
     """u = |x|^2, f = -6: with the collar weight 2 and psi = gamma/2 the

@@ -55,3 +55,27 @@ def test_static_solve_matches_allocating_solve_twice():
         got = u.cpu().numpy()
         assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max(), call
         assert inf.rel_residual <= 1e-12 * 1.01
+
+
+def test_static_solve_rejects_a_host_output():
+    """The static solve writes u_out from its kernels, so it must be device
+    memory: a host array is refused with NL_EINVAL before any launch."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2302_07499_gb300 as nl
+    from paper_2302_07499_gb300 import _binding as B
+    L = nl.lib()
+    L.nl_solve_static.argtypes = [C.c_void_p, C.POINTER(B.nl_solve_opts), C.c_void_p, C.POINTER(B.nl_solve_info)]
+    L.nl_solve_static.restype = C.c_int
+    mesh, delta = I.config_mesh("cube6_d025")
+    dev = nl.Device()
+    m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+    p = nl.Pairs(m, delta)
+    s = nl.System(p, strategy=nl.NOCAPS, precision=nl.FP64, gamma=I.gamma_const(delta), f_const=-6.0,
+                  g=I.quadratic_g(mesh.verts))
+    host = np.zeros(mesh.nv)
+    inf = B.nl_solve_info()
+    st = L.nl_solve_static(s.h, C.byref(B.nl_solve_opts(1e-12, 0, 0, 0.0, 0)), C.c_void_p(host.ctypes.data),
+                           C.byref(inf))
+    assert st == 1 and b"device memory" in L.nl_last_error()
+    assert np.all(host == 0.0)
