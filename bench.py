@@ -723,8 +723,8 @@ def run_spmv(args, ws, rank, local):
     does not depend on the values' origin), everything but the system is
     released, and the kernel is timed back to back (as in CG, where A partly
     stays in the 129 MB L2) and, launch by launch, after a write of 512 MiB
-    that flushes L2 (the HBM-bound figure).  Small in device memory, so that
-    a profiler can replay it."""
+    that flushes L2 (the HBM-bound figure), after a warm-up of --warmup x 100
+    launches.  Small in device memory, so that a profiler can replay it."""
     import torch
     import paper_2302_07499_gb300 as nl
 
@@ -739,8 +739,11 @@ def run_spmv(args, ws, rank, local):
     hbm = _measured_peak("hbm_gbs", 6800.0)
     out = {}
     for name, prec in (("fp32", nl.FP32_COMP), ("fp64", nl.FP64)):
-        ms_b2b, by = s.spmv_time(prec, reps=args.steps)
-        ms_cold, _ = s.spmv_time(prec, reps=args.steps, flush_bytes=512 * 2 ** 20)
+        # warm-up: a few hundred launches (tens of ms) bring the clocks up;
+        # a handful timed straight after a short assembly read 1.5x slower
+        s.spmv_time(prec, reps=max(args.warmup, 1) * 100)
+        ms_b2b, by = s.spmv_time(prec, reps=max(args.steps, 50))
+        ms_cold, _ = s.spmv_time(prec, reps=max(args.steps, 20), flush_bytes=512 * 2 ** 20)
         out[name] = {"bytes": by, "back_to_back_us": ms_b2b * 1e3, "cold_l2_us": ms_cold * 1e3,
                      "frac_of_measured_hbm_back_to_back": by / (ms_b2b / 1e3) / 1e9 / hbm[0],
                      "frac_of_measured_hbm_cold_l2": by / (ms_cold / 1e3) / 1e9 / hbm[0]}

@@ -52,12 +52,14 @@ def test_traffic_record_missing_or_malformed(fake_root):
 
 
 def test_committed_traffic_record_is_consistent():
-    """The committed record scales the captured launch's bytes by the sample
-    ratio it states, so its per-step figure follows from its own fields."""
+    """The committed record scales the captured launch's bytes by the ratio of
+    cut events it states, so its per-step figure follows from its own fields,
+    and it was taken on the current kernel sources."""
     rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))
     cap = rec["dram_read_bytes_captured"] + rec["dram_write_bytes_captured"]
-    want = cap * rec["mc_samples_per_step"] / rec["mc_samples_captured"]
+    want = cap * rec["cut_points_per_step"] / rec["cut_points_captured"]
     assert abs(rec["dram_bytes_per_step"] - want) <= 1e-9 * want
+    assert rec["source_sha"] == bench._kernel_source_sha()
     assert len(rec["source_sha"]) == 16
 
 
