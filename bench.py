@@ -750,7 +750,7 @@ def run_spmv(args, ws, rank, local):
     line = {"metric": "CG SpMV GB/s on the jittered 38^3 workload's A", "unit": "fraction of measured HBM",
             "value": out["fp32"]["frac_of_measured_hbm_back_to_back"], "higher_is_better": True, "n_gpus": ws,
             "config": {"workload": "jitter38_d3h_spmv", "n_free": p.info["n_free"], "nnz_A": p.info["nnz_a"],
-                       "kernel": "k_spmv_dot_pad (rows padded to multiples of 4 entries, 8 lanes per row)"},
+                       "kernel": "k_spmv_dot_pad (rows padded to multiples of 4 entries; 16 lanes per row for FP32 values, 8 for FP64; at most the resident blocks)"},
             "hbm_peak_gbs": hbm[0], "hbm_peak_source": hbm[1], "spmv": out}
     if rank == 0:
         print(json.dumps(line), flush=True)

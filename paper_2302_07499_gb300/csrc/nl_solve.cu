@@ -63,13 +63,13 @@ __device__ __forceinline__ bool last_block(CgState *st)
     return last && threadIdx.x < 32;
 }
 
-// One row of A p on the padded rows, by the 8 lanes sub = 0..7 of a lane group
-// (each lane's partial sum; the caller adds the 8): FP32 values as float4
-// with int4 columns, FP64 values as double2 with int2 columns, and four
-// 16-byte chunks of each lane loaded before their gathers, so that a row of
-// several hundred entries costs a few memory round trips, not one per 32
+// One row of A p on the padded rows, by the L lanes sub = 0..L-1 of a lane
+// group (each lane's partial sum; the caller adds the L): FP32 values as
+// float4 with int4 columns, FP64 values as double2 with int2 columns, and
+// four 16-byte chunks of each lane loaded before their gathers, so that a row
+// of several hundred entries costs a few memory round trips, not one per 32
 // entries.  Pads hold value 0 and the row's own column.
-template <class VT, class XT>
+template <class VT, class XT, int L = 8>
 __device__ __forceinline__ VT pad_row(const int64_t *__restrict__ rp4, const int32_t *__restrict__ cp,
                                       const VT *__restrict__ vp, const XT *__restrict__ p, int64_t r, int sub)
 {
@@ -79,12 +79,12 @@ __device__ __forceinline__ VT pad_row(const int64_t *__restrict__ rp4, const int
         const int4 *c4 = reinterpret_cast<const int4 *>(cp);
         const float4 *v4 = reinterpret_cast<const float4 *>(vp);
         const int64_t e0 = rp4[r], e1 = rp4[r + 1];
-        for (int64_t e = e0 + sub; e < e1; e += 8 * U) {
+        for (int64_t e = e0 + sub; e < e1; e += L * U) {
             float4 v[U];
             int4 c[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int64_t ee = e + 8 * u;
+                const int64_t ee = e + L * u;
                 if (ee < e1) { v[u] = __ldcs(v4 + ee); c[u] = __ldcs(c4 + ee); }
                 else { v[u] = make_float4(0.f, 0.f, 0.f, 0.f); c[u] = make_int4(0, 0, 0, 0); }
             }
@@ -100,12 +100,12 @@ __device__ __forceinline__ VT pad_row(const int64_t *__restrict__ rp4, const int
         const int2 *c2 = reinterpret_cast<const int2 *>(cp);
         const double2 *v2 = reinterpret_cast<const double2 *>(vp);
         const int64_t e0 = 2 * rp4[r], e1 = 2 * rp4[r + 1];
-        for (int64_t e = e0 + sub; e < e1; e += 8 * U) {
+        for (int64_t e = e0 + sub; e < e1; e += L * U) {
             double2 v[U];
             int2 c[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int64_t ee = e + 8 * u;
+                const int64_t ee = e + L * u;
                 if (ee < e1) { v[u] = __ldcs(v2 + ee); c[u] = __ldcs(c2 + ee); }
                 else { v[u] = make_double2(0.0, 0.0); c[u] = make_int2(0, 0); }
             }
@@ -119,25 +119,30 @@ __device__ __forceinline__ VT pad_row(const int64_t *__restrict__ rp4, const int
     return s;
 }
 
-// q = A p on the padded rows (8 lanes per row, 4 rows per warp) with the
-// per-block partials of p.q; in the CG the last block forms alpha.  Every
-// warp walks the same number of row groups (rows beyond n are skipped), so
-// the lane-group sums can use full-warp shuffles.
+// q = A p on the padded rows (spmv_lanes<VT> lanes per row: 16 for FP32
+// values, 8 for FP64) with the per-block partials of p.q; in the CG the last
+// block forms alpha.  Every warp walks the same number of row groups (rows
+// beyond n are skipped), so the lane-group sums can use full-warp shuffles.
+// The grid is the resident blocks at most (spmv_blocks): each row group walks
+// a few rows with all of them in flight, and no second wave of blocks trails
+// the first.
+template <class VT> __host__ __device__ constexpr int spmv_lanes() { return sizeof(VT) == 4 ? 16 : 8; }
+
 template <class VT, class XT>
 __global__ void __launch_bounds__(RB) k_spmv_dot_pad(const int64_t *__restrict__ rp4, const int32_t *__restrict__ cp,
                                                      const VT *__restrict__ vp, const XT *__restrict__ p, XT *q,
                                                      int64_t n, double *part, CgState *st)
 {
+    constexpr int L = spmv_lanes<VT>();
     __shared__ double sh[RB / 32];
     if (st && st->done) return;
-    const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
-    const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+    const int lane = threadIdx.x & 31, sub = lane & (L - 1), grp = lane / L;
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / L);
     double acc = 0.0;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; r - grp < n; r += groups) {
-        VT sum = r < n ? pad_row<VT, XT>(rp4, cp, vp, p, r, sub) : VT(0);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-        sum += __shfl_xor_sync(0xffffffffu, sum, 4);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L; r - grp < n; r += groups) {
+        VT sum = r < n ? pad_row<VT, XT, L>(rp4, cp, vp, p, r, sub) : VT(0);
+#pragma unroll
+        for (int o = 1; o < L; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (sub == 0 && r < n) {
             q[r] = (XT)sum;
             acc += (double)p[r] * (double)sum;
@@ -419,13 +424,29 @@ __global__ void k_scatter_u(const double *x, const int32_t *free_nodes, const do
     if (i < nf) u[free_nodes[i]] = x[i];
 }
 
-// Blocks of the CG kernels: a warp per row up to 16 blocks of 256 threads per
-// SM (the SpMV gathers are latency-bound; full occupancy keeps the most
-// loads in flight), at most 4096 (the partials of the no-allocation solve).
+// Blocks of the CG's vector kernels and of the FP64 residual: up to 16
+// blocks of 256 threads per SM and 32 threads per row, at most 4096 (the
+// partials of the no-allocation solve).
 int cg_blocks(int64_t n)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>((int64_t)nl_num_sms() * 16, 4096),
                                                        nl_cdiv<int64_t>(n * 32, RB)));
+}
+
+// Blocks of k_spmv_dot_pad: one row group per row up to the blocks resident
+// at once (never more than cg_blocks, whose partials array the kernel
+// writes).
+template <class VT, class XT>
+int spmv_blocks(int64_t n)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_dot_pad<VT, XT>, RB, 0) != cudaSuccess || occ < 1) {
+        (void)cudaGetLastError();
+        occ = 1;
+    }
+    const int64_t rows = nl_cdiv<int64_t>(n * spmv_lanes<VT>(), RB);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>((int64_t)occ * nl_num_sms(), rows),
+                                                       cg_blocks(n)));
 }
 
 // systems up to this many rows update p in the last block of the x/r update
@@ -510,10 +531,11 @@ int run_cg(const int64_t *rp, const int32_t *ci, const VT *val, const int64_t *r
             }
         }
     }
+    const int nbs = spmv_blocks<VT, XT>(n);
     while (launched < max_it) {
         int k = std::min(check_every, max_it - launched);
         for (int j = 0; j < k; ++j) {
-            { k_spmv_dot_pad<VT, XT><<<nb, RB, 0, s>>>(rp4, cp, vp, p, q, n, cg.part, cg.st); nl_count_launch(); }
+            { k_spmv_dot_pad<VT, XT><<<nbs, RB, 0, s>>>(rp4, cp, vp, p, q, n, cg.part, cg.st); nl_count_launch(); }
             if (n <= kFuseRows) {
                 { k_update_xr<XT, true><<<nb, RB, 0, s>>>(x, r, p, q, n, cg.part, cg.st); nl_count_launch(); }
             } else {
@@ -657,7 +679,7 @@ extern "C" nl_status nl_spmv_time(nl_system *S, int precision, int reps, int64_t
         unsigned char *fl = flush_bytes > 0 ? sc.get<unsigned char>(flush_bytes) : nullptr;
         { k_fill_ones<<<(unsigned)nl_cdiv<int64_t>(n, 256), 256, 0, s>>>(xd, xf, n); nl_count_launch(); }
         NL_CHECK_LAUNCH();
-        const int nb = cg_blocks(n);
+        const int nb = precision == NL_FP64 ? spmv_blocks<double, double>(n) : spmv_blocks<float, float>(n);
         auto launch = [&]() {
             if (precision == NL_FP64)
                 { k_spmv_dot_pad<double, double><<<nb, RB, 0, s>>>(P->ap_rowptr4, P->ap_col, S->Ap, xd, yd, n, nullptr, nullptr); nl_count_launch(); }
