@@ -769,7 +769,9 @@ def run_paper3d(args, ws, rank, local):
     solution (FP32-comp assembly, mixed CG to 1e-10) and the assembly's device
     time (quadrature + reduction); per strategy the efficiency ratio
     lambda_n = -log(e_{n-1}/e_n) / log(t_{n-1}/t_n) between consecutive
-    meshes."""
+    meshes.  On the meshes of --paper3d-unfolded-inv-h the unfolded form of
+    Eq. weak0 (every element an outer element, no collar weight) runs beside
+    the folded one (rows marked by "form"; lambda uses the folded rows)."""
     import torch
     import paper_2302_07499_gb300 as nl
 
@@ -779,6 +781,7 @@ def run_paper3d(args, ws, rank, local):
     gamma = I.paper3d_gamma(delta)
     rows = []
     launches0 = nl.kernel_launches()
+    unfolded_at = {int(x) for x in args.paper3d_unfolded_inv_h.split(",") if x}
     for inv_h in [int(x) for x in args.paper3d_inv_h.split(",")]:
         mesh = I.paper3d_mesh(inv_h, delta)
         e = mesh.verts[mesh.tets]
@@ -786,24 +789,26 @@ def run_paper3d(args, ws, rank, local):
         h_avg = float(np.mean(np.concatenate(edges)))
         f = I.paper3d_f(mesh.verts, delta)
         g = I.paper3d_u(mesh.verts)
-        m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
-        p = nl.Pairs(m, delta)
-        for name, code, nmc in PAPER3D_STRATEGIES:
-            sys_ = nl.System(p, strategy=code, mc_points=max(nmc, 1), seed=1, precision=nl.FP32_COMP, gamma=gamma,
-                             f_const=0.0, g=g, f=f)
-            st = sys_.stats()
-            u, info = sys_.solve(rtol=1e-10, mixed=True)
-            rows.append({"inv_h": inv_h, "h_avg": h_avg, "delta_over_h": delta * inv_h, "tets": mesh.nt,
-                         "element_pairs": p.info["n_pairs"], "strategy": name, "mc_points": nmc,
-                         "assembly_ms": st["quadrature_ms"] + st["reduce_ms"],
-                         "l2_error": l2_error(mesh, u, I.paper3d_u), "cg_iterations": info["iterations"],
-                         "rel_residual": info["rel_residual"]})
-            sys_.close()
-            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
-        p.close(); m.close()
+        forms = ("folded", "unfolded") if inv_h in unfolded_at else ("folded",)
+        for form in forms:
+            m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev, unfolded=form == "unfolded")
+            p = nl.Pairs(m, delta)
+            for name, code, nmc in PAPER3D_STRATEGIES:
+                sys_ = nl.System(p, strategy=code, mc_points=max(nmc, 1), seed=1, precision=nl.FP32_COMP,
+                                 gamma=gamma, f_const=0.0, g=g, f=f)
+                st = sys_.stats()
+                u, info = sys_.solve(rtol=1e-10, mixed=True)
+                rows.append({"inv_h": inv_h, "h_avg": h_avg, "delta_over_h": delta * inv_h, "tets": mesh.nt,
+                             "form": form, "element_pairs": p.info["n_pairs"], "strategy": name, "mc_points": nmc,
+                             "assembly_ms": st["quadrature_ms"] + st["reduce_ms"],
+                             "l2_error": l2_error(mesh, u, I.paper3d_u), "cg_iterations": info["iterations"],
+                             "rel_residual": info["rel_residual"]})
+                sys_.close()
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            p.close(); m.close()
     lam = {}
     for name, _, _ in PAPER3D_STRATEGIES:
-        r = [x for x in rows if x["strategy"] == name]
+        r = [x for x in rows if x["strategy"] == name and x["form"] == "folded"]
         lam[name] = [-float(np.log(a["l2_error"] / b["l2_error"]) / np.log(a["assembly_ms"] / b["assembly_ms"]))
                      for a, b in zip(r[:-1], r[1:])]
     line = {"metric": "paper 3D experiment shape: L2 error and assembly time per strategy", "unit": "ms, L2 error",
@@ -878,6 +883,8 @@ def main():
     ap.add_argument("--workers", type=int, default=4, help="workload serve_stream_seed5: server workers")
     ap.add_argument("--paper3d-inv-h", default="18,21,24,28,32,36,40",
                     help="workload paper3d_delta01: 1/h of the meshes of the sweep")
+    ap.add_argument("--paper3d-unfolded-inv-h", default="18,24",
+                    help="workload paper3d_delta01: meshes on which the unfolded form runs too")
     ap.add_argument("--batch-pairs", type=float, default=6e8,
                     help="element-pair budget of one sub-batch (workload batch256_seed3)")
     args = ap.parse_args()

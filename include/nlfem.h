@@ -93,6 +93,16 @@ typedef struct nl_system nl_system;
  *                 0 = node in the closed collar, dOmega included (Sec. 3.2),
  *                 where the volume constraint fixes the value.
  *   where         NL_HOST or NL_DEVICE for all four arrays.
+ * The folded and the unfolded forms.  The elements marked 1 are the outer
+ * elements of the assembly, and a collar element T' (marked 0) carries the
+ * weight 2.  So with the true Omega/collar split the assembly is the folded
+ * form of Sec. 2.2 (Eqs. weak1 and Ah), whose outer integral runs over Omega
+ * only.  Marking every element 1, with node_free unchanged, assembles the
+ * unfolded form of Eq. weak0 instead: outer integral over all of Omega-hat,
+ * no weight 2.  The load vector then integrates f over every element, and
+ * its rows for free nodes are unchanged, because a free node lies in the
+ * open Omega and touches no collar element.  So the system (A, b) is that of
+ * Eq. weak0.
  * Errors: NL_EINVAL for nv<4, nt<1, an id out of range or an element with
  * non-positive signed volume (vertices must be positively oriented);
  * NL_ENOMEM; NL_ECUDA.  The mesh keeps a pointer to *dev (must outlive it). */

@@ -18,6 +18,7 @@ paper's unstructured meshes (Sec. 5.2), which are not published.
 from __future__ import annotations
 
 import itertools
+import dataclasses
 from dataclasses import dataclass
 
 import numpy as np
@@ -44,6 +45,13 @@ class Mesh:
     @property
     def nt(self):
         return int(self.tets.shape[0])
+
+
+def unfolded(mesh: Mesh) -> Mesh:
+    """The same mesh with every element marked as an outer element and
+    node_free unchanged: assembled, it gives the unfolded form of Eq. weak0
+    (outer integral over all of Omega-hat, no collar weight)."""
+    return dataclasses.replace(mesh, tet_in_omega=np.ones_like(mesh.tet_in_omega))
 
 
 def philox4x32_10(ctr, key):

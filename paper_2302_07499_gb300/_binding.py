@@ -235,10 +235,16 @@ def _as_tensor(ptr, n, dtype):
 
 
 class Mesh:
-    def __init__(self, verts, tets, tet_in_omega, node_free, device: Device | None = None):
+    def __init__(self, verts, tets, tet_in_omega, node_free, device: Device | None = None, unfolded: bool = False):
+        """unfolded=True marks every element as an outer element (tet_in_omega
+        all 1): the assembly is then the unfolded form of Eq. weak0, outer
+        integral over all of Omega-hat and no collar weight (nl_mesh_create)."""
         import torch
         self.device = device or Device()
         self._keep = []
+        if unfolded:
+            tet_in_omega = (torch.ones_like(tet_in_omega) if isinstance(tet_in_omega, torch.Tensor)
+                            else np.ones(len(tet_in_omega), dtype=np.uint8))
         if isinstance(verts, torch.Tensor) and verts.is_cuda:
             arrs = [verts.contiguous().double(), tets.contiguous().int(), tet_in_omega.contiguous().to(torch.uint8),
                     node_free.contiguous().to(torch.uint8)]

@@ -13,7 +13,7 @@ import pytest
 import nl_inputs as I
 import oracle as O
 
-from _helpers import FLOOR_FP64, entry_rel_err, tol_fp64
+from _helpers import FLOOR_FP32, FLOOR_FP64, entry_rel_err, tol_fp64
 
 pytestmark = pytest.mark.gpu
 
@@ -204,6 +204,34 @@ def test_K_fp32_comp_matches_oracle(nl, dev, name, mesh, delta, strategy):
     K = s.scipy(nl.MAT_K)
     Kref = O.assemble_K(mesh, delta, I.gamma_const(delta), strategy, nmc=64, seed=1)
     assert entry_rel_err(K, Kref) <= 1e-5
+
+
+@pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("name,mesh,delta", [_meshes()[1], _meshes()[3]])
+def test_unfolded_form_matches_oracle(nl, dev, name, mesh, delta, strategy):
+    """Eq. weak0 (every element an outer element, no collar weight): the
+    device's K over all nodes, A and b against the oracle's unfolded
+    assembly, FP64 at the per-entry bar and FP32-comp at 1e-5; the unfolded
+    K has collar rows the folded one lacks."""
+    mu = I.unfolded(mesh)
+    g = I.quadratic_g(mesh.verts)
+    m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev, unfolded=True)
+    p = nl.Pairs(m, delta)
+    assert p.info["n_pairs"] == len(O.pairs(mu, delta)[2])
+    Kref = O.assemble_K(mu, delta, I.gamma_const(delta), strategy, nmc=64, seed=1)
+    A, b, free = O.system(mu, Kref, O.load_vector(mu, -6.0), g)
+    for precision, bar, floor in ((nl.FP64, tol_fp64(strategy), FLOOR_FP64), (nl.FP32_COMP, 1e-5, FLOOR_FP32)):
+        s = nl.System(p, strategy=strategy, mc_points=64, seed=1, precision=precision,
+                      gamma=I.gamma_const(delta), f_const=-6.0, g=g)
+        K = s.scipy(nl.MAT_K)
+        assert entry_rel_err(K, Kref, floor) <= bar
+        assert entry_rel_err(s.scipy(nl.MAT_A), A, floor) <= bar
+        bg = s.rhs()[0].cpu().numpy()
+        assert np.abs(bg - b).max() <= (1e-12 if precision == nl.FP64 else 1e-5) * np.abs(b).max()
+        s.close()
+    con = np.nonzero(mesh.node_free == 0)[0]
+    Kfold = O.assemble_K(mesh, delta, I.gamma_const(delta), strategy, nmc=64, seed=1).tocsr()
+    assert abs(Kref.tocsr()[con][:, con]).sum() > 2 * abs(Kfold[con][:, con]).sum()
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -846,6 +846,45 @@ def test_folded_system_equals_unfolded_form_when_balls_cover_the_mesh(strat):
     assert np.allclose(b, b_want, rtol=1e-11, atol=1e-13 * np.abs(b_want).max())
 
 
+@pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS])
+def test_unfolded_form_equals_its_closed_form_on_every_entry(strat):
+    """Eq. weak0, the unfolded form: every element is an outer element and
+    no collar weight applies.  With delta above the mesh's diameter every
+    ball holds the whole mesh and every strategy is exact, so the full matrix,
+    collar rows and columns included, is gamma (|mesh| M - a a^T) (M the P1
+    mass matrix, a_i = int phi_i: the closed form of the folded pin, here on
+    all nodes).  The load vector's rows of free nodes do not depend on the
+    marking (a free node touches no collar element), and the system then
+    equals the folded one: Eqs. weak0 and weak1 are the same problem."""
+    mesh, _ = I.cube_problem(3, 1, jitter_frac=0.2, seed=17)
+    delta = 1.01 * np.linalg.norm(mesh.verts.max(axis=0) - mesh.verts.min(axis=0))
+    gamma = 0.7
+    mu = I.unfolded(mesh)
+    o, ptr, tp = O.pairs(mu, delta)
+    assert np.array_equal(o, np.arange(mesh.nt)) and np.all(np.diff(ptr) == mesh.nt)
+    K = O.assemble_K(mu, delta, gamma, strat, nmc=8, seed=3, prs=(o, ptr, tp))
+    M = np.zeros((mesh.nv, mesh.nv))
+    vol_all = 0.0
+    for t in mesh.tets:
+        v = mesh.verts[t]
+        vol = abs(np.linalg.det(v[1:] - v[0])) / 6
+        vol_all += vol
+        M[np.ix_(t, t)] += vol / 20 * (np.ones((4, 4)) + np.eye(4))
+    a = M.sum(axis=1)
+    Kc = gamma * (vol_all * M - np.outer(a, a))
+    assert np.allclose(K.toarray(), Kc, rtol=1e-11, atol=1e-13 * np.abs(Kc).max())
+    free = np.nonzero(mesh.node_free)[0]
+    F, Fu = O.load_vector(mesh, -6.0), O.load_vector(mu, -6.0)
+    assert np.array_equal(Fu[free], F[free])
+    assert not np.array_equal(Fu, F)             # the collar rows do change
+    g = I.quadratic_g(mesh.verts)
+    A, b, _ = O.system(mu, K, Fu, g)
+    Kf = O.assemble_K(mesh, delta, gamma, strat, nmc=8, seed=3)
+    Af, bf, _ = O.system(mesh, Kf, F, g)
+    assert np.allclose(A.toarray(), Af.toarray(), rtol=1e-11, atol=1e-13 * np.abs(Af).max())
+    assert np.allclose(b, bf, rtol=1e-11, atol=1e-13 * np.abs(bf).max())
+
+
 @pytest.mark.parametrize("strat", [O.NOCAPS, O.APPROXCAPS, O.FULLCAPS, O.BARYCENTER, O.OVERLAP, O.INSIDE])
 def test_stiffness_symmetric_zero_row_sums_psd(strat):
     # delta = h leaves no element wholly inside a ball; the element-level
