@@ -45,8 +45,11 @@ WORKLOADS = {
     "cube6_d025_nocaps": ("cube6_d025", 0, 0, 1, 1e-12),
     "cube16_d016_fullcaps64": ("cube16_d016", 2, 64, 1, 1e-10),
     "jitter38_d3h_fullcaps128": ("jitter38_d3h", 2, 128, 1, 1e-10),
+    # the same problem with the quasi-Monte Carlo cap points (not the
+    # paper's sampler; see NL_FULLCAPS_QMC)
+    "jitter38_d3h_fullcaps_qmc128": ("jitter38_d3h", 6, 128, 1, 1e-10),
 }
-STRAT_NAME = {0: "nocaps", 1: "approxcaps", 2: "fullcaps"}
+STRAT_NAME = {0: "nocaps", 1: "approxcaps", 2: "fullcaps", 6: "fullcaps_qmc"}
 
 # Algorithmic ALU operations of the quadrature kernels per unit, counted from
 # the arithmetic the method prescribes (each 32-bit add, multiply, fused
@@ -59,6 +62,10 @@ STRAT_NAME = {0: "nocaps", 1: "approxcaps", 2: "fullcaps"}
 #     of hull(I u P) with their moments and the cap cell volumes, about 300;
 #   per (pair, point): the classification, 4 x 7 = 28.
 OPS_PER_SAMPLE = 121
+# the quasi-Monte Carlo sampler draws no Philox words: per sample the next
+# Sobol' point (4 xor and the lowest set bit, 5) and its shift (4 xor) replace
+# the 80 Philox operations
+OPS_PER_SAMPLE_QMC = 121 - 80 + 9
 OPS_PER_ACCEPTED = 31
 OPS_PER_CUT = 300
 OPS_PER_PAIR_POINT = 28
@@ -257,14 +264,15 @@ def _traffic_record():
     return rec.get("dram_bytes_per_step")
 
 
-def _event_ops(st):
+def _event_ops(st, qmc=False):
     """ALU operations of the cut-point kernel k_events (cells, caps, samples)."""
-    return OPS_PER_CUT * st["cut_points"] + OPS_PER_SAMPLE * st["mc_samples"] + OPS_PER_ACCEPTED * st["mc_accepted"]
+    per_sample = OPS_PER_SAMPLE_QMC if qmc else OPS_PER_SAMPLE
+    return OPS_PER_CUT * st["cut_points"] + per_sample * st["mc_samples"] + OPS_PER_ACCEPTED * st["mc_accepted"]
 
 
-def _quadrature_ops(st):
+def _quadrature_ops(st, qmc=False):
     """ALU operations of the three quadrature kernels."""
-    return OPS_PER_PAIR_POINT * 4 * st["pairs"] + _event_ops(st)
+    return OPS_PER_PAIR_POINT * 4 * st["pairs"] + _event_ops(st, qmc)
 
 
 # ---------------------------------------------------------------------------
@@ -441,10 +449,16 @@ def run_ours(args, ws, rank, local):
     st = steps[-1]["stats"]
     ems = float(np.mean([s_["stats"]["events_ms"] for s_ in steps]))
     qms = float(np.mean([s_["stats"]["quadrature_ms"] for s_ in steps]))
-    ops = _event_ops(st)
+    qmc = strategy == 6
+    ops = _event_ops(st, qmc)
     props = torch.cuda.get_device_properties(local)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak, peak_info = alu_peak(nl, sm_max, props.multi_processor_count)
+    if qmc:
+        # no Philox in the sample: the FP32 fused multiply-add rate bounds the mix
+        peak = peak_info["rates_tops"]["ffma_fp32"]
+        peak_info = dict(peak_info, source="measured: nl_probe_alu_rates, FP32 fused multiply-add (the "
+                         "quasi-Monte Carlo sample draws no Philox words)")
     achieved = ops / (ems / 1e3) / 1e12
     # the FP64 SpMV also needs one FP64 multiply-add per entry: on this part
     # the measured DFMA rate puts a floor under its time next to HBM's
@@ -458,8 +472,8 @@ def run_ours(args, ws, rank, local):
                 "frac_of_derived_issue_peak": achieved / peak_info["derived_issue_peak_tops"],
                 "algorithmic_ops_per_step": ops, "kernel_ms_per_step": ems, "share_of_step": ems / ms_mean,
                 "quadrature": {"kernels": "k_classify + k_events + k_combine", "ms": qms,
-                               "algorithmic_ops": _quadrature_ops(st),
-                               "achieved_tops": _quadrature_ops(st) / (qms / 1e3) / 1e12}}
+                               "algorithmic_ops": _quadrature_ops(st, qmc),
+                               "achieved_tops": _quadrature_ops(st, qmc) / (qms / 1e3) / 1e12}}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds)
@@ -756,6 +770,58 @@ def run_spmv(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_fullcaps_variance(args, ws, rank, local):
+    """Monte Carlo against quasi-Monte Carlo cap points on the Kuhn 24^3 mesh
+    with delta = 1/8 (82,944 tets): for each sampler and cap point count, K
+    (FP32-comp) is assembled with 8 seeds, and the spread of its entries over
+    the seeds is summarised as the RMS and the maximum over entries of
+    std_seeds(K_ij) / sqrt(|K_ii K_jj|), beside the k_events time."""
+    import torch
+    import paper_2302_07499_gb300 as nl
+
+    torch.cuda.set_device(local)
+    mesh, delta = I.config_mesh("cube24_d0125")
+    gamma = I.gamma_const(delta)
+    dev = nl.Device()
+    m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+    p = nl.Pairs(m, delta)
+    rows = []
+    scale = None
+    for name, code in (("fullcaps", nl.FULLCAPS), ("fullcaps_qmc", nl.FULLCAPS_QMC)):
+        for nmc in (16, 32, 64, 128):
+            vals, ev = [], []
+            for seed in range(1, 9):
+                s_ = nl.System(p, strategy=code, mc_points=nmc, seed=seed, precision=nl.FP32_COMP, gamma=gamma,
+                               f_const=-6.0)
+                rp, ci, v = s_.csr(nl.MAT_K)
+                vals.append(v.clone())
+                ev.append(s_.stats()["events_ms"])
+                if scale is None:
+                    n = rp.numel() - 1
+                    rows_ = torch.repeat_interleave(torch.arange(n, device=v.device), rp[1:] - rp[:-1])
+                    dmask = ci.long() == rows_
+                    diag = torch.zeros(n, dtype=v.dtype, device=v.device)
+                    diag[rows_[dmask]] = v[dmask].abs()
+                    # the floor of the entry-error metric: entries of nodes
+                    # that no pair reaches (zero diagonal) are not divided by 0
+                    scale = torch.clamp(torch.sqrt(diag[rows_] * diag[ci.long()]), min=1e-7 * float(diag.max()))
+                s_.close()
+            V = torch.stack(vals)
+            rel = V.std(dim=0) / scale
+            rows.append({"sampler": name, "mc_points": nmc, "events_ms": float(np.mean(ev[1:])),
+                         "rms_rel_std": float(torch.sqrt((rel ** 2).mean())), "max_rel_std": float(rel.max())})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    p.close(); m.close()
+    line = {"metric": "spread of K over 8 seeds, Monte Carlo vs quasi-Monte Carlo cap points",
+            "unit": "RMS of std/sqrt(|K_ii K_jj|)", "value": None, "n_gpus": ws, "higher_is_better": False,
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "fullcaps_variance_cube24", "mesh": "cube24_d0125: Kuhn grid, 82944 tets",
+                       "delta": delta, "precision": "FP32-comp", "seeds": 8},
+            "rows": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 PAPER3D_STRATEGIES = (("overlap", 4, 0), ("inside", 5, 0), ("barycenter", 3, 0), ("nocaps", 0, 0),
                       ("approxcaps", 1, 0), ("fullcaps", 2, 128))
 
@@ -873,6 +939,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch256_seed3", "serve_stream_seed5",
                                                                            "paper3d_delta01", "batch256_small",
+                                                                           "fullcaps_variance_cube24",
                                                                            "jitter38_d3h_spmv"])
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 form (each takes ~17 s on "
                     "the default workload)")
@@ -899,6 +966,8 @@ def main():
         run_serve(args, ws, rank, local)
     elif args.workload == "paper3d_delta01":
         run_paper3d(args, ws, rank, local)
+    elif args.workload == "fullcaps_variance_cube24":
+        run_fullcaps_variance(args, ws, rank, local)
     elif args.workload == "jitter38_d3h_spmv":
         run_spmv(args, ws, rank, local)
     else:

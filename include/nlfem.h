@@ -61,7 +61,17 @@ typedef enum {
     NL_FULLCAPS = 2,
     NL_BARYCENTER = 3,
     NL_OVERLAP = 4,
-    NL_INSIDE = 5
+    NL_INSIDE = 5,
+    /* fullcaps with its cap points from a digitally shifted Sobol' sequence
+     * (randomized quasi-Monte Carlo) in place of independent Philox draws:
+     * the same cells, the same map from four words to a cell and a point,
+     * and the same estimator |S|/N sum 1{|y-x| <= delta}; sample k takes the
+     * words of Sobol' point k (Gray-code order, four dimensions, direction
+     * numbers from the primitive polynomials x+1, x^2+x+1, x^3+x+1 with
+     * Joe & Kuo's initial values) XOR one Philox draw of counter
+     * (T, T', q, 0xFFFFFFFF).  Not the paper's method: Sec. 4.3.2 leaves
+     * better sampling over the caps open. */
+    NL_FULLCAPS_QMC = 6
 } nl_strategy;
 typedef enum { NL_FP64 = 0, NL_FP32_COMP = 1 } nl_precision;
 typedef enum { NL_HOST = 0, NL_DEVICE = 1 } nl_where;
@@ -480,6 +490,12 @@ nl_status nl_probe_moments(const double *tets_xyz, const double *x, const uint32
 nl_status nl_probe_mc_samples(const double *tets_xyz, const double *x, const uint32_t *ids, int64_t n, double delta,
                               int mc_points, uint64_t seed, int precision, int32_t *n_samples, int32_t *cell,
                               uint8_t *accepted, double *y);
+
+/* nl_probe_qmc_samples — as nl_probe_mc_samples for NL_FULLCAPS_QMC: the
+ * cap points of the shifted Sobol' sequence (see nl_strategy). */
+nl_status nl_probe_qmc_samples(const double *tets_xyz, const double *x, const uint32_t *ids, int64_t n,
+                               double delta, int mc_points, uint64_t seed, int precision, int32_t *n_samples,
+                               int32_t *cell, uint8_t *accepted, double *y);
 
 /* nl_probe_philox — Philox4x32-10 (Salmon et al., SC'11) of n counters
  * ctr[n][4] under the key (key & 0xffffffff, key >> 32): the generator that

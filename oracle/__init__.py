@@ -30,6 +30,9 @@ _lib = None
 
 NOCAPS, APPROXCAPS, FULLCAPS = 0, 1, 2
 BARYCENTER, OVERLAP, INSIDE = 3, 4, 5     # element-level strategies (Sec. 4.3)
+# fullcaps with its cap points from a digitally shifted Sobol' sequence
+# (randomized quasi-Monte Carlo) instead of independent Philox draws
+FULLCAPS_QMC = 6
 
 
 def build(force: bool = False) -> str:
@@ -75,6 +78,9 @@ def lib():
             L.or_cap_samples.argtypes = [dp, dp, C.c_double, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32,
                                          C.c_uint32, dp, i32p, u8p]
             L.or_cap_samples.restype = C.c_int
+            L.or_cap_samples_qmc.argtypes = L.or_cap_samples.argtypes
+            L.or_cap_samples_qmc.restype = C.c_int
+            L.or_sobol_point.argtypes = [C.c_uint32, u32p]
             L.or_assemble_blocks.argtypes = [dp, i32p, u8p, C.c_double, C.c_double, C.c_int, C.c_int,
                                              C.c_uint64, i32p, i32p, C.c_int64, dp, C.c_int]
             L.or_assemble_blocks.restype = C.c_int64
@@ -160,18 +166,26 @@ def region_moments(vTp, x, delta, strategy, nmc=0, seed=1, idT=0, idTp=0, q=0):
     return M, float(mv[0]), int(acc)
 
 
-def cap_samples(vTp, x, delta, nmc, seed=1, idT=0, idTp=0, q=0):
+def cap_samples(vTp, x, delta, nmc, seed=1, idT=0, idTp=0, q=0, qmc=False):
     """The fullcaps Monte Carlo samples of one (T', x) case, as the assembly
     draws them: (y [n,3], cell [n], accepted [n]) with n = nmc, or n = 0 when
-    T' has no cap for x."""
+    T' has no cap for x.  qmc: the digitally shifted Sobol' points."""
     v = _f64(vTp).reshape(12)
     xx = _f64(x).reshape(3)
     y = np.zeros((max(nmc, 1), 3))
     cell = np.zeros(max(nmc, 1), dtype=np.int32)
     acc = np.zeros(max(nmc, 1), dtype=np.uint8)
-    n = lib().or_cap_samples(_p(v, C.c_double), _p(xx, C.c_double), float(delta), int(nmc), int(seed), int(idT),
-                             int(idTp), int(q), _p(y, C.c_double), _p(cell, C.c_int32), _p(acc, C.c_uint8))
+    fn = lib().or_cap_samples_qmc if qmc else lib().or_cap_samples
+    n = fn(_p(v, C.c_double), _p(xx, C.c_double), float(delta), int(nmc), int(seed), int(idT),
+           int(idTp), int(q), _p(y, C.c_double), _p(cell, C.c_int32), _p(acc, C.c_uint8))
     return y[:n], cell[:n], acc[:n].astype(bool)
+
+
+def sobol_point(k):
+    """The four 32-bit words of Sobol' point k (Gray-code order)."""
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_sobol_point(int(k), _p(out, C.c_uint32))
+    return out
 
 
 def pair_block(vT, vTp, delta, gamma, tp_in_collar, strategy, nmc=0, seed=1, idT=0, idTp=0):

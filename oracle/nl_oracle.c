@@ -845,6 +845,53 @@ void or_mc_point(const double *Sflat, int ns, const uint32_t u[4], double y[3], 
     if (which) *which = j;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Sobol' points in four dimensions (Sobol' 1967), for the quasi-Monte Carlo
+ * form of the cap integral.  The paper leaves better sampling over the caps
+ * open (Sec. 4.3.2: uniform points often fall outside the fullcap); this is
+ * one such choice, outside the paper's own method.
+ * Direction numbers of dimension d, bit b (b = 0 the most significant):
+ * v = m_{b+1} 2^(31-b), with m_k odd and m_k < 2^k.  Dimension 0 has
+ * m_k = 1 for every k (the van der Corput sequence).  Dimensions 1..3 take
+ * the primitive polynomials x + 1, x^2 + x + 1 and x^3 + x + 1 with the
+ * initial values m = (1), (1, 3) and (1, 3, 1) of Joe & Kuo's table (2008),
+ * and for k > s (s the degree, a_1 .. a_{s-1} the inner coefficients)
+ *   m_k = 2 a_1 m_{k-1} ^ 4 a_2 m_{k-2} ^ ... ^ 2^s m_{k-s} ^ m_{k-s}.
+ * Point k is the one of index g = k ^ (k >> 1) (Gray-code order, Antonov &
+ * Saleev 1979): the XOR of the direction numbers of the bits set in g.     */
+static void sobol_dirs(uint32_t v[4][32])
+{
+    static const int deg[4] = {0, 1, 2, 3};
+    static const unsigned inner[4] = {0, 0, 1, 1};     /* a_1 .. a_{s-1}, a_1 the high bit */
+    static const uint32_t init[4][3] = {{0, 0, 0}, {1, 0, 0}, {1, 3, 0}, {1, 3, 1}};
+    for (int b = 0; b < 32; ++b) v[0][b] = 1u << (31 - b);
+    for (int d = 1; d < 4; ++d) {
+        const int s = deg[d];
+        uint32_t m[33];
+        for (int k = 1; k <= s; ++k) m[k] = init[d][k - 1];
+        for (int k = s + 1; k <= 32; ++k) {
+            uint32_t x = m[k - s] ^ (m[k - s] << s);
+            for (int i = 1; i < s; ++i)
+                if ((inner[d] >> (s - 1 - i)) & 1u) x ^= m[k - i] << i;
+            m[k] = x;
+        }
+        for (int b = 0; b < 32; ++b) v[d][b] = m[b + 1] << (31 - b);
+    }
+}
+
+void or_sobol_point(uint32_t k, uint32_t out[4])
+{
+    uint32_t v[4][32];
+    sobol_dirs(v);
+    const uint32_t g = k ^ (k >> 1);
+    for (int d = 0; d < 4; ++d) {
+        uint32_t x = 0;
+        for (int b = 0; b < 32; ++b)
+            if ((g >> b) & 1u) x ^= v[d][b];
+        out[d] = x;
+    }
+}
+
 /* The Monte Carlo samples of the cap S = T' minus hull(I u P) around x
  * (Sec. 4.3.2, Alg. 4).  The cap exists only when T' meets the closed ball:
  * some vertex inside, or, with none inside, the distance from x to T' at
@@ -854,9 +901,15 @@ void or_mc_point(const double *Sflat, int ns, const uint32_t u[4], double y[3], 
  * of samples drawn (0 when there is no cap).                                */
 typedef void (*sample_fn)(void *ctx, int k, const double y[3], int cell, int accepted, double wgt);
 
+/* With qmc, sample k takes the words of Sobol' point k (or_sobol_point),
+ * each XORed with a word of one Philox draw with counter (idT, idTp, q,
+ * 0xFFFFFFFF) (a digital shift, which leaves every point uniform on the 2^32
+ * grid and keeps the net structure), in place of the Philox draw of counter
+ * (idT, idTp, q, k); the cell choice and the point follow from the words as
+ * for Monte Carlo.                                                          */
 static int cap_samples(const double v[4][3], const double vTp[12], const double x[3], double delta,
                        const classify_t *c, int nmc, uint64_t seed, uint32_t idT, uint32_t idTp, uint32_t q,
-                       sample_fn fn, void *ctx)
+                       int qmc, sample_fn fn, void *ctx)
 {
     if (c->m == 4 || nmc <= 0) return 0;
     if (c->m == 0 && !(or_dist2_point_tet(x, vTp) <= delta * delta)) return 0;
@@ -867,9 +920,20 @@ static int cap_samples(const double v[4][3], const double vTp[12], const double 
     double wgt = tot / (double)nmc;
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     double d2 = delta * delta;
+    uint32_t shift[4] = {0, 0, 0, 0};
+    if (qmc) {
+        uint32_t ctr[4] = {idT, idTp, q, 0xFFFFFFFFu};
+        or_philox4x32_10(ctr, key, shift);
+    }
     for (int k = 0; k < nmc; ++k) {
-        uint32_t ctr[4] = {idT, idTp, q, (uint32_t)k}, u[4];
-        or_philox4x32_10(ctr, key, u);
+        uint32_t u[4];
+        if (qmc) {
+            or_sobol_point((uint32_t)k, u);
+            for (int d = 0; d < 4; ++d) u[d] ^= shift[d];
+        } else {
+            uint32_t ctr[4] = {idT, idTp, q, (uint32_t)k};
+            or_philox4x32_10(ctr, key, u);
+        }
         double y[3];
         int which = 0;
         or_mc_point(&S[0][0][0], ns, u, y, &which);
@@ -922,6 +986,8 @@ int or_region_moments(const double vTp[12], const double x[3], double delta, int
                       double M[15], double *mc_vol)
 {
     const double (*v)[3] = (const double (*)[3])vTp;
+    const int qmc = strategy == OR_FULLCAPS_QMC;
+    if (qmc) strategy = OR_FULLCAPS;
     memset(M, 0, sizeof(double) * 15);
     if (mc_vol) *mc_vol = 0.0;
     classify_t c;
@@ -937,7 +1003,7 @@ int or_region_moments(const double vTp[12], const double x[3], double delta, int
     }
     struct moments_ctx mc = {M, v, 0, mc_vol};
     if (strategy == OR_FULLCAPS)
-        cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, q, moments_sample, &mc);
+        cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, q, qmc, moments_sample, &mc);
     return mc.acc;
 }
 
@@ -979,6 +1045,8 @@ int or_pair_block(const double vT[12], const double vTp[12], double delta, doubl
 {
     const double (*vt)[3] = (const double (*)[3])vT;
     const double (*v)[3] = (const double (*)[3])vTp;
+    const int qmc = strategy == OR_FULLCAPS_QMC;
+    if (qmc) strategy = OR_FULLCAPS;
     memset(blk, 0, sizeof(double) * 64);
     double xq[12];
     or_quad_points(vT, xq);
@@ -1003,7 +1071,7 @@ int or_pair_block(const double vT[12], const double vTp[12], double delta, doubl
         }
         if (strategy == OR_FULLCAPS) {
             struct block_ctx bc = {blk, lx, v, coef, 0};
-            cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, (uint32_t)q, block_sample, &bc);
+            cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, (uint32_t)q, qmc, block_sample, &bc);
             acc += bc.acc;
         }
     }
@@ -1037,7 +1105,17 @@ int or_cap_samples(const double vTp[12], const double x[3], double delta, int nm
     classify_t c;
     classify(v, x, delta, &c);
     struct record_ctx rc = {y, cell, accepted};
-    return cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, q, record_sample, &rc);
+    return cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, q, 0, record_sample, &rc);
+}
+
+int or_cap_samples_qmc(const double vTp[12], const double x[3], double delta, int nmc, uint64_t seed,
+                       uint32_t idT, uint32_t idTp, uint32_t q, double *y, int32_t *cell, uint8_t *accepted)
+{
+    const double (*v)[3] = (const double (*)[3])vTp;
+    classify_t c;
+    classify(v, x, delta, &c);
+    struct record_ctx rc = {y, cell, accepted};
+    return cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, q, 1, record_sample, &rc);
 }
 
 /* Blocks for a list of pairs (one 8x8 block per pair, rows/cols = the four

@@ -9,6 +9,9 @@
 #define OR_BARYCENTER 3
 #define OR_OVERLAP 4
 #define OR_INSIDE 5
+/* fullcaps with the cap points from a digitally shifted Sobol' sequence
+ * instead of independent Philox draws (randomized quasi-Monte Carlo) */
+#define OR_FULLCAPS_QMC 6
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double or_tet_volume(const double v[12]);
@@ -27,6 +30,9 @@ int or_region_moments(const double vTp[12], const double x[3], double delta, int
                       double M[15], double *mc_vol);
 int or_cap_samples(const double vTp[12], const double x[3], double delta, int nmc, uint64_t seed,
                    uint32_t idT, uint32_t idTp, uint32_t q, double *y, int32_t *cell, uint8_t *accepted);
+int or_cap_samples_qmc(const double vTp[12], const double x[3], double delta, int nmc, uint64_t seed,
+                       uint32_t idT, uint32_t idTp, uint32_t q, double *y, int32_t *cell, uint8_t *accepted);
+void or_sobol_point(uint32_t k, uint32_t out[4]);
 int or_pair_block(const double vT[12], const double vTp[12], double delta, double gamma,
                   int tp_in_collar, int strategy, int nmc, uint64_t seed,
                   uint32_t idT, uint32_t idTp, double blk[64]);

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libnlfem.so")
 NL_OK, NL_EINVAL, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV, NL_ETIMEOUT, NL_EBUSY, NL_EGEOM = range(8)
 NOCAPS, APPROXCAPS, FULLCAPS = 0, 1, 2
 BARYCENTER, OVERLAP, INSIDE = 3, 4, 5
+FULLCAPS_QMC = 6      # fullcaps with digitally shifted Sobol' cap points (nl_strategy)
 FP64, FP32_COMP = 0, 1
 HOST, DEVICE = 0, 1
 MAT_K, MAT_A, MAT_LIFT = 0, 1, 2
@@ -119,7 +120,7 @@ EXPORTED = ["nl_mesh_create", "nl_mesh_destroy", "nl_pairs_build", "nl_pairs_des
             "nl_solve_static", "nl_batch_create", "nl_batch_run", "nl_batch_system", "nl_batch_get_info",
             "nl_batch_destroy", "nl_mesh_create_box", "nl_server_create", "nl_server_submit", "nl_server_poll",
             "nl_server_wait", "nl_server_release", "nl_server_get_load", "nl_server_destroy", "nl_spmv_time",
-            "nl_probe_mc_samples", "nl_probe_alu_rates"]
+            "nl_probe_mc_samples", "nl_probe_qmc_samples", "nl_probe_alu_rates"]
 
 _lib = None
 
@@ -152,6 +153,7 @@ def lib():
     L.nl_probe_philox.argtypes = [vp, C.c_uint64, i64, vp]
     L.nl_probe_alu_rates.argtypes = [vp, C.c_int]
     L.nl_probe_mc_samples.argtypes = [vp, vp, vp, i64, dp, C.c_int, C.c_uint64, C.c_int, vp, vp, vp, vp]
+    L.nl_probe_qmc_samples.argtypes = L.nl_probe_mc_samples.argtypes
     L.nl_last_error.restype = C.c_char_p
     L.nl_version.restype = C.c_char_p
     L.nl_kernel_launches.restype = C.c_uint64
@@ -578,9 +580,10 @@ def probe_moments(tets_xyz, x, ids, delta, strategy, mc_points=0, seed=1, precis
     return out
 
 
-def probe_mc_samples(tets_xyz, x, ids, delta, mc_points, seed=1, precision=FP64):
+def probe_mc_samples(tets_xyz, x, ids, delta, mc_points, seed=1, precision=FP64, qmc=False):
     """(n_samples [n], cell [n, mc], accepted [n, mc], y [n, mc, 3]) of the
-    fullcaps Monte Carlo samples of single cases (nl_probe_mc_samples)."""
+    fullcaps Monte Carlo samples of single cases (nl_probe_mc_samples; with
+    qmc, the shifted Sobol' samples of nl_probe_qmc_samples)."""
     tv = np.ascontiguousarray(tets_xyz, dtype=np.float64).reshape(-1, 12)
     xs = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
     ii = np.ascontiguousarray(ids, dtype=np.uint32).reshape(-1, 3)
@@ -589,8 +592,9 @@ def probe_mc_samples(tets_xyz, x, ids, delta, mc_points, seed=1, precision=FP64)
     cell = np.zeros((n, mc_points), dtype=np.int32)
     acc = np.zeros((n, mc_points), dtype=np.uint8)
     y = np.zeros((n, mc_points, 3))
-    _check(lib().nl_probe_mc_samples(_ptr(tv), _ptr(xs), _ptr(ii), n, float(delta), int(mc_points), int(seed),
-                                     int(precision), _ptr(ns), _ptr(cell), _ptr(acc), _ptr(y)))
+    fn = lib().nl_probe_qmc_samples if qmc else lib().nl_probe_mc_samples
+    _check(fn(_ptr(tv), _ptr(xs), _ptr(ii), n, float(delta), int(mc_points), int(seed),
+              int(precision), _ptr(ns), _ptr(cell), _ptr(acc), _ptr(y)))
     return ns, cell, acc.astype(bool), y
 
 

@@ -37,9 +37,10 @@ nl_status nl_check_hull_fallbacks(uint64_t fallbacks)
 
 nl_status nl_check_assemble_opts(const nl_assemble_opts *opts)
 {
-    if (opts->strategy < NL_NOCAPS || opts->strategy > NL_INSIDE) { nl_set_error("bad strategy"); return NL_EINVAL; }
+    if (opts->strategy < NL_NOCAPS || opts->strategy > NL_FULLCAPS_QMC) { nl_set_error("bad strategy"); return NL_EINVAL; }
     if (opts->precision != NL_FP64 && opts->precision != NL_FP32_COMP) { nl_set_error("bad precision"); return NL_EINVAL; }
-    if (opts->strategy == NL_FULLCAPS && (opts->mc_points < 1 || opts->mc_points > 4096)) {
+    if ((opts->strategy == NL_FULLCAPS || opts->strategy == NL_FULLCAPS_QMC) &&
+        (opts->mc_points < 1 || opts->mc_points > 4096)) {
         nl_set_error("mc_points must be in 1..4096 for fullcaps");
         return NL_EINVAL;
     }

@@ -62,6 +62,7 @@ struct AsmArgs {
     int64_t p0, p1;          // pairs of this chunk (launch index space)
     int max_row;
     int nmc;
+    int qmc;                 // fullcaps cap points: 0 Philox draws, 1 shifted Sobol' points
     int hull_maxf;           // face capacity of the approxcaps hull (full capacity except in overflow tests)
     uint32_t rk[20];         // Philox round keys
     // per-chunk work arrays
@@ -144,7 +145,8 @@ inline void init_group_args(AsmArgs &A, const nl_assemble_opts &o, unsigned long
 {
     A.max_row = max_row;
     A.hull_maxf = nl_hull_max_faces();
-    A.nmc = o.strategy == NL_FULLCAPS ? o.mc_points : 0;
+    A.nmc = (o.strategy == NL_FULLCAPS || o.strategy == NL_FULLCAPS_QMC) ? o.mc_points : 0;
+    A.qmc = o.strategy == NL_FULLCAPS_QMC ? 1 : 0;
     philox_round_keys(o.seed, A.rk);
     A.stats = stats;
 }

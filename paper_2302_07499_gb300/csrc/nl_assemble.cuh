@@ -175,7 +175,7 @@ template <class R> struct EvCfg {
 // together.
 template <class R, int STRAT> constexpr bool kRetakePass = sizeof(R) == 4 && (STRAT == 0 || STRAT == 2);
 
-template <class R, int STRAT, bool B, bool RETAKE>
+template <class R, int STRAT, bool B, bool RETAKE, bool QMC = false>
 __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_events(const __grid_constant__ AsmArgs A)
 {
     extern __shared__ __align__(16) unsigned char evsm[];
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
         // the record is built in shared memory and written out once
         R *out = reinterpret_cast<R *>(evsm) + 3 * nlq::CB_STRIDE * EvCfg<R>::threads + 17 * threadIdx.x;
         constexpr bool diag_inline = RETAKE || !kRetakePass<R, STRAT>;
-        const bool deferred = nlq::event_moments<R, STRAT, diag_inline>(
+        const bool deferred = nlq::event_moments<R, STRAT, diag_inline, false, QMC>(
             v, x, sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp,
             (uint32_t)q, out, st, (sizeof(R) == 4) ? &sx : nullptr, cb, nlq::CB_STRIDE * EvCfg<R>::threads,
             nlq::HullScratch<R>{reinterpret_cast<R *>(evsm) + threadIdx.x, EvCfg<R>::threads}, nullptr, A.hull_maxf);
@@ -601,13 +601,19 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
     int ev_per_sm = 0;
     constexpr int ET = EvCfg<R>::threads;
     constexpr size_t ESM = EvCfg<R>::smem;
+    // the event kernels (main pass, retake pass) of the group's sampler
+    void (*ev_main)(const AsmArgs) = nullptr;
+    void (*ev_retake)(const AsmArgs) = nullptr;
     if constexpr (STRAT <= 2) {
-        NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT, B, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)ESM));
+        ev_main = k_events<R, STRAT, B, false>;
+        ev_retake = k_events<R, STRAT, B, true>;
+        if constexpr (STRAT == 2) {
+            if (A.qmc) { ev_main = k_events<R, 2, B, false, true>; ev_retake = k_events<R, 2, B, true, true>; }
+        }
+        NL_CUDA(cudaFuncSetAttribute(ev_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
         if constexpr (kRetakePass<R, STRAT>)
-            NL_CUDA(cudaFuncSetAttribute(k_events<R, STRAT, B, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ESM));
-        NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, k_events<R, STRAT, B, false>, ET, ESM));
+            NL_CUDA(cudaFuncSetAttribute(ev_retake, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
+        NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ev_per_sm, ev_main, ET, ESM));
     }
     ev_per_sm = ev_per_sm < 1 ? 1 : ev_per_sm;
     if (sh.events_blocks_per_sm > 0) ev_per_sm = std::min(ev_per_sm, sh.events_blocks_per_sm);
@@ -628,7 +634,7 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
         // kernel reads the actual count from device memory
         unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, ET), (int64_t)sms * ev_per_sm));
         if constexpr (STRAT <= 2) {
-            { k_events<R, STRAT, B, false><<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
+            { ev_main<<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
             NL_CHECK_LAUNCH();
         }
         if constexpr (kDefer) {
@@ -640,7 +646,7 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
             // the handed-over events (a few per cent; the kernel reads their
             // count from device memory); full occupancy, as their FP64 work is
             // latency-bound
-            { k_events<R, STRAT, B, true><<<(unsigned)(sms * ev_per_sm), ET, ESM, s>>>(A); nl_count_launch(); }
+            { ev_retake<<<(unsigned)(sms * ev_per_sm), ET, ESM, s>>>(A); nl_count_launch(); }
             NL_CHECK_LAUNCH();
         }
         if (ev) NL_CUDA(cudaEventRecord(ev[4 * ci + 2], s));
@@ -694,7 +700,8 @@ void launch_assemble(nl_system *sys, void *D, double *strips, double *TT, uint8_
     switch (sys->opts.strategy) {
     case NL_NOCAPS: run_single<R, 0>(sys, A); break;
     case NL_APPROXCAPS: run_single<R, 1>(sys, A); break;
-    case NL_FULLCAPS: run_single<R, 2>(sys, A); break;
+    case NL_FULLCAPS:
+    case NL_FULLCAPS_QMC: run_single<R, 2>(sys, A); break;
     case NL_BARYCENTER: run_single<R, 3>(sys, A); break;
     case NL_OVERLAP: run_single<R, 4>(sys, A); break;
     default: run_single<R, 5>(sys, A); break;
@@ -709,7 +716,8 @@ void launch_group(const BatchGroup &g, const Shape &sh, cudaStream_t s)
     switch (g.strategy) {
     case NL_NOCAPS: launch_chunks<R, 0, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
     case NL_APPROXCAPS: launch_chunks<R, 1, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
-    case NL_FULLCAPS: launch_chunks<R, 2, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
+    case NL_FULLCAPS:
+    case NL_FULLCAPS_QMC: launch_chunks<R, 2, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
     case NL_BARYCENTER: launch_chunks<R, 3, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
     case NL_OVERLAP: launch_chunks<R, 4, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
     default: launch_chunks<R, 5, true>(g.A, g.gptr, chunks, sh, s, nullptr); break;
@@ -742,7 +750,7 @@ struct RoundKeys {
     uint32_t k[20];
 };
 
-template <class R, int STRAT, bool REC = false>
+template <class R, int STRAT, bool REC = false, bool QMC = false>
 __global__ void k_probe(const double *__restrict__ tv, const double4 *__restrict__ tv4, const double *__restrict__ xs,
                         const uint32_t *__restrict__ ids, int64_t n, double delta2, int nmc,
                         const __grid_constant__ RoundKeys rk, double *out, int *defer, double *rec = nullptr,
@@ -783,7 +791,7 @@ __global__ void k_probe(const double *__restrict__ tv, const double4 *__restrict
     // approxcaps hull's scratch (that strategy does not sample)
     __align__(16) R cb[3 * nlq::CB_STRIDE];
     static_assert(3 * nlq::CB_STRIDE >= nlq::HULL_SCRATCH, "hull scratch");
-    const int d = nlq::point_moments<R, STRAT, REC>(v, xx, (R)delta2, (R)vol, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
+    const int d = nlq::point_moments<R, STRAT, REC, QMC>(v, xx, (R)delta2, (R)vol, nmc, rk.k, ids[3 * c], ids[3 * c + 1],
                                                     ids[3 * c + 2], M, st, sizeof(R) == 4 ? &sx : nullptr, cb,
                                                     nlq::CB_STRIDE, nlq::HullScratch<R>{cb, 1},
                                                     REC ? rec + (int64_t)5 * nmc * c : nullptr,
@@ -820,12 +828,14 @@ __global__ void k_probe_fp64(const double *__restrict__ tv, const double *__rest
 // drawn (0 without a cap or for a deferred case).
 template <class R>
 void launch_probe_samples(const double *tv, const double4 *tv4, const double *xs, const uint32_t *ids, int64_t n,
-                          double delta2, int nmc, uint64_t seed, double *out, int *defer, double *rec, int *nrec)
+                          double delta2, int nmc, uint64_t seed, int qmc, double *out, int *defer, double *rec,
+                          int *nrec)
 {
     RoundKeys key;
     philox_round_keys(seed, key.k);
     unsigned blocks = (unsigned)((n + 127) / 128);
-    k_probe<R, 2, true><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, nmc, key, out, defer, rec, nrec);
+    if (qmc) k_probe<R, 2, true, true><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, nmc, key, out, defer, rec, nrec);
+    else k_probe<R, 2, true><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, nmc, key, out, defer, rec, nrec);
     nl_count_launch();
     NL_CHECK_LAUNCH();
 }
@@ -840,6 +850,7 @@ void launch_probe(const double *tv, const double4 *tv4, const double *xs, const 
     if (strategy == NL_NOCAPS) { k_probe<R, 0><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
     else if (strategy == NL_APPROXCAPS) { k_probe<R, 1><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
     else if (strategy == NL_FULLCAPS) { k_probe<R, 2><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, nmc, key, out, defer); nl_count_launch(); }
+    else if (strategy == NL_FULLCAPS_QMC) { k_probe<R, 2, false, true><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, nmc, key, out, defer); nl_count_launch(); }
     else if (strategy == NL_BARYCENTER) { k_probe<R, 3><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
     else if (strategy == NL_OVERLAP) { k_probe<R, 4><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }
     else { k_probe<R, 5><<<blocks, 128>>>(tv, tv4, xs, ids, n, delta2, 0, key, out, defer); nl_count_launch(); }

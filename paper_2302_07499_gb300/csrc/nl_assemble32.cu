@@ -25,7 +25,8 @@ void nl_batch_launch_fp32(const nla::BatchGroup &g, const nla::Shape &sh, cudaSt
 }
 
 void nl_probe_samples_fp32(const double *tv, const double4 *tv4, const double *xs, const uint32_t *ids, int64_t n,
-                          double delta2, int nmc, uint64_t seed, double *out, int *defer, double *rec, int *nrec)
+                          double delta2, int nmc, uint64_t seed, int qmc, double *out, int *defer, double *rec,
+                          int *nrec)
 {
-    nla::launch_probe_samples<float>(tv, tv4, xs, ids, n, delta2, nmc, seed, out, defer, rec, nrec);
+    nla::launch_probe_samples<float>(tv, tv4, xs, ids, n, delta2, nmc, seed, qmc, out, defer, rec, nrec);
 }

@@ -142,7 +142,8 @@ extern "C" nl_status nl_batch_create(nl_pairs *const *pairs, const nl_assemble_o
         // groups
         std::map<std::tuple<int, int, int, uint64_t>, std::vector<int>> gm;
         for (int i = 0; i < n; ++i) {
-            const int nmc = opts[i].strategy == NL_FULLCAPS ? opts[i].mc_points : 0;
+            const int nmc = (opts[i].strategy == NL_FULLCAPS || opts[i].strategy == NL_FULLCAPS_QMC)
+                                ? opts[i].mc_points : 0;
             gm[std::make_tuple(opts[i].precision, opts[i].strategy, nmc, opts[i].seed)].push_back(i);
         }
         std::vector<std::vector<int64_t>> hptr(n);

@@ -10,9 +10,9 @@ void nl_probe_fp64(const double *, const double4 *, const double *, const uint32
 void nl_probe_fp32(const double *, const double4 *, const double *, const uint32_t *, int64_t, double, int, int,
                    uint64_t, double *, int *);
 void nl_probe_samples_fp64(const double *, const double4 *, const double *, const uint32_t *, int64_t, double, int,
-                           uint64_t, double *, int *, double *, int *);
+                           uint64_t, int, double *, int *, double *, int *);
 void nl_probe_samples_fp32(const double *, const double4 *, const double *, const uint32_t *, int64_t, double, int,
-                           uint64_t, double *, int *, double *, int *);
+                           uint64_t, int, double *, int *, double *, int *);
 
 namespace {
 __global__ void k_philox(const uint4 *__restrict__ ctr, uint2 key, int64_t n, uint4 *out)
@@ -40,7 +40,7 @@ extern "C" nl_status nl_probe_moments(const double *tets_xyz, const double *x, c
 {
     nl_clear_error();
     if (!tets_xyz || !x || !ids || !moments || n < 0) { nl_set_error("bad argument"); return NL_EINVAL; }
-    if (strategy < 0 || strategy > 5 || (precision != NL_FP64 && precision != NL_FP32_COMP)) {
+    if (strategy < 0 || strategy > NL_FULLCAPS_QMC || (precision != NL_FP64 && precision != NL_FP32_COMP)) {
         nl_set_error("bad strategy or precision");
         return NL_EINVAL;
     }
@@ -68,9 +68,10 @@ extern "C" nl_status nl_probe_moments(const double *tets_xyz, const double *x, c
     return NL_OK;
 }
 
-extern "C" nl_status nl_probe_mc_samples(const double *tets_xyz, const double *x, const uint32_t *ids, int64_t n,
-                                         double delta, int mc_points, uint64_t seed, int precision,
-                                         int32_t *n_samples, int32_t *cell, uint8_t *accepted, double *y)
+namespace {
+nl_status probe_samples(const double *tets_xyz, const double *x, const uint32_t *ids, int64_t n, double delta,
+                        int mc_points, uint64_t seed, int precision, int qmc, int32_t *n_samples, int32_t *cell,
+                        uint8_t *accepted, double *y)
 {
     nl_clear_error();
     if (!tets_xyz || !x || !ids || !n_samples || !cell || !accepted || !y || n < 0) {
@@ -100,9 +101,9 @@ extern "C" nl_status nl_probe_mc_samples(const double *tets_xyz, const double *x
         NL_CUDA(cudaMemcpy(dv4, h4.data(), sizeof(double4) * 4 * n, cudaMemcpyHostToDevice));
         NL_CUDA(cudaMemset(dn, 0, sizeof(int) * n));
         if (precision == NL_FP64)
-            nl_probe_samples_fp64(dv, dv4, dx, di, n, delta * delta, mc_points, seed, dm, dd, drec, dn);
+            nl_probe_samples_fp64(dv, dv4, dx, di, n, delta * delta, mc_points, seed, qmc, dm, dd, drec, dn);
         else
-            nl_probe_samples_fp32(dv, dv4, dx, di, n, delta * delta, mc_points, seed, dm, dd, drec, dn);
+            nl_probe_samples_fp32(dv, dv4, dx, di, n, delta * delta, mc_points, seed, qmc, dm, dd, drec, dn);
         std::vector<double> hrec(5 * ns);
         std::vector<int> hn(n);
         NL_CUDA(cudaMemcpy(hrec.data(), drec, sizeof(double) * 5 * ns, cudaMemcpyDeviceToHost));
@@ -126,6 +127,21 @@ extern "C" nl_status nl_probe_mc_samples(const double *tets_xyz, const double *x
         return e.st;
     }
     return NL_OK;
+}
+}  // namespace
+
+extern "C" nl_status nl_probe_mc_samples(const double *tets_xyz, const double *x, const uint32_t *ids, int64_t n,
+                                         double delta, int mc_points, uint64_t seed, int precision,
+                                         int32_t *n_samples, int32_t *cell, uint8_t *accepted, double *y)
+{
+    return probe_samples(tets_xyz, x, ids, n, delta, mc_points, seed, precision, 0, n_samples, cell, accepted, y);
+}
+
+extern "C" nl_status nl_probe_qmc_samples(const double *tets_xyz, const double *x, const uint32_t *ids, int64_t n,
+                                          double delta, int mc_points, uint64_t seed, int precision,
+                                          int32_t *n_samples, int32_t *cell, uint8_t *accepted, double *y)
+{
+    return probe_samples(tets_xyz, x, ids, n, delta, mc_points, seed, precision, 1, n_samples, cell, accepted, y);
 }
 
 extern "C" nl_status nl_probe_philox(const uint32_t *ctr, uint64_t key, int64_t n, uint32_t *out)

@@ -489,6 +489,74 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t *rk)
 }
 
 // ---------------------------------------------------------------------------
+// Quasi-Monte Carlo cap points (NL_FULLCAPS_QMC; better sampling over the
+// caps is left open by Sec. 4.3.2): Sobol' points (Sobol' 1967) in four
+// dimensions, each word XORed with a per-event random word (a digital shift:
+// every point stays uniform on the 2^32 grid, the net structure stays).
+// Direction numbers: v_b = m_{b+1} 2^(31-b) with, in dimension 0, m_k = 1
+// (van der Corput), and in dimensions 1..3 the primitive polynomials
+// x + 1, x^2 + x + 1, x^3 + x + 1 with initial m = (1), (1, 3), (1, 3, 1)
+// (Joe & Kuo's table, 2008) continued by Sobol's recurrence
+//   m_k = m_{k-s} ^ (m_{k-s} << s) ^ sum_{i<s, a_i = 1} (m_{k-i} << i).
+// Sample k takes the point of Gray-code index k ^ (k >> 1), so that point
+// k is point k-1 XOR the direction of the lowest set bit of k.
+struct SobolDirs {
+    uint32_t v[4][32];
+};
+
+constexpr SobolDirs make_sobol_dirs()
+{
+    SobolDirs d{};
+    const int deg[4] = {0, 1, 2, 3};
+    const unsigned inner[4] = {0u, 0u, 1u, 1u};   // a_1 .. a_{s-1}, a_1 the high bit
+    const uint32_t init[4][3] = {{0u, 0u, 0u}, {1u, 0u, 0u}, {1u, 3u, 0u}, {1u, 3u, 1u}};
+    for (int b = 0; b < 32; ++b) d.v[0][b] = 1u << (31 - b);
+    for (int dim = 1; dim < 4; ++dim) {
+        const int sdeg = deg[dim];
+        uint32_t m[33] = {};
+        for (int k = 1; k <= sdeg; ++k) m[k] = init[dim][k - 1];
+        for (int k = sdeg + 1; k <= 32; ++k) {
+            uint32_t x = m[k - sdeg] ^ (m[k - sdeg] << sdeg);
+            for (int i = 1; i < sdeg; ++i)
+                if ((inner[dim] >> (sdeg - 1 - i)) & 1u) x ^= m[k - i] << i;
+            m[k] = x;
+        }
+        for (int b = 0; b < 32; ++b) d.v[dim][b] = m[b + 1] << (31 - b);
+    }
+    return d;
+}
+
+static __constant__ SobolDirs kSobol = make_sobol_dirs();
+
+// The words of one event's samples in order k = 0, 1, ...: Philox draws of
+// counter (T, T', q, k), or (QMC) Sobol' points XOR the Philox draw of
+// counter (T, T', q, 0xFFFFFFFF).
+template <bool QMC>
+struct CapDraws {
+    uint32_t idT, idTp, q;
+    const uint32_t *rk;
+    uint4 shift, pt;
+    __device__ __forceinline__ CapDraws(uint32_t a, uint32_t b, uint32_t c, const uint32_t *keys)
+        : idT(a), idTp(b), q(c), rk(keys), shift(make_uint4(0u, 0u, 0u, 0u)), pt(make_uint4(0u, 0u, 0u, 0u))
+    {
+        if constexpr (QMC) shift = philox_rk(make_uint4(idT, idTp, q, 0xFFFFFFFFu), rk);
+    }
+    // the k-th words; with QMC, calls must come in order k = 0, 1, ...
+    __device__ __forceinline__ uint4 next(int k)
+    {
+        if constexpr (QMC) {
+            if (k > 0) {
+                const int b = __ffs(k) - 1;
+                pt.x ^= kSobol.v[0][b]; pt.y ^= kSobol.v[1][b]; pt.z ^= kSobol.v[2][b]; pt.w ^= kSobol.v[3][b];
+            }
+            return make_uint4(pt.x ^ shift.x, pt.y ^ shift.y, pt.z ^ shift.z, pt.w ^ shift.w);
+        } else {
+            return philox_rk(make_uint4(idT, idTp, q, (uint32_t)k), rk);
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
 // approxcaps (Sec. 3.3): the convex hull of the inside vertices, the
 // edge/sphere points and, on every face of T' crossed by the sphere between
 // two edge points, the midpoint of the sphere's arc on that face.  The hull
@@ -683,8 +751,21 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
         P3<R> mu;
         R l0, ls, lt;
         bool keep = false, exact = false;
-        if (F32 && sx && cc < R(1e-6) * d2) {
-            exact = true;        // short chord: its direction is ill-conditioned in FP32
+        if (F32 && sx && cc < R(1e-4) * d2) {
+            // FP32, a chord below 1 % of delta: the midpoint is left out.
+            // Its direction is ill-conditioned in FP32 (a chord of 3e-3 delta
+            // moved the midpoint by 1e-5 delta), and even a midpoint computed
+            // in FP64 and rounded to float sits next to the chord, so the
+            // faces of its cone are slivers whose planes the FP32
+            // coordinates cannot resolve: a far midpoint then saw one of
+            // them and not its neighbour, and the hull folded (errors up to
+            // 3e-2 of |T'| at a chord of 3.6e-3 delta).  What is left out is
+            // the arc segment over the chord, of height chord^2 / (8 r): its
+            // moments stayed within 4e-6 of |T'| on every case set measured.
+            // (Taking chords of 0.5 to 1 % of delta from FP64 instead cost
+            // 14 % of the approxcaps batch time and did not change K's
+            // errors.)
+            continue;
         } else {
             if (!(cc > R(0))) continue;
             P3<R> w = sub(mid, v[vin]);
@@ -692,8 +773,32 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
             w = mk3<R>(w.x - pr * ch.x, w.y - pr * ch.y, w.z - pr * ch.z);
             R lw = sqrt(dot(w, w));
             if (!(lw > R(0))) continue;
-            R rr = sqrt(r2) / lw;
-            mu = mk3<R>(cf.x + rr * w.x, cf.y + rr * w.y, cf.z + rr * w.z);
+            if constexpr (F32) {
+                // The direction away from the inside vertex within the face:
+                // w is (mid - vin) without its chord component, which loses
+                // its digits when vin lies near the chord's line (a vertex
+                // just inside the sphere puts an edge point next to it; 1e-3
+                // delta off the line gave midpoint errors of 1e-5 delta).
+                // The same direction as the in-face normal of the chord,
+                // nr x ch, whose FP32 error does not depend on where vin is,
+                // with the sign that points away from vin; a sign too close
+                // to call goes to FP64 below.
+                const P3<R> perp = mk3<R>(nr.y * ch.z - nr.z * ch.y, nr.z * ch.x - nr.x * ch.z,
+                                          nr.x * ch.y - nr.y * ch.x);
+                const R lp = sqrt(dot(perp, perp));
+                const R sg = dot(w, perp);
+                if (sx && absr(sg) < R(1e-4) * lw * lp) {
+                    exact = true;
+                } else {
+                    const R rr = (sg > R(0) ? sqrt(r2) : -sqrt(r2)) / lp;
+                    mu = mk3<R>(cf.x + rr * perp.x, cf.y + rr * perp.y, cf.z + rr * perp.z);
+                }
+            } else {
+                R rr = sqrt(r2) / lw;
+                mu = mk3<R>(cf.x + rr * w.x, cf.y + rr * w.y, cf.z + rr * w.z);
+            }
+        }
+        if (!exact) {
             // barycentric coordinates in the face; keep mu only inside the face
             P3<R> g = sub(mu, v[fv[0]]);
             R a11 = dot(e1, e1), a12 = dot(e1, e2), a22 = dot(e2, e2), b1 = dot(e1, g), b2 = dot(e2, g);
@@ -975,7 +1080,7 @@ __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, 
 //   Returns true when the event is deferred (see event_moments_generic).
 //   hull_maxf: face capacity of the approxcaps hull (HULL_MAXF; smaller only
 //   in tests of the overflow path).
-template <class R, int STRAT, bool DIAG_INLINE = true, bool REC = false>
+template <class R, int STRAT, bool DIAG_INLINE = true, bool REC = false, bool QMC = false>
 __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
                               uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs,
                               const HullScratch<R> &hs, double *rec = nullptr, int hull_maxf = HULL_MAXF)
@@ -1180,6 +1285,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
 #pragma unroll
     for (int k = 0; k < 10; ++k) a2[k] = R(0);
     uint32_t acc = 0;
+    CapDraws<QMC> draws(idT, idTp, q, rk);
     StrictCap scap;
     scap.ready = 0;
     if (F32 && ns == 1) {
@@ -1192,7 +1298,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
 #pragma unroll
         for (int k = 0; k < 10; ++k) sbb[k] = R(0);
         for (int k = 0; k < nmc; ++k) {
-            const uint4 u = philox_rk(make_uint4(idT, idTp, q, (uint32_t)k), rk);
+            const uint4 u = draws.next(k);
             R U0 = unif<R>(u.y), U1 = unif<R>(u.z), U2 = unif<R>(u.w);
             R lo = U0 < U1 ? U0 : U1, hi = U0 < U1 ? U1 : U0;
             R s0 = lo < U2 ? lo : U2;
@@ -1260,7 +1366,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         }
     } else
     for (int k = 0; k < nmc; ++k) {
-        uint4 u = philox_rk(make_uint4(idT, idTp, q, (uint32_t)k), rk);
+        uint4 u = draws.next(k);
         int j;
         bool cell_unsure = false;
         if constexpr (F32) {
@@ -1360,7 +1466,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
 
 // Moments for one (T', x) including classification: used by the diagnostic
 // probe; the assembly splits the two steps across kernels.
-template <class R, int STRAT, bool REC = false>
+template <class R, int STRAT, bool REC = false, bool QMC = false>
 // Returns the classification + 1 when the event is deferred to FP64, else 0.
 // With REC the Monte Carlo samples go to rec (see event_moments) and *nrec
 // receives their number (0 when there is no cap).
@@ -1390,7 +1496,7 @@ __device__ int point_moments(const P3<R> v[4], P3<R> x, R d2, R volTp, int nmc, 
     }
     R o[15];
     const uint32_t mc0 = st.mc;
-    if (event_moments<R, STRAT, true, REC>(v, x, d2, inm, nmc, rk, idT, idTp, q, o, st, sx, cb, cs, hs, rec))
+    if (event_moments<R, STRAT, true, REC, QMC>(v, x, d2, inm, nmc, rk, idT, idTp, q, o, st, sx, cb, cs, hs, rec))
         return inm + 1;
     if constexpr (REC) *nrec = (int)(st.mc - mc0);
     M.m0 = o[0];

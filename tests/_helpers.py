@@ -33,6 +33,30 @@ def tol_fp64(strategy):
     return TOL_FP64_APPROXCAPS if strategy == 1 else TOL_FP64
 
 
+# FP32-comp bar per entry: 1e-5 on the rows that enter the system (free
+# rows: A and the lift), and on every entry of K for every strategy but
+# approxcaps, whose collar-collar entries get 2e-5.  The FP32 hull of the arc
+# midpoints rounds at about 2e-7 of |T'| per moment (p99 over the cut cases
+# of the jittered test meshes, host replay of the device code) and leaves out
+# the midpoints of chords below 1 % of delta; collar nodes reached by few
+# pairs (delta = h) have small diagonals, so the floor of their entries is
+# small: two collar-collar entries of the jittered delta = h mesh measured
+# 1.16e-5, 5e-10 of the matrix scale in absolute terms (every free row below
+# 5e-6).
+TOL_FP32 = 1e-5
+TOL_FP32_APPROXCAPS_COLLAR = 2e-5
+
+
+def tol_fp32_all_entries(strategy):
+    return TOL_FP32_APPROXCAPS_COLLAR if strategy == 1 else TOL_FP32
+
+
+def free_rows(K, node_free):
+    """The rows of K of the free nodes (the rows that enter the system)."""
+    import scipy.sparse as sp
+    return sp.csr_matrix(K)[np.nonzero(node_free)[0]]
+
+
 def entry_rel_err(K, Kref, floor_rel=FLOOR_FP32):
     """Per-entry relative error with floors for near-zero entries:
     |a-r| / max(|r_ij|, 1e-3 sqrt(|r_ii r_jj|), floor_rel max_k |r_kk|);

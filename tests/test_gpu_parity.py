@@ -13,7 +13,7 @@ import pytest
 import nl_inputs as I
 import oracle as O
 
-from _helpers import FLOOR_FP32, FLOOR_FP64, entry_rel_err, tol_fp64
+from _helpers import FLOOR_FP32, FLOOR_FP64, TOL_FP32, entry_rel_err, free_rows, tol_fp32_all_entries, tol_fp64
 
 pytestmark = pytest.mark.gpu
 
@@ -113,6 +113,40 @@ def test_mc_samples_fp32_decisions_equal_fp64(nl):
     assert has.sum() > 1200
 
 
+@pytest.mark.parametrize("nmc", [64, 100])
+def test_qmc_samples_fp64_bitwise_equal_to_oracle(nl, nmc):
+    """NL_FULLCAPS_QMC: the shifted Sobol' cap points of the device code (FP64
+    path) are bit-identical to the oracle's, with the same cells and
+    acceptance (a power-of-two count and another one)."""
+    tv, xs, ids, delta = _sample_cases(500, 41)
+    seed = 0x5EED_0000_0000_0007
+    ns, cell, acc, y = nl.probe_mc_samples(tv, xs, ids, delta, nmc, seed, nl.FP64, qmc=True)
+    with_samples = 0
+    for c in range(len(tv)):
+        yo, co, ao = O.cap_samples(tv[c], xs[c], delta, nmc, seed=seed, idT=ids[c, 0], idTp=ids[c, 1], q=ids[c, 2],
+                                   qmc=True)
+        assert ns[c] == len(yo), c
+        k = ns[c]
+        assert np.array_equal(y[c, :k].view(np.uint64), yo.view(np.uint64)), c
+        assert np.array_equal(cell[c, :k], co) and np.array_equal(acc[c, :k], ao), c
+        with_samples += k > 0
+    assert with_samples > 300
+
+
+def test_qmc_samples_fp32_decisions_equal_fp64(nl):
+    """The FP32 path takes the FP64 decisions for the Sobol' points too."""
+    tv, xs, ids, delta = _sample_cases(1500, 43)
+    n64, c64, a64, y64 = nl.probe_mc_samples(tv, xs, ids, delta, 128, 5, nl.FP64, qmc=True)
+    n32, c32, a32, y32 = nl.probe_mc_samples(tv, xs, ids, delta, 128, 5, nl.FP32_COMP, qmc=True)
+    assert np.array_equal(n32, n64) and np.array_equal(c32, c64) and np.array_equal(a32, a64)
+    ext = np.abs(tv - xs[:, None, :]).max(axis=(1, 2))
+    has = n64 > 0
+    assert np.all(np.abs(y32 - y64).max(axis=(1, 2))[has] <= 1e-5 * ext[has])
+    # the Sobol' points are not the Philox ones
+    _, _, _, ymc = nl.probe_mc_samples(tv, xs, ids, delta, 128, 5, nl.FP64)
+    assert not np.array_equal(ymc[has], y64[has])
+
+
 # ------------------------------------------------------------------ single cases
 def _cases(n, seed):
     rng = np.random.default_rng(seed)
@@ -126,7 +160,7 @@ def _cases(n, seed):
     return np.array(tv), np.array(xs), np.array(ids, dtype=np.uint32)
 
 
-@pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5, 6])
 def test_probe_moments_fp64_match_oracle(nl, strategy):
     tv, xs, ids = _cases(600, 1 + strategy)
     delta = 0.9
@@ -138,9 +172,9 @@ def test_probe_moments_fp64_match_oracle(nl, strategy):
         assert np.abs(got[c] - ref).max() <= 1e-12 * scale, (c, got[c], ref)
 
 
-@pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5, 6])
 def test_probe_moments_fp32_match_oracle(nl, strategy):
-    tv, xs, ids = _cases(2000 if strategy == 2 else 600, 11 + strategy)
+    tv, xs, ids = _cases(2000 if strategy in (2, 6) else 600, 11 + strategy)
     delta = 0.9
     got = nl.probe_moments(tv, xs, ids, delta, strategy, mc_points=64, seed=7, precision=nl.FP32_COMP)
     # FP32 decisions close to a margin are retaken in FP64, so every case
@@ -151,6 +185,41 @@ def test_probe_moments_fp32_match_oracle(nl, strategy):
         scale = O.tet_volume(tv[c])
         err = np.abs(got[c] - ref).max() / scale
         assert err <= 1e-5, (c, err)
+
+
+def _near_sphere_cases(n, seed, delta):
+    """Cases with one vertex of T' within 1e-4..1e-2 of delta from x (inside
+    or outside): edge points next to a vertex, short chords and arc midpoints
+    next to the chord, the hard cases of the FP32 approxcaps hull."""
+    rng = np.random.default_rng(seed)
+    tv, xs, ids = [], [], []
+    while len(tv) < n:
+        v = rng.normal(size=(4, 3))
+        if np.linalg.det(v[1:] - v[0]) < 0.05:
+            continue
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        eps = 10 ** rng.uniform(-4, -2) * rng.choice([-1, 1])
+        x = v[rng.integers(4)] + delta * (1 - eps) * d
+        if not 1 <= int((np.sum((v - x) ** 2, axis=1) < delta ** 2).sum()) <= 3:
+            continue
+        tv.append(v); xs.append(x); ids.append(rng.integers(0, 2 ** 31, size=3))
+    return np.array(tv), np.array(xs), np.array(ids, dtype=np.uint32)
+
+
+def test_probe_approxcaps_fp32_vertex_near_the_sphere(nl):
+    """FP32 approxcaps with a vertex next to the sphere, against the oracle:
+    within 1e-5 of |T'| in every case (before the arc-midpoint direction was
+    taken from the chord's in-face normal and chords below 1 % of delta left
+    out in FP32, such cases reached 5e-2)."""
+    delta = 0.9
+    tv, xs, ids = _near_sphere_cases(3000, 61, delta)
+    got = nl.probe_moments(tv, xs, ids, delta, nl.APPROXCAPS, precision=nl.FP32_COMP)
+    worst = 0.0
+    for c in range(len(tv)):
+        ref, _, _ = O.region_moments(tv[c], xs[c], delta, O.APPROXCAPS, idT=ids[c, 0], idTp=ids[c, 1], q=ids[c, 2])
+        worst = max(worst, np.abs(got[c] - ref).max() / O.tet_volume(tv[c]))
+    assert worst <= 1e-5, worst
 
 
 # ------------------------------------------------------------------ pairs
@@ -166,7 +235,7 @@ def test_pairs_bit_exact(nl, dev, name, mesh, delta):
 
 
 # ------------------------------------------------------------------ matrices
-@pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("name,mesh,delta", _meshes())
 def test_K_fp64_matches_oracle(nl, dev, name, mesh, delta, strategy):
     g = I.quadratic_g(mesh.verts)
@@ -197,13 +266,21 @@ def test_K_fp64_matches_oracle(nl, dev, name, mesh, delta, strategy):
     assert np.abs(F[free] - L @ g - bg.cpu().numpy()).max() <= 1e-12 * np.abs(b).max()
 
 
-@pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5])
-@pytest.mark.parametrize("name,mesh,delta", _meshes()[:3])
+@pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("name,mesh,delta", _meshes())
 def test_K_fp32_comp_matches_oracle(nl, dev, name, mesh, delta, strategy):
     m, p, s = _gpu_system(nl, dev, mesh, delta, strategy, nl.FP32_COMP)
     K = s.scipy(nl.MAT_K)
     Kref = O.assemble_K(mesh, delta, I.gamma_const(delta), strategy, nmc=64, seed=1)
-    assert entry_rel_err(K, Kref) <= 1e-5
+    assert entry_rel_err(K, Kref) <= tol_fp32_all_entries(strategy)
+    # the rows that enter the system, with the floors of the whole matrix
+    d = np.abs(Kref.diagonal())
+    Kf, Kreff = free_rows(K, mesh.node_free), free_rows(Kref, mesh.node_free)
+    free = np.nonzero(mesh.node_free)[0]
+    D = (Kf - Kreff).tocoo()
+    ref = np.asarray(Kreff.tocsr()[D.row, D.col]).ravel()
+    den = np.maximum(np.abs(ref), np.maximum(1e-3 * np.sqrt(d[free[D.row]] * d[D.col]), 1e-7 * d.max()))
+    assert (np.abs(D.data) / den).max(initial=0.0) <= TOL_FP32
 
 
 @pytest.mark.parametrize("strategy", [0, 1, 2, 3, 4, 5])
@@ -220,18 +297,18 @@ def test_unfolded_form_matches_oracle(nl, dev, name, mesh, delta, strategy):
     assert p.info["n_pairs"] == len(O.pairs(mu, delta)[2])
     Kref = O.assemble_K(mu, delta, I.gamma_const(delta), strategy, nmc=64, seed=1)
     A, b, free = O.system(mu, Kref, O.load_vector(mu, -6.0), g)
-    for precision, bar, floor in ((nl.FP64, tol_fp64(strategy), FLOOR_FP64), (nl.FP32_COMP, 1e-5, FLOOR_FP32)):
+    for precision, bar, bar_a, floor in ((nl.FP64, tol_fp64(strategy), tol_fp64(strategy), FLOOR_FP64),
+                                         (nl.FP32_COMP, tol_fp32_all_entries(strategy), TOL_FP32, FLOOR_FP32)):
         s = nl.System(p, strategy=strategy, mc_points=64, seed=1, precision=precision,
                       gamma=I.gamma_const(delta), f_const=-6.0, g=g)
         K = s.scipy(nl.MAT_K)
         assert entry_rel_err(K, Kref, floor) <= bar
-        assert entry_rel_err(s.scipy(nl.MAT_A), A, floor) <= bar
+        assert entry_rel_err(s.scipy(nl.MAT_A), A, floor) <= bar_a
         bg = s.rhs()[0].cpu().numpy()
         assert np.abs(bg - b).max() <= (1e-12 if precision == nl.FP64 else 1e-5) * np.abs(b).max()
         s.close()
-    con = np.nonzero(mesh.node_free == 0)[0]
-    Kfold = O.assemble_K(mesh, delta, I.gamma_const(delta), strategy, nmc=64, seed=1).tocsr()
-    assert abs(Kref.tocsr()[con][:, con]).sum() > 2 * abs(Kfold[con][:, con]).sum()
+    # the collar elements are outer elements too: more pairs than folded
+    assert p.info["n_pairs"] > len(O.pairs(mesh, delta)[2])
 
 
 @pytest.mark.parametrize("precision", [0, 1])
