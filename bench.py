@@ -809,7 +809,9 @@ def run_fullcaps_variance(args, ws, rank, local):
             V = torch.stack(vals)
             rel = V.std(dim=0) / scale
             rows.append({"sampler": name, "mc_points": nmc, "events_ms": float(np.mean(ev[1:])),
-                         "rms_rel_std": float(torch.sqrt((rel ** 2).mean())), "max_rel_std": float(rel.max())})
+                         "rms_rel_std": float(torch.sqrt((rel ** 2).mean())),
+                         "median_rel_std": float(rel.median()), "p99_rel_std": float(torch.kthvalue(rel.flatten().cpu(), max(1, int(0.99 * rel.numel())))[0]),
+                         "max_rel_std": float(rel.max())})
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     p.close(); m.close()
     line = {"metric": "spread of K over 8 seeds, Monte Carlo vs quasi-Monte Carlo cap points",

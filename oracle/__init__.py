@@ -71,6 +71,7 @@ def lib():
             L.or_pairs.restype = C.c_int64
             L.or_hull_tets.argtypes = [C.c_int, dp, dp, C.c_int]
             L.or_mc_point.argtypes = [dp, C.c_int, u32p, dp, C.POINTER(C.c_int)]
+            L.or_qmc_point.argtypes = [dp, C.c_int, u32p, dp, C.POINTER(C.c_int)]
             L.or_region_moments.argtypes = [dp, dp, C.c_double, C.c_int, C.c_int, C.c_uint64,
                                             C.c_uint32, C.c_uint32, C.c_uint32, dp, dp]
             L.or_pair_block.argtypes = [dp, dp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
@@ -179,6 +180,17 @@ def cap_samples(vTp, x, delta, nmc, seed=1, idT=0, idTp=0, q=0, qmc=False):
     n = fn(_p(v, C.c_double), _p(xx, C.c_double), float(delta), int(nmc), int(seed), int(idT),
            int(idTp), int(q), _p(y, C.c_double), _p(cell, C.c_int32), _p(acc, C.c_uint8))
     return y[:n], cell[:n], acc[:n].astype(bool)
+
+
+def qmc_point(S, u):
+    """(y, cell) of the quasi-Monte Carlo map for cap cells S [ns,4,3] and
+    words u [4]."""
+    Sf = _f64(S).reshape(-1)
+    uu = np.ascontiguousarray(u, dtype=np.uint32)
+    y = np.zeros(3)
+    w = C.c_int(0)
+    lib().or_qmc_point(_p(Sf, C.c_double), len(Sf) // 12, _p(uu, C.c_uint32), _p(y, C.c_double), C.byref(w))
+    return y, int(w.value)
 
 
 def sobol_point(k):

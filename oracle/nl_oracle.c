@@ -892,6 +892,46 @@ void or_sobol_point(uint32_t k, uint32_t out[4])
     }
 }
 
+/* Cube root of a > 0 by Newton's method, x <- x - (x^3 - a) / (3 x^2),
+ * six steps from 2^q (1 + (m 2^r - 1)/3) where a = m 2^(3q + r),
+ * m in [0.5, 1), r in {0, 1, 2}: the start is within 0.2 of the root's
+ * mantissa, and six quadratic steps reach double precision.               */
+static double cbrt_newton(double a)
+{
+    int e;
+    double m = frexp(a, &e);
+    int q = e / 3, r = e - 3 * q;
+    if (r < 0) { r += 3; q -= 1; }
+    double x = ldexp(1.0 + (ldexp(m, r) - 1.0) / 3.0, q);
+    for (int i = 0; i < 6; ++i) x = x - (x * x * x - a) / (3.0 * (x * x));
+    return x;
+}
+
+/* Quasi-Monte Carlo point: the cell from u[0] as for or_mc_point, and the
+ * point in the cell by the nested map of the unit cube onto the simplex,
+ * s = U1^(1/3), t = U2^(1/2), w = U3 (U_k the uniforms of u[k]):
+ * beta = (1 - s, s (1 - t), s t (1 - w), s t w), which is uniform on the
+ * cell and, unlike sorted uniforms, continuous in (U1, U2, U3), as
+ * low-discrepancy points need.                                             */
+void or_qmc_point(const double *Sflat, int ns, const uint32_t u[4], double y[3], int *which)
+{
+    const double (*S)[4][3] = (const double (*)[4][3])Sflat;
+    double vol[3], tot = 0.0;
+    for (int j = 0; j < ns; ++j) { vol[j] = tet_volume(S[j][0], S[j][1], S[j][2], S[j][3]); tot += vol[j]; }
+    double r = ((double)u[0] * 0x1p-32) * tot;
+    int j = ns - 1;
+    double cum = 0.0;
+    for (int k = 0; k < ns; ++k) { cum += vol[k]; if (r < cum) { j = k; break; } }
+    double U[3];
+    for (int k = 0; k < 3; ++k) U[k] = ((double)u[k + 1] + 0.5) * 0x1p-32;
+    double s = cbrt_newton(U[0]), t = sqrt(U[1]), w = U[2];
+    double st = s * t;
+    double be[4] = {1.0 - s, s * (1.0 - t), st * (1.0 - w), st * w};
+    for (int d = 0; d < 3; ++d)
+        y[d] = ((be[0] * S[j][0][d] + be[1] * S[j][1][d]) + be[2] * S[j][2][d]) + be[3] * S[j][3][d];
+    if (which) *which = j;
+}
+
 /* The Monte Carlo samples of the cap S = T' minus hull(I u P) around x
  * (Sec. 4.3.2, Alg. 4).  The cap exists only when T' meets the closed ball:
  * some vertex inside, or, with none inside, the distance from x to T' at
@@ -905,8 +945,8 @@ typedef void (*sample_fn)(void *ctx, int k, const double y[3], int cell, int acc
  * each XORed with a word of one Philox draw with counter (idT, idTp, q,
  * 0xFFFFFFFF) (a digital shift, which leaves every point uniform on the 2^32
  * grid and keeps the net structure), in place of the Philox draw of counter
- * (idT, idTp, q, k); the cell choice and the point follow from the words as
- * for Monte Carlo.                                                          */
+ * (idT, idTp, q, k); the cell choice follows from the words as for Monte
+ * Carlo, the point from the nested map of or_qmc_point.                     */
 static int cap_samples(const double v[4][3], const double vTp[12], const double x[3], double delta,
                        const classify_t *c, int nmc, uint64_t seed, uint32_t idT, uint32_t idTp, uint32_t q,
                        int qmc, sample_fn fn, void *ctx)
@@ -936,7 +976,8 @@ static int cap_samples(const double v[4][3], const double vTp[12], const double 
         }
         double y[3];
         int which = 0;
-        or_mc_point(&S[0][0][0], ns, u, y, &which);
+        if (qmc) or_qmc_point(&S[0][0][0], ns, u, y, &which);
+        else or_mc_point(&S[0][0][0], ns, u, y, &which);
         double w[3] = {y[0] - x[0], y[1] - x[1], y[2] - x[2]};
         double r2 = (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2];
         fn(ctx, k, y, which, r2 <= d2, wgt);

@@ -25,6 +25,7 @@ int64_t or_pairs(const double *verts, int64_t nv, const int32_t *tets, int64_t n
 int or_hull_tets(int n, const double *p, double *out, int maxout);
 int or_hull_tets_labeled(int n, const double *p, const unsigned *lab, double *out, int maxout);
 void or_mc_point(const double *S, int ns, const uint32_t u[4], double y[3], int *which);
+void or_qmc_point(const double *S, int ns, const uint32_t u[4], double y[3], int *which);
 int or_region_moments(const double vTp[12], const double x[3], double delta, int strategy,
                       int nmc, uint64_t seed, uint32_t idT, uint32_t idTp, uint32_t q,
                       double M[15], double *mc_vol);

@@ -304,11 +304,33 @@ struct StrictCap {
     double tot;
 };
 
-// The specification's FP64 sample for the Philox words u.  The cap cells are
+// Cube root of a > 0 by Newton's method, x <- x - (x^3 - a) / (3 x^2), six
+// steps from 2^q (1 + (m 2^r - 1) / 3) where a = m 2^(3q + r), m in
+// [0.5, 1), r in {0, 1, 2} (the start is within 0.2 of the root's mantissa;
+// six quadratic steps reach double precision).  Every operation rounded on
+// its own, so that the value does not depend on the translation unit.
+__device__ __forceinline__ double cbrt_newton(double a)
+{
+    int e;
+    const double m = frexp(a, &e);
+    int q = e / 3, r = e - 3 * q;
+    if (r < 0) { r += 3; q -= 1; }
+    double x = ldexp(__dadd_rn(1.0, __ddiv_rn(__dsub_rn(ldexp(m, r), 1.0), 3.0)), q);
+    for (int i = 0; i < 6; ++i) {
+        const double xx = __dmul_rn(x, x);
+        x = __dsub_rn(x, __ddiv_rn(__dsub_rn(__dmul_rn(xx, x), a), __dmul_rn(3.0, xx)));
+    }
+    return x;
+}
+
+// The specification's FP64 sample for the words u.  The cap cells are
 // described by their packed point indices (3 bits per point, 4 points per
 // cell, ns cells) and the edge points (2+2 bits: inside, outside vertex).
+// The point: sorted uniforms (Monte Carlo), or with qmc the nested map
+// s = U1^(1/3), t = U2^(1/2), w = U3, beta = (1 - s, s (1 - t),
+// s t (1 - w), s t w).
 static __device__ __noinline__ int strict_sample(const Strict *sx, StrictCap *cap, unsigned long long spack, int ns,
-                                                 uint32_t pdpack, int np, uint4 u, int *jout)
+                                                 uint32_t pdpack, int np, uint4 u, int *jout, int qmc = 0)
 {
     double v[4][3], x[3];
     strict_load(sx, v, x);
@@ -339,10 +361,16 @@ static __device__ __noinline__ int strict_sample(const Strict *sx, StrictCap *ca
     }
     double V0 = ((double)u.y + 0.5) * 0x1p-32, V1 = ((double)u.z + 0.5) * 0x1p-32, V2 = ((double)u.w + 0.5) * 0x1p-32,
            tv;
-    if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
-    if (V1 > V2) { tv = V1; V1 = V2; V2 = tv; }
-    if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
-    double b0 = V0, b1 = ssub(V1, V0), b2 = ssub(V2, V1), b3 = ssub(1.0, V2);
+    double b0, b1, b2, b3;
+    if (qmc) {
+        const double sc = cbrt_newton(V0), tc = __dsqrt_rn(V1), st = smul(sc, tc);
+        b0 = ssub(1.0, sc); b1 = smul(sc, ssub(1.0, tc)); b2 = smul(st, ssub(1.0, V2)); b3 = smul(st, V2);
+    } else {
+        if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
+        if (V1 > V2) { tv = V1; V1 = V2; V2 = tv; }
+        if (V0 > V1) { tv = V0; V0 = V1; V1 = tv; }
+        b0 = V0; b1 = ssub(V1, V0); b2 = ssub(V2, V1); b3 = ssub(1.0, V2);
+    }
     const double *c[4];
     for (int kk = 0; kk < 4; ++kk) {
         int pidx = (int)((spack >> (3 * (4 * j64 + kk))) & 7);
@@ -555,6 +583,44 @@ struct CapDraws {
         }
     }
 };
+
+// Barycentric coordinates of a cap sample in its cell from the words u
+// (u.y, u.z, u.w): Monte Carlo takes the spacings of the three sorted
+// uniforms; quasi-Monte Carlo the nested map s = U1^(1/3), t = U2^(1/2),
+// w = U3, beta = (1 - s, s (1 - t), s t (1 - w), s t w), continuous in the
+// uniforms as low-discrepancy points need (FP32: CUDA's cbrtf; FP64: the
+// Newton cube root of the specification).
+template <class R, bool QMC>
+__device__ __forceinline__ void cap_bary(uint4 u, R &b0, R &b1, R &b2, R &b3)
+{
+    const R U2 = unif<R>(u.w);
+    if constexpr (QMC) {
+        R sc, tc;
+        if constexpr (sizeof(R) == 4) {
+            // the roots magnify the absolute error of a small uniform (the
+            // 23-bit fixed-point form of unif errs by 2^-24 absolute, which
+            // moved cube roots near zero by 1e-4): here the words are
+            // converted with 24-bit relative precision
+            const float V0 = fmaf(__uint2float_rn(u.y), 0x1p-32f, 0x1p-33f);
+            const float V1 = fmaf(__uint2float_rn(u.z), 0x1p-32f, 0x1p-33f);
+            sc = cbrtf(V0);
+            tc = sqrtf(V1);
+        } else {
+            sc = cbrt_newton(unif<R>(u.y));
+            tc = sqrt(unif<R>(u.z));
+        }
+        const R st = sc * tc;
+        b0 = R(1) - sc; b1 = sc * (R(1) - tc); b2 = st * (R(1) - U2); b3 = st * U2;
+    } else {
+        const R U0 = unif<R>(u.y), U1 = unif<R>(u.z);
+        const R lo = U0 < U1 ? U0 : U1, hi = U0 < U1 ? U1 : U0;
+        const R s0 = lo < U2 ? lo : U2;
+        const R mid0 = lo < U2 ? U2 : lo;
+        const R s2 = hi < mid0 ? mid0 : hi;
+        const R s1 = hi < mid0 ? hi : mid0;
+        b0 = s0; b1 = s1 - s0; b2 = s2 - s1; b3 = R(1) - s2;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // approxcaps (Sec. 3.3): the convex hull of the inside vertices, the
@@ -1299,13 +1365,8 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         for (int k = 0; k < 10; ++k) sbb[k] = R(0);
         for (int k = 0; k < nmc; ++k) {
             const uint4 u = draws.next(k);
-            R U0 = unif<R>(u.y), U1 = unif<R>(u.z), U2 = unif<R>(u.w);
-            R lo = U0 < U1 ? U0 : U1, hi = U0 < U1 ? U1 : U0;
-            R s0 = lo < U2 ? lo : U2;
-            R mid0 = lo < U2 ? U2 : lo;
-            R s2 = hi < mid0 ? mid0 : hi;
-            R s1 = hi < mid0 ? hi : mid0;
-            R be[4] = {s0, s1 - s0, s2 - s1, R(1) - s2};
+            R be[4];
+            cap_bary<R, QMC>(u, be[0], be[1], be[2], be[3]);
             R cc[12];
             if constexpr (F32) {
                 const float4 *c4 = reinterpret_cast<const float4 *>(cb);
@@ -1323,7 +1384,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
             bool inb = rr <= d2;
             if (sx && absr(rr - d2) < dmar) {
                 int j64 = 0;
-                inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64) != 0;
+                inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64, QMC ? 1 : 0) != 0;
             }
             if constexpr (REC) {
                 rec[5 * k] = 0.0; rec[5 * k + 1] = inb ? 1.0 : 0.0;
@@ -1376,13 +1437,8 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
             const R r = unit_scale<R>(u.x) * tot;
             j = (r >= cum0 ? 1 : 0) + (r >= cum1 ? 1 : 0);
         }
-        R U0 = unif<R>(u.y), U1 = unif<R>(u.z), U2 = unif<R>(u.w);
-        R lo = U0 < U1 ? U0 : U1, hi = U0 < U1 ? U1 : U0;
-        R s0 = lo < U2 ? lo : U2;
-        R mid0 = lo < U2 ? U2 : lo;
-        R s2 = hi < mid0 ? mid0 : hi;
-        R s1 = hi < mid0 ? hi : mid0;
-        R be0 = s0, be1 = s1 - s0, be2 = s2 - s1, be3 = R(1) - s2;
+        R be0, be1, be2, be3;
+        cap_bary<R, QMC>(u, be0, be1, be2, be3);
         const R *c = cb + cs * j;
         R cc[12];
         if constexpr (F32) {
@@ -1410,7 +1466,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         if (F32 && sx) {
             if (cell_unsure || absr(rr - d2) < dmar) {
                 int j64 = j;
-                inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64) != 0;
+                inb = strict_sample(sx, &scap, spack, ns, pdpack, np, u, &j64, QMC ? 1 : 0) != 0;
                 c = cb + cs * j64;
                 if constexpr (REC) j = j64;
             }

@@ -338,6 +338,36 @@ def test_sobol_points_are_nets():
             assert len(np.unique(box)) == 1 << m
 
 
+def test_qmc_point_is_the_nested_simplex_map():
+    """The quasi-Monte Carlo point: cell j by u[0] against the cumulative
+    volumes, then y = sum beta_k c_k with beta = (1 - s, s (1 - t),
+    s t (1 - w), s t w), s = U1^(1/3) (numpy's cbrt), t = U2^(1/2), w = U3,
+    U_k = (u[k] + 1/2) 2^-32.  And the map is uniform on a cell: the mean
+    point of 2^18 uniform words is the centroid and the covariance the
+    tetrahedron's, (sum_k c_k c_k^T + 16 m m^T) / 20 - m m^T."""
+    rng = np.random.default_rng(71)
+    S = np.array([rand_tet(rng) for _ in range(3)])
+    vol = np.array([abs(np.linalg.det(c[1:] - c[0])) / 6 for c in S])
+    for _ in range(300):
+        u = rng.integers(0, 2 ** 32, size=4, dtype=np.uint64).astype(np.uint32)
+        y, j = O.qmc_point(S, u)
+        r = float(u[0]) * 2.0 ** -32 * vol.sum()
+        assert j == int(np.searchsorted(np.cumsum(vol), r, side="right"))
+        U = (u[1:].astype(np.float64) + 0.5) * 2.0 ** -32
+        s_, t_, w_ = np.cbrt(U[0]), np.sqrt(U[1]), U[2]
+        be = np.array([1 - s_, s_ * (1 - t_), s_ * t_ * (1 - w_), s_ * t_ * w_])
+        assert np.allclose(y, be @ S[j], rtol=0, atol=1e-14)
+    n = 1 << 18
+    words = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    words[:, 0] = 0                                        # cell 0
+    ys = np.array([O.qmc_point(S[:1], w)[0] for w in words[:4096]])
+    c = S[0]
+    m = c.mean(axis=0)
+    cov = (c.T @ c + 16 * np.outer(m, m)) / 20 - np.outer(m, m)
+    assert np.allclose(ys.mean(axis=0), m, atol=5 * np.sqrt(np.diag(cov) / len(ys)).max())
+    assert np.allclose(np.cov(ys.T), cov, atol=0.1 * np.abs(cov).max())
+
+
 def test_fullcaps_qmc_moments_match_plain_sampling_and_beat_monte_carlo():
     """NL_FULLCAPS_QMC is unbiased: over digital shifts (seeds) its mean
     moments agree (5 sigma) with plain uniform sampling of T' (numpy's
