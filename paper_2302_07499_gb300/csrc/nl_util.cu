@@ -251,6 +251,50 @@ __global__ void k_seg_warp(int32_t *keys, const int64_t *ptr, int64_t nseg)
     else warp_bitonic<32>(keys, b, n, lane);
 }
 
+// Segments of 1025..2048 keys: two warps per segment, each sorting one half
+// of up to 1024 keys in registers (warp_bitonic<32>, in place), then a merge
+// through shared memory: every key of one half finds its rank in the other
+// by binary search (lower bound for the first half, upper bound for the
+// second, so that equal keys keep the order of the halves) and goes to its
+// own index plus that rank.  Shorter segments in the same launch take the
+// one-warp path.
+__global__ void __launch_bounds__(64) k_seg_2k(int32_t *keys, const int64_t *ptr, int64_t nseg)
+{
+    __shared__ int32_t sh[2048];
+    const int64_t sg = blockIdx.x;
+    if (sg >= nseg) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t b = ptr[sg];
+    const int n = (int)(ptr[sg + 1] - b);
+    if (n <= 1024) {
+        if (w == 0 && n > 1) {
+            if (n <= 512) warp_bitonic<16>(keys, b, n, lane);
+            else warp_bitonic<32>(keys, b, n, lane);
+        }
+        return;
+    }
+    const int na = 1024, nb = n - 1024;      // n <= 2048
+    if (w == 0) warp_bitonic<32>(keys, b, na, lane);
+    else warp_bitonic<32>(keys, b + na, nb, lane);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += 64) sh[i] = keys[b + i];
+    __syncthreads();
+    const int32_t *A = sh, *Bv = sh + na;
+    for (int i = threadIdx.x; i < n; i += 64) {
+        const int32_t k = sh[i];
+        int lo = 0, hi;
+        if (i < na) {
+            hi = nb;                          // lower bound of k in B
+            while (lo < hi) { const int mid = (lo + hi) >> 1; if (Bv[mid] < k) lo = mid + 1; else hi = mid; }
+            keys[b + i + lo] = k;
+        } else {
+            hi = na;                          // upper bound of k in A
+            while (lo < hi) { const int mid = (lo + hi) >> 1; if (A[mid] <= k) lo = mid + 1; else hi = mid; }
+            keys[b + (i - na) + lo] = k;
+        }
+    }
+}
+
 void nl_segmented_sort_i32(int32_t *keys, const int64_t *ptr, int64_t nseg, int64_t max_seg,
                            DevArena *arena, cudaStream_t s)
 {
@@ -261,6 +305,14 @@ void nl_segmented_sort_i32(int32_t *keys, const int64_t *ptr, int64_t nseg, int6
         for (int64_t b0 = 0; b0 < blocks; b0 += 2147483647LL) {
             const int64_t nb = std::min<int64_t>(blocks - b0, 2147483647LL);
             { k_seg_warp<<<(unsigned)nb, 256, 0, s>>>(keys, ptr + 8 * b0, nseg - 8 * b0); nl_count_launch(); }
+            NL_CHECK_LAUNCH();
+        }
+        return;
+    }
+    if (max_seg <= 2048) {
+        for (int64_t s0 = 0; s0 < nseg; s0 += 2147483647LL) {
+            const int64_t cnt = std::min<int64_t>(nseg - s0, 2147483647LL);
+            { k_seg_2k<<<(unsigned)cnt, 64, 0, s>>>(keys, ptr + s0, cnt); nl_count_launch(); }
             NL_CHECK_LAUNCH();
         }
         return;
