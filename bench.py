@@ -480,6 +480,10 @@ def run_ours(args, ws, rank, local):
         one = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds / 2, threads=1)
         cpu["one_core"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
 
+    served = None
+    if rank == 0 and ws == 1 and args.serve_requests > 0:
+        served = served_comparison(nl, args.serve_requests, args.serve_fp64_requests)
+
     phases = {k: float(np.mean([s_[k] for s_ in steps])) for k in ("mesh_ms", "pairs_ms", "assemble_ms", "solve_ms")}
     phases["quadrature_ms"] = qms
     for k in ("classify_ms", "events_ms", "combine_ms"):
@@ -508,6 +512,7 @@ def run_ours(args, ws, rank, local):
         "roofline": roofline,
         "spmv": spmv,
         "cpu_baseline": cpu,
+        "served": served,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(launches),
@@ -687,6 +692,29 @@ def _serve_summary(res, arrivals_span):
             "max_queue_depth": int(max(r["queue_depth_at_start"] for r in ok)),
             "cache_hits": int(sum(r["cache_hit"] for r in ok)),
             "failures": sorted({"%d: %s" % (r["status"], r["message"]) for r in res if r["status"] not in (0, 4)})}
+
+
+def served_comparison(nl, n_req, n_fp64, workers=4):
+    """A prefix of the served request stream (serve_stream_seed5: Poisson
+    arrivals at 20/s, mixed sizes, delta/h and strategies), replayed in real
+    time in FP32-comp with mixed CG, and its first n_fp64 requests again in
+    plain FP64: element pairs/s and p50/p99 latency of the two forms on the
+    same requests and the same GPU."""
+    reqs = I.request_stream(2000, 20.0, 5)[:n_req]
+    budget = 150 * 10 ** 9
+    warm = [dict(r, arrival=0.0) for r in sorted(reqs, key=lambda r: r["inv_h"])[:2]]
+    _serve_stream(nl, warm, nl.FP32_COMP, True, workers, budget)
+    res32 = _serve_stream(nl, reqs, nl.FP32_COMP, True, workers, budget)
+    nf = max(2, min(n_fp64, len(reqs)))
+    res64 = _serve_stream(nl, reqs[:nf], nl.FP64, False, workers, budget)
+    span_f = reqs[nf - 1]["arrival"] - reqs[0]["arrival"]
+    s32 = _serve_summary(res32, reqs[-1]["arrival"] - reqs[0]["arrival"])
+    s32f = _serve_summary(res32[:nf], span_f)
+    s64 = _serve_summary(res64, span_f)
+    return {"workload": "serve_stream_seed5: the first %d requests, FP64 on the first %d" % (len(reqs), nf),
+            "workers": workers, "fp32_comp": s32, "fp32_comp_same_requests_as_fp64": s32f, "fp64": s64,
+            "mixed_over_fp64": {"pairs_per_s": s32f["pairs_per_s"] / s64["pairs_per_s"],
+                                "p99_latency": s64["p99_ms"] / s32f["p99_ms"]}}
 
 
 def run_serve(args, ws, rank, local):
@@ -947,6 +975,10 @@ def main():
                     "the default workload)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=16,
+                    help="default workload: requests of the served-stream comparison after the timed region (0: none)")
+    ap.add_argument("--serve-fp64-requests", type=int, default=4,
+                    help="default workload: of those, how many are served again in plain FP64")
     ap.add_argument("--requests", type=int, default=300, help="workload serve_stream_seed5: requests replayed")
     ap.add_argument("--fp64-requests", type=int, default=60, help="workload serve_stream_seed5: FP64 prefix")
     ap.add_argument("--workers", type=int, default=4, help="workload serve_stream_seed5: server workers")
