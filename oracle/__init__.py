@@ -73,9 +73,9 @@ def lib():
             L.or_mc_point.argtypes = [dp, C.c_int, u32p, dp, C.POINTER(C.c_int)]
             L.or_qmc_point.argtypes = [dp, C.c_int, u32p, dp, C.POINTER(C.c_int)]
             L.or_region_moments.argtypes = [dp, dp, C.c_double, C.c_int, C.c_int, C.c_uint64,
-                                            C.c_uint32, C.c_uint32, C.c_uint32, dp, dp]
+                                            C.c_uint32, C.c_uint32, C.c_uint32, dp, dp, dp]
             L.or_pair_block.argtypes = [dp, dp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
-                                        C.c_uint64, C.c_uint32, C.c_uint32, dp]
+                                        C.c_uint64, C.c_uint32, C.c_uint32, dp, dp]
             L.or_cap_samples.argtypes = [dp, dp, C.c_double, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32,
                                          C.c_uint32, dp, i32p, u8p]
             L.or_cap_samples.restype = C.c_int
@@ -83,7 +83,7 @@ def lib():
             L.or_cap_samples_qmc.restype = C.c_int
             L.or_sobol_point.argtypes = [C.c_uint32, u32p]
             L.or_assemble_blocks.argtypes = [dp, i32p, u8p, C.c_double, C.c_double, C.c_int, C.c_int,
-                                             C.c_uint64, i32p, i32p, C.c_int64, dp, C.c_int]
+                                             C.c_uint64, dp, i32p, i32p, C.c_int64, dp, C.c_int]
             L.or_assemble_blocks.restype = C.c_int64
             L.or_load_vector.argtypes = [dp, i32p, C.c_int64, u8p, C.c_int64, C.c_double, dp, dp]
             L.or_num_threads.restype = C.c_int
@@ -97,6 +97,16 @@ def _p(a, ct):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _kpoly(kernel):
+    """The kernel shape phi(s) = c0 + c1 s + c2 s^2 + c3 s^3, s = |x - y|^2 /
+    delta^2, as 4 coefficients (None: the constant kernel, phi = 1)."""
+    if kernel is None:
+        return None
+    k = _f64(kernel).reshape(-1)
+    assert k.size == 4
+    return k
 
 
 # --------------------------------------------------------------------------
@@ -156,14 +166,17 @@ def mc_point(S, u):
     return y, w.value
 
 
-def region_moments(vTp, x, delta, strategy, nmc=0, seed=1, idT=0, idTp=0, q=0):
-    """(M, mc_vol, accepted): M[0]=|R|, M[1:5]=int lambda', M[5:15]=int lambda'_a lambda'_b (a<=b)."""
+def region_moments(vTp, x, delta, strategy, nmc=0, seed=1, idT=0, idTp=0, q=0, kernel=None):
+    """(M, mc_vol, accepted): M[0]=int phi, M[1:5]=int phi lambda', M[5:15]=int phi lambda'_a lambda'_b (a<=b)
+    over the approximate ball R inside T' (phi = 1 unless a kernel shape is given, see _kpoly)."""
     v = _f64(vTp).reshape(12)
     xx = _f64(x).reshape(3)
     M = np.zeros(15)
     mv = np.zeros(1)
+    kp = _kpoly(kernel)
     acc = lib().or_region_moments(_p(v, C.c_double), _p(xx, C.c_double), float(delta), int(strategy), int(nmc),
-                                  int(seed), int(idT), int(idTp), int(q), _p(M, C.c_double), _p(mv, C.c_double))
+                                  int(seed), int(idT), int(idTp), int(q), None if kp is None else _p(kp, C.c_double),
+                                  _p(M, C.c_double), _p(mv, C.c_double))
     return M, float(mv[0]), int(acc)
 
 
@@ -200,12 +213,14 @@ def sobol_point(k):
     return out
 
 
-def pair_block(vT, vTp, delta, gamma, tp_in_collar, strategy, nmc=0, seed=1, idT=0, idTp=0):
+def pair_block(vT, vTp, delta, gamma, tp_in_collar, strategy, nmc=0, seed=1, idT=0, idTp=0, kernel=None):
     a = _f64(vT).reshape(12)
     b = _f64(vTp).reshape(12)
     blk = np.zeros(64)
+    kp = _kpoly(kernel)
     lib().or_pair_block(_p(a, C.c_double), _p(b, C.c_double), float(delta), float(gamma), int(tp_in_collar),
-                        int(strategy), int(nmc), int(seed), int(idT), int(idTp), _p(blk, C.c_double))
+                        int(strategy), int(nmc), int(seed), int(idT), int(idTp),
+                        None if kp is None else _p(kp, C.c_double), _p(blk, C.c_double))
     return blk.reshape(8, 8)
 
 
@@ -243,7 +258,7 @@ def pair_arrays(outer, ptr, tp):
     return np.repeat(outer, counts).astype(np.int32), np.ascontiguousarray(tp, dtype=np.int32)
 
 
-def assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads=0):
+def assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads=0, kernel=None):
     L = lib()
     verts = _f64(mesh.verts)
     tets = np.ascontiguousarray(mesh.tets, dtype=np.int32)
@@ -251,8 +266,10 @@ def assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads=0
     pT = np.ascontiguousarray(pT, dtype=np.int32)
     pTp = np.ascontiguousarray(pTp, dtype=np.int32)
     blocks = np.zeros((pT.size, 64))
+    kp = _kpoly(kernel)
     acc = L.or_assemble_blocks(_p(verts, C.c_double), _p(tets, C.c_int32), _p(om, C.c_uint8), float(delta),
-                               float(gamma), int(strategy), int(nmc), int(seed), _p(pT, C.c_int32),
+                               float(gamma), int(strategy), int(nmc), int(seed),
+                               None if kp is None else _p(kp, C.c_double), _p(pT, C.c_int32),
                                _p(pTp, C.c_int32), pT.size, _p(blocks, C.c_double), int(nthreads))
     return blocks.reshape(-1, 8, 8), int(acc)
 
@@ -267,11 +284,11 @@ def blocks_to_matrix(mesh, pT, pTp, blocks):
     return K
 
 
-def assemble_K(mesh, delta, gamma, strategy, nmc=0, seed=1, prs=None, nthreads=0):
+def assemble_K(mesh, delta, gamma, strategy, nmc=0, seed=1, prs=None, nthreads=0, kernel=None):
     if prs is None:
         prs = pairs(mesh, delta)
     pT, pTp = pair_arrays(*prs)
-    blocks, _ = assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads)
+    blocks, _ = assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads, kernel=kernel)
     return blocks_to_matrix(mesh, pT, pTp, blocks)
 
 

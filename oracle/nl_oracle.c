@@ -993,6 +993,22 @@ static int cap_samples(const double v[4][3], const double vTp[12], const double 
  * Monte Carlo estimate |S|/N sum 1{|y-x|<=delta} on the cap (Sec. 4.3.2).
  * Returns the number of accepted samples; *mc_vol receives the MC part of
  * M[0].                                                                     */
+/* Kernel shape phi on the ball: the kernel is gamma phi(|x - y|) (Sec. 2,
+ * with the constant kernel as phi = 1).  kpoly NULL: phi = 1; otherwise the
+ * polynomial phi = c0 + c1 s + c2 s^2 + c3 s^3 in s = |x - y|^2 / delta^2,
+ * kpoly = (c0, c1, c2, c3), with s capped at 1: the element-level strategies
+ * take T' whole and so place points past the sphere, where phi keeps its
+ * value on the sphere.  The inner integrals weight every point of the
+ * 4-point rule and every accepted cap sample by phi there (Sec. 4.3.1 keeps
+ * the 4-point rule, no longer exact when phi varies).                      */
+static double kshape(const double *kpoly, const double x[3], const double y[3], double delta)
+{
+    if (!kpoly) return 1.0;
+    double s = dist2(x, y) / (delta * delta);
+    if (s > 1.0) s = 1.0;
+    return kpoly[0] + s * (kpoly[1] + s * (kpoly[2] + s * kpoly[3]));
+}
+
 static void add_point(double M[15], const double v[4][3], const double y[3], double w)
 {
     double lam[4];
@@ -1010,6 +1026,9 @@ struct moments_ctx {
     const double (*v)[3];
     int acc;
     double *mc_vol;
+    const double *kpoly;
+    const double *x;
+    double delta;
 };
 
 static void moments_sample(void *p, int k, const double y[3], int cell, int accepted, double wgt)
@@ -1017,14 +1036,15 @@ static void moments_sample(void *p, int k, const double y[3], int cell, int acce
     struct moments_ctx *ctx = (struct moments_ctx *)p;
     (void)k; (void)cell;
     if (!accepted) return;
-    add_point(ctx->M, ctx->v, y, wgt);
+    const double w = wgt * kshape(ctx->kpoly, ctx->x, y, ctx->delta);
+    add_point(ctx->M, ctx->v, y, w);
     ctx->acc++;
-    if (ctx->mc_vol) *ctx->mc_vol += wgt;
+    if (ctx->mc_vol) *ctx->mc_vol += w;
 }
 
 int or_region_moments(const double vTp[12], const double x[3], double delta, int strategy,
                       int nmc, uint64_t seed, uint32_t idT, uint32_t idTp, uint32_t q,
-                      double M[15], double *mc_vol)
+                      const double *kpoly, double M[15], double *mc_vol)
 {
     const double (*v)[3] = (const double (*)[3])vTp;
     const int qmc = strategy == OR_FULLCAPS_QMC;
@@ -1040,9 +1060,9 @@ int or_region_moments(const double vTp[12], const double x[3], double delta, int
         double flat[12], yq[12];
         memcpy(flat, cells[s], sizeof(flat));
         or_quad_points(flat, yq);
-        for (int k = 0; k < 4; ++k) add_point(M, v, yq + 3 * k, vol / 4.0);
+        for (int k = 0; k < 4; ++k) add_point(M, v, yq + 3 * k, (vol / 4.0) * kshape(kpoly, x, yq + 3 * k, delta));
     }
-    struct moments_ctx mc = {M, v, 0, mc_vol};
+    struct moments_ctx mc = {M, v, 0, mc_vol, kpoly, x, delta};
     if (strategy == OR_FULLCAPS)
         cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, q, qmc, moments_sample, &mc);
     return mc.acc;
@@ -1069,6 +1089,9 @@ struct block_ctx {
     const double (*v)[3];
     double coef;
     int acc;
+    const double *kpoly;
+    const double *x;
+    double delta;
 };
 
 static void block_sample(void *p, int k, const double y[3], int cell, int accepted, double wgt)
@@ -1076,13 +1099,13 @@ static void block_sample(void *p, int k, const double y[3], int cell, int accept
     struct block_ctx *ctx = (struct block_ctx *)p;
     (void)k; (void)cell;
     if (!accepted) return;
-    add_block(ctx->blk, ctx->lx, ctx->v, y, ctx->coef * wgt);
+    add_block(ctx->blk, ctx->lx, ctx->v, y, ctx->coef * (wgt * kshape(ctx->kpoly, ctx->x, y, ctx->delta)));
     ctx->acc++;
 }
 
 int or_pair_block(const double vT[12], const double vTp[12], double delta, double gamma,
                   int tp_in_collar, int strategy, int nmc, uint64_t seed,
-                  uint32_t idT, uint32_t idTp, double blk[64])
+                  uint32_t idT, uint32_t idTp, const double *kpoly, double blk[64])
 {
     const double (*vt)[3] = (const double (*)[3])vT;
     const double (*v)[3] = (const double (*)[3])vTp;
@@ -1108,10 +1131,11 @@ int or_pair_block(const double vT[12], const double vTp[12], double delta, doubl
             double flat[12], yq[12];
             memcpy(flat, cells[s], sizeof(flat));
             or_quad_points(flat, yq);
-            for (int k = 0; k < 4; ++k) add_block(blk, lx, v, yq + 3 * k, coef * (vol / 4.0));
+            for (int k = 0; k < 4; ++k)
+                add_block(blk, lx, v, yq + 3 * k, coef * ((vol / 4.0) * kshape(kpoly, x, yq + 3 * k, delta)));
         }
         if (strategy == OR_FULLCAPS) {
-            struct block_ctx bc = {blk, lx, v, coef, 0};
+            struct block_ctx bc = {blk, lx, v, coef, 0, kpoly, x, delta};
             cap_samples(v, vTp, x, delta, &c, nmc, seed, idT, idTp, (uint32_t)q, qmc, block_sample, &bc);
             acc += bc.acc;
         }
@@ -1164,7 +1188,7 @@ int or_cap_samples_qmc(const double vTp[12], const double x[3], double delta, in
  * only its own block, so the result does not depend on the thread count.  */
 int64_t or_assemble_blocks(const double *verts, const int32_t *tets, const uint8_t *in_omega,
                            double delta, double gamma, int strategy, int nmc, uint64_t seed,
-                           const int32_t *pT, const int32_t *pTp, int64_t npairs,
+                           const double *kpoly, const int32_t *pT, const int32_t *pTp, int64_t npairs,
                            double *blocks, int nthreads)
 {
     int64_t acc = 0;
@@ -1177,7 +1201,7 @@ int64_t or_assemble_blocks(const double *verts, const int32_t *tets, const uint8
         tet_coords(verts, tets, pT[p], vT);
         tet_coords(verts, tets, pTp[p], vTp);
         acc += or_pair_block(vT, vTp, delta, gamma, in_omega[pTp[p]] ? 0 : 1, strategy, nmc, seed,
-                             (uint32_t)pT[p], (uint32_t)pTp[p], blocks + 64 * p);
+                             (uint32_t)pT[p], (uint32_t)pTp[p], kpoly, blocks + 64 * p);
     }
     (void)nthreads;
     return acc;

@@ -28,7 +28,7 @@ void or_mc_point(const double *S, int ns, const uint32_t u[4], double y[3], int 
 void or_qmc_point(const double *S, int ns, const uint32_t u[4], double y[3], int *which);
 int or_region_moments(const double vTp[12], const double x[3], double delta, int strategy,
                       int nmc, uint64_t seed, uint32_t idT, uint32_t idTp, uint32_t q,
-                      double M[15], double *mc_vol);
+                      const double *kpoly, double M[15], double *mc_vol);
 int or_cap_samples(const double vTp[12], const double x[3], double delta, int nmc, uint64_t seed,
                    uint32_t idT, uint32_t idTp, uint32_t q, double *y, int32_t *cell, uint8_t *accepted);
 int or_cap_samples_qmc(const double vTp[12], const double x[3], double delta, int nmc, uint64_t seed,
@@ -36,10 +36,10 @@ int or_cap_samples_qmc(const double vTp[12], const double x[3], double delta, in
 void or_sobol_point(uint32_t k, uint32_t out[4]);
 int or_pair_block(const double vT[12], const double vTp[12], double delta, double gamma,
                   int tp_in_collar, int strategy, int nmc, uint64_t seed,
-                  uint32_t idT, uint32_t idTp, double blk[64]);
+                  uint32_t idT, uint32_t idTp, const double *kpoly, double blk[64]);
 int64_t or_assemble_blocks(const double *verts, const int32_t *tets, const uint8_t *in_omega,
                            double delta, double gamma, int strategy, int nmc, uint64_t seed,
-                           const int32_t *pT, const int32_t *pTp, int64_t npairs,
+                           const double *kpoly, const int32_t *pT, const int32_t *pTp, int64_t npairs,
                            double *blocks, int nthreads);
 void or_load_vector(const double *verts, const int32_t *tets, int64_t nt, const uint8_t *in_omega,
                     int64_t nv, double fconst, const double *fnodal, double *F);
