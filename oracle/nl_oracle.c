@@ -728,6 +728,20 @@ static int element_level_full(const double v[4][3], const double x[3], double de
 /* Deterministic cells of the approximate ball inside T' (nocaps/approxcaps,
  * the nocaps part of fullcaps, and T' itself or nothing for the
  * element-level strategies).  Returns the number of tetrahedra.            */
+/* The cells of hull(I u P) (Def. simplexdiv: E_k^0, whose split into
+ * simplices the paper leaves open; with a varying kernel the 4-point rule
+ * depends on it): the cone from the first inside vertex a over the hull's
+ * faces away from a, with the m = 2 diagonal of the cap table below.
+ *   m = 1: (a, p_1, p_2, p_3), p_k the edge point towards the k-th outside
+ *          vertex;
+ *   m = 2: (a, b, c2, d2), then (a, c1, c2, d2) (a, c1, d2, d1), or with the
+ *          diagonal c2-d1 (a, c1, c2, d1) (a, c2, d2, d1), where c1, d1 are
+ *          the edge points from a and c2, d2 those from b (towards the
+ *          first and second outside vertex);
+ *   m = 3: (a, f1, f2, f3) (a, b, c, f3) (a, b, f3, f2), f_k the edge point
+ *          from the k-th inside vertex.                                     */
+static int nocaps_cells(const double v[4][3], const classify_t *c, double S[3][4][3]);
+
 static int region_cells(const double v[4][3], const double x[3], double delta, int strategy,
                         const classify_t *c, double cells[][4][3], int maxcells)
 {
@@ -741,6 +755,7 @@ static int region_cells(const double v[4][3], const double x[3], double delta, i
         return 1;
     }
     if (c->m == 0) return 0;
+    if (strategy != OR_APPROXCAPS && maxcells >= 3) return nocaps_cells(v, c, (double (*)[4][3])cells);
     /* each point carries the faces of T' it lies on (face f = opposite vertex
      * f): a vertex k lies on the faces f != k, an edge point (i,o) on the
      * faces f not in {i,o}, an arc midpoint of face o on face o */
@@ -786,6 +801,43 @@ static void set_tet(double t[4][3], const double *a, const double *b, const doub
     cpy3(t[0], a); cpy3(t[1], b); cpy3(t[2], c); cpy3(t[3], d);
 }
 
+static int m2_other_diagonal(const double v[4][3], const classify_t *c)
+{
+    int a = c->in[0], cc = c->out[0], d = c->out[1], b = c->in[1];
+    const double *c1 = c->P[a][cc], *d1 = c->P[a][d], *c2 = c->P[b][cc], *d2 = c->P[b][d];
+    double o1 = orient4(c1, c2, d2, d1), o2 = orient4(c1, c2, d2, v[a]);
+    return (o1 > 0.0 && o2 < 0.0) || (o1 < 0.0 && o2 > 0.0);
+}
+
+static int nocaps_cells(const double v[4][3], const classify_t *c, double S[3][4][3])
+{
+    switch (c->m) {
+    case 1: {
+        int a = c->in[0];
+        set_tet(S[0], v[a], c->P[a][c->out[0]], c->P[a][c->out[1]], c->P[a][c->out[2]]);
+        return 1;
+    }
+    case 2: {
+        int a = c->in[0], b = c->in[1], cc = c->out[0], d = c->out[1];
+        const double *c1 = c->P[a][cc], *d1 = c->P[a][d], *c2 = c->P[b][cc], *d2 = c->P[b][d];
+        set_tet(S[0], v[a], v[b], c2, d2);
+        if (!m2_other_diagonal(v, c)) { set_tet(S[1], v[a], c1, c2, d2); set_tet(S[2], v[a], c1, d2, d1); }
+        else                          { set_tet(S[1], v[a], c1, c2, d1); set_tet(S[2], v[a], c2, d2, d1); }
+        return 3;
+    }
+    case 3: {
+        int a = c->in[0], b = c->in[1], cc = c->in[2], d = c->out[0];
+        const double *f1 = c->P[a][d], *f2 = c->P[b][d], *f3 = c->P[cc][d];
+        set_tet(S[0], v[a], f1, f2, f3);
+        set_tet(S[1], v[a], v[b], v[cc], f3);
+        set_tet(S[2], v[a], v[b], f3, f2);
+        return 3;
+    }
+    default:
+        return 0;
+    }
+}
+
 static int cap_cells(const double v[4][3], const classify_t *c, double S[3][4][3])
 {
     switch (c->m) {
@@ -803,8 +855,7 @@ static int cap_cells(const double v[4][3], const classify_t *c, double S[3][4][3
     case 2: {
         int a = c->in[0], b = c->in[1], cc = c->out[0], d = c->out[1];
         const double *c1 = c->P[a][cc], *d1 = c->P[a][d], *c2 = c->P[b][cc], *d2 = c->P[b][d];
-        double o1 = orient4(c1, c2, d2, d1), o2 = orient4(c1, c2, d2, v[a]);
-        int other = (o1 > 0.0 && o2 < 0.0) || (o1 < 0.0 && o2 > 0.0);
+        int other = m2_other_diagonal(v, c);
         set_tet(S[0], v[cc], v[d], d1, d2);
         if (!other) { set_tet(S[1], v[cc], c1, c2, d2); set_tet(S[2], v[cc], c1, d2, d1); }
         else        { set_tet(S[1], v[cc], c1, c2, d1); set_tet(S[2], v[cc], c2, d2, d1); }
