@@ -48,7 +48,13 @@ WORKLOADS = {
     # the same problem with the quasi-Monte Carlo cap points (not the
     # paper's sampler; see NL_FULLCAPS_QMC)
     "jitter38_d3h_fullcaps_qmc128": ("jitter38_d3h", 6, 128, 1, 1e-10),
+    # the same problem under the parabola kernel gamma (1 - |x - y|^2 / delta^2)
+    # (a non-constant kernel: every cell and whole element takes the 4-point
+    # rule with the kernel at its points)
+    "jitter38_d3h_fullcaps128_parabola": ("jitter38_d3h", 2, 128, 1, 1e-10),
 }
+# kernel shapes phi(s) = c0 + c1 s + c2 s^2 + c3 s^3 of the workloads that have one
+WORKLOAD_KERNEL = {"jitter38_d3h_fullcaps128_parabola": (1.0, -1.0, 0.0, 0.0)}
 STRAT_NAME = {0: "nocaps", 1: "approxcaps", 2: "fullcaps", 6: "fullcaps_qmc"}
 
 # Algorithmic ALU operations of the quadrature kernels per unit, counted from
@@ -292,6 +298,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
 
     cfg, strategy, nmc, seed, rtol = WORKLOADS[args.workload]
+    kernel = WORKLOAD_KERNEL.get(args.workload)
     mesh, delta = I.config_mesh(cfg)
     gamma = I.gamma_const(delta)
     g_host = I.quadratic_g(mesh.verts)
@@ -313,7 +320,7 @@ def run_ours(args, ws, rank, local):
         p = nl.Pairs(m, delta)
         ev[2].record(stream)
         s = nl.System(p, strategy=strategy, mc_points=nmc, seed=seed, precision=precision, gamma=gamma,
-                      f_const=-6.0, g=d_g)
+                      f_const=-6.0, g=d_g, kernel=kernel)
         ev[3].record(stream)
         _, info = s.solve(rtol=rtol, mixed=mixed, out=d_u)
         ev[4].record(stream)
@@ -390,9 +397,13 @@ def run_ours(args, ws, rank, local):
         l2_64 = l2_error_quadratic(mesh, r64[-1]["u"])
         accuracy = {"entry_rel_err_fp32comp_vs_fp64": {"max": float(err.max()),
                                                        "p99_9": float(np.percentile(err, 99.9)),
-                                                       "entries": int(err.size), "bar": 1e-5},
+                                                       "entries": int(err.size),
+                                                       "bar": 5e-4 if kernel else 1e-5},
                     "l2_error_vs_exact_u": {"fp32comp_mixed_cg": l2_32, "fp64_cg": l2_64,
-                                            "ratio": l2_32 / l2_64 if l2_64 > 0 else None, "bar_ratio": 1.01},
+                                            "ratio": l2_32 / l2_64 if l2_64 > 0 else None, "bar_ratio": 1.01,
+                                            "note": "u = |x|^2 solves the constant kernel's problem only; under "
+                                                    "the kernel shape only the ratio is meaningful"
+                                            if kernel else None},
                     "cg": {"fp32comp_mixed": {"iterations": kept32["cg"]["iterations"],
                                               "refinements": kept32["cg"]["refinements"],
                                               "rel_residual": kept32["cg"]["rel_residual"]},
@@ -465,9 +476,12 @@ def run_ours(args, ws, rank, local):
     dfma = peak_info["rates_tops"]["dfma_fp64"] * 1e12
     spmv["fp64"]["dfma_floor_ms"] = steps[0]["nnz_a"] / dfma * 1e3
     spmv["fp64"]["frac_of_measured_dfma"] = spmv["fp64"]["dfma_floor_ms"] / spmv["fp64"]["ms"]
-    roofline = {"bound": "alu", "kernel": "k_events<float,%s>" % STRAT_NAME[strategy],
+    roofline = {"bound": "alu",
+                "kernel": ("k_events_shape<float,%s> (every unit with a region, whole elements included; the "
+                           "operation count leaves the rule points of whole elements out)" % STRAT_NAME[strategy])
+                if kernel else "k_events<float,%s>" % STRAT_NAME[strategy],
                 "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": _traffic_record(),
+                "traffic": None if kernel else _traffic_record(),
                 "peak_source": peak_info["source"], "peak_detail": peak_info,
                 "frac_of_derived_issue_peak": achieved / peak_info["derived_issue_peak_tops"],
                 "algorithmic_ops_per_step": ops, "kernel_ms_per_step": ems, "share_of_step": ems / ms_mean,
@@ -476,8 +490,9 @@ def run_ours(args, ws, rank, local):
                                "achieved_tops": _quadrature_ops(st, qmc) / (qms / 1e3) / 1e12}}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds)
-        one = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds / 2, threads=1)
+        cpu = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds, kernel=kernel)
+        one = cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=args.cpu_seconds / 2, threads=1,
+                           kernel=kernel)
         cpu["one_core"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
 
     served = None
@@ -498,6 +513,8 @@ def run_ours(args, ws, rank, local):
                    % (cfg, ", interior vertices jittered by up to 0.2h (seed 7)" if cfg.startswith("jitter") else "",
                       mesh.nt, mesh.nv, delta),
                    "strategy": STRAT_NAME[strategy], "mc_points": nmc, "seed": seed,
+                   "kernel_shape": ("phi(s) = %g + %g s + %g s^2 + %g s^3, s = min(|x-y|^2/delta^2, 1)" % kernel)
+                   if kernel else "constant",
                    "precision": "FP32 per-(pair,point) arithmetic, FP64 accumulation and entries",
                    "solve": "mixed CG (FP32 inner, FP64 residual/updates) to rel. residual %g" % rtol,
                    "element_pairs": npairs, "nnz_K": steps[0]["nnz"], "n_free": steps[0]["n_free"],
@@ -525,7 +542,7 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
-def cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=15.0, threads=0):
+def cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=15.0, threads=0, kernel=None):
     """The oracle as it stands, on the host cores (all of them, or `threads`),
     over a bounded contiguous sample of outer elements of the same workload
     (pair search + per-pair blocks + accumulation into K)."""
@@ -537,7 +554,8 @@ def cpu_baseline(mesh, delta, gamma, strategy, nmc, seed, budget_s=15.0, threads
         t0 = time.perf_counter()
         prs = O.pairs(mesh, delta, outer=outer)
         pT, pTp = O.pair_arrays(*prs)
-        blocks, _ = O.assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads=cores)
+        blocks, _ = O.assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads=cores,
+                                      kernel=kernel)
         O.blocks_to_matrix(mesh, pT, pTp, blocks)
         return len(pT), time.perf_counter() - t0
 
@@ -925,6 +943,7 @@ def run_reference(args, ws, rank):
         return
     import oracle as O
     cfg, strategy, nmc, seed, rtol = WORKLOADS[args.workload]
+    kernel = WORKLOAD_KERNEL.get(args.workload)
     mesh, delta = I.config_mesh(cfg)
     gamma = I.gamma_const(delta)
     outer_all = np.nonzero(mesh.tet_in_omega)[0].astype(np.int32)
@@ -937,7 +956,8 @@ def run_reference(args, ws, rank):
         t0 = time.perf_counter()
         prs = O.pairs(mesh, delta, outer=sel)
         pT, pTp = O.pair_arrays(*prs)
-        blocks, _ = O.assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads=cores)
+        blocks, _ = O.assemble_blocks(mesh, delta, gamma, strategy, nmc, seed, pT, pTp, nthreads=cores,
+                                      kernel=kernel)
         O.blocks_to_matrix(mesh, pT, pTp, blocks)
         return len(pT), time.perf_counter() - t0
 

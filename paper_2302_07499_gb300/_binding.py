@@ -50,7 +50,7 @@ class nl_pairs_info(C.Structure):
 class nl_assemble_opts(C.Structure):
     _fields_ = [("strategy", C.c_int), ("mc_points", C.c_int), ("seed", C.c_uint64), ("precision", C.c_int),
                 ("gamma", C.c_double), ("f_const", C.c_double), ("g_nodal", C.c_void_p), ("g_where", C.c_int),
-                ("f_nodal", C.c_void_p), ("f_where", C.c_int)]
+                ("f_nodal", C.c_void_p), ("f_where", C.c_int), ("kernel_poly", C.c_void_p)]
 
 
 class nl_csr_view(C.Structure):
@@ -315,11 +315,12 @@ class Pairs:
 
 class System:
     def __init__(self, pairs: Pairs, strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, gamma=1.0,
-                 f_const=0.0, g=None, f=None):
+                 f_const=0.0, g=None, f=None, kernel=None):
         """g: nodal volume constraint; f: nodal source values added to f_const
-        (numpy arrays or CUDA tensors of n_vert doubles, or None)."""
+        (numpy arrays or CUDA tensors of n_vert doubles, or None); kernel: the
+        kernel shape's 4 coefficients (None: constant kernel)."""
         self.pairs = pairs
-        o, keep = _assemble_opts(strategy, mc_points, seed, precision, gamma, f_const, g, f)
+        o, keep = _assemble_opts(strategy, mc_points, seed, precision, gamma, f_const, g, f, kernel)
         h = C.c_void_p()
         _check(lib().nl_assemble(pairs.h, C.byref(o), C.byref(h)))
         self.h = h
@@ -404,13 +405,22 @@ def _nodal(a):
     return k, _ptr(k), DEVICE
 
 
-def _assemble_opts(strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, gamma=1.0, f_const=0.0, g=None, f=None):
-    """nl_assemble_opts and the arrays that must stay alive while the call runs."""
+def _assemble_opts(strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, gamma=1.0, f_const=0.0, g=None, f=None,
+                   kernel=None):
+    """nl_assemble_opts and the arrays that must stay alive while the call runs.
+    kernel: None (constant kernel) or the 4 coefficients of the kernel shape
+    phi(s) = c0 + c1 s + c2 s^2 + c3 s^3, s = min(|x - y|^2 / delta^2, 1)."""
     kg, gp, gw = _nodal(g)
     kf, fp, fw = _nodal(f)
+    kk, kp = None, None
+    if kernel is not None:
+        kk = (C.c_double * 4)(*[float(c) for c in kernel])
+        if len(list(kernel)) != 4:
+            raise ValueError("kernel needs 4 coefficients")
+        kp = C.cast(kk, C.c_void_p)
     o = nl_assemble_opts(int(strategy), int(mc_points), int(seed), int(precision), float(gamma), float(f_const),
-                         gp, gw, fp, fw)
-    return o, (kg, kf)
+                         gp, gw, fp, fw, kp)
+    return o, (kg, kf, kk)
 
 
 class _BorrowedSystem(System):

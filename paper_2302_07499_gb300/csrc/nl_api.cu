@@ -47,6 +47,15 @@ nl_status nl_check_assemble_opts(const nl_assemble_opts *opts)
     if (!isfinite(opts->gamma) || !isfinite(opts->f_const)) { nl_set_error("gamma and f_const must be finite"); return NL_EINVAL; }
     if (opts->g_nodal && opts->g_where != NL_HOST && opts->g_where != NL_DEVICE) { nl_set_error("bad g_where"); return NL_EINVAL; }
     if (opts->f_nodal && opts->f_where != NL_HOST && opts->f_where != NL_DEVICE) { nl_set_error("bad f_where"); return NL_EINVAL; }
+    if (opts->kernel_poly) {
+        for (int k = 0; k < 4; ++k)
+            if (!isfinite(opts->kernel_poly[k])) { nl_set_error("kernel_poly coefficients must be finite"); return NL_EINVAL; }
+        if (opts->strategy == NL_APPROXCAPS) {
+            nl_set_error("approxcaps takes the constant kernel only (the split of its hull into simplices, "
+                         "which the 4-point rule depends on under a kernel shape, is not fixed)");
+            return NL_EINVAL;
+        }
+    }
     return NL_OK;
 }
 
@@ -61,6 +70,10 @@ nl_system *nl_system_alloc(nl_pairs *P, const nl_assemble_opts *opts, const nl_d
     S->opts = *opts;
     S->opts.g_nodal = nullptr;
     S->opts.f_nodal = nullptr;
+    if (opts->kernel_poly) {
+        for (int k = 0; k < 4; ++k) S->kernel_c[k] = opts->kernel_poly[k];
+        S->opts.kernel_poly = S->kernel_c;
+    }
     try {
         cudaStream_t s = S->arena.stream();
         S->K = S->arena.get<double>(P->nnz);

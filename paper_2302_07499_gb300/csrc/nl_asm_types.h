@@ -64,6 +64,8 @@ struct AsmArgs {
     int nmc;
     int qmc;                 // fullcaps cap points: 0 Philox draws, 1 shifted Sobol' points
     int hull_maxf;           // face capacity of the approxcaps hull (full capacity except in overflow tests)
+    int kpoly;               // 1: kernel shape phi = kc[0] + kc[1] s + kc[2] s^2 + kc[3] s^3 (else phi = 1)
+    double kc[4];
     uint32_t rk[20];         // Philox round keys
     // per-chunk work arrays
     uint8_t *uinfo;          // [4*(p1-p0)] vertex-inside mask | 0x10 event | 0x20 zero
@@ -147,6 +149,8 @@ inline void init_group_args(AsmArgs &A, const nl_assemble_opts &o, unsigned long
     A.hull_maxf = nl_hull_max_faces();
     A.nmc = (o.strategy == NL_FULLCAPS || o.strategy == NL_FULLCAPS_QMC) ? o.mc_points : 0;
     A.qmc = o.strategy == NL_FULLCAPS_QMC ? 1 : 0;
+    A.kpoly = o.kernel_poly ? 1 : 0;
+    for (int k = 0; k < 4; ++k) A.kc[k] = o.kernel_poly ? o.kernel_poly[k] : (k == 0 ? 1.0 : 0.0);
     philox_round_keys(o.seed, A.rk);
     A.stats = stats;
 }

@@ -136,6 +136,8 @@ __global__ void __launch_bounds__(256, 3) k_classify(const __grid_constant__ Asm
                 if (ev) info |= 0x10;
                 else info |= 0x20;
             }
+            // kernel shapes: a whole T' gets a record too (k_whole_shape)
+            if (A.kpoly && (info & 15) == 15) info = 15 | 0x10;
         }
         // warp-aggregated slot allocation within the event's class (number of
         // inside vertices), so that each warp of K2 runs one geometry case:
@@ -175,7 +177,7 @@ template <class R> struct EvCfg {
 // together.
 template <class R, int STRAT> constexpr bool kRetakePass = sizeof(R) == 4 && (STRAT == 0 || STRAT == 2);
 
-template <class R, int STRAT, bool B, bool RETAKE, bool QMC = false>
+template <class R, int STRAT, bool B, bool RETAKE, bool QMC = false, class KER = nlq::KerConst>
 __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_events(const __grid_constant__ AsmArgs A)
 {
     extern __shared__ __align__(16) unsigned char evsm[];
@@ -205,10 +207,14 @@ __global__ void __launch_bounds__(EvCfg<R>::threads, EvCfg<R>::min_blocks) k_eve
         // the record is built in shared memory and written out once
         R *out = reinterpret_cast<R *>(evsm) + 3 * nlq::CB_STRIDE * EvCfg<R>::threads + 17 * threadIdx.x;
         constexpr bool diag_inline = RETAKE || !kRetakePass<R, STRAT>;
-        const bool deferred = nlq::event_moments<R, STRAT, diag_inline, false, QMC>(
-            v, x, sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp,
+        const R d2 = sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2;
+        KER ker{};
+        if constexpr (!KER::constant) ker = KER{(R)A.kc[0], (R)A.kc[1], (R)A.kc[2], (R)A.kc[3], d2};
+        const bool deferred = nlq::event_moments<R, STRAT, diag_inline, false, QMC, KER>(
+            v, x, d2, inm, A.nmc, A.rk, (uint32_t)T, (uint32_t)Tp,
             (uint32_t)q, out, st, (sizeof(R) == 4) ? &sx : nullptr, cb, nlq::CB_STRIDE * EvCfg<R>::threads,
-            nlq::HullScratch<R>{reinterpret_cast<R *>(evsm) + threadIdx.x, EvCfg<R>::threads}, nullptr, A.hull_maxf);
+            nlq::HullScratch<R>{reinterpret_cast<R *>(evsm) + threadIdx.x, EvCfg<R>::threads}, nullptr, A.hull_maxf,
+            ker);
         if (deferred) {
             if constexpr (!RETAKE) A.fix[atomicAdd(&A.nev[4], 1)] = e;
         } else if constexpr (sizeof(R) == 4) {
@@ -280,6 +286,47 @@ __global__ void __launch_bounds__(64) k_events_fp64(const __grid_constant__ AsmA
     if (st.fallback) atomicAdd(&A.stats[4], (unsigned long long)st.fallback);
 }
 
+
+// ---------------------------------------------------------------------------
+// K2' with a kernel shape phi (Sec. 2's gamma(x, y) = gamma phi(|x - y|)):
+// the units whose T' is whole (every vertex inside, or an element-level
+// strategy's full T') have no closed form any more; one thread per such unit
+// takes the 4-point rule on T' with phi at the rule points and writes its
+// record.  The cut units go through k_events with the same shape.
+template <class R, bool B>
+__global__ void __launch_bounds__(256) k_whole_shape(const __grid_constant__ AsmArgs A)
+{
+    const int64_t nu = 4 * (A.p1 - A.p0);
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
+        if (A.uinfo[u] != (15 | 0x10)) continue;
+        int64_t p;
+        const Prob &P = prob_of_pair<B>(A, A.p0 + (u >> 2), p);
+        const int q = (int)(u & 3);
+        const int32_t T = P.pair_T[p], Tp = P.pair_tp[p];
+        const int32_t o = P.outer_of[T];
+        P3<R> v[4];
+        P3<R> x;
+        nlq::Strict sx;
+        load_point_geometry<R>(P, P.tets[Tp], o, q, v, x, sx);
+        const R d2 = sizeof(R) == 4 ? (R)P.delta2f : (R)P.delta2;
+        const nlq::KerShape<R> ker{(R)A.kc[0], (R)A.kc[1], (R)A.kc[2], (R)A.kc[3], d2};
+        Mom<R> M;
+        nlq::whole_moments<R>(v, x, (R)P.tet_vol[Tp], ker, M);
+        if constexpr (sizeof(R) == 4) {
+            float4 *g = reinterpret_cast<float4 *>(A.Mq) + (MQ_STRIDE / 4) * u;
+            g[0] = make_float4(M.m0, M.m1[0], M.m1[1], M.m1[2]);
+            g[1] = make_float4(M.m1[3], M.m2[0], M.m2[1], M.m2[2]);
+            g[2] = make_float4(M.m2[3], M.m2[4], M.m2[5], M.m2[6]);
+            g[3] = make_float4(M.m2[7], M.m2[8], M.m2[9], 0.f);
+        } else {
+            double2 *g = reinterpret_cast<double2 *>(A.Mq) + (MQ_STRIDE / 2) * u;
+            g[0] = make_double2(M.m0, M.m1[0]); g[1] = make_double2(M.m1[1], M.m1[2]);
+            g[2] = make_double2(M.m1[3], M.m2[0]); g[3] = make_double2(M.m2[1], M.m2[2]);
+            g[4] = make_double2(M.m2[3], M.m2[4]); g[5] = make_double2(M.m2[5], M.m2[6]);
+            g[6] = make_double2(M.m2[7], M.m2[8]); g[7] = make_double2(M.m2[9], 0.0);
+        }
+    }
+}
 
 // ---------------------------------------------------------------------------
 // K3: one block per outer element T (persistent over the chunk's outer
@@ -359,7 +406,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                 for (int q = 0; q < 4; ++q) {
                     const uint8_t info = (uint8_t)(info4 >> (8 * q));
                     Mom<R> M;
-                    if ((info & 15) == 15) {
+                    if ((info & 15) == 15 && !(info & 0x10)) {
                         if constexpr (F32) {
                             nlq::mom_zero(M);
                             fullmask |= 1 << q;
@@ -368,6 +415,8 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         }
                         inside++;
                     } else if (info & 0x10) {
+                        // (with a kernel shape, a whole T' has a record too)
+                        if ((info & 15) == 15) inside++;
                         // the unit's record (records are stored by unit: the
                         // pair's four are contiguous)
                         const int64_t ev = u0 + q;
@@ -610,6 +659,16 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
         if constexpr (STRAT == 2) {
             if (A.qmc) { ev_main = k_events<R, 2, B, false, true>; ev_retake = k_events<R, 2, B, true, true>; }
         }
+        if constexpr (!B && STRAT != 1) {
+            if (A.kpoly) {
+                using KS = nlq::KerShape<R>;
+                ev_main = k_events<R, STRAT, B, false, false, KS>;
+                ev_retake = k_events<R, STRAT, B, true, false, KS>;
+                if constexpr (STRAT == 2) {
+                    if (A.qmc) { ev_main = k_events<R, 2, B, false, true, KS>; ev_retake = k_events<R, 2, B, true, true, KS>; }
+                }
+            }
+        }
         NL_CUDA(cudaFuncSetAttribute(ev_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
         if constexpr (kRetakePass<R, STRAT>)
             NL_CUDA(cudaFuncSetAttribute(ev_retake, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ESM));
@@ -617,6 +676,10 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
     }
     ev_per_sm = ev_per_sm < 1 ? 1 : ev_per_sm;
     if (sh.events_blocks_per_sm > 0) ev_per_sm = std::min(ev_per_sm, sh.events_blocks_per_sm);
+    // kernel shapes (single problems, not approxcaps): the event kernels with
+    // the shape, and k_whole_shape for the whole T' units
+    const bool shape = !B && STRAT != 1 && A.kpoly;
+    (void)shape;
     const int sms = nl_num_sms();
     const int ct = sh.classify_threads;
     size_t ci = 0;
@@ -633,6 +696,14 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
         // enough resident threads for the largest possible event count; the
         // kernel reads the actual count from device memory
         unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, ET), (int64_t)sms * ev_per_sm));
+        if constexpr (!B) {
+            if (shape) {
+                const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, 256),
+                                                                                     (int64_t)sms * 8));
+                { k_whole_shape<R, B><<<gw, 256, 0, s>>>(A); nl_count_launch(); }
+                NL_CHECK_LAUNCH();
+            }
+        }
         if constexpr (STRAT <= 2) {
             { ev_main<<<g2, ET, ESM, s>>>(A); nl_count_launch(); }
             NL_CHECK_LAUNCH();

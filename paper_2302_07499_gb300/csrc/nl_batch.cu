@@ -110,6 +110,7 @@ extern "C" nl_status nl_batch_create(nl_pairs *const *pairs, const nl_assemble_o
     for (int i = 0; i < n; ++i) {
         if (!pairs[i]) { nl_set_error("pairs[%d] is NULL", i); return NL_EINVAL; }
         if (nl_status st = nl_check_assemble_opts(&opts[i])) return st;
+        if (opts[i].kernel_poly) { nl_set_error("a kernel shape (kernel_poly) runs through nl_assemble only"); return NL_EINVAL; }
         if (pairs[i]->arena.dev.stream != pairs[0]->arena.dev.stream) {
             nl_set_error("all problems of a batch must use the same stream");
             return NL_EINVAL;

@@ -144,6 +144,7 @@ struct nl_system {
     DevArena arena;
     nl_pairs *pairs = nullptr;
     nl_assemble_opts opts{};
+    double kernel_c[4] = {1.0, 0.0, 0.0, 0.0};   // the kernel shape's coefficients (opts.kernel_poly points here)
     double *K = nullptr;           // [nnz]
     double *A = nullptr;           // [nnz_a]
     float *A32 = nullptr;          // [nnz_a]

@@ -132,6 +132,83 @@ __device__ __forceinline__ void add_cell(Mom<R> &M, R vol, const R L0[4], const 
         }
 }
 
+// Kernel shape phi(|x - y|): the kernel is gamma phi (Sec. 2; the constant
+// kernel is phi = 1).  KerConst: phi = 1, integrated in closed form.
+// KerShape: phi = c0 + c1 s + c2 s^2 + c3 s^3 in s = min(|x - y|^2 / delta^2,
+// 1) (the element-level strategies place points past the sphere, where phi
+// keeps its value on it); cells then take the 4-point rule with phi at the
+// rule points (Sec. 4.3.1), and accepted cap samples are weighted by phi.
+struct KerConst {
+    static constexpr bool constant = true;
+};
+template <class R> struct KerShape {
+    static constexpr bool constant = false;
+    R c0, c1, c2, c3, d2;
+    // phi at squared distance rr
+    __device__ __forceinline__ R operator()(R rr) const
+    {
+        R s = rr / d2;
+        s = s < R(1) ? s : R(1);
+        return c0 + s * (c1 + s * (c2 + s * c3));
+    }
+};
+
+// The weight of an accepted cap sample at squared distance rr
+template <class R, class KER> __device__ __forceinline__ R kweight(const KER &ker, R rr)
+{
+    if constexpr (KER::constant) {
+        (void)ker; (void)rr;
+        return R(1);
+    } else {
+        return ker(rr);
+    }
+}
+
+// The 4-point rule's weights a (own vertex) and b (the others)
+template <class R> __device__ __forceinline__ R rule_a() { return R(0x1.2bbae2a27f931p-1); }
+template <class R> __device__ __forceinline__ R rule_b() { return R(0x1.1b06d1d200913p-3); }
+
+// Moments of one cell with vertex barycentric rows L0..L3 and vertices
+// p0..p3: closed form for the constant kernel, else the 4-point rule with the
+// kernel shape at the rule points y_k = b (p0 + p1 + p2 + p3) + (a - b) p_k,
+// where lambda' = b (L0 + L1 + L2 + L3) + (a - b) L_k.
+template <class R, class KER>
+__device__ __forceinline__ void add_cell_k(Mom<R> &M, R vol, const R L0[4], const R L1[4], const R L2[4],
+                                           const R L3[4], P3<R> p0, P3<R> p1, P3<R> p2, P3<R> p3, P3<R> x,
+                                           const KER &ker)
+{
+    if constexpr (KER::constant) {
+        (void)p0; (void)p1; (void)p2; (void)p3; (void)x; (void)ker;
+        add_cell(M, vol, L0, L1, L2, L3);
+    } else {
+        const R qa = rule_a<R>(), qb = rule_b<R>(), qd = qa - qb;
+        const P3<R> ps = mk3<R>((p0.x + p1.x) + (p2.x + p3.x), (p0.y + p1.y) + (p2.y + p3.y),
+                                (p0.z + p1.z) + (p2.z + p3.z));
+        R S[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) S[a] = (L0[a] + L1[a]) + (L2[a] + L3[a]);
+        const P3<R> pk[4] = {p0, p1, p2, p3};
+        const R *Lk[4] = {L0, L1, L2, L3};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const P3<R> w = mk3<R>(qb * ps.x + qd * pk[k].x - x.x, qb * ps.y + qd * pk[k].y - x.y,
+                                   qb * ps.z + qd * pk[k].z - x.z);
+            const R f = (vol * R(0.25)) * ker((w.x * w.x + w.y * w.y) + w.z * w.z);
+            R lam[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) lam[a] = qb * S[a] + qd * Lk[k][a];
+            M.m0 += f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) M.m1[a] += f * lam[a];
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = a; b < 4; ++b) M.m2[t++] += (f * lam[a]) * lam[b];
+        }
+    }
+}
+
 // Squared distance from x to T' (zero inside): closest point on each face the
 // point lies outside of.
 template <class R> __device__ R d2_point_tri(P3<R> p, P3<R> a, P3<R> b, P3<R> c)
@@ -504,6 +581,20 @@ template <class R> __device__ __forceinline__ void closed_form_inside(Mom<R> &M,
     M.m2[5] = q20; M.m2[6] = q20; M.m2[7] = q10; M.m2[8] = q20; M.m2[9] = q10;
 }
 
+// Moments of the whole T' (volume volTp) under a kernel shape: the 4-point
+// rule on T', whose rule points have lambda' = (a on vertex k, b elsewhere).
+template <class R>
+__device__ __forceinline__ void whole_moments(const P3<R> v[4], P3<R> x, R volTp, const KerShape<R> &ker, Mom<R> &M)
+{
+    mom_zero(M);
+    R L[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) L[k][a] = (a == k) ? R(1) : R(0);
+    add_cell_k(M, volTp, L[0], L[1], L[2], L[3], v[0], v[1], v[2], v[3], x, ker);
+}
+
 // Philox with the per-round keys precomputed (rk[2r], rk[2r+1] = key + r*Weyl).
 __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t *rk)
 {
@@ -723,10 +814,10 @@ template <class R> struct HullScratch {
     __device__ __forceinline__ R &operator()(int i) const { return p[i * s]; }
 };
 
-template <class R>
+template <class R, class KER = KerConst>
 __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, const int role[4], const P3<R> pp[4],
                                     const R pt[4], const PDesc pd[4], bool diag_c2d1, Mom<R> &M, const Strict *sx,
-                                    const HullScratch<R> &hs, int maxf)
+                                    const HullScratch<R> &hs, int maxf, const KER &ker = KER{})
 {
     constexpr bool F32 = sizeof(R) == 4;
     auto X = [&](int k) -> P3<R> { return mk3<R>(hs(3 * k), hs(3 * k + 1), hs(3 * k + 2)); };
@@ -958,7 +1049,7 @@ __device__ bool approx_hull_moments(const P3<R> v[4], P3<R> x, R d2, int m, cons
         R vol = vol4(c, X(i0), X(i1), X(i2));
         R L0[4], L1[4], L2[4];
         for (int aa = 0; aa < 4; ++aa) { L0[aa] = Lr(i0, aa); L1[aa] = Lr(i1, aa); L2[aa] = Lr(i2, aa); }
-        add_cell(M, vol, Lc, L0, L1, L2);
+        add_cell_k(M, vol, Lc, L0, L1, L2, c, X(i0), X(i1), X(i2), x, ker);
     }
     return true;
 }
@@ -987,10 +1078,10 @@ static_assert((CB_STRIDE * sizeof(float)) % 16 == 0 && (12 * sizeof(float)) % 16
 //   DIAG_INLINE is false, an m = 2 diagonal that the FP32 orientation cannot
 //   decide.  A hull that cannot be completed is counted in st.fallback (its
 //   nocaps cells stand in for it here, and the assembly reports an error).
-template <class R, int STRAT, bool DIAG_INLINE = true>
+template <class R, int STRAT, bool DIAG_INLINE = true, class KER = KerConst>
 __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk,
                                       uint32_t idT, uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx,
-                                      R *cb, int cs, const HullScratch<R> &hs, int hull_maxf)
+                                      R *cb, int cs, const HullScratch<R> &hs, int hull_maxf, const KER &ker = KER{})
 {
     Mom<R> M;
     constexpr bool F32 = sizeof(R) == 4;
@@ -1072,7 +1163,7 @@ __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, 
             }
         }
         if (near) return true;
-        done_hull = approx_hull_moments<R>(v, x, d2, m, role, pp, pt, pd, diag_c2d1, H, sx, hs, hull_maxf);
+        done_hull = approx_hull_moments<R, KER>(v, x, d2, m, role, pp, pt, pd, diag_c2d1, H, sx, hs, hull_maxf, ker);
         if (done_hull) M = H;
         else st.fallback++;                   // counted: the assembly then reports an error
     }
@@ -1109,7 +1200,7 @@ __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, 
             lam_row<R>(cells[j][2], pd, pt, L2);
             lam_row<R>(cells[j][3], pd, pt, L3);
             R vol = vol4(P(cells[j][0]), P(cells[j][1]), P(cells[j][2]), P(cells[j][3]));
-            add_cell(M, vol, L0, L1, L2, L3);
+            add_cell_k(M, vol, L0, L1, L2, L3, P(cells[j][0]), P(cells[j][1]), P(cells[j][2]), P(cells[j][3]), x, ker);
         }
     }
 
@@ -1146,14 +1237,15 @@ __device__ bool event_moments_generic(const P3<R> v[4], P3<R> x, R d2, int inm, 
 //   Returns true when the event is deferred (see event_moments_generic).
 //   hull_maxf: face capacity of the approxcaps hull (HULL_MAXF; smaller only
 //   in tests of the overflow path).
-template <class R, int STRAT, bool DIAG_INLINE = true, bool REC = false, bool QMC = false>
+template <class R, int STRAT, bool DIAG_INLINE = true, bool REC = false, bool QMC = false, class KER = KerConst>
 __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc, const uint32_t *rk, uint32_t idT,
                               uint32_t idTp, uint32_t q, R *out, Stats &st, const Strict *sx, R *cb, int cs,
-                              const HullScratch<R> &hs, double *rec = nullptr, int hull_maxf = HULL_MAXF)
+                              const HullScratch<R> &hs, double *rec = nullptr, int hull_maxf = HULL_MAXF,
+                              const KER &ker = KER{})
 {
     if constexpr (STRAT == 1) {
-        return event_moments_generic<R, STRAT, DIAG_INLINE>(v, x, d2, inm, nmc, rk, idT, idTp, q, out, st, sx, cb,
-                                                             cs, hs, hull_maxf);
+        return event_moments_generic<R, STRAT, DIAG_INLINE, KER>(v, x, d2, inm, nmc, rk, idT, idTp, q, out, st, sx,
+                                                                  cb, cs, hs, hull_maxf, ker);
     } else {
     Mom<R> M;
     constexpr bool F32 = sizeof(R) == 4;
@@ -1255,7 +1347,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
             R L0[4], L1[4], L2[4], L3[4];
             Lrow(p0, L0); Lrow(p1, L1); Lrow(p2, L2); Lrow(p3, L3);
             const R vc = vol4(Pt(p0), Pt(p1), Pt(p2), Pt(p3));
-            add_cell(M, vc, L0, L1, L2, L3);
+            add_cell_k(M, vc, L0, L1, L2, L3, Pt(p0), Pt(p1), Pt(p2), Pt(p3), x, ker);
         };
         if constexpr (Mi == 1) {
             cell(0, 4, 5, 6);
@@ -1390,7 +1482,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
                 rec[5 * k] = 0.0; rec[5 * k + 1] = inb ? 1.0 : 0.0;
                 rec[5 * k + 2] = (double)w.x; rec[5 * k + 3] = (double)w.y; rec[5 * k + 4] = (double)w.z;
             }
-            const R f = inb ? R(1) : R(0);
+            const R f = inb ? kweight<R>(ker, rr) : R(0);
             acc += inb ? 1u : 0u;
             cnt += f;
             R fb[4];
@@ -1477,7 +1569,7 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         }
         // branch-free accumulation of the accepted sample (the sums of
         // lambda' are the row sums of lambda' lambda'^T: lambda' sums to 1)
-        const R f = inb ? R(1) : R(0);
+        const R f = inb ? kweight<R>(ker, rr) : R(0);
         R Lr[16];
         if constexpr (F32) {
             const float4 *l4 = reinterpret_cast<const float4 *>(c + 12);
@@ -1492,17 +1584,27 @@ __device__ bool event_moments(const P3<R> v[4], P3<R> x, R d2, int inm, int nmc,
         }
         const R *L = Lr;
         R lam[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-            lam[a] = f * (((be0 * L[a] + be1 * L[4 + a]) + be2 * L[8 + a]) + be3 * L[12 + a]);
         acc += inb ? 1u : 0u;
         cnt += f;
-        {
+        if constexpr (KER::constant) {
+            // f is 0 or 1: lambda' lambda'^T f = (f lambda') (f lambda')^T
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                lam[a] = f * (((be0 * L[a] + be1 * L[4 + a]) + be2 * L[8 + a]) + be3 * L[12 + a]);
             int kk = 0;
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = a; b < 4; ++b) a2[kk++] += lam[a] * lam[b];
+        } else {
+            // weight phi once: (f lambda') lambda'^T
+#pragma unroll
+            for (int a = 0; a < 4; ++a) lam[a] = ((be0 * L[a] + be1 * L[4 + a]) + be2 * L[8 + a]) + be3 * L[12 + a];
+            int kk = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = a; b < 4; ++b) a2[kk++] += (f * lam[a]) * lam[b];
         }
     }
     st.mc += (uint32_t)nmc;

@@ -376,6 +376,7 @@ extern "C" nl_status nl_server_submit(nl_server *S, const nl_request *req, uint6
     }
     if (req->assemble.g_nodal) { nl_set_error("requests carry g as g_quadratic, not g_nodal"); return NL_EINVAL; }
     if (req->assemble.f_nodal) { nl_set_error("requests carry a constant f (f_nodal must be NULL)"); return NL_EINVAL; }
+    if (req->assemble.kernel_poly) { nl_set_error("a kernel shape (kernel_poly) runs through nl_assemble only"); return NL_EINVAL; }
     if (nl_status st = nl_check_assemble_opts(&req->assemble)) return st;
     std::lock_guard<std::mutex> lk(S->mu);
     if ((int)S->queue.size() >= S->opts.queue_capacity) { nl_set_error("queue full"); return NL_EBUSY; }

@@ -1,0 +1,124 @@
+"""GPU parity for non-constant kernels gamma phi(|x - y|).
+
+The shape is phi = c0 + c1 s + c2 s^2 + c3 s^3, with s = min(|x - y|^2 /
+delta^2, 1).  The assembly (through the C-ABI) is compared with the CPU
+oracle, which evaluates the same 4-point rule on the same cells.
+
+* nocaps, fullcaps and the element-level strategies use the cone of hull(I u
+  P) from the first inside vertex on both sides.  FP64 entries must match
+  within the constant kernel's 1e-12.
+* FP32-comp has the bar TOL_FP32_SHAPE.  With the constant kernel, whole
+  elements enter as closed forms in double-float.  With a shape, their
+  rule-based moments come through FP32 records, and K's small entries
+  (floored at 1e-3 sqrt(K_ii K_jj)) magnify that rounding.  The largest
+  errors measured were 7.5e-5 on these meshes (the inside strategy, where
+  every unit is a whole element) and 2.6e-4 on the jittered 38^3 mesh, whose
+  p99.9 is 4.5e-7.
+* approxcaps is refused with a shape.  The two sides split its hull into
+  simplices differently, and under a varying phi the rule depends on that
+  split: on these meshes they differed by 1.6 % (delta = 3h) and 15 %
+  (delta = h).
+"""
+import numpy as np
+import pytest
+
+import nl_inputs as I
+import oracle as O
+
+from _helpers import FLOOR_FP64, entry_rel_err, tol_fp64
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SHAPE = (1.0, -0.6, 0.35, -0.5)
+TOL_FP32_SHAPE = 5e-4
+
+
+@pytest.fixture(scope="module")
+def nl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2302_07499_gb300 as nl
+    from paper_2302_07499_gb300 import build
+    build.build()
+    return nl
+
+
+@pytest.fixture(scope="module")
+def dev(nl):
+    return nl.Device()
+
+
+def _meshes():
+    return [("jit6", I.kuhn_box(-0.25, 1.25, 6, jitter_frac=0.2, seed=3), 0.25),
+            ("jit5r3", *I.cube_problem(5, 3, jitter_frac=0.2, seed=9))]
+
+
+def _system(nl, dev, mesh, delta, strategy, precision, kernel, nmc=64):
+    m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+    p = nl.Pairs(m, delta)
+    s = nl.System(p, strategy=strategy, mc_points=nmc, seed=1, precision=precision,
+                  gamma=I.gamma_const(delta), f_const=-6.0, kernel=kernel)
+    return m, p, s
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("strategy", [0, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("name,mesh,delta", _meshes())
+def test_K_with_a_kernel_shape_matches_oracle(nl, dev, name, mesh, delta, strategy, precision):
+    prec = nl.FP64 if precision == "fp64" else nl.FP32_COMP
+    m, p, s = _system(nl, dev, mesh, delta, strategy, prec, SHAPE)
+    K = s.scipy(nl.MAT_K)
+    Kref = O.assemble_K(mesh, delta, I.gamma_const(delta), strategy, nmc=64, seed=1, kernel=SHAPE)
+    if precision == "fp64":
+        err = entry_rel_err(K, Kref, FLOOR_FP64)
+        bar, rows = tol_fp64(strategy), 1e-13
+    else:
+        err = entry_rel_err(K, Kref)
+        bar, rows = TOL_FP32_SHAPE, 1e-6
+    print("kernel shape", name, strategy, precision, "entry error", err)
+    assert err <= bar
+    Kd = K.toarray()
+    assert np.abs(Kd - Kd.T).max() <= 1e-14 * np.abs(Kd).max()
+    assert np.abs(Kd.sum(1)).max() <= rows * np.abs(Kd).sum(1).max()
+    assert s.stats()["hull_fallbacks"] == 0
+    # the shape changes the matrix: it is not the constant kernel's
+    K1 = O.assemble_K(mesh, delta, I.gamma_const(delta), strategy, nmc=64, seed=1)
+    assert entry_rel_err(K, K1, FLOOR_FP64) > 1e-3
+
+
+@pytest.mark.parametrize("strategy", [0, 2, 5])
+def test_constant_shape_is_the_constant_kernel(nl, dev, strategy):
+    """phi = 1 and phi = 2 through the rule-based path give the constant
+    kernel's matrix (closed forms), and twice it, up to rounding."""
+    name, mesh, delta = _meshes()[0]
+    _, _, s0 = _system(nl, dev, mesh, delta, strategy, nl.FP64, None)
+    K0 = s0.scipy(nl.MAT_K)
+    _, _, s1 = _system(nl, dev, mesh, delta, strategy, nl.FP64, (1.0, 0.0, 0.0, 0.0))
+    assert entry_rel_err(s1.scipy(nl.MAT_K), K0, FLOOR_FP64) <= 1e-12
+    _, _, s2 = _system(nl, dev, mesh, delta, strategy, nl.FP64, (2.0, 0.0, 0.0, 0.0))
+    assert entry_rel_err(s2.scipy(nl.MAT_K), 2.0 * K0, FLOOR_FP64) <= 1e-12
+
+
+def test_kernel_shape_deterministic_and_solvable(nl, dev):
+    name, mesh, delta = _meshes()[1]
+    _, _, s1 = _system(nl, dev, mesh, delta, 2, nl.FP32_COMP, SHAPE)
+    _, _, s2 = _system(nl, dev, mesh, delta, 2, nl.FP32_COMP, SHAPE)
+    assert np.array_equal(s1.scipy(nl.MAT_K).data, s2.scipy(nl.MAT_K).data)
+    u, info = s1.solve(rtol=1e-10, mixed=True)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+
+
+def test_kernel_shape_rejected_where_unsupported(nl, dev):
+    """Batches, the server and approxcaps take the constant kernel only;
+    bad coefficients are refused."""
+    name, mesh, delta = _meshes()[0]
+    m = nl.Mesh(mesh.verts, mesh.tets, mesh.tet_in_omega, mesh.node_free, dev)
+    p = nl.Pairs(m, delta)
+    with pytest.raises(Exception):
+        nl.Batch([(p, dict(strategy=0, precision=nl.FP64, gamma=1.0, kernel=SHAPE))])
+    with pytest.raises(Exception):
+        nl.System(p, strategy=0, precision=nl.FP64, gamma=1.0, kernel=(1.0, float("nan"), 0.0, 0.0))
+    with pytest.raises(Exception):
+        nl.System(p, strategy=1, precision=nl.FP64, gamma=1.0, kernel=SHAPE)
