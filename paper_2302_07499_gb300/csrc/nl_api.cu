@@ -129,6 +129,8 @@ nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_dev
         double *strips = sc.get<double>(P->strip_total);
         double *TT = sc.get<double>(10 * m->n_outer);
         uint8_t *nfull = f32 ? sc.get<uint8_t>(P->npairs) : nullptr;
+        S->Dw = (f32 && S->opts.kernel_poly && S->opts.strategy >= NL_BARYCENTER && S->opts.strategy <= NL_INSIDE)
+                    ? sc.get<double>(10 * P->npairs) : nullptr;
         uint64_t *st = sc.get<uint64_t>(8);
         NL_CUDA(cudaMemsetAsync(st, 0, sizeof(uint64_t) * 8, s));
         ScopedEvent ev[3];
@@ -139,6 +141,7 @@ nl_status nl_assemble_on(nl_pairs *P, const nl_assemble_opts *opts, const nl_dev
         nl_reduce_system(S, D, f32 ? 1 : 0, nfull, strips, TT);
         NL_CUDA(cudaEventRecord(ev[2], s));
         NL_CUDA(cudaEventSynchronize(ev[2]));
+        S->Dw = nullptr;   // scratch, released with sc
         float ms0 = 0.f, ms1 = 0.f;
         NL_CUDA(cudaEventElapsedTime(&ms0, ev[0], ev[1]));
         NL_CUDA(cudaEventElapsedTime(&ms1, ev[1], ev[2]));

@@ -49,6 +49,7 @@ struct Prob {
     int64_t pair_base, outer_base;
     void *D;                 // [npairs][10] staged T'T' moments (R)
     uint8_t *nfull;          // FP32: [npairs] points at which T' is whole (their T'T' part is added in FP64)
+    double *Dw;              // FP32 with a kernel shape: [npairs][10] T'T' moments of the whole-T' points (FP64)
     double *strips;          // [strip_total]
     double *TT;              // [n_outer][10]
 };
@@ -136,7 +137,7 @@ inline Prob make_prob(nl_system *sys, void *D, double *strips, double *TT, uint8
     r.delta2 = P->delta * P->delta;
     r.delta2f = (float)r.delta2;
     r.half_gamma = sys->opts.gamma / 2.0;
-    r.D = D; r.strips = strips; r.TT = TT; r.nfull = nfull;
+    r.D = D; r.strips = strips; r.TT = TT; r.nfull = nfull; r.Dw = sys->Dw;
     NL_REQUIRE(r.verts && r.vhi && r.vlo && r.vol_hl && r.tets && r.xq && r.xq_hl && r.pair_ptr && r.pair_tp && r.pair_T &&
                    r.rowptr && r.col && r.strip_off && r.outer_of && r.outer_ids,
                "internal: an input array of the assembly is missing");

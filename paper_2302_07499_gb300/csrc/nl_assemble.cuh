@@ -343,7 +343,12 @@ constexpr int NT = 128;
 // reads of 8 pairs at a time pile up on a few banks
 constexpr int XS = 17;
 
-template <class R, bool B>
+// SHAPE (FP32, a kernel shape, element-level strategies): the points at
+// which T' is whole (info 15 | 0x10) take no FP32 record; their moments come
+// from the kernel shape at T''s rule points in FP64 here, and enter the V_q
+// sums and cross coefficients in double-float and the T'T' part through P.Dw
+// in FP64, as the constant kernel's closed forms do.
+template <class R, bool B, bool SHAPE = false>
 __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                 const int64_t u0 = 4 * (P.pair_base + p - A.p0);
                 // FP32: points where T' is whole enter in double (their moments
                 // are closed forms of |T'|), the others from their FP32 records
-                int fullmask = 0;
+                int fullmask = 0, wmask = 0;
                 // the pair's 4 units: 4 info bytes in one load (u0 is a multiple
                 // of 4)
                 const uint32_t info4 = *reinterpret_cast<const uint32_t *>(A.uinfo + u0);
@@ -406,7 +411,13 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                 for (int q = 0; q < 4; ++q) {
                     const uint8_t info = (uint8_t)(info4 >> (8 * q));
                     Mom<R> M;
-                    if ((info & 15) == 15 && !(info & 0x10)) {
+                    bool wshape = false;
+                    if constexpr (SHAPE) wshape = info == (15 | 0x10);
+                    if (wshape) {
+                        nlq::mom_zero(M);
+                        wmask |= 1 << q;
+                        inside++;
+                    } else if ((info & 15) == 15 && !(info & 0x10)) {
                         if constexpr (F32) {
                             nlq::mom_zero(M);
                             fullmask |= 1 << q;
@@ -456,6 +467,57 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                 if constexpr (F32) {
                     const int nfull = __popc(fullmask);
                     P.nfull[p] = (uint8_t)nfull;
+                    // kernel shapes: phi at T''s rule points for its whole points
+                    // (FP64), the unit's moments being (|T'|/4) sums of phi
+                    // times the rule's barycentrics (a on the own vertex, b else)
+                    double wphi[4][4], wS[4];
+                    const double V4 = P.tet_vol[Tp] * 0.25;
+                    const double wqa = 0x1.2bbae2a27f931p-1, wqb = 0x1.1b06d1d200913p-3, wqd = wqa - wqb;
+                    if constexpr (SHAPE) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            wS[q] = 0.0;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) wphi[q][k] = 0.0;
+                        }
+                        if (wmask) {
+                            const double4 g0 = P.verts[eP.x], g1 = P.verts[eP.y], g2 = P.verts[eP.z], g3 = P.verts[eP.w];
+                            const double sx = (g0.x + g1.x) + (g2.x + g3.x), sy = (g0.y + g1.y) + (g2.y + g3.y),
+                                         sz = (g0.z + g1.z) + (g2.z + g3.z);
+                            const double4 gk[4] = {g0, g1, g2, g3};
+                            const double *xo = P.xq + 12 * o;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                if (!((wmask >> q) & 1)) continue;
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    const double wx = wqb * sx + wqd * gk[k].x - xo[3 * q];
+                                    const double wy = wqb * sy + wqd * gk[k].y - xo[3 * q + 1];
+                                    const double wz = wqb * sz + wqd * gk[k].z - xo[3 * q + 2];
+                                    double ss = ((wx * wx + wy * wy) + wz * wz) / P.delta2;
+                                    ss = ss < 1.0 ? ss : 1.0;
+                                    const double ph = A.kc[0] + ss * (A.kc[1] + ss * (A.kc[2] + ss * A.kc[3]));
+                                    wphi[q][k] = ph;
+                                    wS[q] += ph;
+                                }
+                            }
+                        }
+                        // T'T' part: sum over the whole points of
+                        // (|T'|/4) (b^2 S + b d (phi_a + phi_b) + [a = b] d^2 phi_a)
+                        double *dw = P.Dw + 10 * p;
+                        int t = 0;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+#pragma unroll
+                            for (int b = a; b < 4; ++b) {
+                                double v = 0.0;
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    v += V4 * ((wqb * wqb) * wS[q] + (wqb * wqd) * (wphi[q][a] + wphi[q][b]) +
+                                               (a == b ? (wqd * wqd) * wphi[q][a] : 0.0));
+                                dw[t++] = v;
+                            }
+                    }
                     // |T'| as float hi + lo; omega is 1 or 2 (exact scaling)
                     const float2 vhl = P.vol_hl[Tp];
                     const float omf = P.in_omega[Tp] ? 1.f : 2.f;
@@ -464,6 +526,9 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                     for (int q = 0; q < 4; ++q) {
                         vqf[q] = df_add(vqf[q], DF{omf * (float)V[q], 0.f});
                         if ((fullmask >> q) & 1) vqf[q] = df_add(vqf[q], wV);
+                        if constexpr (SHAPE) {
+                            if ((wmask >> q) & 1) vqf[q] = df_add(vqf[q], df_from((double)omf * (V4 * wS[q])));
+                        }
                     }
                     // weights of the 4-point rule as float hi + lo
                     const DF qa = df_const(0x1.2bbae2a27f931p-1), qb = df_const(0x1.1b06d1d200913p-3);
@@ -482,7 +547,18 @@ __global__ void __launch_bounds__(NT) k_combine(const __grid_constant__ AsmArgs 
                         for (int k = 0; k < 4; ++k) {
                             const float ev = ((qlam<float>(i, 0) * (float)Y[0][k] + qlam<float>(i, 1) * (float)Y[1][k]) +
                                               qlam<float>(i, 2) * (float)Y[2][k]) + qlam<float>(i, 3) * (float)Y[3][k];
-                            reinterpret_cast<DF *>(Xs)[tid * XS + 4 * i + k] = df_add(xc, DF{ev, 0.f});
+                            DF xs = df_add(xc, DF{ev, 0.f});
+                            if constexpr (SHAPE) {
+                                if (wmask) {
+                                    // the whole points' first moments, (|T'|/4)(b S + d phi_k)
+                                    double xw = 0.0;
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q)
+                                        xw += qlam<double>(i, q) * (V4 * (wqb * wS[q] + wqd * wphi[q][k]));
+                                    xs = df_add(xs, df_from(xw));
+                                }
+                            }
+                            reinterpret_cast<DF *>(Xs)[tid * XS + 4 * i + k] = xs;
                         }
                     }
                 } else {
@@ -641,11 +717,20 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
     constexpr bool kDefer = sizeof(R) == 4 && STRAT == 1;
     const size_t smem = combine_smem_bytes(A.max_row, sizeof(R));
     NL_REQUIRE(smem <= 220 * 1024, "rows of %d columns need %zu bytes of shared memory", A.max_row, smem);
+    // kernel shapes, FP32, element-level strategies (every unit is a whole
+    // T'): k_combine takes the whole points itself in FP64; otherwise they
+    // come from k_whole_shape's records, and the cut units' FP32 records set
+    // the accuracy anyway
+    constexpr bool kShapeCombine = sizeof(R) == 4 && !B && STRAT >= 3;
+    void (*k3)(const AsmArgs) = k_combine<R, B>;
+    if constexpr (kShapeCombine) {
+        if (A.kpoly) k3 = k_combine<R, B, true>;
+    }
     // the attribute is per function and process-wide: always the same limit,
     // so concurrent launches of other sizes (other threads) never lower it
-    NL_CUDA(cudaFuncSetAttribute(k_combine<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    NL_CUDA(cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     int per_sm = 0;
-    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_combine<R, B>, NT, smem));
+    NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3, NT, smem));
     per_sm = per_sm < 1 ? 1 : per_sm;
     int ev_per_sm = 0;
     constexpr int ET = EvCfg<R>::threads;
@@ -696,7 +781,7 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
         // enough resident threads for the largest possible event count; the
         // kernel reads the actual count from device memory
         unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, ET), (int64_t)sms * ev_per_sm));
-        if constexpr (!B) {
+        if constexpr (!B && !kShapeCombine) {
             if (shape) {
                 const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nl_cdiv<int64_t>(nu, 256),
                                                                                      (int64_t)sms * 8));
@@ -723,7 +808,7 @@ void launch_chunks(AsmArgs A, const std::vector<int64_t> &gptr, const std::vecto
         if (ev) NL_CUDA(cudaEventRecord(ev[4 * ci + 2], s));
         int64_t no = A.o1 - A.o0;
         unsigned g3 = (unsigned)std::min<int64_t>(no, (int64_t)sms * per_sm);
-        { k_combine<R, B><<<g3, NT, smem, s>>>(A); nl_count_launch(); }
+        { k3<<<g3, NT, smem, s>>>(A); nl_count_launch(); }
         NL_CHECK_LAUNCH();
         if (ev) NL_CUDA(cudaEventRecord(ev[4 * ci + 3], s));
         ++ci;

@@ -145,6 +145,8 @@ struct nl_system {
     nl_pairs *pairs = nullptr;
     nl_assemble_opts opts{};
     double kernel_c[4] = {1.0, 0.0, 0.0, 0.0};   // the kernel shape's coefficients (opts.kernel_poly points here)
+    double *Dw = nullptr;          // FP32-comp with a kernel shape, during assembly: [npairs][10] T'T' moments
+                                   // of the points at which T' is whole, in FP64
     double *K = nullptr;           // [nnz]
     double *A = nullptr;           // [nnz_a]
     float *A32 = nullptr;          // [nnz_a]

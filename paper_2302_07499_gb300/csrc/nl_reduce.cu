@@ -95,8 +95,8 @@ __global__ void k_elem_blocks_df(const int64_t *__restrict__ tp_ptr, const int32
                                  const int32_t *__restrict__ pair_T, const double *__restrict__ tet_vol,
                                  const float2 *__restrict__ vol_hl, const uint8_t *__restrict__ in_omega,
                                  const int32_t *__restrict__ outer_of, const float *__restrict__ D,
-                                 const uint8_t *__restrict__ nfull, const double *__restrict__ TT, double half_gamma,
-                                 int64_t nt, double *E)
+                                 const uint8_t *__restrict__ nfull, const double *__restrict__ Dw,
+                                 const double *__restrict__ TT, double half_gamma, int64_t nt, double *E)
 {
     using nla::DF;
     int64_t el = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -115,6 +115,12 @@ __global__ void k_elem_blocks_df(const int64_t *__restrict__ tp_ptr, const int32
 #pragma unroll
         for (int k = 0; k < 10; ++k) acc[k] = nla::df_add(acc[k], nla::df_mul(w, d[k]));
         if (nfull) sw = nla::df_add(sw, nla::df_mul(w, (float)nfull[p]));
+        if (Dw) {
+            // kernel shapes: the whole-T' points' moments, in FP64
+            const double *dw = Dw + 10 * (int64_t)p;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) acc[k] = nla::df_add(acc[k], nla::df_mul2(w, nla::df_from(dw[k])));
+        }
     }
 #pragma unroll
     for (int k = 0; k < 10; ++k)
@@ -263,8 +269,8 @@ void nl_reduce_system_into(nl_system *sys, const void *D, int d_is_float, const 
     NL_CHECK_LAUNCH();
     if (d_is_float)
         { k_elem_blocks_df<<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->vol_hl,
-                                                         m->in_omega, m->outer_of, (const float *)D, nfull, TT,
-                                                         sys->opts.gamma / 2.0, m->nt, E); nl_count_launch(); }
+                                                         m->in_omega, m->outer_of, (const float *)D, nfull, sys->Dw,
+                                                         TT, sys->opts.gamma / 2.0, m->nt, E); nl_count_launch(); }
     else
         { k_elem_blocks<<<wblocks(m->nt), 256, 0, s>>>(P->tp_ptr, P->tp_pair, P->pair_T, m->tet_vol, m->in_omega,
                                                     m->outer_of, (const double *)D, TT, sys->opts.gamma / 2.0, m->nt,

@@ -7,13 +7,15 @@ oracle, which evaluates the same 4-point rule on the same cells.
 * nocaps, fullcaps and the element-level strategies use the cone of hull(I u
   P) from the first inside vertex on both sides.  FP64 entries must match
   within the constant kernel's 1e-12.
-* FP32-comp has the bar TOL_FP32_SHAPE.  With the constant kernel, whole
-  elements enter as closed forms in double-float.  With a shape, their
-  rule-based moments come through FP32 records, and K's small entries
-  (floored at 1e-3 sqrt(K_ii K_jj)) magnify that rounding.  The largest
-  errors measured were 7.5e-5 on these meshes (the inside strategy, where
-  every unit is a whole element) and 2.6e-4 on the jittered 38^3 mesh, whose
-  p99.9 is 4.5e-7.
+* FP32-comp has the bar TOL_FP32_SHAPE.
+  * For the element-level strategies, whole elements come in FP64
+    (k_combine), as the constant kernel's closed forms do.  Measured:
+    2e-14 to 4e-12.
+  * For nocaps and fullcaps, whole elements and cut units come through FP32
+    records.  A kernel that vanishes at the sphere makes K's far entries
+    small, and the entry metric's floor, 1e-3 sqrt(K_ii K_jj), magnifies
+    their rounding.  Measured: 3.7e-6 to 1.7e-5 on these meshes, and 2.6e-4
+    on the jittered 38^3 mesh, whose p99.9 is 4.5e-7.
 * approxcaps is refused with a shape.  The two sides split its hull into
   simplices differently, and under a varying phi the rule depends on that
   split: on these meshes they differed by 1.6 % (delta = 3h) and 15 %
