@@ -414,9 +414,10 @@ def _assemble_opts(strategy=NOCAPS, mc_points=64, seed=1, precision=FP64, gamma=
     kf, fp, fw = _nodal(f)
     kk, kp = None, None
     if kernel is not None:
-        kk = (C.c_double * 4)(*[float(c) for c in kernel])
-        if len(list(kernel)) != 4:
+        coef = [float(c) for c in kernel]
+        if len(coef) != 4:
             raise ValueError("kernel needs 4 coefficients")
+        kk = (C.c_double * 4)(*coef)
         kp = C.cast(kk, C.c_void_p)
     o = nl_assemble_opts(int(strategy), int(mc_points), int(seed), int(precision), float(gamma), float(f_const),
                          gp, gw, fp, fw, kp)
