@@ -971,7 +971,9 @@ def run_reference(args, ws, rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "mesh": cfg, "strategy": STRAT_NAME[strategy], "mc_points": nmc,
-                       "seed": seed},
+                       "seed": seed,
+                       "kernel_shape": ("phi(s) = %g + %g s + %g s^2 + %g s^3, s = min(|x-y|^2/delta^2, 1)" % kernel)
+                       if kernel else "constant"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d outer elements per step (%d element pairs over %d steps): pair search, "
                                        "per-pair blocks, accumulation into K" % (n_sample, npairs, args.steps)},
