@@ -477,8 +477,8 @@ def run_ours(args, ws, rank, local):
     spmv["fp64"]["dfma_floor_ms"] = steps[0]["nnz_a"] / dfma * 1e3
     spmv["fp64"]["frac_of_measured_dfma"] = spmv["fp64"]["dfma_floor_ms"] / spmv["fp64"]["ms"]
     roofline = {"bound": "alu",
-                "kernel": ("k_events_shape<float,%s> (every unit with a region, whole elements included; the "
-                           "operation count leaves the rule points of whole elements out)" % STRAT_NAME[strategy])
+                "kernel": ("k_events<float,%s,kernel shape> + k_whole_shape (the events phase; the operation "
+                           "count leaves the rule points of cells and whole elements out)" % STRAT_NAME[strategy])
                 if kernel else "k_events<float,%s>" % STRAT_NAME[strategy],
                 "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": None if kernel else _traffic_record(),
