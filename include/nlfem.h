@@ -226,12 +226,15 @@ nl_status nl_pairs_export(const nl_pairs *pairs, int32_t *outer, int64_t *ptr, i
  *              sample is weighted by phi.  Single systems only: the batch
  *              and the server reject a kernel shape (NL_EINVAL), and so does
  *              approxcaps (the rule would depend on how its hull is split
- *              into simplices, which Sec. 3.3 does not fix).  Whole elements
- *              then enter through FP32 records in NL_FP32_COMP (with the
- *              constant kernel they enter as closed forms in double-float),
- *              so that precision's entries are within 5e-4 rather than
- *              1e-5 (measured: 2.6e-4 at worst, 4.5e-7 at the 99.9th
- *              percentile, on a 329,232-element mesh). */
+ *              into simplices, which Sec. 3.3 does not fix).  In
+ *              NL_FP32_COMP the element-level strategies take whole
+ *              elements in FP64, as the constant kernel's closed forms are
+ *              taken; nocaps and fullcaps take them, and the cut units,
+ *              through FP32 records, and a kernel that vanishes at the
+ *              sphere leaves K's far entries small, so their entries are
+ *              within 5e-4 rather than 1e-5 (measured: 2.6e-4 at worst,
+ *              4.5e-7 at the 99.9th percentile, on a 329,232-element
+ *              mesh). */
 typedef struct {
     int strategy;            /* nl_strategy */
     int mc_points;           /* fullcaps samples per cap (ignored otherwise) */
